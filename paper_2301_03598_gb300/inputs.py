@@ -1,0 +1,98 @@
+"""Seeded synthetic inputs for the Stream-K GEMM library.
+
+This module is the one piece shared by the oracle side and the GPU side: it
+draws random matrices and shape lists and stores them in the input formats.
+It holds none of the GEMM's arithmetic.  Workload recipes follow the paper's
+evaluation corpus (Section 6: m, n, k log-sampled in [128, 8192]) and the
+synthetic stand-ins named in the repository's design notes.
+
+Random values are drawn in float32 by numpy's PCG64 (host) or by torch's
+Philox generator (device pools), then rounded to the storage format by the
+library conversions (numpy float16 cast / torch bfloat16 cast, both
+round-to-nearest-even).  The float64 copy returned beside a host matrix holds
+exactly the stored values, since FP16 and BF16 widen to FP64 without error.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Tuple
+
+import numpy as np
+import torch
+
+DTYPES = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}
+
+
+def _draw(rng: np.random.Generator, shape, dist: str) -> np.ndarray:
+    if dist == "uniform":          # U[-1, 1]
+        return rng.uniform(-1.0, 1.0, size=shape).astype(np.float32)
+    if dist == "normal":           # N(0, 1)
+        return rng.standard_normal(size=shape, dtype=np.float32)
+    if dist == "ones":
+        return np.ones(shape, np.float32)
+    if dist == "smallint":         # integers in [-4, 4]: exact in every format
+        return rng.integers(-4, 5, size=shape).astype(np.float32)
+    raise ValueError(f"unknown distribution {dist!r}")
+
+
+def to_storage(values_f32: np.ndarray, dtype: str) -> torch.Tensor:
+    """Round float32 values to the storage dtype (RN-even), as a CPU tensor."""
+    t = torch.from_numpy(np.ascontiguousarray(values_f32, dtype=np.float32))
+    return t.to(DTYPES[dtype]).contiguous()
+
+
+def widen(t: torch.Tensor) -> np.ndarray:
+    """Exact float64 copy of a CPU tensor of FP16 / BF16 / FP32 values."""
+    return t.to(torch.float64).numpy()
+
+
+def host_matrix(rows: int, cols: int, dtype: str, dist: str, seed: int):
+    """A rows x cols matrix (row-major storage tensor on the CPU) and the exact
+    float64 values it holds."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    stor = to_storage(_draw(rng, (rows, cols), dist), dtype)
+    return stor, widen(stor)
+
+
+def device_pool(numel: int, dtype: str, dist: str, seed: int, device) -> torch.Tensor:
+    """A flat device tensor of ``numel`` seeded values in ``dtype`` (Philox on
+    the device; used where host generation of gigabytes would be too slow)."""
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    out = torch.empty(numel, dtype=DTYPES[dtype], device=device)
+    chunk = 1 << 28
+    for s in range(0, numel, chunk):
+        e = min(numel, s + chunk)
+        if dist == "normal":
+            v = torch.randn(e - s, generator=gen, device=device, dtype=torch.float32)
+        elif dist == "uniform":
+            v = torch.rand(e - s, generator=gen, device=device, dtype=torch.float32) * 2 - 1
+        else:
+            raise ValueError(dist)
+        out[s:e] = v.to(out.dtype)
+    return out
+
+
+def log_uniform_shapes(count: int, seed: int, lo: int = 128, hi: int = 8192,
+                       multiple: int = 16) -> List[Tuple[int, int, int]]:
+    """``count`` shapes (m, n, k), each drawn log-uniform in [lo, hi] and rounded
+    to the nearest multiple of ``multiple`` (at least ``multiple``)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    logs = rng.uniform(math.log(lo), math.log(hi), size=(count, 3))
+    vals = np.maximum(multiple, np.rint(np.exp(logs) / multiple).astype(np.int64) * multiple)
+    return [tuple(int(v) for v in row) for row in vals]
+
+
+# The shape-sweep workload: 2,000 single BF16 GEMMs with m, n, k log-uniform
+# in [128, 8192], multiples of 16.
+SWEEP_SEED = 2301_03598 + 2
+SWEEP_COUNT = 2000
+
+
+def sweep_shapes(count: int = SWEEP_COUNT, seed: int = SWEEP_SEED):
+    return log_uniform_shapes(count, seed)
+
+
+# Extreme-quantisation shapes (m, n, k): square, deep-K skinny, tall-skinny,
+# and a tile count near the SM count.
+EXTREME_SHAPES = [(8192, 8192, 8192), (256, 256, 65536), (8192, 128, 4096), (1536, 1536, 1536)]
