@@ -1,0 +1,208 @@
+/*
+ * streamk.h -- C ABI of the GB300 (sm_103a) Stream-K GEMM library.
+ *
+ * The library computes the GEMM of the paper's problem statement (Stream-K,
+ * Osama, Merrill, Cecka, Garland, Owens; Section 2 "Background"):
+ *
+ *     C = alpha * A * B + beta * C,   A: m x k,  B: k x n,  C: m x n,
+ *
+ * with FP16 or BF16 inputs, FP32 accumulation (including the cross-CTA fixup)
+ * and an FP32, BF16 or FP16 result.  The work decomposition is the paper's:
+ * the aggregate MAC-loop iterations (output tiles x k-blocks) are split evenly,
+ * within one, over a persistent grid of CTAs (Algorithm 5); CTAs that finish a
+ * tile they did not start spill FP32 partial sums to a workspace and signal a
+ * flag; the CTA that ran the tile's k = 0 iteration waits for them in
+ * increasing CTA order, adds their partials and stores the tile.  The two
+ * hybrids of Section 5.2 ("DP + one-tile SK" and "two-tile SK + DP") and the
+ * data-parallel decomposition (Algorithm 2) are the same kernel with a
+ * different schedule.  The grid size of basic Stream-K is chosen by the
+ * analytical model of Appendix A.1.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns an sk_status; nothing is thrown across the ABI.
+ *   - "device pointer" means memory the CUDA device of the plan can address
+ *     (cudaMalloc, or memory registered/mapped for it).  The caller keeps
+ *     ownership of every matrix it passes.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  sk_gemm is asynchronous (stream-ordered) and returns after the
+ *     launch; device-side failures are reported by sk_last_error.
+ *   - A plan is not thread-safe and must not be used by two streams at once
+ *     (its workspace would be shared by two launches).
+ */
+#ifndef STREAMK_H
+#define STREAMK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SK_OK = 0,
+  SK_ERR_INVALID = 1,     /* bad argument: sizes, null or misaligned pointer, bad leading dim */
+  SK_ERR_UNSUPPORTED = 2, /* dtype / layout / mode combination this build does not implement */
+  SK_ERR_CUDA = 3,        /* a CUDA runtime call failed (no device, launch failure, ...) */
+  SK_ERR_TIMEOUT = 4,     /* a bounded wait on the device ran out (fixup flag or pipeline) */
+  SK_ERR_NOMEM = 5,       /* device allocation failed */
+  SK_ERR_DEVICE = 6       /* the current device is not sm_103 (GB300) */
+} sk_status;
+
+typedef enum { SK_F16 = 0, SK_BF16 = 1, SK_F32 = 2 } sk_dtype;
+
+/* Storage order of a matrix.  For A (m x k): ROW_MAJOR = k contiguous;
+ * for B (k x n): COL_MAJOR = k contiguous; for C (m x n): ROW_MAJOR = n
+ * contiguous.  Supported: A row-major with B column-major (both K-contiguous),
+ * C row-major or column-major. */
+typedef enum { SK_ROW_MAJOR = 0, SK_COL_MAJOR = 1 } sk_layout;
+
+/* Work decomposition (Sections 3-5 of the paper). */
+typedef enum {
+  SK_MODE_AUTO = 0,            /* two-tile hybrid when t >= p, DP on a perfect wave count,
+                                  basic Stream-K with the modelled grid below one wave */
+  SK_MODE_DP = 1,              /* Algorithm 2: one CTA per tile (persistent waves) */
+  SK_MODE_SK = 2,              /* Algorithm 5: basic Stream-K over all tiles */
+  SK_MODE_HYBRID = 3,          /* Section 5.2: "two-tile Stream-K + data-parallel" */
+  SK_MODE_HYBRID_ONE_TILE = 4  /* Section 5.2: "data-parallel + one-tile Stream-K" */
+} sk_mode;
+
+/* Plan attributes (sk_plan_set / sk_plan_get).  Settable ones re-plan. */
+typedef enum {
+  SK_ATTR_TILE_N = 1,        /* set/get: BLK_N, 128 or 256; set 0 for automatic */
+  SK_ATTR_GRID = 2,          /* set: grid size g for SK_MODE_SK (0 = model); get: the g in use */
+  SK_ATTR_RASTER_GROUP = 3,  /* set/get: tile-raster band height in tiles (0 = automatic) */
+  SK_ATTR_TIMEOUT_NS = 4,    /* set/get: limit of every device-side wait, nanoseconds */
+  SK_ATTR_LDA = 5,           /* set/get: leading dimension of A in elements (default dense) */
+  SK_ATTR_LDB = 6,           /* set/get: leading dimension of B in elements */
+  SK_ATTR_LDC = 7,           /* set/get: leading dimension of C in elements */
+  SK_ATTR_DEBUG_SKIP_SIGNAL = 8, /* set: a CTA index that withholds its fixup Signal, so the
+                                    owner's bounded Wait must expire (failure-detection
+                                    tests); -1 = off */
+  SK_ATTR_MODE = 20,         /* get: resolved sk_mode */
+  SK_ATTR_TILE_M = 21,       /* get: BLK_M (128) */
+  SK_ATTR_TILE_K = 22,       /* get: BLK_K (64) */
+  SK_ATTR_TILES_M = 23,      /* get: ceil(m / BLK_M) */
+  SK_ATTR_TILES_N = 24,      /* get: ceil(n / BLK_N) */
+  SK_ATTR_TILES = 25,        /* get: t */
+  SK_ATTR_ITERS_PER_TILE = 26, /* get: ceil(k / BLK_K) */
+  SK_ATTR_SK_TILES = 27,     /* get: tiles in the Stream-K region */
+  SK_ATTR_DP_TILES = 28,     /* get: tiles in the data-parallel region */
+  SK_ATTR_WORKSPACE_BYTES = 29, /* get: device workspace this plan needs (partials + flags) */
+  SK_ATTR_NUM_SMS = 30,      /* get: SM count p of the plan's device */
+  SK_ATTR_TRACE_INTS = 31,   /* get: int32 entries sk_gemm_traced needs */
+  SK_ATTR_TRACE_CAP = 32     /* get: trace records per CTA */
+} sk_attr;
+
+typedef struct sk_plan_s* sk_plan_t;
+
+/* Host-only description of a schedule (sk_plan_describe). */
+typedef struct {
+  int32_t mode;            /* resolved sk_mode */
+  int32_t tile_m, tile_n, tile_k;
+  int32_t tiles_m, tiles_n;
+  int64_t tiles;           /* t */
+  int32_t iters_per_tile;  /* ceil(k / BLK_K) */
+  int32_t grid;            /* g, CTAs of the persistent launch */
+  int64_t sk_tiles;        /* Stream-K region: tiles [0, sk_tiles) */
+  int64_t dp_tiles;        /* data-parallel region: tiles [sk_tiles, t) */
+  int64_t sk_iters;        /* sk_tiles * iters_per_tile */
+  int32_t raster_group;    /* tile raster band height */
+  int32_t max_segments;    /* most tile segments any CTA processes */
+  int64_t workspace_bytes; /* partials (grid x BLK_M x BLK_N x 4 B) + flags, 0 when no split */
+} sk_schedule_info;
+
+/*
+ * Create a plan for one GEMM shape on the current CUDA device.
+ *   m, n, k   >= 0 (m*n == 0: sk_gemm is a no-op; k == 0: C = beta*C).
+ *   a_type == b_type in {SK_F16, SK_BF16}; c_type in {SK_F32, SK_BF16, SK_F16};
+ *   compute_type must be SK_F32 (FP32 accumulation, Section 6).
+ *   a_layout SK_ROW_MAJOR, b_layout SK_COL_MAJOR, c_layout either.
+ *   mode: an sk_mode.
+ * Allocates the plan's device workspace (fixup partials and flags, Algorithm 5
+ * "partials" and "flags") and a status word; the plan owns them until
+ * sk_plan_destroy.  On error *out is set to NULL.
+ */
+int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk_dtype b_type,
+            sk_dtype c_type, sk_dtype compute_type, sk_layout a_layout, sk_layout b_layout,
+            sk_layout c_layout, int mode);
+
+/*
+ * C = alpha * A * B + beta * C on `stream` (paper, Section 2).
+ *   A, B: device pointers, 16-byte aligned, in the plan's layouts and leading
+ *   dimensions (each leading dimension times the element size a multiple of
+ *   16 bytes).  C: device pointer, 16-byte aligned; read only if beta != 0.
+ *   C may not alias A or B.
+ * The launch is persistent (g <= SM count CTAs, co-resident by cooperative
+ * launch whenever CTAs wait on one another).  Results are bitwise reproducible
+ * run to run for a given plan: the fixup adds the contributing CTAs' partials
+ * in increasing CTA order.  Returns SK_ERR_INVALID for bad pointers,
+ * SK_ERR_CUDA if the launch fails.
+ */
+int sk_gemm(sk_plan_t plan, const void* A, const void* B, void* C, float alpha, float beta,
+            void* stream);
+
+/*
+ * sk_gemm that also records the schedule each CTA executed: for CTA x, at
+ * trace[x * (1 + cap * 9)] the number of records, followed by records of 9
+ * int32 (cta, tile_idx, tm, tn, local_iter, local_iter_end, role,
+ * peer_first, peer_last) where role 0 = whole tile stored, 1 = partials
+ * spilled and signalled, 2 = owner that waited for peers peer_first ..
+ * peer_last (-1 when none).  cap = SK_ATTR_TRACE_CAP; `trace` is a device
+ * buffer of SK_ATTR_TRACE_INTS int32 owned by the caller.
+ */
+int sk_gemm_traced(sk_plan_t plan, const void* A, const void* B, void* C, float alpha,
+                   float beta, int32_t* trace, int64_t trace_ints, void* stream);
+
+/*
+ * Wait for the plan's last launch (synchronises its stream), then report and
+ * clear the device status: returns SK_OK or SK_ERR_TIMEOUT (also SK_ERR_CUDA
+ * if the stream reports a CUDA error).  *device_status (may be NULL) receives
+ * the raw device code: 0 ok, 1 pipeline wait expired, 2 fixup-flag wait
+ * expired, 3 aborted after another CTA failed.
+ */
+int sk_last_error(sk_plan_t plan, int* device_status);
+
+/* Release the plan and the device memory it owns.  NULL is accepted. */
+int sk_plan_destroy(sk_plan_t plan);
+
+/* Set / get an sk_attr.  Setting a schedule attribute re-plans; the
+ * workspace is reallocated when it must grow. */
+int sk_plan_set(sk_plan_t plan, int attr, int64_t value);
+int sk_plan_get(sk_plan_t plan, int attr, int64_t* value);
+
+/*
+ * Use caller-owned device memory as the plan's workspace (for example one
+ * buffer shared by many plans that run one after another on one stream).
+ * `bytes` must be at least SK_ATTR_WORKSPACE_BYTES and `ws` 256-byte aligned.
+ * The flag area is zeroed here (synchronously).  The plan frees its own
+ * workspace and never frees `ws`.
+ */
+int sk_plan_attach_workspace(sk_plan_t plan, void* ws, size_t bytes);
+
+/*
+ * Host-only planning, no GPU needed: the schedule sk_plan would choose for
+ * this shape on a device with `num_sms` SMs.  tile_n / grid / raster_group as
+ * the attributes above (0 = automatic).
+ */
+int sk_plan_describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid,
+                     int raster_group, int num_sms, sk_schedule_info* out);
+
+/*
+ * The grid-size model of Appendix A.1, host only: the g in [1, p] minimising
+ *   time_CTA(g) = a + b*[FixupPeers(g) > 1] + c*ItersPerCta(g) + d*(FixupPeers(g) - 1),
+ *   ItersPerCta(g) = ceil(ceil(m/bm) * ceil(n/bn) * ceil(k/bk) / g),
+ *   FixupPeers(g) = ceil(ceil(k/bk) / ItersPerCta(g)),
+ * ties to the smallest g.  coef = {a, b, c, d}.
+ */
+int sk_grid_model(int64_t m, int64_t n, int64_t k, int bm, int bn, int bk, int p,
+                  const double coef[4], int* g_out);
+
+/* Human-readable name of an sk_status. */
+const char* sk_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STREAMK_H */

@@ -1,0 +1,489 @@
+// C ABI of the Stream-K GEMM library (declared in include/streamk.h): plan
+// objects, device workspace ownership, TMA descriptors, launches and status.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <type_traits>
+
+#include "../../include/streamk.h"
+#include "launch.h"
+#include "planner.h"
+#include "sk_args.h"
+
+namespace {
+
+constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;  // 2 s per device-side wait
+
+// Launch epochs are unique per process, so flags left in a workspace by any
+// earlier launch (of any plan sharing it) never match a later launch.
+std::atomic<uint32_t> g_epoch{0};
+
+uint32_t next_epoch() {
+  uint32_t e = g_epoch.fetch_add(1, std::memory_order_relaxed) + 1;
+  while (e == 0) e = g_epoch.fetch_add(1, std::memory_order_relaxed) + 1;
+  return e;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// C = beta * C for k == 0 (no MAC-loop iterations).
+template <typename TC>
+__global__ void scale_kernel(TC* C, int64_t m, int64_t n, int64_t ldc, float beta) {
+  const int64_t total = m * n;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    TC* p = C + i * ldc + j;
+    float v = 0.0f;
+    if (beta != 0.0f) {
+      if constexpr (sizeof(TC) == 4)
+        v = beta * static_cast<float>(*p);
+      else if constexpr (std::is_same<TC, __nv_bfloat16>::value)
+        v = beta * __bfloat162float(*p);
+      else
+        v = beta * __half2float(*p);
+    }
+    if constexpr (sizeof(TC) == 4)
+      *p = v;
+    else if constexpr (std::is_same<TC, __nv_bfloat16>::value)
+      *p = __float2bfloat16_rn(v);
+    else
+      *p = __float2half_rn(v);
+  }
+}
+
+size_t dtype_size(int t) { return t == SK_F32 ? 4 : 2; }
+
+}  // namespace
+
+struct sk_plan_s {
+  // problem as the caller stated it
+  int64_t m, n, k;
+  int a_type, b_type, c_type;
+  int a_layout, b_layout, c_layout;
+  int mode_req;
+  int tile_n_req = 0, grid_req = 0, group_req = 0;
+  int64_t lda, ldb, ldc;
+  // problem as the kernel runs it (C column-major runs C^T = B^T A^T)
+  bool swap = false;
+  // device
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_bytes = 0;
+  sk_schedule_info info{};
+  // device memory
+  char* ws = nullptr;  // partials then flags
+  size_t ws_bytes = 0;
+  bool ws_owned = true;
+  int32_t* err = nullptr;  // 4 words, see SkArgs::err
+  // knobs
+  uint64_t timeout_ns = kDefaultTimeoutNs;
+  int debug_skip_signal = -1;
+  // TMA descriptor cache
+  const void* cached_a = nullptr;
+  const void* cached_b = nullptr;
+  CUtensorMap tm_a{}, tm_b{};
+  cudaStream_t last_stream = nullptr;
+  bool launched = false;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return SK_OK;
+  if (e == cudaErrorMemoryAllocation) return SK_ERR_NOMEM;
+  return SK_ERR_CUDA;
+}
+
+// Run the planner for the plan's (possibly swapped) shape and make sure the
+// workspace is large enough.
+int replan(sk_plan_s* p) {
+  const int64_t m = p->swap ? p->n : p->m;
+  const int64_t n = p->swap ? p->m : p->n;
+  sk_schedule_info s;
+  int st = sk::describe(m, n, p->k, p->mode_req, p->tile_n_req, p->grid_req, p->group_req,
+                        p->num_sms, &s);
+  if (st != SK_OK) return st;
+  if (s.workspace_bytes > 0 && static_cast<size_t>(s.workspace_bytes) > p->ws_bytes) {
+    if (!p->ws_owned) return SK_ERR_INVALID;  // attached buffer too small for the new schedule
+    if (p->ws) cudaFree(p->ws);
+    p->ws = nullptr;
+    p->ws_bytes = 0;
+    void* w = nullptr;
+    cudaError_t e = cudaMalloc(&w, static_cast<size_t>(s.workspace_bytes));
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMemset(w, 0, static_cast<size_t>(s.workspace_bytes));
+    if (e != cudaSuccess) {
+      cudaFree(w);
+      return cuda_status(e);
+    }
+    p->ws = static_cast<char*>(w);
+    p->ws_bytes = static_cast<size_t>(s.workspace_bytes);
+  }
+  p->info = s;
+  p->cached_a = p->cached_b = nullptr;
+  return SK_OK;
+}
+
+int encode_operand(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows, int64_t kdim,
+                   int64_t ld, int box_rows) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return SK_ERR_CUDA;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(kdim), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(sk::kBlkK), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUtensorMapDataType dt =
+      dtype == SK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUresult r = fn(tm, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SK_OK : SK_ERR_INVALID;
+}
+
+// tcgen05 kind::f16 instruction descriptor: FP32 accumulator, A/B format,
+// both operands K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+uint32_t make_idesc(int in_dtype, int tile_n) {
+  const uint32_t fmt = in_dtype == SK_BF16 ? 1u : 0u;
+  uint32_t d = 0;
+  d |= 1u << 4;                                         // D: F32
+  d |= fmt << 7;                                        // A: F16 / BF16
+  d |= fmt << 10;                                       // B: F16 / BF16
+  d |= static_cast<uint32_t>(tile_n >> 3) << 17;        // N
+  d |= static_cast<uint32_t>(sk::kBlkM >> 4) << 24;     // M
+  return d;
+}
+
+int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, float beta,
+              int32_t* trace, int64_t trace_ints, void* stream_v) {
+  if (p == nullptr) return SK_ERR_INVALID;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+  if (p->m == 0 || p->n == 0) return SK_OK;
+  if (C == nullptr || (reinterpret_cast<uintptr_t>(C) & 15u)) return SK_ERR_INVALID;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device) return SK_ERR_INVALID;
+  const sk_schedule_info& s = p->info;
+  p->last_stream = stream;
+  p->launched = true;
+
+  if (p->k == 0) {
+    const int64_t m = p->swap ? p->n : p->m, n = p->swap ? p->m : p->n;
+    const int64_t total = m * n;
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<int64_t>((total + threads - 1) / threads, 4096));
+    if (p->c_type == SK_F32)
+      scale_kernel<float><<<blocks, threads, 0, stream>>>(static_cast<float*>(C), m, n, p->ldc, beta);
+    else if (p->c_type == SK_BF16)
+      scale_kernel<__nv_bfloat16><<<blocks, threads, 0, stream>>>(static_cast<__nv_bfloat16*>(C), m,
+                                                                   n, p->ldc, beta);
+    else
+      scale_kernel<__half><<<blocks, threads, 0, stream>>>(static_cast<__half*>(C), m, n, p->ldc, beta);
+    return cuda_status(cudaGetLastError());
+  }
+
+  if (A == nullptr || B == nullptr || (reinterpret_cast<uintptr_t>(A) & 15u) ||
+      (reinterpret_cast<uintptr_t>(B) & 15u))
+    return SK_ERR_INVALID;
+  if (trace != nullptr) {
+    const int64_t need = static_cast<int64_t>(s.grid) * (1 + static_cast<int64_t>(s.max_segments) *
+                                                                 sk::kTraceFields);
+    if (trace_ints < need) return SK_ERR_INVALID;
+  }
+
+  // Kernel operands: "A" is m x k K-contiguous, "B" is n x k K-contiguous.
+  const void* ka = p->swap ? B : A;
+  const void* kb = p->swap ? A : B;
+  const int64_t km = p->swap ? p->n : p->m;
+  const int64_t kn = p->swap ? p->m : p->n;
+  const int64_t klda = p->swap ? p->ldb : p->lda;
+  const int64_t kldb = p->swap ? p->lda : p->ldb;
+  if (ka != p->cached_a) {
+    int st = encode_operand(&p->tm_a, ka, p->a_type, km, p->k, klda, sk::kBlkM);
+    if (st != SK_OK) return st;
+    p->cached_a = ka;
+  }
+  if (kb != p->cached_b) {
+    int st = encode_operand(&p->tm_b, kb, p->b_type, kn, p->k, kldb, s.tile_n);
+    if (st != SK_OK) return st;
+    p->cached_b = kb;
+  }
+
+  sk::SkArgs a{};
+  a.m = static_cast<int32_t>(km);
+  a.n = static_cast<int32_t>(kn);
+  a.k = static_cast<int32_t>(p->k);
+  a.tiles_m = s.tiles_m;
+  a.tiles_n = s.tiles_n;
+  a.tiles = static_cast<int32_t>(s.tiles);
+  a.iters_per_tile = s.iters_per_tile;
+  a.group_m = s.raster_group;
+  a.sk_tiles = static_cast<int32_t>(s.sk_tiles);
+  a.grid = s.grid;
+  a.sk_q = static_cast<int32_t>(s.sk_iters / s.grid);
+  a.sk_r = static_cast<int32_t>(s.sk_iters % s.grid);
+  a.idesc = make_idesc(p->a_type, s.tile_n);
+  a.C = C;
+  a.ldc = p->ldc;
+  a.c_vec = (p->ldc * static_cast<int64_t>(dtype_size(p->c_type))) % 16 == 0 ? 1 : 0;
+  a.alpha = alpha;
+  a.beta = beta;
+  const bool split = s.workspace_bytes > 0;
+  a.flags = split ? reinterpret_cast<uint32_t*>(p->ws) : nullptr;
+  a.partials = split ? reinterpret_cast<float*>(p->ws + sk::kFlagBytes) : nullptr;
+  a.epoch = next_epoch();
+  a.err = p->err;
+  a.trace = trace;
+  a.trace_cap = s.max_segments;
+  a.debug_skip_signal = p->debug_skip_signal;
+  a.timeout_ns = p->timeout_ns;
+
+  cudaError_t e = s.tile_n == 256
+                      ? sk::launch_bn256(p->c_type, p->tm_a, p->tm_b, a, split, stream)
+                      : sk::launch_bn128(p->c_type, p->tm_a, p->tm_b, a, split, stream);
+  return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sk_status_string(int status) {
+  switch (status) {
+    case SK_OK: return "SK_OK";
+    case SK_ERR_INVALID: return "SK_ERR_INVALID";
+    case SK_ERR_UNSUPPORTED: return "SK_ERR_UNSUPPORTED";
+    case SK_ERR_CUDA: return "SK_ERR_CUDA";
+    case SK_ERR_TIMEOUT: return "SK_ERR_TIMEOUT";
+    case SK_ERR_NOMEM: return "SK_ERR_NOMEM";
+    case SK_ERR_DEVICE: return "SK_ERR_DEVICE";
+    default: return "SK_ERR_UNKNOWN";
+  }
+}
+
+int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk_dtype b_type,
+            sk_dtype c_type, sk_dtype compute_type, sk_layout a_layout, sk_layout b_layout,
+            sk_layout c_layout, int mode) {
+  if (out == nullptr) return SK_ERR_INVALID;
+  *out = nullptr;
+  if (m < 0 || n < 0 || k < 0) return SK_ERR_INVALID;
+  if (mode < SK_MODE_AUTO || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
+  if (!((a_type == SK_F16 || a_type == SK_BF16) && b_type == a_type)) return SK_ERR_UNSUPPORTED;
+  if (!(c_type == SK_F32 || c_type == SK_BF16 || c_type == SK_F16)) return SK_ERR_UNSUPPORTED;
+  if (compute_type != SK_F32) return SK_ERR_UNSUPPORTED;
+  if (a_layout != SK_ROW_MAJOR || b_layout != SK_COL_MAJOR) return SK_ERR_UNSUPPORTED;
+  if (c_layout != SK_ROW_MAJOR && c_layout != SK_COL_MAJOR) return SK_ERR_INVALID;
+
+  int dev = 0, major = 0, minor = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SK_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SK_ERR_CUDA;
+  if (major != 10 || minor != 3) return SK_ERR_DEVICE;
+
+  sk_plan_s* p = new (std::nothrow) sk_plan_s();
+  if (p == nullptr) return SK_ERR_NOMEM;
+  p->m = m;
+  p->n = n;
+  p->k = k;
+  p->a_type = a_type;
+  p->b_type = b_type;
+  p->c_type = c_type;
+  p->a_layout = a_layout;
+  p->b_layout = b_layout;
+  p->c_layout = c_layout;
+  p->mode_req = mode;
+  p->lda = k;
+  p->ldb = k;
+  p->ldc = c_layout == SK_ROW_MAJOR ? n : m;
+  p->swap = c_layout == SK_COL_MAJOR;
+  p->device = dev;
+  p->num_sms = sms;
+  size_t s1 = 0, s2 = 0;
+  cudaError_t e = sk::prepare_bn128(&s1);
+  if (e == cudaSuccess) e = sk::prepare_bn256(&s2);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_status(e);
+  }
+  void* errw = nullptr;
+  e = cudaMalloc(&errw, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(errw, 0, 4 * sizeof(int32_t));
+  if (e != cudaSuccess) {
+    if (errw) cudaFree(errw);
+    delete p;
+    return cuda_status(e);
+  }
+  p->err = static_cast<int32_t*>(errw);
+  int st = replan(p);
+  if (st != SK_OK) {
+    sk_plan_destroy(p);
+    return st;
+  }
+  *out = p;
+  return SK_OK;
+}
+
+int sk_plan_destroy(sk_plan_t p) {
+  if (p == nullptr) return SK_OK;
+  if (p->ws && p->ws_owned) cudaFree(p->ws);
+  if (p->err) cudaFree(p->err);
+  delete p;
+  return SK_OK;
+}
+
+int sk_gemm(sk_plan_t p, const void* A, const void* B, void* C, float alpha, float beta,
+            void* stream) {
+  return gemm_impl(p, A, B, C, alpha, beta, nullptr, 0, stream);
+}
+
+int sk_gemm_traced(sk_plan_t p, const void* A, const void* B, void* C, float alpha, float beta,
+                   int32_t* trace, int64_t trace_ints, void* stream) {
+  if (trace == nullptr) return SK_ERR_INVALID;
+  return gemm_impl(p, A, B, C, alpha, beta, trace, trace_ints, stream);
+}
+
+int sk_last_error(sk_plan_t p, int* device_status) {
+  if (p == nullptr) return SK_ERR_INVALID;
+  if (device_status) *device_status = 0;
+  cudaError_t e = p->launched ? cudaStreamSynchronize(p->last_stream) : cudaSuccess;
+  if (e != cudaSuccess) return SK_ERR_CUDA;
+  int32_t h[4] = {0, 0, 0, 0};
+  e = cudaMemcpy(h, p->err, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return SK_ERR_CUDA;
+  if (h[0] != 0) {
+    e = cudaMemset(p->err, 0, 3 * sizeof(int32_t));
+    if (e != cudaSuccess) return SK_ERR_CUDA;
+  }
+  if (device_status) *device_status = h[0];
+  return h[0] == 0 ? SK_OK : SK_ERR_TIMEOUT;
+}
+
+int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
+  if (p == nullptr) return SK_ERR_INVALID;
+  const int64_t min_ld_a = p->k, min_ld_b = p->k;
+  const int64_t min_ld_c = p->c_layout == SK_ROW_MAJOR ? p->n : p->m;
+  switch (attr) {
+    case SK_ATTR_TILE_N: {
+      if (v != 0 && v != 128 && v != 256) return SK_ERR_UNSUPPORTED;
+      const int old = p->tile_n_req;
+      p->tile_n_req = static_cast<int>(v);
+      int st = replan(p);
+      if (st != SK_OK) {
+        p->tile_n_req = old;
+        replan(p);
+      }
+      return st;
+    }
+    case SK_ATTR_GRID: {
+      if (v < 0 || v > p->num_sms) return SK_ERR_INVALID;
+      const int old = p->grid_req;
+      p->grid_req = static_cast<int>(v);
+      int st = replan(p);
+      if (st != SK_OK) {
+        p->grid_req = old;
+        replan(p);
+      }
+      return st;
+    }
+    case SK_ATTR_RASTER_GROUP: {
+      if (v < 0 || v > (1 << 20)) return SK_ERR_INVALID;
+      p->group_req = static_cast<int>(v);
+      return replan(p);
+    }
+    case SK_ATTR_TIMEOUT_NS:
+      if (v <= 0) return SK_ERR_INVALID;
+      p->timeout_ns = static_cast<uint64_t>(v);
+      return SK_OK;
+    case SK_ATTR_LDA:
+      if (v < min_ld_a || (v * static_cast<int64_t>(dtype_size(p->a_type))) % 16) return SK_ERR_INVALID;
+      p->lda = v;
+      p->cached_a = p->cached_b = nullptr;
+      return SK_OK;
+    case SK_ATTR_LDB:
+      if (v < min_ld_b || (v * static_cast<int64_t>(dtype_size(p->b_type))) % 16) return SK_ERR_INVALID;
+      p->ldb = v;
+      p->cached_a = p->cached_b = nullptr;
+      return SK_OK;
+    case SK_ATTR_LDC:
+      if (v < min_ld_c) return SK_ERR_INVALID;
+      p->ldc = v;
+      return SK_OK;
+    case SK_ATTR_DEBUG_SKIP_SIGNAL:
+      if (v < -1 || v >= p->num_sms) return SK_ERR_INVALID;
+      p->debug_skip_signal = static_cast<int>(v);
+      return SK_OK;
+    default:
+      return SK_ERR_INVALID;
+  }
+}
+
+int sk_plan_get(sk_plan_t p, int attr, int64_t* v) {
+  if (p == nullptr || v == nullptr) return SK_ERR_INVALID;
+  const sk_schedule_info& s = p->info;
+  switch (attr) {
+    case SK_ATTR_TILE_N: *v = s.tile_n; return SK_OK;
+    case SK_ATTR_GRID: *v = s.grid; return SK_OK;
+    case SK_ATTR_RASTER_GROUP: *v = s.raster_group; return SK_OK;
+    case SK_ATTR_TIMEOUT_NS: *v = static_cast<int64_t>(p->timeout_ns); return SK_OK;
+    case SK_ATTR_LDA: *v = p->lda; return SK_OK;
+    case SK_ATTR_LDB: *v = p->ldb; return SK_OK;
+    case SK_ATTR_LDC: *v = p->ldc; return SK_OK;
+    case SK_ATTR_DEBUG_SKIP_SIGNAL: *v = p->debug_skip_signal; return SK_OK;
+    case SK_ATTR_MODE: *v = s.mode; return SK_OK;
+    case SK_ATTR_TILE_M: *v = s.tile_m; return SK_OK;
+    case SK_ATTR_TILE_K: *v = s.tile_k; return SK_OK;
+    case SK_ATTR_TILES_M: *v = s.tiles_m; return SK_OK;
+    case SK_ATTR_TILES_N: *v = s.tiles_n; return SK_OK;
+    case SK_ATTR_TILES: *v = s.tiles; return SK_OK;
+    case SK_ATTR_ITERS_PER_TILE: *v = s.iters_per_tile; return SK_OK;
+    case SK_ATTR_SK_TILES: *v = s.sk_tiles; return SK_OK;
+    case SK_ATTR_DP_TILES: *v = s.dp_tiles; return SK_OK;
+    case SK_ATTR_WORKSPACE_BYTES: *v = s.workspace_bytes; return SK_OK;
+    case SK_ATTR_NUM_SMS: *v = p->num_sms; return SK_OK;
+    case SK_ATTR_TRACE_CAP: *v = s.max_segments; return SK_OK;
+    case SK_ATTR_TRACE_INTS:
+      *v = static_cast<int64_t>(s.grid) * (1 + static_cast<int64_t>(s.max_segments) * sk::kTraceFields);
+      return SK_OK;
+    default:
+      return SK_ERR_INVALID;
+  }
+}
+
+int sk_plan_attach_workspace(sk_plan_t p, void* ws, size_t bytes) {
+  if (p == nullptr || ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255u)) return SK_ERR_INVALID;
+  if (bytes < static_cast<size_t>(p->info.workspace_bytes)) return SK_ERR_INVALID;
+  if (p->ws && p->ws_owned) cudaFree(p->ws);
+  p->ws = static_cast<char*>(ws);
+  p->ws_bytes = bytes;
+  p->ws_owned = false;
+  if (bytes >= static_cast<size_t>(sk::kFlagBytes)) {
+    cudaError_t e = cudaMemset(p->ws, 0, static_cast<size_t>(sk::kFlagBytes));
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return SK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// Host planner: tile shape, decomposition (Algorithms 2 and 5, the hybrids of
+// Section 5.2) and grid size (Appendix A.1).  Pure integer/host arithmetic, no
+// CUDA calls, so it is testable without a GPU through sk_plan_describe and
+// sk_grid_model.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "../../include/streamk.h"
+#include "planner.h"
+
+namespace sk {
+
+static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Appendix A.1 time_CTA(g) with ItersPerCta(g) and FixupPeers(g) as printed.
+static double model_time(int64_t tiles, int64_t ipt, int64_t g, const double* c) {
+  const int64_t iters_per_cta = cdiv(tiles * ipt, g);
+  const int64_t peers = cdiv(ipt, iters_per_cta);
+  return c[0] + c[1] * (peers > 1 ? 1.0 : 0.0) + c[2] * static_cast<double>(iters_per_cta) +
+         c[3] * static_cast<double>(peers - 1);
+}
+
+int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]) {
+  int best = 1;
+  double best_t = 0.0;
+  for (int g = 1; g <= p; ++g) {
+    const double t = model_time(tiles, ipt, g, coef);
+    if (g == 1 || t < best_t) {
+      best = g;
+      best_t = t;
+    }
+  }
+  return best;
+}
+
+// Model constants for this kernel family on GB300, in units of one MAC-loop
+// iteration (BLK_M x BLK_N x BLK_K = 128 x BN x 64): a = fixed per-CTA cost,
+// b = spilling a partial tile, c = one iteration, d = reading and adding one
+// peer's partials in the owner.
+void model_coefficients(int tile_n, double out[4]) {
+  if (tile_n == 256) {
+    out[0] = 0.0;
+    out[1] = 4.0;
+    out[2] = 1.0;
+    out[3] = 4.0;
+  } else {
+    out[0] = 0.0;
+    out[1] = 5.0;
+    out[2] = 1.0;
+    out[3] = 5.0;
+  }
+}
+
+static int auto_tile_n(int64_t m, int64_t n, int num_sms) {
+  const int64_t pad128 = cdiv(n, 128) * 128;
+  const int64_t pad256 = cdiv(n, 256) * 256;
+  const int64_t t256 = cdiv(m, kTileM) * cdiv(n, 256);
+  if (pad256 == pad128 && t256 >= num_sms) return 256;
+  return 128;
+}
+
+int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
+             int num_sms, sk_schedule_info* out) {
+  if (out == nullptr || m < 0 || n < 0 || k < 0 || num_sms < 1 || grid < 0 || raster_group < 0)
+    return SK_ERR_INVALID;
+  if (num_sms > kMaxGrid || grid > num_sms) return SK_ERR_INVALID;
+  if (mode < SK_MODE_AUTO || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
+  if (tile_n != 0 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  // Index arithmetic on the device is 32-bit for tiles and k-blocks.
+  if (m > (int64_t(1) << 31) - 1 || n > (int64_t(1) << 31) - 1 || k > (int64_t(1) << 31) - 1)
+    return SK_ERR_INVALID;
+
+  sk_schedule_info s{};
+  s.tile_m = kTileM;
+  s.tile_k = kTileK;
+  s.tile_n = tile_n ? tile_n : auto_tile_n(m, n, num_sms);
+  s.tiles_m = static_cast<int32_t>(cdiv(m, s.tile_m));
+  s.tiles_n = static_cast<int32_t>(cdiv(n, s.tile_n));
+  s.tiles = static_cast<int64_t>(s.tiles_m) * s.tiles_n;
+  s.iters_per_tile = static_cast<int32_t>(cdiv(k, s.tile_k));
+  if (s.tiles > (int64_t(1) << 31) - 1 || s.tiles * std::max<int64_t>(1, s.iters_per_tile) >
+                                               (int64_t(1) << 40))
+    return SK_ERR_INVALID;
+  s.raster_group = raster_group ? raster_group : std::min<int32_t>(std::max(1, s.tiles_m), 16);
+
+  const int64_t t = s.tiles;
+  const int64_t ipt = s.iters_per_tile;
+  const int p = num_sms;
+  double coef[4];
+  model_coefficients(s.tile_n, coef);
+
+  if (t == 0 || ipt == 0) {
+    // Nothing to multiply: no MAC loop, C = beta * C handled by the launcher.
+    s.mode = SK_MODE_DP;
+    s.grid = static_cast<int32_t>(std::min<int64_t>(std::max<int64_t>(t, 1), p));
+    s.sk_tiles = 0;
+    s.dp_tiles = t;
+  } else {
+    int resolved = mode;
+    if (mode == SK_MODE_AUTO) {
+      if (t % p == 0)
+        resolved = SK_MODE_DP;
+      else if (t >= p)
+        resolved = SK_MODE_HYBRID;
+      else
+        resolved = SK_MODE_SK;
+    }
+    s.mode = resolved;
+    const int64_t w = t / p, rem = t % p;
+    switch (resolved) {
+      case SK_MODE_DP:
+        s.sk_tiles = 0;
+        s.grid = static_cast<int32_t>(std::min<int64_t>(t, p));
+        break;
+      case SK_MODE_SK: {
+        s.sk_tiles = t;
+        int64_t g = grid ? grid : grid_model(t, ipt, p, coef);
+        g = std::min<int64_t>(g, std::min<int64_t>(p, t * ipt));
+        s.grid = static_cast<int32_t>(std::max<int64_t>(g, 1));
+        break;
+      }
+      case SK_MODE_HYBRID:
+      case SK_MODE_HYBRID_ONE_TILE: {
+        if (rem == 0) {  // perfect quantization: full waves only
+          s.sk_tiles = 0;
+          s.grid = static_cast<int32_t>(std::min<int64_t>(t, p));
+        } else if (w == 0) {  // no full wave to trade: basic Stream-K over all tiles
+          s.sk_tiles = t;
+          int64_t g = grid ? grid : grid_model(t, ipt, p, coef);
+          g = std::min<int64_t>(g, std::min<int64_t>(p, t * ipt));
+          s.grid = static_cast<int32_t>(std::max<int64_t>(g, 1));
+        } else if (resolved == SK_MODE_HYBRID) {
+          s.sk_tiles = rem + p;  // one fewer full wave; each CTA gets 1..2 tiles
+          s.grid = p;
+        } else {
+          s.sk_tiles = rem;  // only the partial wave is balanced
+          s.grid = p;
+        }
+        break;
+      }
+      default:
+        return SK_ERR_INVALID;
+    }
+    s.dp_tiles = t - s.sk_tiles;
+  }
+  s.sk_iters = s.sk_tiles * ipt;
+
+  // Most segments a CTA can see: its Stream-K share (at most q+1 iterations,
+  // so ceil((q+1)/ipt) + 1 segments) plus its round-robin data-parallel tiles.
+  int64_t segs = 0;
+  if (s.sk_tiles > 0 && ipt > 0) {
+    const int64_t q = s.sk_iters / s.grid;
+    segs += cdiv(q + 1, ipt) + 1;
+  }
+  segs += cdiv(s.dp_tiles, s.grid);
+  s.max_segments = static_cast<int32_t>(std::max<int64_t>(segs, 1));
+
+  // Workspace: one BLK_M x BLK_N FP32 partial slot and one flag per CTA,
+  // only when some tile is split across CTAs.
+  bool split = false;
+  if (s.sk_tiles > 0 && ipt > 0) {
+    const int64_t q = s.sk_iters / s.grid, r = s.sk_iters % s.grid;
+    // Every range begins on a tile boundary iff ipt divides each CTA's start.
+    for (int64_t x = 1; x < s.grid && !split; ++x) {
+      const int64_t begin = x * q + std::min<int64_t>(x, r);
+      if (begin % ipt != 0) split = true;
+    }
+  }
+  s.workspace_bytes = split ? workspace_bytes_for(s.grid, s.tile_n) : 0;
+  *out = s;
+  return SK_OK;
+}
+
+int64_t workspace_bytes_for(int grid, int tile_n) {
+  return kFlagBytes + static_cast<int64_t>(grid) * kTileM * tile_n * 4;
+}
+
+}  // namespace sk
+
+extern "C" int sk_plan_describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid,
+                                int raster_group, int num_sms, sk_schedule_info* out) {
+  return sk::describe(m, n, k, mode, tile_n, grid, raster_group, num_sms, out);
+}
+
+extern "C" int sk_grid_model(int64_t m, int64_t n, int64_t k, int bm, int bn, int bk, int p,
+                             const double coef[4], int* g_out) {
+  if (m < 1 || n < 1 || k < 1 || bm < 1 || bn < 1 || bk < 1 || p < 1 || coef == nullptr ||
+      g_out == nullptr)
+    return SK_ERR_INVALID;
+  const int64_t tiles = sk::cdiv(m, bm) * sk::cdiv(n, bn);
+  const int64_t ipt = sk::cdiv(k, bk);
+  *g_out = sk::grid_model(tiles, ipt, p, coef);
+  return SK_OK;
+}

@@ -1,0 +1,22 @@
+// Host planner interface (see planner.cpp).
+#pragma once
+#include <cstdint>
+
+#include "../../include/streamk.h"
+
+namespace sk {
+
+constexpr int kTileM = 128;
+constexpr int kTileK = 64;
+// Workspace layout: kFlagBytes of flags (one uint32 per CTA, at most
+// kMaxGrid CTAs) at offset 0, then one BLK_M x BLK_N FP32 partial slot per CTA.
+constexpr int kMaxGrid = 1024;
+constexpr int64_t kFlagBytes = kMaxGrid * 4;
+
+int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
+             int num_sms, sk_schedule_info* out);
+int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]);
+void model_coefficients(int tile_n, double out[4]);
+int64_t workspace_bytes_for(int grid, int tile_n);
+
+}  // namespace sk

@@ -1,0 +1,54 @@
+// Kernel-argument block of the persistent Stream-K GEMM kernel, filled by the
+// host planner and passed by value at launch.
+#pragma once
+#include <cstdint>
+
+namespace sk {
+
+constexpr int kBlkM = 128;  // BLK_M: one tcgen05 M=128 MMA covers the tile height
+constexpr int kBlkK = 64;   // BLK_K: 64 16-bit elements = one 128-byte swizzle row
+
+// Segment roles (the trace format; see include/streamk.h).
+constexpr int kRoleWhole = 0;    // tile_started && tile_ended: store the tile
+constexpr int kRolePartial = 1;  // !tile_started: spill FP32 partials, then Signal
+constexpr int kRoleOwner = 2;    // tile_started && !tile_ended: Wait peers, fix up, store
+
+constexpr int kTraceFields = 9;  // cta, tile, tm, tn, kb0, kb1, role, peer_first, peer_last
+
+// Device status codes written to the error word.
+constexpr int kDevOk = 0;
+constexpr int kDevTimeoutPipeline = 1;  // an mbarrier wait ran out
+constexpr int kDevTimeoutFlag = 2;      // a fixup wait on a peer's flag ran out
+constexpr int kDevAborted = 3;          // gave up because another CTA reported an error
+
+struct SkArgs {
+  // problem
+  int32_t m, n, k;
+  int32_t tiles_m, tiles_n, tiles;
+  int32_t iters_per_tile;  // ceil(k / BLK_K)
+  int32_t group_m;         // raster band height in tiles
+  // Stream-K region: tiles [0, sk_tiles), sk_iters = sk_tiles * iters_per_tile
+  // split within one over the grid: CTA x owns [x*q + min(x,r), ...)
+  int32_t sk_tiles;
+  int32_t sk_q, sk_r;
+  int32_t grid;  // g, persistent CTAs; data-parallel tiles sk_tiles + x + j*g
+  // MMA instruction descriptor (input format bits, N, M)
+  uint32_t idesc;
+  // epilogue
+  void* C;
+  int64_t ldc;  // elements
+  int32_t c_vec;  // rows of C start 16-byte aligned: 16-byte vector loads/stores allowed
+  float alpha, beta;
+  // fixup workspace: grid slots of BLK_M x BLK_N FP32, plus one flag per slot
+  float* partials;
+  uint32_t* flags;
+  uint32_t epoch;
+  // status, tracing, bounded waits
+  int32_t* err;         // err[0]: first device status, err[1]: CTA, err[2]: where
+  int32_t* trace;       // nullptr: off; else grid x (1 + trace_cap * kTraceFields)
+  int32_t trace_cap;    // records per CTA
+  int32_t debug_skip_signal;  // CTA index that withholds its Signal (tests), -1 off
+  uint64_t timeout_ns;
+};
+
+}  // namespace sk

@@ -1,0 +1,529 @@
+// Persistent Stream-K GEMM kernel for sm_103a.
+//
+// One kernel serves every schedule of the paper: data-parallel (Algorithm 2,
+// Stream-K region empty), basic Stream-K (Algorithm 5, data-parallel region
+// empty) and the hybrids of Section 5.2 (a Stream-K region over the first
+// sk_tiles tiles followed by full data-parallel waves).  The schedule is a pure
+// function of (blockIdx.x, SkArgs) that all three warp roles walk in lockstep.
+//
+// Roles (192 threads, one CTA per SM):
+//   warp 0      TMA producer: streams the A and B fragments of every MAC-loop
+//               iteration (Algorithm 3's LoadFragment) into an S-stage ring of
+//               128-byte-swizzled shared-memory tiles.
+//   warp 1      TMEM allocator and MMA issuer: one thread issues BLK_K/16
+//               tcgen05.mma per iteration into one of two TMEM accumulators.
+//   warps 2..5  epilogue: per tile segment, either spill the FP32 partial sums
+//               to this CTA's workspace slot and Signal (segment does not start
+//               the tile), or Wait for the contributing CTAs in increasing order
+//               and add their partials (tile started here, not finished here),
+//               then compute alpha*acc + beta*C and store the tile.
+//
+// Every wait is bounded by SkArgs::timeout_ns; on expiry the kernel records a
+// status in SkArgs::err and all roles unwind, drain their in-flight TMA loads
+// and MMAs, free TMEM and return.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "ptx.cuh"
+#include "sk_args.h"
+
+namespace sk {
+
+constexpr int kThreads = 192;
+constexpr int kEpiWarp0 = 2;
+constexpr int kEpiThreads = 128;
+constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
+
+template <int BN>
+struct Cfg {
+  static constexpr int kStages = (BN == 256) ? 4 : 6;
+  static constexpr int kABytes = kBlkM * kBlkK * 2;
+  static constexpr int kBBytes = BN * kBlkK * 2;
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kTmemCols = 2 * BN;  // two FP32 accumulators of BN columns
+  static constexpr int kBarOffset = kStages * kStageBytes;
+  static constexpr int kNumBars = 2 * kStages + 5;
+  static constexpr int kSmemBytes = kBarOffset + 256 + 1024;  // + barriers, + 1 KiB alignment
+  static_assert(kNumBars * 8 + 8 <= 256, "barrier area");
+};
+
+// Where a bounded wait gave up (err[2]).
+enum : int { kAtProducerEmpty = 1, kAtMmaAccEmpty, kAtMmaFull, kAtEpiAccFull, kAtFlag, kAtDrain };
+
+__device__ __forceinline__ void report(const SkArgs& a, int code, int where) {
+  if (atomicCAS(&a.err[0], 0, code) == 0) {
+    a.err[1] = static_cast<int32_t>(blockIdx.x);
+    a.err[2] = where;
+  }
+  atomicExch(reinterpret_cast<unsigned*>(&a.err[3]), a.epoch);
+  __threadfence();
+}
+
+// Bounded mbarrier wait.  Returns false if this CTA is aborting or the time
+// limit ran out (then it also records the timeout and raises the CTA's abort).
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                         const SkArgs& a, int where) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer_ns() - t0 > a.timeout_ns) {
+        report(a, kDevTimeoutPipeline, where);
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+// Bounded Wait(flags[y]) of Algorithms 4/5: acquire-load until the peer has
+// published this launch's epoch.
+__device__ __forceinline__ bool wait_flag(const uint32_t* flag, volatile int* abort_flag,
+                                          const SkArgs& a) {
+  if (ld_acquire_gpu(flag) == a.epoch) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t i = 1;; ++i) {
+    __nanosleep(64);
+    if (ld_acquire_gpu(flag) == a.epoch) return true;
+    if ((i & 31u) == 0) {
+      if (*abort_flag) return false;
+      if (static_cast<uint32_t>(ld_volatile_s32(&a.err[3])) == a.epoch) {  // another CTA failed
+        report(a, kDevAborted, kAtFlag);
+        *abort_flag = 1;
+        return false;
+      }
+      if (globaltimer_ns() - t0 > a.timeout_ns) {
+        report(a, kDevTimeoutFlag, kAtFlag);
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+// Epilogue-wide OR of a per-thread predicate (bar.red over the 128 epilogue
+// threads), so that every epilogue thread takes the same branch.
+__device__ __forceinline__ bool epi_any(bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(out)
+      : "r"(pred ? 1u : 0u), "r"(kEpiBarrier), "r"(kEpiThreads)
+      : "memory");
+  return out != 0;
+}
+
+// The CTA's walk over its tile segments: first its within-one share of the
+// Stream-K iteration range (Algorithm 5), then its data-parallel tiles.
+struct Walker {
+  int64_t it, it_end;
+  int32_t dp_tile;
+
+  __device__ __forceinline__ void init(const SkArgs& a, int x) {
+    const int64_t q = a.sk_q, r = a.sk_r;
+    it = static_cast<int64_t>(x) * q + min(static_cast<int64_t>(x), r);
+    it_end = it + q + (x < r ? 1 : 0);
+    dp_tile = a.sk_tiles + x;
+  }
+
+  __device__ __forceinline__ bool next(const SkArgs& a, int& tile, int& kb0, int& kb1) {
+    if (it < it_end) {
+      const int64_t ipt = a.iters_per_tile;
+      tile = static_cast<int>(it / ipt);
+      const int64_t tile_iter = static_cast<int64_t>(tile) * ipt;
+      const int64_t tile_iter_end = tile_iter + ipt;
+      kb0 = static_cast<int>(it - tile_iter);
+      kb1 = static_cast<int>(min(it_end, tile_iter_end) - tile_iter);
+      it = tile_iter_end;
+      return true;
+    }
+    if (dp_tile < a.tiles) {
+      tile = dp_tile;
+      kb0 = 0;
+      kb1 = a.iters_per_tile;
+      dp_tile += a.grid;
+      return true;
+    }
+    return false;
+  }
+};
+
+// The CTA whose Stream-K range holds global iteration i.
+__device__ __forceinline__ int cta_of_iter(const SkArgs& a, int64_t i) {
+  const int64_t q = a.sk_q, r = a.sk_r;
+  const int64_t big = r * (q + 1);
+  if (i < big) return static_cast<int>(i / (q + 1));
+  return static_cast<int>(r + (i - big) / q);
+}
+
+// Tile raster: m fastest within bands of group_m tile rows.
+__device__ __forceinline__ void tile_coords(const SkArgs& a, int tile, int& tm, int& tn) {
+  const int band_tiles = a.group_m * a.tiles_n;
+  const int band = tile / band_tiles;
+  const int first_m = band * a.group_m;
+  const int rows = min(a.group_m, a.tiles_m - first_m);
+  const int local = tile - band * band_tiles;
+  tm = first_m + local % rows;
+  tn = local / rows;
+}
+
+template <typename TC>
+__device__ __forceinline__ float to_f32(TC v);
+template <>
+__device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+
+template <typename TC>
+__device__ __forceinline__ TC from_f32(float v);
+template <>
+__device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi, __nv_bfloat16*) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack2(float lo, float hi, __half*) {
+  __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 unpack2(uint32_t u, __nv_bfloat16*) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&u);
+  return __bfloat1622float2(h);
+}
+__device__ __forceinline__ float2 unpack2(uint32_t u, __half*) {
+  __half2 h = *reinterpret_cast<__half2*>(&u);
+  return __half22float2(h);
+}
+
+// StoreTile for one thread's 32 consecutive columns of one row:
+// C[row, col .. col+31] = alpha * v + beta * C[row, col .. col+31].
+template <typename TC>
+__device__ __forceinline__ void store_row32(const SkArgs& a, int grow, int gcol, const float (&v)[32]) {
+  if (grow >= a.m) return;
+  TC* crow = reinterpret_cast<TC*>(a.C) + static_cast<int64_t>(grow) * a.ldc + gcol;
+  const float alpha = a.alpha, beta = a.beta;
+  if (a.c_vec && gcol + 32 <= a.n) {
+    if constexpr (sizeof(TC) == 4) {
+      float4* p = reinterpret_cast<float4*>(crow);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float4 o = make_float4(alpha * v[4 * j], alpha * v[4 * j + 1], alpha * v[4 * j + 2],
+                               alpha * v[4 * j + 3]);
+        if (beta != 0.0f) {
+          const float4 c = p[j];
+          o.x = fmaf(beta, c.x, o.x);
+          o.y = fmaf(beta, c.y, o.y);
+          o.z = fmaf(beta, c.z, o.z);
+          o.w = fmaf(beta, c.w, o.w);
+        }
+        p[j] = o;
+      }
+    } else {
+      uint4* p = reinterpret_cast<uint4*>(crow);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float o[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) o[e] = alpha * v[8 * j + e];
+        if (beta != 0.0f) {
+          const uint4 c = p[j];
+          const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 f = unpack2(cw[e], static_cast<TC*>(nullptr));
+            o[2 * e] = fmaf(beta, f.x, o[2 * e]);
+            o[2 * e + 1] = fmaf(beta, f.y, o[2 * e + 1]);
+          }
+        }
+        uint4 w;
+        w.x = pack2(o[0], o[1], static_cast<TC*>(nullptr));
+        w.y = pack2(o[2], o[3], static_cast<TC*>(nullptr));
+        w.z = pack2(o[4], o[5], static_cast<TC*>(nullptr));
+        w.w = pack2(o[6], o[7], static_cast<TC*>(nullptr));
+        p[j] = w;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (gcol + j < a.n) {
+        float o = alpha * v[j];
+        if (beta != 0.0f) o = fmaf(beta, to_f32<TC>(crow[j]), o);
+        crow[j] = from_f32<TC>(o);
+      }
+    }
+  }
+}
+
+template <int BN, typename TC>
+__global__ void __launch_bounds__(kThreads, 1)
+    sk_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ SkArgs a) {
+  using C_ = Cfg<BN>;
+  constexpr int S = C_::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // 128-byte swizzle atoms need 1 KiB alignment
+  uint8_t* base_ptr = smem_raw + (base - raw);
+  const uint32_t bar0 = base + C_::kBarOffset;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + C_::kBarOffset + 8 * C_::kNumBars);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  auto stage_a = [&](int s) { return base + static_cast<uint32_t>(s * C_::kStageBytes); };
+  auto stage_b = [&](int s) { return base + static_cast<uint32_t>(s * C_::kStageBytes + C_::kABytes); };
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
+  auto accf_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
+  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * S + 4);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int x = blockIdx.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf_bar(b), 1);
+      mbar_init(acce_bar(b), kEpiThreads / 32);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), C_::kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      Walker w;
+      w.init(a, x);
+      int tile, kb0, kb1;
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t issued = 0;
+      bool ok = true;
+      while (ok && w.next(a, tile, kb0, kb1)) {
+        int tm, tn;
+        tile_coords(a, tile, tm, tn);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(full_bar(stage), C_::kStageBytes);
+          tma_load_2d(stage_a(stage), &tmA, full_bar(stage), kb * kBlkK, tm * kBlkM);
+          tma_load_2d(stage_b(stage), &tmB, full_bar(stage), kb * kBlkK, tn * BN);
+          ++issued;
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (ok) {
+        // Tail: wait until the MMA warp has released every stage, so no
+        // tcgen05.commit arrival is still in flight when the CTA exits.
+        for (int i = 0; i < S; ++i) {
+          if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) break;
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      } else {
+        // Unwind: let the loads already issued land before shared memory goes away.
+        const int64_t first = issued > S ? issued - S : 0;
+        for (int64_t j = first; j < issued; ++j) {
+          const int s = static_cast<int>(j % S);
+          const uint32_t par = static_cast<uint32_t>((j / S) & 1);
+          const uint64_t t0 = globaltimer_ns();
+          while (!mbar_try_wait(full_bar(s), par) && globaltimer_ns() - t0 < a.timeout_ns) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ MMA issuer
+      Walker w;
+      w.init(a, x);
+      int tile, kb0, kb1;
+      int stage = 0, acc = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      bool ok = true;
+      while (ok && w.next(a, tile, kb0, kb1)) {
+        if (!wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t adesc = smem_desc_sw128(stage_a(stage));
+          const uint64_t bdesc = smem_desc_sw128(stage_b(stage));
+#pragma unroll
+          for (int kk = 0; kk < kBlkK / 16; ++kk) {
+            // advance 16 elements (32 B) along K inside the swizzle atom
+            mma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
+                    (kb > kb0 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(empty_bar(stage));  // frees the stage once these MMAs finish
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(accf_bar(acc));  // accumulator complete
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1u;
+      }
+      // Drain: every MMA issued above completes before TMEM is released.
+      mma_commit(drain_bar);
+      const uint64_t t0 = globaltimer_ns();
+      while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < a.timeout_ns) {
+      }
+    }
+  } else {
+    // -------------------------------------------------------------- epilogue
+    const int quarter = warp & 3;  // TMEM lanes this warp may access
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+    const int ipt = a.iters_per_tile;
+    Walker w;
+    w.init(a, x);
+    int tile, kb0, kb1, acc = 0, nrec = 0;
+    uint32_t acc_phase = 0;
+    float* const my_slot = a.partials + static_cast<size_t>(x) * (kBlkM * BN);
+    while (w.next(a, tile, kb0, kb1)) {
+      const bool started = kb0 == 0;
+      const bool ended = kb1 == ipt;
+      const int role = !started ? kRolePartial : (!ended ? kRoleOwner : kRoleWhole);
+      int peer_first = -1, peer_last = -1;
+      if (role == kRoleOwner) {
+        peer_first = x + 1;
+        peer_last = cta_of_iter(a, static_cast<int64_t>(tile) * ipt + ipt - 1);
+      }
+      int tm, tn;
+      tile_coords(a, tile, tm, tn);
+
+      bool fail = !wait_bar(accf_bar(acc), acc_phase, abort_flag, a, kAtEpiAccFull);
+      if (epi_any(fail)) break;
+      tc_fence_after();
+      if (role == kRoleOwner) {
+        for (int y = peer_first; y <= peer_last && !fail; ++y) fail = !wait_flag(&a.flags[y], abort_flag, a);
+        if (epi_any(fail)) break;
+      }
+
+      const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(acc * BN);
+      const int grow = tm * kBlkM + row;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld_x32(tbase + static_cast<uint32_t>(c * 32), r);
+        tmem_wait_ld();
+        if (c == BN / 32 - 1) {
+          // all of this warp's TMEM reads are done: hand the buffer back to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce_bar(acc));
+        }
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+        // Workspace slot layout: [c][j][row] float4, so a warp's 16-byte
+        // accesses are contiguous.
+        if (role == kRolePartial) {
+          float4* dst = reinterpret_cast<float4*>(my_slot) + (c * 8) * kBlkM + row;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            __stcg(dst + j * kBlkM, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+        } else {
+          if (role == kRoleOwner) {
+            for (int y = peer_first; y <= peer_last; ++y) {
+              const float4* src = reinterpret_cast<const float4*>(
+                                      a.partials + static_cast<size_t>(y) * (kBlkM * BN)) +
+                                  (c * 8) * kBlkM + row;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float4 p = __ldcg(src + j * kBlkM);
+                v[4 * j] += p.x;
+                v[4 * j + 1] += p.y;
+                v[4 * j + 2] += p.z;
+                v[4 * j + 3] += p.w;
+              }
+            }
+          }
+          store_row32<TC>(a, grow, tn * BN + c * 32, v);
+        }
+      }
+      if (role == kRolePartial) {
+        // Signal(flags[x]): all 128 threads' partial stores before the release.
+        __threadfence();
+        named_bar_sync(kEpiBarrier, kEpiThreads);
+        if (warp == kEpiWarp0 && lane == 0 && x != a.debug_skip_signal)
+          st_release_gpu(&a.flags[x], a.epoch);
+      }
+      if (a.trace != nullptr && warp == kEpiWarp0 && lane == 0) {
+        int32_t* tb = a.trace + static_cast<size_t>(x) * (1 + a.trace_cap * kTraceFields);
+        if (nrec < a.trace_cap) {
+          int32_t* rec = tb + 1 + nrec * kTraceFields;
+          rec[0] = x;
+          rec[1] = tile;
+          rec[2] = tm;
+          rec[3] = tn;
+          rec[4] = kb0;
+          rec[5] = kb1;
+          rec[6] = role;
+          rec[7] = peer_first;
+          rec[8] = peer_last;
+        }
+        ++nrec;
+        tb[0] = nrec;
+      }
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1u;
+    }
+  }
+
+  __syncwarp();  // reconverge the producer / MMA warps (one lane worked)
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, C_::kTmemCols);
+  }
+}
+
+}  // namespace sk

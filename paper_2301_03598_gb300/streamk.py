@@ -1,0 +1,267 @@
+"""Python binding of libstreamk (include/streamk.h).
+
+The functions carry the C ABI's names and do argument marshalling only: torch
+tensors are passed as their ``data_ptr()``, streams as their ``cuda_stream``
+handle, names of dtypes/layouts/modes as the C enums.  Every step of the GEMM
+runs in the library's CUDA kernels; there is no fallback, and loading fails
+loudly when libstreamk.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+from .build import INCLUDE, LIB
+
+SK_OK, SK_ERR_INVALID, SK_ERR_UNSUPPORTED, SK_ERR_CUDA, SK_ERR_TIMEOUT, SK_ERR_NOMEM, \
+    SK_ERR_DEVICE = range(7)
+DTYPES = {"f16": 0, "bf16": 1, "f32": 2}
+LAYOUTS = {"row": 0, "col": 1}
+MODES = {"auto": 0, "dp": 1, "sk": 2, "hybrid": 3, "hybrid1": 4}
+MODE_NAMES = {v: k for k, v in MODES.items()}
+ATTRS = {
+    "tile_n": 1, "grid": 2, "raster_group": 3, "timeout_ns": 4, "lda": 5, "ldb": 6, "ldc": 7,
+    "debug_skip_signal": 8, "mode": 20, "tile_m": 21, "tile_k": 22, "tiles_m": 23,
+    "tiles_n": 24, "tiles": 25, "iters_per_tile": 26, "sk_tiles": 27, "dp_tiles": 28,
+    "workspace_bytes": 29, "num_sms": 30, "trace_ints": 31, "trace_cap": 32,
+}
+TRACE_FIELDS = 9
+
+
+class StreamKError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {sk_status_string(status)}")
+        self.status = status
+
+
+class sk_schedule_info(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32),
+                ("tile_k", ctypes.c_int32), ("tiles_m", ctypes.c_int32),
+                ("tiles_n", ctypes.c_int32), ("tiles", ctypes.c_int64),
+                ("iters_per_tile", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("sk_tiles", ctypes.c_int64), ("dp_tiles", ctypes.c_int64),
+                ("sk_iters", ctypes.c_int64), ("raster_group", ctypes.c_int32),
+                ("max_segments", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["mode_name"] = MODE_NAMES.get(d["mode"], "?")
+        return d
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libstreamk.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise ImportError(f"libstreamk.so is not built ({LIB}); run "
+                          "`python -m paper_2301_03598_gb300.build`")
+    L = ctypes.CDLL(LIB)
+    i32, i64, vp, f32 = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float
+    L.sk_plan.argtypes = [ctypes.POINTER(vp), i64, i64, i64, i32, i32, i32, i32, i32, i32, i32,
+                          i32]
+    L.sk_gemm.argtypes = [vp, vp, vp, vp, f32, f32, vp]
+    L.sk_gemm_traced.argtypes = [vp, vp, vp, vp, f32, f32, vp, i64, vp]
+    L.sk_last_error.argtypes = [vp, ctypes.POINTER(i32)]
+    L.sk_plan_destroy.argtypes = [vp]
+    L.sk_plan_set.argtypes = [vp, i32, i64]
+    L.sk_plan_get.argtypes = [vp, i32, ctypes.POINTER(i64)]
+    L.sk_plan_attach_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+    L.sk_plan_describe.argtypes = [i64, i64, i64, i32, i32, i32, i32, i32,
+                                   ctypes.POINTER(sk_schedule_info)]
+    L.sk_grid_model.argtypes = [i64, i64, i64, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(i32)]
+    L.sk_status_string.argtypes = [i32]
+    L.sk_status_string.restype = ctypes.c_char_p
+    for name in ("sk_plan", "sk_gemm", "sk_gemm_traced", "sk_last_error", "sk_plan_destroy",
+                 "sk_plan_set", "sk_plan_get", "sk_plan_attach_workspace", "sk_plan_describe",
+                 "sk_grid_model"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def header_functions():
+    """Names of the functions include/*.h declares (for export checks)."""
+    names = []
+    for f in sorted(os.listdir(INCLUDE)):
+        if f.endswith(".h"):
+            text = open(os.path.join(INCLUDE, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(sk_[a-z_0-9]+)\s*\(", text,
+                                re.M)
+    return names
+
+
+def _code(table, v, what):
+    if isinstance(v, int):
+        return v
+    try:
+        return table[v]
+    except KeyError:
+        raise ValueError(f"unknown {what} {v!r}") from None
+
+
+def _dtype_name(x):
+    try:
+        import torch
+        m = {torch.float16: "f16", torch.bfloat16: "bf16", torch.float32: "f32"}
+        if x in m:
+            return m[x]
+    except ImportError:  # pragma: no cover
+        pass
+    return x
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _check(status, what):
+    if status != SK_OK:
+        raise StreamKError(status, what)
+
+
+class Plan:
+    """Owner of an sk_plan_t handle."""
+
+    def __init__(self, handle: int, m: int, n: int, k: int, a_type: str, c_type: str):
+        self.handle = handle
+        self.m, self.n, self.k = m, n, k
+        self.a_type, self.c_type = a_type, c_type
+
+    def get(self, attr) -> int:
+        return sk_plan_get(self, attr)
+
+    def set(self, attr, value: int) -> None:
+        sk_plan_set(self, attr, value)
+
+    def info(self):
+        return {name: self.get(name) for name in ATTRS}
+
+    def destroy(self):
+        if self.handle:
+            lib().sk_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sk_status_string(status: int) -> str:
+    return lib().sk_status_string(status).decode()
+
+
+def sk_plan(m: int, n: int, k: int, a_type="bf16", b_type=None, c_type="bf16",
+            compute_type="f32", a_layout="row", b_layout="col", c_layout="row",
+            mode="auto") -> Plan:
+    a_type = _dtype_name(a_type)
+    b_type = a_type if b_type is None else _dtype_name(b_type)
+    c_type = _dtype_name(c_type)
+    h = ctypes.c_void_p()
+    st = lib().sk_plan(ctypes.byref(h), m, n, k, _code(DTYPES, a_type, "dtype"),
+                       _code(DTYPES, b_type, "dtype"), _code(DTYPES, c_type, "dtype"),
+                       _code(DTYPES, _dtype_name(compute_type), "dtype"),
+                       _code(LAYOUTS, a_layout, "layout"), _code(LAYOUTS, b_layout, "layout"),
+                       _code(LAYOUTS, c_layout, "layout"), _code(MODES, mode, "mode"))
+    _check(st, "sk_plan")
+    return Plan(h.value, m, n, k, a_type, c_type)
+
+
+def sk_plan_destroy(plan: Plan) -> None:
+    plan.destroy()
+
+
+def sk_plan_set(plan: Plan, attr, value: int) -> None:
+    _check(lib().sk_plan_set(plan.handle, _code(ATTRS, attr, "attr"), int(value)), "sk_plan_set")
+
+
+def sk_plan_get(plan: Plan, attr) -> int:
+    v = ctypes.c_int64()
+    _check(lib().sk_plan_get(plan.handle, _code(ATTRS, attr, "attr"), ctypes.byref(v)),
+           "sk_plan_get")
+    return v.value
+
+
+def sk_plan_attach_workspace(plan: Plan, ws, nbytes: int) -> None:
+    _check(lib().sk_plan_attach_workspace(plan.handle, _ptr(ws), nbytes),
+           "sk_plan_attach_workspace")
+
+
+def sk_gemm(plan: Plan, A, B, C, alpha: float = 1.0, beta: float = 0.0, stream=None) -> None:
+    """C = alpha * A @ B + beta * C (A row-major m x k, B column-major k x n,
+    i.e. an n x k row-major tensor).  Asynchronous on ``stream``."""
+    _check(lib().sk_gemm(plan.handle, _ptr(A), _ptr(B), _ptr(C), alpha, beta, _stream(stream)),
+           "sk_gemm")
+
+
+def sk_gemm_traced(plan: Plan, A, B, C, alpha: float, beta: float, trace, stream=None) -> None:
+    n_ints = trace.numel() if hasattr(trace, "numel") else plan.get("trace_ints")
+    _check(lib().sk_gemm_traced(plan.handle, _ptr(A), _ptr(B), _ptr(C), alpha, beta, _ptr(trace),
+                                n_ints, _stream(stream)), "sk_gemm_traced")
+
+
+def sk_last_error(plan: Plan):
+    """(status, device_status) after waiting for the plan's last launch."""
+    dev = ctypes.c_int(0)
+    st = lib().sk_last_error(plan.handle, ctypes.byref(dev))
+    return st, dev.value
+
+
+def sk_plan_describe(m: int, n: int, k: int, mode="auto", tile_n: int = 0, grid: int = 0,
+                     raster_group: int = 0, num_sms: int = 148):
+    info = sk_schedule_info()
+    _check(lib().sk_plan_describe(m, n, k, _code(MODES, mode, "mode"), tile_n, grid,
+                                  raster_group, num_sms, ctypes.byref(info)), "sk_plan_describe")
+    return info.as_dict()
+
+
+def sk_grid_model(m: int, n: int, k: int, bm: int, bn: int, bk: int, p: int, coef) -> int:
+    c = (ctypes.c_double * 4)(*coef)
+    g = ctypes.c_int(0)
+    _check(lib().sk_grid_model(m, n, k, bm, bn, bk, p, c, ctypes.byref(g)), "sk_grid_model")
+    return g.value
+
+
+def decode_trace(trace_host, grid: int, cap: int):
+    """Turn a copied-back trace buffer into records (tuples of 9 ints)."""
+    vals = [int(v) for v in trace_host]
+    stride = 1 + cap * TRACE_FIELDS
+    out = []
+    for x in range(grid):
+        base = x * stride
+        count = vals[base]
+        if count > cap:
+            raise ValueError(f"CTA {x} recorded {count} segments, capacity {cap}")
+        for r in range(count):
+            o = base + 1 + r * TRACE_FIELDS
+            out.append(tuple(vals[o:o + TRACE_FIELDS]))
+    return out

@@ -1,0 +1,103 @@
+"""The C-ABI library without a GPU: it loads, exports every function the
+header declares, and its host planner agrees with the oracle's schedule model
+(hybrid regions of Section 5.2, grid-size model of Appendix A.1)."""
+import ctypes
+
+import pytest
+
+from oracle import schedule as S
+from paper_2301_03598_gb300 import build, streamk as sk
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+def test_exports_every_header_function():
+    names = sk.header_functions()
+    assert {"sk_plan", "sk_gemm", "sk_plan_destroy", "sk_last_error"} <= set(names)
+    lib = ctypes.CDLL(build.LIB)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings():
+    assert sk.sk_status_string(sk.SK_OK) == "SK_OK"
+    assert sk.sk_status_string(sk.SK_ERR_TIMEOUT) == "SK_ERR_TIMEOUT"
+    assert sk.sk_status_string(99) == "SK_ERR_UNKNOWN"
+
+
+@pytest.mark.parametrize("case", [(256, 3584, 8192, 108), (1024, 1024, 1024, 64),
+                                  (128, 128, 16384, 8)])
+def test_grid_model_reproduces_fig7(case):
+    m, n, k, g = case
+    assert sk.sk_grid_model(m, n, k, 128, 128, 32, 108, (0, 20, 1, 8)) == g
+
+
+@pytest.mark.parametrize("m,n,k", [(384, 384, 4096), (3000, 200, 128), (128, 128, 65536),
+                                   (1536, 1536, 1536), (8192, 128, 4096)])
+@pytest.mark.parametrize("coef", [(0, 20, 1, 8), (3, 1, 2, 5), (0, 5, 1, 5)])
+def test_grid_model_matches_oracle(m, n, k, coef):
+    prob = S.Problem(m, n, k, 128, 128, 64)
+    assert sk.sk_grid_model(m, n, k, 128, 128, 64, 148, coef) == \
+        S.best_grid_size(prob, 148, *coef)
+
+
+@pytest.mark.parametrize("t_m,t_n,ipt", [(19, 16, 4), (3, 3, 64), (64, 32, 128), (13, 12, 2),
+                                         (38, 8, 3), (12, 12, 24), (2, 2, 1024)])
+@pytest.mark.parametrize("p", [148, 132, 4])
+def test_hybrid_regions_match_oracle(t_m, t_n, ipt, p):
+    m, n, k = t_m * 128, t_n * 128, ipt * 64
+    t = t_m * t_n
+    for mode, variant in (("hybrid", S.HYBRID_TWO_TILE), ("hybrid1", S.HYBRID_ONE_TILE)):
+        d = sk.sk_plan_describe(m, n, k, mode, tile_n=128, num_sms=p)
+        sk_tiles, dp_tiles = S.hybrid_regions(t, p, variant)
+        assert (d["sk_tiles"], d["dp_tiles"]) == (sk_tiles, dp_tiles)
+        assert d["tiles"] == t and d["iters_per_tile"] == ipt
+        if 0 < sk_tiles < t:
+            assert d["grid"] == p
+    d = sk.sk_plan_describe(m, n, k, "dp", tile_n=128, num_sms=p)
+    assert d["sk_tiles"] == 0 and d["grid"] == min(t, p) and d["workspace_bytes"] == 0
+
+
+def test_describe_config_shapes():
+    d = sk.sk_plan_describe(384, 384, 4096)
+    assert (d["tile_n"], d["tiles"], d["iters_per_tile"], d["mode_name"]) == (128, 9, 64, "sk")
+    assert 9 <= d["grid"] <= 148 and d["workspace_bytes"] > 0
+    d = sk.sk_plan_describe(8192, 8192, 8192)
+    assert (d["tile_n"], d["tiles"], d["mode_name"]) == (256, 2048, "hybrid")
+    assert d["sk_tiles"] == 2048 % 148 + 148 and d["dp_tiles"] % 148 == 0
+    d = sk.sk_plan_describe(128 * 37, 256, 64)      # 37*2 tiles, below one wave
+    assert d["mode_name"] == "sk"
+
+
+def test_max_segments_bounds_every_cta():
+    for (m, n, k, mode, g) in [(384, 384, 4096, "sk", 148), (19 * 128, 2048, 256, "hybrid", 0),
+                               (1000, 3000, 64, "auto", 0), (128, 128, 64 * 7, "sk", 5)]:
+        d = sk.sk_plan_describe(m, n, k, mode, tile_n=128, grid=g)
+        prob = S.Problem(m, n, k, 128, 128, 64)
+        sched = S.persistent_schedule(prob, d["grid"], d["sk_tiles"], d["raster_group"])
+        assert max(len(c) for c in sched.ctas) <= d["max_segments"]
+
+
+def test_describe_rejects_bad_arguments():
+    with pytest.raises(sk.StreamKError) as e:
+        sk.sk_plan_describe(-1, 8, 8)
+    assert e.value.status == sk.SK_ERR_INVALID
+    with pytest.raises(sk.StreamKError) as e:
+        sk.sk_plan_describe(8, 8, 8, tile_n=96)
+    assert e.value.status == sk.SK_ERR_UNSUPPORTED
+    with pytest.raises(sk.StreamKError):
+        sk.sk_plan_describe(8, 8, 8, mode=9)
+    with pytest.raises(sk.StreamKError):
+        sk.sk_grid_model(0, 8, 8, 128, 128, 64, 148, (0, 1, 1, 1))
+
+
+def test_plan_without_device_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(sk.StreamKError) as e:
+        sk.sk_plan(128, 128, 128)
+    assert e.value.status in (sk.SK_ERR_CUDA, sk.SK_ERR_DEVICE)

@@ -1,0 +1,173 @@
+"""GPU parity: the CUDA Stream-K path against the FP64 oracle, element by
+element, within the bound stated in gemm_check (k * 2^-22 * |alpha| |A||B| +
+2^-22 |beta C| + one output ulp), through the C ABI.
+
+Sizes span several tiles and ragged edges in m, n and k; schedules cover
+data-parallel (Algorithm 2), basic Stream-K (Algorithm 5) at several grid
+sizes, and both hybrids of Section 5.2.
+"""
+import numpy as np
+import pytest
+import torch
+
+from gemm_check import Problem, hybrid_shape, num_sms
+from oracle import schedule as S
+
+pytestmark = pytest.mark.gpu
+
+
+# The single-GEMM workload of the paper's strong-scaling regime: m = n = 384,
+# k = 4096 (nine 128x128 tiles), FP16 A row-major / B column-major, U[-1, 1],
+# FP32 C, alpha = 1, beta = 0.
+@pytest.mark.parametrize("mode,attrs", [
+    ("auto", {}),
+    ("dp", {}),
+    ("sk", {"grid": 9}),      # g = t: data-parallel through the Stream-K path
+    ("sk", {"grid": 18}),
+    ("sk", {"grid": 36}),     # g = 4t: fixed-split s = 4
+    ("sk", {"grid": 100}),
+    ("sk", {"grid": 148}),
+    ("hybrid", {}),
+    ("hybrid1", {}),
+])
+def test_config_384_fp16_fp32(mode, attrs):
+    prob = Problem(384, 384, 4096, "f16", "f32", "uniform", seed=1)
+    (C,), info, _ = prob.run(1.0, 0.0, mode, plan_attrs=attrs)
+    prob.check(C, 1.0, 0.0, f"384x384x4096 {mode} {attrs} g={info['grid']}")
+
+
+@pytest.mark.parametrize("m,n,k,tile_n", [
+    (129, 255, 80, 128), (200, 136, 1000, 128), (16, 16, 16, 128), (1, 8, 8, 128),
+    (130, 300, 72, 256), (257, 513, 64, 256), (127, 1, 8, 128), (128, 128, 64, 128),
+    (300, 40, 2000, 128), (64, 520, 136, 256),
+])
+@pytest.mark.parametrize("mode", ["dp", "sk", "hybrid"])
+def test_ragged_shapes(m, n, k, tile_n, mode):
+    lda = (k + 7) // 8 * 8
+    prob = Problem(m, n, k, "bf16", "f32", "normal", seed=m + n + k, lda=lda, ldb=lda)
+    (C,), info, _ = prob.run(1.0, 0.0, mode, plan_attrs={"tile_n": tile_n})
+    prob.check(C, 1.0, 0.0, f"{m}x{n}x{k} bn={tile_n} {mode} g={info['grid']}")
+
+
+@pytest.mark.parametrize("a_type,c_type", [("bf16", "bf16"), ("bf16", "f16"), ("f16", "f16"),
+                                           ("f16", "bf16"), ("bf16", "f32"), ("f16", "f32")])
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_dtypes_alpha_beta(a_type, c_type, tile_n):
+    prob = Problem(272, 528, 1088, a_type, c_type, "normal", seed=3, beta=0.5)
+    (C,), info, _ = prob.run(1.5, 0.5, "sk", plan_attrs={"tile_n": tile_n, "grid": 60})
+    prob.check(C, 1.5, 0.5, f"{a_type}->{c_type} bn={tile_n}")
+
+
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_two_tile_hybrid_with_dp_waves(tile_n):
+    # t = 2p + 8 tiles (rounded to whole tile rows): w = 2 full waves plus a
+    # partial one; the two-tile hybrid puts (t mod p) + p tiles in the
+    # Stream-K region and one full data-parallel wave after it.
+    p = num_sms()
+    tiles_m = hybrid_shape(p, 2, 8)
+    n = 8 * tile_n
+    prob = Problem(tiles_m * 128, n, 256, "bf16", "bf16", "normal", seed=4, beta=0.5)
+    (C,), info, _ = prob.run(1.0, 0.5, "hybrid", plan_attrs={"tile_n": tile_n})
+    t = tiles_m * 8
+    want = S.hybrid_regions(t, p, S.HYBRID_TWO_TILE)
+    assert info["tiles"] == t and (info["sk_tiles"], info["dp_tiles"]) == want
+    assert want[0] > p and want[1] == p
+    prob.check(C, 1.0, 0.5, f"two-tile hybrid bn={tile_n}")
+
+
+def test_one_tile_hybrid_with_dp_waves():
+    p = num_sms()
+    tiles_m = hybrid_shape(p, 2, 8)
+    prob = Problem(tiles_m * 128, 1024, 512, "bf16", "bf16", "normal", seed=5)
+    (C,), info, _ = prob.run(1.0, 0.0, "hybrid1", plan_attrs={"tile_n": 128})
+    want = S.hybrid_regions(tiles_m * 8, p, S.HYBRID_ONE_TILE)
+    assert (info["sk_tiles"], info["dp_tiles"]) == want and 0 < want[0] < p
+    prob.check(C, 1.0, 0.0, "one-tile hybrid")
+
+
+def test_column_major_c():
+    prob = Problem(200, 328, 512, "bf16", "f32", "normal", seed=6, beta=-1.0)
+    (C,), _, _ = prob.run(0.75, -1.0, "sk", c_layout="col", plan_attrs={"grid": 40})
+    prob.check(C, 0.75, -1.0, "column-major C")
+
+
+def test_run_to_run_bitwise_determinism():
+    prob = Problem(384, 384, 4096, "bf16", "f32", "normal", seed=7)
+    outs, info, _ = prob.run(1.0, 0.0, "sk", plan_attrs={"grid": 148}, reps=3)
+    assert info["workspace_bytes"] > 0
+    for C in outs[1:]:
+        assert torch.equal(C, outs[0])
+    prob.check(outs[0], 1.0, 0.0, "determinism")
+
+
+def test_sk_with_g_equal_t_is_bitwise_dp():
+    # Section 4: with g equal to the number of tiles Stream-K behaves exactly
+    # like the data-parallel decomposition -- the same MMA sequence per tile.
+    prob = Problem(384, 640, 1024, "bf16", "f32", "normal", seed=8)
+    (C_dp,), i1, _ = prob.run(1.0, 0.0, "dp", plan_attrs={"tile_n": 128})
+    (C_sk,), i2, _ = prob.run(1.0, 0.0, "sk", plan_attrs={"tile_n": 128, "grid": 15})
+    assert i1["tiles"] == 15 and i2["grid"] == 15 and i2["workspace_bytes"] == 0
+    assert torch.equal(C_dp, C_sk)
+
+
+def test_k_zero_scales_c():
+    prob = Problem(100, 72, 0, "bf16", "f32", "normal", seed=9, beta=0.5, lda=8, ldb=8)
+    (C,), _, _ = prob.run(2.0, 0.5)
+    want = prob.Cin.to(torch.float64) * 0.5
+    assert torch.equal(C.to(torch.float64), want)
+
+
+def test_empty_output_is_noop():
+    from paper_2301_03598_gb300 import streamk as sk
+    plan = sk.sk_plan(0, 64, 64, "bf16", "bf16", "bf16")
+    try:
+        sk.sk_gemm(plan, 0, 0, 0, 1.0, 0.0)
+        assert sk.sk_last_error(plan)[0] == sk.SK_OK
+    finally:
+        plan.destroy()
+
+
+def test_shared_workspace_between_plans():
+    from paper_2301_03598_gb300 import streamk as sk
+    p1 = Problem(384, 384, 2048, "bf16", "f32", "normal", seed=10)
+    p2 = Problem(256, 640, 4096, "bf16", "f32", "normal", seed=11)
+    plans = [sk.sk_plan(p.m, p.n, p.k, "bf16", "bf16", "f32", mode="sk") for p in (p1, p2)]
+    try:
+        need = max(pl.get("workspace_bytes") for pl in plans)
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        ws.fill_(0xA5)  # garbage: attach must clear the flags
+        for pl in plans:
+            sk.sk_plan_attach_workspace(pl, ws, need)
+        for _ in range(2):
+            for pl, p in zip(plans, (p1, p2)):
+                C = torch.zeros((p.m, p.n), dtype=torch.float32, device="cuda")
+                sk.sk_gemm(pl, p.A.cuda(), p.B.cuda(), C, 1.0, 0.0)
+                assert sk.sk_last_error(pl)[0] == sk.SK_OK
+                p.check(C.cpu(), 1.0, 0.0, "shared workspace")
+    finally:
+        for pl in plans:
+            pl.destroy()
+
+
+def test_invalid_arguments_on_device():
+    from paper_2301_03598_gb300 import streamk as sk
+    plan = sk.sk_plan(128, 128, 64, "bf16", "bf16", "f32")
+    try:
+        A = torch.zeros((128, 64), dtype=torch.bfloat16, device="cuda")
+        C = torch.zeros((128, 128), dtype=torch.float32, device="cuda")
+        with pytest.raises(sk.StreamKError) as e:
+            sk.sk_gemm(plan, A.data_ptr() + 2, A, C, 1.0, 0.0)   # misaligned A
+        assert e.value.status == sk.SK_ERR_INVALID
+        with pytest.raises(sk.StreamKError):
+            sk.sk_gemm(plan, A, 0, C, 1.0, 0.0)                  # null B
+        with pytest.raises(sk.StreamKError):
+            plan.set("lda", 60)                                  # below k
+        with pytest.raises(sk.StreamKError):
+            plan.set("tile_n", 192)
+    finally:
+        plan.destroy()
+    with pytest.raises(sk.StreamKError) as e:
+        sk.sk_plan(64, 64, 64, "bf16", "f16", "f32")               # mixed input types
+    assert e.value.status == sk.SK_ERR_UNSUPPORTED
+    with pytest.raises(sk.StreamKError):
+        sk.sk_plan(64, 64, 64, a_layout="col")
