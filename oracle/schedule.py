@@ -33,7 +33,11 @@ listed with its reason in the design notes of the repository):
    contribute to the tile owned by CTA x are every y > x whose range meets
    [tile_iter, tile_iter_end), i.e. y in [x+1, cta_of_iter(tile_iter_end-1)].
 4. Last CTA.  Algorithm 5 does not clamp iter_end; the within-one split never
-   runs past total_iters, and g <= total_iters is required.
+   runs past total_iters.  Basic Stream-K needs g <= total_iters.  Inside the
+   "DP + one-tile SK" hybrid (Section 5.2) the Stream-K region is balanced over
+   every CTA of the grid while each gets "less than one tile's worth", so when
+   the partial wave holds fewer iterations than there are CTAs the last CTAs'
+   shares are empty (q = 0); they then only run data-parallel tiles.
 5. Hybrid edge cases.  With w = floor(t/p) full waves: t mod p == 0 is a
    perfect quantization (pure data-parallel); w == 0 leaves no wave to give up,
    so both hybrids reduce to basic Stream-K over all t tiles; the Stream-K
@@ -175,8 +179,8 @@ def stream_k(num_tiles: int, iters_per_tile: int, g: int) -> List[List[Segment]]
     """Algorithm 5 over tiles 0 .. num_tiles-1.  Returns the segment list of
     each of the g CTAs, in processing order."""
     total_iters = num_tiles * iters_per_tile
-    if g < 1 or g > total_iters:
-        raise ValueError("need 1 <= g <= total_iters")
+    if g < 1 or total_iters < 1:
+        raise ValueError("need g >= 1 and at least one iteration")
     ctas = []
     for x in range(g):
         it, it_end = cta_iter_range(x, total_iters, g)

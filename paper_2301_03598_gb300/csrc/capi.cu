@@ -373,8 +373,12 @@ int sk_last_error(sk_plan_t p, int* device_status) {
   int32_t h[4] = {0, 0, 0, 0};
   e = cudaMemcpy(h, p->err, sizeof(h), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return SK_ERR_CUDA;
-  if (h[0] != 0) {
-    e = cudaMemset(p->err, 0, 3 * sizeof(int32_t));
+  if (h[0] != 0 || h[3] != 0) {
+    // A failed launch can leave flags raised that no owner consumed: clear
+    // them with the status so the next launch starts clean.
+    e = cudaMemset(p->err, 0, 4 * sizeof(int32_t));
+    if (e == cudaSuccess && p->ws != nullptr)
+      e = cudaMemset(p->ws, 0, static_cast<size_t>(sk::kFlagBytes));
     if (e != cudaSuccess) return SK_ERR_CUDA;
   }
   if (device_status) *device_status = h[0];

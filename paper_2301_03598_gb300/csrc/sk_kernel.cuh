@@ -494,6 +494,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         named_bar_sync(kEpiBarrier, kEpiThreads);
         if (warp == kEpiWarp0 && lane == 0 && x != a.debug_skip_signal)
           st_release_gpu(&a.flags[x], a.epoch);
+      } else if (role == kRoleOwner && warp == kEpiWarp0 && lane == 0) {
+        // Every partial has exactly one consumer: clear the peers' flags so the
+        // next launch (even a graph replay carrying the same epoch) starts clean.
+        // All epilogue threads passed their Waits before the last vote.
+        for (int y = peer_first; y <= peer_last; ++y) a.flags[y] = 0u;
       }
       if (a.trace != nullptr && warp == kEpiWarp0 && lane == 0) {
         int32_t* tb = a.trace + static_cast<size_t>(x) * (1 + a.trace_cap * kTraceFields);

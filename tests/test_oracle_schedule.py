@@ -103,18 +103,17 @@ def test_fig8_strong_scaling():
 
 
 SHAPES = [(1, 1, 1), (1, 37, 11), (9, 32, 4), (9, 64, 4), (21, 32, 4), (56, 256, 108),
-          (3, 1000, 148), (148, 3, 148), (300, 5, 148), (7, 7, 49)]
+          (3, 1000, 148), (148, 3, 148), (300, 5, 148), (7, 7, 49), (8, 5, 152), (1, 3, 4)]
 
 
 @pytest.mark.parametrize("t,ipt,g", SHAPES)
 def test_stream_k_covers_every_iteration_once(t, ipt, g):
-    if g > t * ipt:
-        pytest.skip("g > total iterations")
     ctas = S.stream_k(t, ipt, g)
     got = sorted(covered(ctas))
     assert got == [(tt, i) for tt in range(t) for i in range(ipt)]
     shares = [sum(s.local_iter_end - s.local_iter for s in c) for c in ctas]
     assert max(shares) - min(shares) <= 1                      # within one
+    assert len(ctas) == g and sum(shares) == t * ipt
     for x, segs in enumerate(ctas):
         for j, s in enumerate(segs):
             started = s.local_iter == 0
