@@ -198,6 +198,44 @@ int sk_plan_describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int 
 int sk_grid_model(int64_t m, int64_t n, int64_t k, int bm, int bn, int bk, int p,
                   const double coef[4], int* g_out);
 
+/*
+ * Allocation-free GEMM: C = alpha * A * B + beta * C like sk_gemm, for callers
+ * that cannot allocate device memory -- for example code running while its
+ * stream is captured into a CUDA graph (where an allocation is forbidden or
+ * would synchronise the device), latency-critical serving loops in which an
+ * allocation would stall every stream, and plugins that only receive buffers
+ * from a host framework that owns the memory pool.  The paper has no
+ * counterpart; it is an interface of this library only.
+ *
+ * No plan, no cudaMalloc/cudaFree and no allocating library call: the
+ * schedule is planned on the host stack for this call, with BLK_N = 128, and
+ * the fixup scratch (flags, status words and up to 12 MiB - 8 KiB of FP32
+ * partial tiles) is one fixed 12 MiB device array inside the library, which
+ * every GPU that loads the library keeps until the process exits.  A schedule
+ * that would need more partial-tile scratch than that (more than 191 CTAs)
+ * returns SK_ERR_INVALID.
+ *
+ *   A: m x k row-major, lda >= k; B: k x n column-major (an n x k row-major
+ *   array), ldb >= k; both device pointers 16-byte aligned with lda*2 and
+ *   ldb*2 multiples of 16.  C: m x n row-major, ldc >= n, 16-byte aligned.
+ *   ab_type: SK_F16 or SK_BF16; c_type: SK_F32, SK_BF16 or SK_F16.
+ *   mode: an sk_mode.
+ *   device_status: NULL, or a 4-byte-aligned device int32 that receives, in
+ *   stream order after the kernel, the device status of this call (codes as
+ *   in sk_last_error: 0 ok, 1/2 a bounded wait expired, 3 aborted).
+ *
+ * The first call on a device sets that device up (it looks up the scratch
+ * array's device address and the kernel attributes); make that first call
+ * before any stream capture on the device.  Every call on a device shares the
+ * one scratch array and leaves its contents behind; each call clears the
+ * parts that must start at zero.  Calls whose kernels overlap on the GPU
+ * (other streams, other threads) race on the scratch: serialise them.
+ */
+int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type, sk_dtype c_type,
+                    const void* A, int64_t lda, const void* B, int64_t ldb, void* C,
+                    int64_t ldc, float alpha, float beta, int mode, int32_t* device_status,
+                    void* stream);
+
 /* Human-readable name of an sk_status. */
 const char* sk_status_string(int status);
 

@@ -491,3 +491,158 @@ int sk_plan_attach_workspace(sk_plan_t p, void* ws, size_t bytes) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point (sk_gemm_noalloc, declared in streamk.h).
+//
+// The fixup scratch (flags, status words, FP32 partial tiles) lives in one
+// file-scope __device__ array that every device loading this library holds
+// until the process exits.  Host code never names the array's address
+// directly: its host-side symbol is only a stand-in, so the device address is
+// fetched once per device with cudaGetSymbolAddress (with that device current)
+// and passed to the kernel.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(12) << 20;  // 12 MiB per device
+constexpr size_t kNoAllocStatusOffset = static_cast<size_t>(sk::kFlagBytes);  // 4 words
+constexpr size_t kNoAllocPartialsOffset = kNoAllocStatusOffset + 4096;
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+struct NoAllocDevice {
+  std::once_flag once;
+  int status = SK_ERR_CUDA;
+  char* scratch = nullptr;  // device address of g_noalloc_scratch on this device
+  int num_sms = 0;
+};
+NoAllocDevice g_noalloc_devices[kNoAllocMaxDevices];
+
+void noalloc_setup(NoAllocDevice* d, int dev) {
+  int major = 0, minor = 0, sms = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    d->status = SK_ERR_CUDA;
+    return;
+  }
+  if (major != 10 || minor != 3) {
+    d->status = SK_ERR_DEVICE;
+    return;
+  }
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || ptr == nullptr) {
+    d->status = SK_ERR_CUDA;
+    return;
+  }
+  size_t smem = 0;
+  if (sk::prepare_bn128(&smem) != cudaSuccess) {
+    d->status = SK_ERR_CUDA;
+    return;
+  }
+  d->scratch = static_cast<char*>(ptr);
+  d->num_sms = sms;
+  d->status = SK_OK;
+}
+
+}  // namespace
+
+extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type, sk_dtype c_type,
+                               const void* A, int64_t lda, const void* B, int64_t ldb, void* C,
+                               int64_t ldc, float alpha, float beta, int mode,
+                               int32_t* device_status, void* stream_v) {
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+  if (m < 0 || n < 0 || k < 0) return SK_ERR_INVALID;
+  if (ab_type != SK_F16 && ab_type != SK_BF16) return SK_ERR_UNSUPPORTED;
+  if (c_type != SK_F32 && c_type != SK_BF16 && c_type != SK_F16) return SK_ERR_UNSUPPORTED;
+  if (mode < SK_MODE_AUTO || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
+  if (lda < k || ldb < k || ldc < n) return SK_ERR_INVALID;
+  if (k > 0 && ((lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0)) return SK_ERR_INVALID;
+  if (device_status != nullptr && (reinterpret_cast<uintptr_t>(device_status) & 3u))
+    return SK_ERR_INVALID;
+
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SK_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return SK_ERR_UNSUPPORTED;
+  NoAllocDevice* d = &g_noalloc_devices[dev];
+  std::call_once(d->once, noalloc_setup, d, dev);
+  if (d->status != SK_OK) return d->status;
+
+  if (m == 0 || n == 0) return SK_OK;
+  if (C == nullptr || (reinterpret_cast<uintptr_t>(C) & 15u)) return SK_ERR_INVALID;
+  char* const scratch = d->scratch;
+  int32_t* const err = reinterpret_cast<int32_t*>(scratch + kNoAllocStatusOffset);
+  // The status words must start at zero for every call (flags too, below).
+  cudaError_t e = cudaMemsetAsync(err, 0, 4 * sizeof(int32_t), stream);
+  if (e != cudaSuccess) return cuda_status(e);
+
+  if (k == 0) {  // C = beta * C
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<int64_t>((m * n + threads - 1) / threads, 4096));
+    if (c_type == SK_F32)
+      scale_kernel<float><<<blocks, threads, 0, stream>>>(static_cast<float*>(C), m, n, ldc, beta);
+    else if (c_type == SK_BF16)
+      scale_kernel<__nv_bfloat16><<<blocks, threads, 0, stream>>>(static_cast<__nv_bfloat16*>(C), m,
+                                                                   n, ldc, beta);
+    else
+      scale_kernel<__half><<<blocks, threads, 0, stream>>>(static_cast<__half*>(C), m, n, ldc, beta);
+    e = cudaGetLastError();
+  } else {
+    if (A == nullptr || B == nullptr || (reinterpret_cast<uintptr_t>(A) & 15u) ||
+        (reinterpret_cast<uintptr_t>(B) & 15u))
+      return SK_ERR_INVALID;
+    sk_schedule_info s;
+    int st = sk::describe(m, n, k, mode, 128, 0, 0, d->num_sms, &s);
+    if (st != SK_OK) return st;
+    const bool split = s.workspace_bytes > 0;
+    const size_t partial_bytes = static_cast<size_t>(s.grid) * sk::kBlkM * 128 * 4;
+    if (split && kNoAllocPartialsOffset + partial_bytes > kNoAllocScratchBytes)
+      return SK_ERR_INVALID;  // needs more scratch than the fixed maximum
+    CUtensorMap tma, tmb;
+    if ((st = encode_operand(&tma, A, ab_type, m, k, lda, sk::kBlkM)) != SK_OK) return st;
+    if ((st = encode_operand(&tmb, B, ab_type, n, k, ldb, 128)) != SK_OK) return st;
+    if (split) {
+      e = cudaMemsetAsync(scratch, 0, static_cast<size_t>(sk::kFlagBytes), stream);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    sk::SkArgs a{};
+    a.m = static_cast<int32_t>(m);
+    a.n = static_cast<int32_t>(n);
+    a.k = static_cast<int32_t>(k);
+    a.tiles_m = s.tiles_m;
+    a.tiles_n = s.tiles_n;
+    a.tiles = static_cast<int32_t>(s.tiles);
+    a.iters_per_tile = s.iters_per_tile;
+    a.group_m = s.raster_group;
+    a.sk_tiles = static_cast<int32_t>(s.sk_tiles);
+    a.grid = s.grid;
+    a.sk_q = static_cast<int32_t>(s.sk_iters / s.grid);
+    a.sk_r = static_cast<int32_t>(s.sk_iters % s.grid);
+    a.idesc = make_idesc(ab_type, 128);
+    a.C = C;
+    a.ldc = ldc;
+    a.c_vec = (ldc * static_cast<int64_t>(dtype_size(c_type))) % 16 == 0 ? 1 : 0;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.flags = split ? reinterpret_cast<uint32_t*>(scratch) : nullptr;
+    a.partials = split ? reinterpret_cast<float*>(scratch + kNoAllocPartialsOffset) : nullptr;
+    a.epoch = next_epoch();
+    a.err = err;
+    a.trace = nullptr;
+    a.trace_cap = 0;
+    a.debug_skip_signal = -1;
+    a.timeout_ns = kDefaultTimeoutNs;
+    e = sk::launch_bn128(c_type, tma, tmb, a, split, stream);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  if (device_status != nullptr) {
+    e = cudaMemcpyAsync(device_status, err, sizeof(int32_t), cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return SK_OK;
+}

@@ -77,11 +77,13 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(sk_schedule_info)]
     L.sk_grid_model.argtypes = [i64, i64, i64, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(i32)]
+    L.sk_gemm_noalloc.argtypes = [i64, i64, i64, i32, i32, vp, i64, vp, i64, vp, i64, f32, f32,
+                                  i32, vp, vp]
     L.sk_status_string.argtypes = [i32]
     L.sk_status_string.restype = ctypes.c_char_p
     for name in ("sk_plan", "sk_gemm", "sk_gemm_traced", "sk_last_error", "sk_plan_destroy",
                  "sk_plan_set", "sk_plan_get", "sk_plan_attach_workspace", "sk_plan_describe",
-                 "sk_grid_model"):
+                 "sk_grid_model", "sk_gemm_noalloc"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -227,6 +229,17 @@ def sk_gemm_traced(plan: Plan, A, B, C, alpha: float, beta: float, trace, stream
     n_ints = trace.numel() if hasattr(trace, "numel") else plan.get("trace_ints")
     _check(lib().sk_gemm_traced(plan.handle, _ptr(A), _ptr(B), _ptr(C), alpha, beta, _ptr(trace),
                                 n_ints, _stream(stream)), "sk_gemm_traced")
+
+
+def sk_gemm_noalloc(m: int, n: int, k: int, ab_type, c_type, A, lda: int, B, ldb: int, C,
+                    ldc: int, alpha: float = 1.0, beta: float = 0.0, mode="auto",
+                    device_status=None, stream=None) -> None:
+    """The allocation-free GEMM (no plan; fixed scratch inside the library)."""
+    _check(lib().sk_gemm_noalloc(m, n, k, _code(DTYPES, _dtype_name(ab_type), "dtype"),
+                                 _code(DTYPES, _dtype_name(c_type), "dtype"), _ptr(A), lda,
+                                 _ptr(B), ldb, _ptr(C), ldc, alpha, beta,
+                                 _code(MODES, mode, "mode"), _ptr(device_status),
+                                 _stream(stream)), "sk_gemm_noalloc")
 
 
 def sk_last_error(plan: Plan):

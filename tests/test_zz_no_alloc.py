@@ -1,0 +1,60 @@
+"""The allocation-free entry point sk_gemm_noalloc, for callers that cannot
+allocate device memory (code running under CUDA-graph stream capture,
+latency-critical serving loops, plugins handed buffers by a host framework).
+
+It must give the same results as the plan-based sk_gemm, within the tolerance
+the parity tests use (k * 2^-22 * |alpha| |A||B| + 2^-22 |beta C| + one output
+ulp), on two calls in a row -- the second call finds the first call's leftovers
+in the shared scratch.  This file is collected last on purpose.
+"""
+import pytest
+import torch
+
+from gemm_check import Problem, bound, check_bound
+from paper_2301_03598_gb300 import inputs
+from paper_2301_03598_gb300 import streamk as sk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("m,n,k,a_type,c_type,mode,alpha,beta", [
+    (384, 384, 4096, "f16", "f32", "sk", 1.0, 0.0),       # nine tiles split over many CTAs
+    (1000, 776, 1104, "bf16", "bf16", "hybrid", 1.5, 0.5),
+    (2432, 1024, 256, "bf16", "bf16", "auto", 1.0, 0.0),   # t >= SM count: two-tile hybrid
+])
+def test_noalloc_matches_sk_gemm_twice(m, n, k, a_type, c_type, mode, alpha, beta):
+    prob = Problem(m, n, k, a_type, c_type, "normal", seed=31, beta=beta)
+    A, B = prob.A.cuda(), prob.B.cuda()
+    # reference: the existing plan-based entry point, same schedule (BLK_N = 128)
+    plan = sk.sk_plan(m, n, k, a_type, a_type, c_type, "f32", "row", "col", "row", mode)
+    try:
+        plan.set("tile_n", 128)
+        C_ref = prob.Cin.clone().cuda()
+        sk.sk_gemm(plan, A, B, C_ref, alpha, beta)
+        assert sk.sk_last_error(plan)[0] == sk.SK_OK
+    finally:
+        plan.destroy()
+    C64, absAB = prob.oracle(alpha, beta)
+    tol = bound(k, alpha, beta, absAB, C64, inputs.widen(prob.Cin), c_type)
+    ref = inputs.widen(C_ref.cpu())
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    for call in range(2):
+        C = prob.Cin.clone().cuda()
+        sk.sk_gemm_noalloc(m, n, k, a_type, c_type, A, k, B, k, C, n, alpha, beta, mode,
+                           device_status=status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0, f"call {call}: device status {int(status.item())}"
+        got = inputs.widen(C.cpu())
+        check_bound(got, ref, tol, f"noalloc call {call} vs sk_gemm")
+        check_bound(got, C64, tol, f"noalloc call {call} vs oracle")
+
+
+def test_noalloc_rejects_bad_arguments():
+    A = torch.zeros((128, 64), dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros((128, 128), dtype=torch.float32, device="cuda")
+    with pytest.raises(sk.StreamKError) as e:
+        sk.sk_gemm_noalloc(128, 128, 64, "bf16", "f32", A, 60, A, 64, C, 128)   # lda < k
+    assert e.value.status == sk.SK_ERR_INVALID
+    with pytest.raises(sk.StreamKError) as e:
+        sk.sk_gemm_noalloc(128, 128, 64, "bf16", "f32", A.data_ptr() + 2, 64, A, 64, C, 128)
+    assert e.value.status == sk.SK_ERR_INVALID
