@@ -143,13 +143,16 @@ int sk_gemm(sk_plan_t plan, const void* A, const void* B, void* C, float alpha, 
             void* stream);
 
 /*
- * sk_gemm that also records the schedule each CTA executed: for CTA x, at
- * trace[x * (1 + cap * 9)] the number of records, followed by records of 9
- * int32 (cta, tile_idx, tm, tn, local_iter, local_iter_end, role,
- * peer_first, peer_last) where role 0 = whole tile stored, 1 = partials
- * spilled and signalled, 2 = owner that waited for peers peer_first ..
- * peer_last (-1 when none).  cap = SK_ATTR_TRACE_CAP; `trace` is a device
- * buffer of SK_ATTR_TRACE_INTS int32 owned by the caller.
+ * sk_gemm that also records the schedule each CTA executed, with device
+ * timestamps.  For CTA x the trace holds, at trace[x * (4 + cap * 16)], a
+ * header of 4 int32 (record count, reserved, then the global timer in ns at
+ * the CTA's start as a little-endian u64) followed by records of 16 int32:
+ * (cta, tile_idx, tm, tn, local_iter, local_iter_end, role, peer_first,
+ * peer_last, reserved) and three u64 global-timer stamps in ns (accumulator
+ * ready, fixup waits done, tile stored or partials signalled).  role 0 = whole
+ * tile stored, 1 = partials spilled and signalled, 2 = owner that waited for
+ * peers peer_first .. peer_last (-1 when none).  cap = SK_ATTR_TRACE_CAP;
+ * `trace` is a device buffer of SK_ATTR_TRACE_INTS int32 owned by the caller.
  */
 int sk_gemm_traced(sk_plan_t plan, const void* A, const void* B, void* C, float alpha,
                    float beta, int32_t* trace, int64_t trace_ints, void* stream);

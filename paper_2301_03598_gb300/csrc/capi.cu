@@ -104,7 +104,9 @@ struct sk_plan_s {
   // TMA descriptor cache
   const void* cached_a = nullptr;
   const void* cached_b = nullptr;
-  CUtensorMap tm_a{}, tm_b{};
+  const void* cached_c = nullptr;
+  CUtensorMap tm_a{}, tm_b{}, tm_c{};
+  bool c_tma = false;
   cudaStream_t last_stream = nullptr;
   bool launched = false;
 };
@@ -143,7 +145,7 @@ int replan(sk_plan_s* p) {
     p->ws_bytes = static_cast<size_t>(s.workspace_bytes);
   }
   p->info = s;
-  p->cached_a = p->cached_b = nullptr;
+  p->cached_a = p->cached_b = p->cached_c = nullptr;
   return SK_OK;
 }
 
@@ -161,6 +163,26 @@ int encode_operand(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows, in
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? SK_OK : SK_ERR_INVALID;
+}
+
+// Tensor map of the output for TMA stores: rows x cols (cols contiguous),
+// boxes of 32 rows x 128 bytes, 128-byte swizzle (the epilogue's staging
+// layout).  Returns false when the layout cannot be stored by TMA.
+bool encode_output(CUtensorMap* tm, void* ptr, int c_type, int64_t rows, int64_t cols, int64_t ld) {
+  auto fn = encode_fn();
+  const int64_t esz = static_cast<int64_t>(dtype_size(c_type));
+  if (fn == nullptr || (reinterpret_cast<uintptr_t>(ptr) & 15u) || (ld * esz) % 16 != 0) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * esz)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUtensorMapDataType dt = c_type == SK_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                           : c_type == SK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUresult r = fn(tm, dt, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 // tcgen05 kind::f16 instruction descriptor: FP32 accumulator, A/B format,
@@ -207,8 +229,9 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
       (reinterpret_cast<uintptr_t>(B) & 15u))
     return SK_ERR_INVALID;
   if (trace != nullptr) {
-    const int64_t need = static_cast<int64_t>(s.grid) * (1 + static_cast<int64_t>(s.max_segments) *
-                                                                 sk::kTraceFields);
+    const int64_t need = static_cast<int64_t>(s.grid) *
+                         (sk::kTraceHeaderInts + static_cast<int64_t>(s.max_segments) *
+                                                     sk::kTraceRecordInts);
     if (trace_ints < need) return SK_ERR_INVALID;
   }
 
@@ -230,6 +253,11 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
     p->cached_b = kb;
   }
 
+  if (C != p->cached_c) {
+    p->c_tma = encode_output(&p->tm_c, C, p->c_type, km, kn, p->ldc);
+    p->cached_c = C;
+  }
+
   sk::SkArgs a{};
   a.m = static_cast<int32_t>(km);
   a.n = static_cast<int32_t>(kn);
@@ -247,6 +275,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   a.C = C;
   a.ldc = p->ldc;
   a.c_vec = (p->ldc * static_cast<int64_t>(dtype_size(p->c_type))) % 16 == 0 ? 1 : 0;
+  a.c_tma = p->c_tma ? 1 : 0;
   a.alpha = alpha;
   a.beta = beta;
   const bool split = s.workspace_bytes > 0;
@@ -260,8 +289,8 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   a.timeout_ns = p->timeout_ns;
 
   cudaError_t e = s.tile_n == 256
-                      ? sk::launch_bn256(p->c_type, p->tm_a, p->tm_b, a, split, stream)
-                      : sk::launch_bn128(p->c_type, p->tm_a, p->tm_b, a, split, stream);
+                      ? sk::launch_bn256(p->c_type, p->tm_a, p->tm_b, p->tm_c, a, split, stream)
+                      : sk::launch_bn128(p->c_type, p->tm_a, p->tm_b, p->tm_c, a, split, stream);
   return cuda_status(e);
 }
 
@@ -434,6 +463,7 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
     case SK_ATTR_LDC:
       if (v < min_ld_c) return SK_ERR_INVALID;
       p->ldc = v;
+      p->cached_c = nullptr;
       return SK_OK;
     case SK_ATTR_DEBUG_SKIP_SIGNAL:
       if (v < -1 || v >= p->num_sms) return SK_ERR_INVALID;
@@ -469,7 +499,8 @@ int sk_plan_get(sk_plan_t p, int attr, int64_t* v) {
     case SK_ATTR_NUM_SMS: *v = p->num_sms; return SK_OK;
     case SK_ATTR_TRACE_CAP: *v = s.max_segments; return SK_OK;
     case SK_ATTR_TRACE_INTS:
-      *v = static_cast<int64_t>(s.grid) * (1 + static_cast<int64_t>(s.max_segments) * sk::kTraceFields);
+      *v = static_cast<int64_t>(s.grid) *
+           (sk::kTraceHeaderInts + static_cast<int64_t>(s.max_segments) * sk::kTraceRecordInts);
       return SK_OK;
     default:
       return SK_ERR_INVALID;
@@ -603,9 +634,10 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     const size_t partial_bytes = static_cast<size_t>(s.grid) * sk::kBlkM * 128 * 4;
     if (split && kNoAllocPartialsOffset + partial_bytes > kNoAllocScratchBytes)
       return SK_ERR_INVALID;  // needs more scratch than the fixed maximum
-    CUtensorMap tma, tmb;
+    CUtensorMap tma, tmb, tmc;
     if ((st = encode_operand(&tma, A, ab_type, m, k, lda, sk::kBlkM)) != SK_OK) return st;
     if ((st = encode_operand(&tmb, B, ab_type, n, k, ldb, 128)) != SK_OK) return st;
+    const bool c_tma = encode_output(&tmc, C, c_type, m, n, ldc);
     if (split) {
       e = cudaMemsetAsync(scratch, 0, static_cast<size_t>(sk::kFlagBytes), stream);
       if (e != cudaSuccess) return cuda_status(e);
@@ -627,6 +659,7 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     a.C = C;
     a.ldc = ldc;
     a.c_vec = (ldc * static_cast<int64_t>(dtype_size(c_type))) % 16 == 0 ? 1 : 0;
+    a.c_tma = c_tma ? 1 : 0;
     a.alpha = alpha;
     a.beta = beta;
     a.flags = split ? reinterpret_cast<uint32_t*>(scratch) : nullptr;
@@ -637,7 +670,7 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     a.trace_cap = 0;
     a.debug_skip_signal = -1;
     a.timeout_ns = kDefaultTimeoutNs;
-    e = sk::launch_bn128(c_type, tma, tmb, a, split, stream);
+    e = sk::launch_bn128(c_type, tma, tmb, tmc, a, split, stream);
   }
   if (e != cudaSuccess) return cuda_status(e);
   if (device_status != nullptr) {

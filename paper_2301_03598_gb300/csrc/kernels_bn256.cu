@@ -9,7 +9,8 @@
 namespace sk {
 
 template <typename TC>
-static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb, const SkArgs& args,
+static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
+                              const CUtensorMap& tc, const SkArgs& args,
                               bool cooperative, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(args.grid));
@@ -21,18 +22,19 @@ static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb, cons
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = cooperative ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<256, TC>, ta, tb, args);
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<256, TC>, ta, tb, tc, args);
 }
 
 cudaError_t launch_bn256(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
-                         const SkArgs& args, bool cooperative, cudaStream_t stream) {
+                         const CUtensorMap& tc, const SkArgs& args, bool cooperative,
+                         cudaStream_t stream) {
   switch (c_dtype) {
     case SK_F32:
-      return launch_one<float>(ta, tb, args, cooperative, stream);
+      return launch_one<float>(ta, tb, tc, args, cooperative, stream);
     case SK_BF16:
-      return launch_one<__nv_bfloat16>(ta, tb, args, cooperative, stream);
+      return launch_one<__nv_bfloat16>(ta, tb, tc, args, cooperative, stream);
     case SK_F16:
-      return launch_one<__half>(ta, tb, args, cooperative, stream);
+      return launch_one<__half>(ta, tb, tc, args, cooperative, stream);
     default:
       return cudaErrorInvalidValue;
   }

@@ -10,9 +10,11 @@ namespace sk {
 // c_dtype: SK_F32 / SK_BF16 / SK_F16.  cooperative: CTAs wait on one another,
 // so the launch must guarantee co-residency.
 cudaError_t launch_bn128(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
-                         const SkArgs& args, bool cooperative, cudaStream_t stream);
+                         const CUtensorMap& tc, const SkArgs& args, bool cooperative,
+                         cudaStream_t stream);
 cudaError_t launch_bn256(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
-                         const SkArgs& args, bool cooperative, cudaStream_t stream);
+                         const CUtensorMap& tc, const SkArgs& args, bool cooperative,
+                         cudaStream_t stream);
 // Dynamic shared memory of one CTA; also sets the kernels' opt-in limit.
 cudaError_t prepare_bn128(size_t* smem_bytes);
 cudaError_t prepare_bn256(size_t* smem_bytes);

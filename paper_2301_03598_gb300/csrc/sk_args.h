@@ -14,6 +14,13 @@ constexpr int kRolePartial = 1;  // !tile_started: spill FP32 partials, then Sig
 constexpr int kRoleOwner = 2;    // tile_started && !tile_ended: Wait peers, fix up, store
 
 constexpr int kTraceFields = 9;  // cta, tile, tm, tn, kb0, kb1, role, peer_first, peer_last
+// Trace layout per CTA: a header of kTraceHeaderInts int32 (record count,
+// reserved, u64 global-timer ns at kernel start) then records of
+// kTraceRecordInts int32: the kTraceFields schedule fields, one reserved, and
+// three u64 global-timer stamps (accumulator ready, fixup waits done, tile
+// stored or partials signalled).
+constexpr int kTraceHeaderInts = 4;
+constexpr int kTraceRecordInts = 16;
 
 // Device status codes written to the error word.
 constexpr int kDevOk = 0;
@@ -38,6 +45,7 @@ struct SkArgs {
   void* C;
   int64_t ldc;  // elements
   int32_t c_vec;  // rows of C start 16-byte aligned: 16-byte vector loads/stores allowed
+  int32_t c_tma;  // C is stored with TMA tensor stores (tensor map valid)
   float alpha, beta;
   // fixup workspace: grid slots of BLK_M x BLK_N FP32, plus one flag per slot
   float* partials;
@@ -45,7 +53,7 @@ struct SkArgs {
   uint32_t epoch;
   // status, tracing, bounded waits
   int32_t* err;         // err[0]: first device status, err[1]: CTA, err[2]: where
-  int32_t* trace;       // nullptr: off; else grid x (1 + trace_cap * kTraceFields)
+  int32_t* trace;       // nullptr: off; else grid x (header + trace_cap records)
   int32_t trace_cap;    // records per CTA
   int32_t debug_skip_signal;  // CTA index that withholds its Signal (tests), -1 off
   uint64_t timeout_ns;

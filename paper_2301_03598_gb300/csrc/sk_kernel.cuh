@@ -36,17 +36,30 @@ constexpr int kEpiWarp0 = 2;
 constexpr int kEpiThreads = 128;
 constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 
+#ifndef SK_STAGES_BN128
+#define SK_STAGES_BN128 6
+#endif
+#ifndef SK_STAGES_BN256
+#define SK_STAGES_BN256 4
+#endif
+
 template <int BN>
 struct Cfg {
-  static constexpr int kStages = (BN == 256) ? 4 : 6;
+  static constexpr int kStages = (BN == 256) ? SK_STAGES_BN256 : SK_STAGES_BN128;
   static constexpr int kABytes = kBlkM * kBlkK * 2;
   static constexpr int kBBytes = BN * kBlkK * 2;
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kTmemCols = 2 * BN;  // two FP32 accumulators of BN columns
-  static constexpr int kBarOffset = kStages * kStageBytes;
+  // Output staging for TMA stores: per epilogue warp two buffers of 32 rows x
+  // 128 B, 128-byte swizzled (1 KiB aligned).
+  static constexpr int kStagingOffset = kStages * kStageBytes;
+  static constexpr int kStagingBytesPerWarp = 2 * 32 * 128;
+  static constexpr int kStagingBytes = 4 * kStagingBytesPerWarp;
+  static constexpr int kBarOffset = kStagingOffset + kStagingBytes;
   static constexpr int kNumBars = 2 * kStages + 5;
   static constexpr int kSmemBytes = kBarOffset + 256 + 1024;  // + barriers, + 1 KiB alignment
   static_assert(kNumBars * 8 + 8 <= 256, "barrier area");
+  static_assert(kSmemBytes <= 232448, "shared memory per CTA");
 };
 
 // Where a bounded wait gave up (err[2]).
@@ -269,10 +282,48 @@ __device__ __forceinline__ void store_row32(const SkArgs& a, int grow, int gcol,
   }
 }
 
+// v[j] += beta * C[row, col + j] for the columns of this chunk inside the matrix.
+template <typename TC>
+__device__ __forceinline__ void add_beta_c(const SkArgs& a, int grow, int gcol, float (&v)[32]) {
+  if (grow >= a.m) return;
+  const TC* crow = reinterpret_cast<const TC*>(a.C) + static_cast<int64_t>(grow) * a.ldc + gcol;
+  const float beta = a.beta;
+  if (a.c_vec && gcol + 32 <= a.n) {
+    if constexpr (sizeof(TC) == 4) {
+      const float4* p = reinterpret_cast<const float4*>(crow);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 c = p[j];
+        v[4 * j] = fmaf(beta, c.x, v[4 * j]);
+        v[4 * j + 1] = fmaf(beta, c.y, v[4 * j + 1]);
+        v[4 * j + 2] = fmaf(beta, c.z, v[4 * j + 2]);
+        v[4 * j + 3] = fmaf(beta, c.w, v[4 * j + 3]);
+      }
+    } else {
+      const uint4* p = reinterpret_cast<const uint4*>(crow);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint4 c = p[j];
+        const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = unpack2(cw[e], static_cast<TC*>(nullptr));
+          v[8 * j + 2 * e] = fmaf(beta, f.x, v[8 * j + 2 * e]);
+          v[8 * j + 2 * e + 1] = fmaf(beta, f.y, v[8 * j + 2 * e + 1]);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (gcol + j < a.n) v[j] = fmaf(beta, to_f32<TC>(crow[j]), v[j]);
+  }
+}
+
 template <int BN, typename TC>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ SkArgs a) {
+                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ SkArgs a) {
   using C_ = Cfg<BN>;
   constexpr int S = C_::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -311,6 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0 && lane == 0) {
     tma_prefetch_desc(&tmA);
     tma_prefetch_desc(&tmB);
+    if (a.c_tma) tma_prefetch_desc(&tmC);
   }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), C_::kTmemCols);
@@ -426,6 +478,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     int tile, kb0, kb1, acc = 0, nrec = 0;
     uint32_t acc_phase = 0;
     float* const my_slot = a.partials + static_cast<size_t>(x) * (kBlkM * BN);
+    const uint32_t staging = base + static_cast<uint32_t>(C_::kStagingOffset +
+                                                         (warp - kEpiWarp0) * C_::kStagingBytesPerWarp);
+    int nstores = 0;  // TMA stores this warp has issued
+    const bool tracer = a.trace != nullptr && warp == kEpiWarp0 && lane == 0;
+    int32_t* const tb =
+        a.trace + static_cast<size_t>(x) * (kTraceHeaderInts + a.trace_cap * kTraceRecordInts);
+    if (tracer) {
+      const uint64_t t = globaltimer_ns();
+      tb[0] = 0;
+      tb[1] = 0;
+      tb[2] = static_cast<int32_t>(t & 0xffffffffu);
+      tb[3] = static_cast<int32_t>(t >> 32);
+    }
     while (w.next(a, tile, kb0, kb1)) {
       const bool started = kb0 == 0;
       const bool ended = kb1 == ipt;
@@ -441,19 +506,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool fail = !wait_bar(accf_bar(acc), acc_phase, abort_flag, a, kAtEpiAccFull);
       if (epi_any(fail)) break;
       tc_fence_after();
+      const uint64_t t_acc = tracer ? globaltimer_ns() : 0;
       if (role == kRoleOwner) {
         for (int y = peer_first; y <= peer_last && !fail; ++y) fail = !wait_flag(&a.flags[y], abort_flag, a);
         if (epi_any(fail)) break;
       }
+      const uint64_t t_fix = tracer ? globaltimer_ns() : 0;
 
       const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(acc * BN);
       const int grow = tm * kBlkM + row;
+      const int col0 = tn * BN;
+      // Only the chunks holding columns < n are read, spilled, fixed up and stored.
+      const int nchunks = (min(BN, a.n - col0) + 31) / 32;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = 0; c < nchunks; ++c) {
         uint32_t r[32];
         tmem_ld_x32(tbase + static_cast<uint32_t>(c * 32), r);
         tmem_wait_ld();
-        if (c == BN / 32 - 1) {
+        if (c == nchunks - 1) {
           // all of this warp's TMEM reads are done: hand the buffer back to the MMA warp
           tc_fence_before();
           __syncwarp();
@@ -469,23 +539,69 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int j = 0; j < 8; ++j)
             __stcg(dst + j * kBlkM, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
-        } else {
-          if (role == kRoleOwner) {
-            for (int y = peer_first; y <= peer_last; ++y) {
-              const float4* src = reinterpret_cast<const float4*>(
-                                      a.partials + static_cast<size_t>(y) * (kBlkM * BN)) +
-                                  (c * 8) * kBlkM + row;
+          continue;
+        }
+        if (role == kRoleOwner) {
+          for (int y = peer_first; y <= peer_last; ++y) {
+            const float4* src = reinterpret_cast<const float4*>(
+                                    a.partials + static_cast<size_t>(y) * (kBlkM * BN)) +
+                                (c * 8) * kBlkM + row;
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const float4 p = __ldcg(src + j * kBlkM);
-                v[4 * j] += p.x;
-                v[4 * j + 1] += p.y;
-                v[4 * j + 2] += p.z;
-                v[4 * j + 3] += p.w;
-              }
+            for (int j = 0; j < 8; ++j) {
+              const float4 p = __ldcg(src + j * kBlkM);
+              v[4 * j] += p.x;
+              v[4 * j + 1] += p.y;
+              v[4 * j + 2] += p.z;
+              v[4 * j + 3] += p.w;
             }
           }
-          store_row32<TC>(a, grow, tn * BN + c * 32, v);
+        }
+        if (!a.c_tma) {
+          store_row32<TC>(a, grow, col0 + c * 32, v);
+          continue;
+        }
+        // StoreTile through a swizzled staging row and a TMA tensor store of
+        // 32 rows x 128 B (32 FP32 or 64 16-bit columns).
+        const float alpha = a.alpha, beta = a.beta;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] *= alpha;
+        if (beta != 0.0f) add_beta_c<TC>(a, grow, col0 + c * 32, v);
+        constexpr int kChunksPerStore = (sizeof(TC) == 4) ? 1 : 2;
+        const int half = (kChunksPerStore == 2) ? (c & 1) : 0;
+        const int buf = nstores & 1;  // alternate buffers across stores (and tiles)
+        const uint32_t srow = staging + static_cast<uint32_t>(buf * 4096 + lane * 128);
+        if (half == 0) {
+          // the store that last used this buffer has finished reading it
+          if (lane == 0) bulk_wait_group_read<1>();
+          __syncwarp();
+        }
+        if constexpr (sizeof(TC) == 4) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)), __float_as_uint(v[4 * j]),
+                         __float_as_uint(v[4 * j + 1]), __float_as_uint(v[4 * j + 2]),
+                         __float_as_uint(v[4 * j + 3]));
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = half * 4 + jj;
+            st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)),
+                         pack2(v[8 * jj], v[8 * jj + 1], static_cast<TC*>(nullptr)),
+                         pack2(v[8 * jj + 2], v[8 * jj + 3], static_cast<TC*>(nullptr)),
+                         pack2(v[8 * jj + 4], v[8 * jj + 5], static_cast<TC*>(nullptr)),
+                         pack2(v[8 * jj + 6], v[8 * jj + 7], static_cast<TC*>(nullptr)));
+          }
+        }
+        if (half == kChunksPerStore - 1 || c == nchunks - 1) {
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&tmC, staging + static_cast<uint32_t>(buf * 4096),
+                         col0 + (c / kChunksPerStore) * (32 * kChunksPerStore),
+                         tm * kBlkM + quarter * 32);
+            bulk_commit_group();
+          }
+          ++nstores;
         }
       }
       if (role == kRolePartial) {
@@ -500,10 +616,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // All epilogue threads passed their Waits before the last vote.
         for (int y = peer_first; y <= peer_last; ++y) a.flags[y] = 0u;
       }
-      if (a.trace != nullptr && warp == kEpiWarp0 && lane == 0) {
-        int32_t* tb = a.trace + static_cast<size_t>(x) * (1 + a.trace_cap * kTraceFields);
+      if (tracer) {
+        const uint64_t t_done = globaltimer_ns();
         if (nrec < a.trace_cap) {
-          int32_t* rec = tb + 1 + nrec * kTraceFields;
+          int32_t* rec = tb + kTraceHeaderInts + nrec * kTraceRecordInts;
           rec[0] = x;
           rec[1] = tile;
           rec[2] = tm;
@@ -513,6 +629,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           rec[6] = role;
           rec[7] = peer_first;
           rec[8] = peer_last;
+          rec[9] = 0;
+          const uint64_t ts[3] = {t_acc, t_fix, t_done};
+          for (int i = 0; i < 3; ++i) {
+            rec[10 + 2 * i] = static_cast<int32_t>(ts[i] & 0xffffffffu);
+            rec[11 + 2 * i] = static_cast<int32_t>(ts[i] >> 32);
+          }
         }
         ++nrec;
         tb[0] = nrec;
@@ -520,6 +642,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
+    // The output tiles must be written before the kernel ends.
+    if (lane == 0) bulk_wait_group<0>();
+    __syncwarp();
   }
 
   __syncwarp();  // reconverge the producer / MMA warps (one lane worked)

@@ -28,6 +28,8 @@ ATTRS = {
     "workspace_bytes": 29, "num_sms": 30, "trace_ints": 31, "trace_cap": 32,
 }
 TRACE_FIELDS = 9
+TRACE_HEADER = 4
+TRACE_RECORD = 16
 
 
 class StreamKError(RuntimeError):
@@ -264,17 +266,29 @@ def sk_grid_model(m: int, n: int, k: int, bm: int, bn: int, bk: int, p: int, coe
     return g.value
 
 
-def decode_trace(trace_host, grid: int, cap: int):
-    """Turn a copied-back trace buffer into records (tuples of 9 ints)."""
+def decode_trace(trace_host, grid: int, cap: int, with_times: bool = False):
+    """Turn a copied-back trace buffer into records: tuples of the 9 schedule
+    fields, or (fields, (t_acc, t_fix, t_done), t_cta_start) with ``with_times``
+    (global-timer nanoseconds)."""
     vals = [int(v) for v in trace_host]
-    stride = 1 + cap * TRACE_FIELDS
+    stride = TRACE_HEADER + cap * TRACE_RECORD
+
+    def u64(lo, hi):
+        return (lo & 0xffffffff) | ((hi & 0xffffffff) << 32)
+
     out = []
     for x in range(grid):
         base = x * stride
         count = vals[base]
+        t0 = u64(vals[base + 2], vals[base + 3])
         if count > cap:
             raise ValueError(f"CTA {x} recorded {count} segments, capacity {cap}")
         for r in range(count):
-            o = base + 1 + r * TRACE_FIELDS
-            out.append(tuple(vals[o:o + TRACE_FIELDS]))
+            o = base + TRACE_HEADER + r * TRACE_RECORD
+            fields = tuple(vals[o:o + TRACE_FIELDS])
+            if with_times:
+                ts = tuple(u64(vals[o + 10 + 2 * i], vals[o + 11 + 2 * i]) for i in range(3))
+                out.append((fields, ts, t0))
+            else:
+                out.append(fields)
     return out

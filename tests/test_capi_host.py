@@ -63,8 +63,12 @@ def test_hybrid_regions_match_oracle(t_m, t_n, ipt, p):
 
 def test_describe_config_shapes():
     d = sk.sk_plan_describe(384, 384, 4096)
-    assert (d["tile_n"], d["tiles"], d["iters_per_tile"], d["mode_name"]) == (128, 9, 64, "sk")
-    assert 9 <= d["grid"] <= 148 and d["workspace_bytes"] > 0
+    assert (d["tile_n"], d["tiles"], d["iters_per_tile"], d["mode_name"]) == (256, 6, 64, "sk")
+    assert 6 <= d["grid"] <= 148 and d["workspace_bytes"] > 0
+    d = sk.sk_plan_describe(384, 384, 4096, tile_n=128)
+    assert (d["tile_n"], d["tiles"]) == (128, 9)
+    d = sk.sk_plan_describe(4096, 128, 4096)
+    assert d["tile_n"] == 128
     d = sk.sk_plan_describe(8192, 8192, 8192)
     assert (d["tile_n"], d["tiles"], d["mode_name"]) == (256, 2048, "hybrid")
     assert d["sk_tiles"] == 2048 % 148 + 148 and d["dp_tiles"] % 148 == 0
