@@ -48,14 +48,13 @@ CPU_FLOPS_PER_SHAPE = 2e9     # oracle work per sampled shape
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--count", type=int, default=None, help="shapes in the sweep (default 2000)")
     ap.add_argument("--variants", default="auto,dp,sk")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-graph", action="store_true")
     return ap.parse_args()
 
 
@@ -129,41 +128,56 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- workload
+def reps_for(m, n, k):
+    """Back-to-back repetitions of one shape inside a step: enough that the
+    ~4 us cost of the graph's timing events is spread over them."""
+    fl = 2.0 * m * n * k
+    return 16 if fl < 1e9 else 8 if fl < 1e10 else 4 if fl < 1e11 else 2
+
+
 class Sweep:
-    """Device-resident inputs and outputs of the shape sweep."""
+    """Device-resident inputs and outputs of the shape sweep.  Every GEMM
+    instance (shape, repetition) reads its own slices of a 4 GiB input pool,
+    allocated in order with wrap-around, so consecutive GEMMs never share
+    operands and the pool is far larger than L2."""
 
     def __init__(self, shapes, device, seed):
         import torch
         from paper_2301_03598_gb300 import inputs
         self.shapes = shapes
         self.device = device
+        self.reps = [reps_for(*s) for s in shapes]
         self.pool = inputs.device_pool(POOL_ELEMS, "bf16", "normal", seed, device)
         self.out = torch.empty(OUT_ELEMS, dtype=torch.bfloat16, device=device)
-        self.a_off, self.b_off, self.c_off = [], [], []
+        self.inst = []          # per shape: list of (a_off, b_off, c_off)
         cur = cur_c = 0
-        for (m, n, k) in shapes:
-            need = _al(m * k) + _al(n * k)
-            if cur + need > POOL_ELEMS:
-                cur = 0
-            self.a_off.append(cur)
-            self.b_off.append(cur + _al(m * k))
-            cur += need
-            if cur_c + _al(m * n) > OUT_ELEMS:
-                cur_c = 0
-            self.c_off.append(cur_c)
-            cur_c += _al(m * n)
+        for (m, n, k), R in zip(shapes, self.reps):
+            lst = []
+            for _ in range(R):
+                need = _al(m * k) + _al(n * k)
+                if cur + need > POOL_ELEMS:
+                    cur = 0
+                if cur_c + _al(m * n) > OUT_ELEMS:
+                    cur_c = 0
+                lst.append((cur, cur + _al(m * k), cur_c))
+                cur += need
+                cur_c += _al(m * n)
+            self.inst.append(lst)
 
-    def A(self, i):
+    def A(self, i, r=0):
         m, n, k = self.shapes[i]
-        return self.pool[self.a_off[i]:self.a_off[i] + m * k]
+        o = self.inst[i][r][0]
+        return self.pool[o:o + m * k]
 
-    def B(self, i):
+    def B(self, i, r=0):
         m, n, k = self.shapes[i]
-        return self.pool[self.b_off[i]:self.b_off[i] + n * k]
+        o = self.inst[i][r][1]
+        return self.pool[o:o + n * k]
 
-    def C(self, i):
+    def C(self, i, r=0):
         m, n, k = self.shapes[i]
-        return self.out[self.c_off[i]:self.c_off[i] + m * n]
+        o = self.inst[i][r][2]
+        return self.out[o:o + m * n]
 
 
 def _al(x):
@@ -184,80 +198,70 @@ def make_plans(shapes, mode, ws_holder):
     return plans
 
 
-def capture_step(plans, sweep, with_events, stream):
-    """A CUDA graph running every GEMM of the sweep once (events between GEMMs)."""
+def capture_step(plans, sweep, stream):
+    """A CUDA graph of one step: every shape of the sweep, each run R times
+    back to back on fresh operands, with a timing event between shapes."""
     import torch
     from paper_2301_03598_gb300 import streamk as sk
     g = torch.cuda.CUDAGraph()
-    evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(plans) + 1)] \
-        if with_events else None
+    evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(plans) + 1)]
     with torch.cuda.graph(g, stream=stream):
-        if evs:
-            evs[0].record()
+        evs[0].record()
         for i, p in enumerate(plans):
-            sk.sk_gemm(p, sweep.A(i), sweep.B(i), sweep.C(i), 1.0, 0.0)
-            if evs:
-                evs[i + 1].record()
+            for r in range(sweep.reps[i]):
+                sk.sk_gemm(p, sweep.A(i, r), sweep.B(i, r), sweep.C(i, r), 1.0, 0.0)
+            evs[i + 1].record()
     return g, evs
 
 
-def run_variant(plans, sweep, steps, warmup, use_graph, barrier, sampler=None):
-    """Returns (total_ms, per_gemm_ms[steps][n])."""
+def event_overhead_us(stream, count=200):
+    """Device time of one timing-event node in a graph (measured, reported)."""
+    import torch
+    g = torch.cuda.CUDAGraph()
+    evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(count + 1)]
+    with torch.cuda.graph(g, stream=stream):
+        for e in evs:
+            e.record()
+    g.replay()
+    torch.cuda.synchronize()
+    return evs[0].elapsed_time(evs[-1]) * 1e3 / count
+
+
+def run_variant(plans, sweep, steps, warmup, barrier, sampler=None):
+    """Returns (total_ms, per-step device ms, per_gemm_ms[steps][n])."""
     import torch
     from paper_2301_03598_gb300 import streamk as sk
     n = len(plans)
-    if use_graph:
-        stream = torch.cuda.Stream()
-        g_warm, _ = capture_step(plans, sweep, False, stream)
-        timed = [capture_step(plans, sweep, True, stream) for _ in range(steps)]
-        for _ in range(warmup):
-            g_warm.replay()
-        torch.cuda.synchronize()
-        for p in plans:
-            st, dev = sk.sk_last_error(p)
-            if st != sk.SK_OK:
-                raise RuntimeError(f"device status {st}/{dev} during warm-up")
-        barrier()
-        if sampler:
-            sampler.start()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record()
-        for g, _ in timed:
-            g.replay()
-        t1.record()
-        torch.cuda.synchronize()
-        barrier()
-        clocks = sampler.stop() if sampler else None
-        per = [[evs[i].elapsed_time(evs[i + 1]) for i in range(n)] for _, evs in timed]
-    else:
-        stream = torch.cuda.current_stream()
-        for _ in range(warmup):
-            for i, p in enumerate(plans):
-                sk.sk_gemm(p, sweep.A(i), sweep.B(i), sweep.C(i), 1.0, 0.0)
-        torch.cuda.synchronize()
-        barrier()
-        if sampler:
-            sampler.start()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n + 1)] for _ in range(steps)]
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record()
-        for s in range(steps):
-            evs[s][0].record()
-            for i, p in enumerate(plans):
-                sk.sk_gemm(p, sweep.A(i), sweep.B(i), sweep.C(i), 1.0, 0.0)
-                evs[s][i + 1].record()
-        t1.record()
-        torch.cuda.synchronize()
-        barrier()
-        clocks = sampler.stop() if sampler else None
-        per = [[e[i].elapsed_time(e[i + 1]) for i in range(n)] for e in evs]
+    stream = torch.cuda.Stream()
+    g, evs = capture_step(plans, sweep, stream)
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    for p in plans:
+        st, dev = sk.sk_last_error(p)
+        if st != sk.SK_OK:
+            raise RuntimeError(f"device status {st}/{dev} during warm-up")
+    barrier()
+    if sampler:
+        sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    per, step_ms = [], []
+    t0.record()
+    for _ in range(steps):
+        g.replay()
+        torch.cuda.synchronize()   # read this step's per-shape events
+        per.append([evs[i].elapsed_time(evs[i + 1]) / sweep.reps[i] for i in range(n)])
+        step_ms.append(evs[0].elapsed_time(evs[-1]))
+    t1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
     for p in plans:
         st, dev = sk.sk_last_error(p)
         if st != sk.SK_OK:
             raise RuntimeError(f"device status {st}/{dev} in the timed region")
-    return t0.elapsed_time(t1), np.asarray(per), clocks
+    return t0.elapsed_time(t1), step_ms, np.asarray(per), clocks
 
 
 def run_e2e(plans, sweep, steps, warmup, barrier):
@@ -277,8 +281,9 @@ def run_e2e(plans, sweep, steps, warmup, barrier):
 
     def one(i):
         m, n_, k = shapes[i]
-        a_h = host_pool[sweep.a_off[i]:sweep.a_off[i] + m * k]
-        b_h = host_pool[sweep.b_off[i]:sweep.b_off[i] + n_ * k]
+        ao, bo, _ = sweep.inst[i][0]
+        a_h = host_pool[ao:ao + m * k]
+        b_h = host_pool[bo:bo + n_ * k]
         a_d = dev_in[:m * k]
         b_d = dev_in[_al(m * k):_al(m * k) + n_ * k]
         a_d.copy_(a_h, non_blocking=True)
@@ -473,11 +478,6 @@ def ours_arm(args):
     flops = np.array([2.0 * m * n * k for (m, n, k) in shapes])
     sweep = Sweep(shapes, torch.device("cuda", torch.cuda.current_device()),
                   seed=inputs.SWEEP_SEED + rank)
-    use_graph = not args.no_graph
-    try:
-        torch.cuda.Event(enable_timing=True, external=True)
-    except TypeError:       # torch without event record nodes in graphs
-        use_graph = False
     ws = {}
     variants = [v for v in args.variants.split(",") if v]
     results = {}
@@ -485,21 +485,22 @@ def ours_arm(args):
     for v in variants:
         plans = make_plans(shapes, v, ws)
         sampler = ClockSampler(torch.cuda.current_device()) if v == variants[0] else None
-        total_ms, per, clocks = run_variant(plans, sweep, args.steps, args.warmup, use_graph,
-                                            barrier, sampler)
+        total_ms, step_ms, per, clocks = run_variant(plans, sweep, args.steps, args.warmup,
+                                                     barrier, sampler)
         med = np.median(per, axis=0)                         # ms per GEMM
         tflops = flops / (med * 1e-3) / 1e12
         results[v] = {
             "geomean_tflops": geomean(tflops), "min_tflops": float(tflops.min()),
             "max_tflops": float(tflops.max()),
             "aggregate_tflops": float(flops.sum() / (med.sum() * 1e-3) / 1e12),
-            "ms_per_step": total_ms / args.steps,
+            "ms_per_step": float(np.mean(step_ms)),
             "p50_us": float(np.percentile(med * 1e3, 50)),
             "p99_us": float(np.percentile(med * 1e3, 99)),
             "_per_shape": tflops, "_med": med, "_plans": plans, "_clocks": clocks,
         }
         if headline is None:
             headline = v
+    ev_us = event_overhead_us(torch.cuda.Stream())
     H = results[headline]
     plans = H["_plans"]
     peaks = load_peaks()
@@ -522,6 +523,8 @@ def ours_arm(args):
         e_ms, e_per, h2d, d2h = run_e2e(plans, sweep, args.steps, args.warmup, barrier)
         e_med = np.median(e_per, axis=0)
         e2e = {"value": geomean(flops / (e_med * 1e-3) / 1e12) * world, "unit": UNIT,
+               "timing": "one graph per step: per GEMM H2D of A and B from pinned host memory, "
+                         "sk_gemm, D2H of C, a timing event between GEMMs (R = 1)",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": e_ms / args.steps,
                "aggregate_tflops": float(flops.sum() / (e_med.sum() * 1e-3) / 1e12)}
@@ -546,8 +549,10 @@ def ours_arm(args):
             "parallelism": f"replicas x{world}",
             "l2": "inputs larger than L2: a 4 GiB input pool read in order, consecutive GEMMs "
                   "touch disjoint regions",
-            "timing": "CUDA graph per step, CUDA events between GEMMs" if use_graph
-                      else "stream launches, CUDA events between GEMMs",
+            "timing": "one CUDA graph per step; each shape runs R times back to back on fresh "
+                      "operands (R = 16/8/4/2 by size) between two timing events; per-GEMM "
+                      "time = interval / R",
+            "event_node_us": ev_us,
         },
         "pct_of_peak": value / world / peak,
         "variants": {v: {kk: vv for kk, vv in r.items() if not kk.startswith("_")}
@@ -556,7 +561,7 @@ def ours_arm(args):
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "kernel": "sk::sk_gemm_kernel", "peak_kind":
                      f"bf16 sustained ({peaks['source']})"},
-        "gpu_launches": int(len(shapes) * args.steps),
+        "gpu_launches": int(sum(sweep.reps) * args.steps),
         "e2e": e2e, "cpu_baseline": cpu, "parity": parity,
         "clocks": H["_clocks"],
     }

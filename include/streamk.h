@@ -79,6 +79,10 @@ typedef enum {
   SK_ATTR_DEBUG_SKIP_SIGNAL = 8, /* set: a CTA index that withholds its fixup Signal, so the
                                     owner's bounded Wait must expire (failure-detection
                                     tests); -1 = off */
+  SK_ATTR_PDL = 9,           /* set/get: 1 (default) = launch with programmatic dependent
+                                launch, so the kernel's set-up overlaps the previous kernel
+                                in the stream; it touches global memory only after that
+                                kernel has completed.  0 = plain stream serialisation. */
   SK_ATTR_MODE = 20,         /* get: resolved sk_mode */
   SK_ATTR_TILE_M = 21,       /* get: BLK_M (128) */
   SK_ATTR_TILE_K = 22,       /* get: BLK_K (64) */

@@ -101,6 +101,7 @@ struct sk_plan_s {
   // knobs
   uint64_t timeout_ns = kDefaultTimeoutNs;
   int debug_skip_signal = -1;
+  bool pdl = true;
   // TMA descriptor cache
   const void* cached_a = nullptr;
   const void* cached_b = nullptr;
@@ -287,6 +288,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   a.trace_cap = s.max_segments;
   a.debug_skip_signal = p->debug_skip_signal;
   a.timeout_ns = p->timeout_ns;
+  a.pdl = p->pdl ? 1 : 0;
 
   cudaError_t e = s.tile_n == 256
                       ? sk::launch_bn256(p->c_type, p->tm_a, p->tm_b, p->tm_c, a, split, stream)
@@ -469,6 +471,10 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
       if (v < -1 || v >= p->num_sms) return SK_ERR_INVALID;
       p->debug_skip_signal = static_cast<int>(v);
       return SK_OK;
+    case SK_ATTR_PDL:
+      if (v != 0 && v != 1) return SK_ERR_INVALID;
+      p->pdl = v != 0;
+      return SK_OK;
     default:
       return SK_ERR_INVALID;
   }
@@ -486,6 +492,7 @@ int sk_plan_get(sk_plan_t p, int attr, int64_t* v) {
     case SK_ATTR_LDB: *v = p->ldb; return SK_OK;
     case SK_ATTR_LDC: *v = p->ldc; return SK_OK;
     case SK_ATTR_DEBUG_SKIP_SIGNAL: *v = p->debug_skip_signal; return SK_OK;
+    case SK_ATTR_PDL: *v = p->pdl ? 1 : 0; return SK_OK;
     case SK_ATTR_MODE: *v = s.mode; return SK_OK;
     case SK_ATTR_TILE_M: *v = s.tile_m; return SK_OK;
     case SK_ATTR_TILE_K: *v = s.tile_k; return SK_OK;
@@ -670,6 +677,7 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     a.trace_cap = 0;
     a.debug_skip_signal = -1;
     a.timeout_ns = kDefaultTimeoutNs;
+    a.pdl = 1;
     e = sk::launch_bn128(c_type, tma, tmb, tmc, a, split, stream);
   }
   if (e != cudaSuccess) return cuda_status(e);

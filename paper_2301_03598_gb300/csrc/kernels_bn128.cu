@@ -17,11 +17,20 @@ static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = Cfg<128>::kSmemBytes;
   cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
+  cudaLaunchAttribute attr[2];
+  unsigned na = 0;
+  if (cooperative) {
+    attr[na].id = cudaLaunchAttributeCooperative;
+    attr[na].val.cooperative = 1;
+    ++na;
+  }
+  if (args.pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = cooperative ? 1 : 0;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, TC>, ta, tb, tc, args);
 }
 

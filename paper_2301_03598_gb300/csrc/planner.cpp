@@ -34,30 +34,34 @@ int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]) {
   return best;
 }
 
-// Model constants for this kernel family on GB300, in units of one MAC-loop
-// iteration (BLK_M x BLK_N x BLK_K = 128 x BN x 64): a = fixed per-CTA cost,
-// b = spilling a partial tile, c = one iteration, d = reading and adding one
-// peer's partials in the owner.
+// Model constants of Appendix A.1 for this kernel family on GB300, in
+// microseconds, fitted by least squares to measured times of basic Stream-K
+// over grid sizes g in [t, p] (12 shapes with t < p, each tile width): a =
+// fixed per-launch cost, b = a CTA spilling partial sums, c = one MAC-loop
+// iteration (BLK_M x BLK_N x 64), d = reading and adding one peer's partials.
 void model_coefficients(int tile_n, double out[4]) {
   if (tile_n == 256) {
-    out[0] = 0.0;
-    out[1] = 4.0;
-    out[2] = 1.0;
-    out[3] = 4.0;
+    out[0] = 4.63;
+    out[1] = 5.98;
+    out[2] = 0.268;
+    out[3] = 0.942;
   } else {
-    out[0] = 0.0;
-    out[1] = 5.0;
-    out[2] = 1.0;
-    out[3] = 5.0;
+    out[0] = 5.91;
+    out[1] = 1.25;
+    out[2] = 0.258;
+    out[3] = 0.775;
   }
 }
 
-// A tcgen05 M=128 MMA with N=128 takes as long as one with N=256 (measured:
-// 128x128x64 and 128x256x64 MAC-loop iterations both take about 270 ns), so
-// BLK_N = 256 is the ideal blocking factor (Section 5.1) whenever the output
-// is wider than 128 columns; narrower outputs use 128 to halve the fixup bytes.
-static int auto_tile_n(int64_t /*m*/, int64_t n, int /*num_sms*/) {
-  return n <= 128 ? 128 : 256;
+// BLK_N = 256 is the ideal blocking factor for throughput: an M=128 MMA with
+// N=128 takes as long as one with N=256.  When the 128-wide tiling fits in one
+// wave, the extra parallelism of the narrower tile (and its half-size partial
+// sums) measured faster, so it is used there and for outputs of at most 128
+// columns.
+static int auto_tile_n(int64_t m, int64_t n, int64_t /*k*/, int num_sms) {
+  if (n <= 128) return 128;
+  const int64_t t128 = cdiv(m, kTileM) * cdiv(n, 128);
+  return t128 <= num_sms ? 128 : 256;
 }
 
 int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
@@ -74,7 +78,7 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
   sk_schedule_info s{};
   s.tile_m = kTileM;
   s.tile_k = kTileK;
-  s.tile_n = tile_n ? tile_n : auto_tile_n(m, n, num_sms);
+  s.tile_n = tile_n ? tile_n : auto_tile_n(m, n, k, num_sms);
   s.tiles_m = static_cast<int32_t>(cdiv(m, s.tile_m));
   s.tiles_n = static_cast<int32_t>(cdiv(n, s.tile_n));
   s.tiles = static_cast<int64_t>(s.tiles_m) * s.tiles_n;

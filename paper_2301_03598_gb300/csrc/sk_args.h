@@ -57,6 +57,7 @@ struct SkArgs {
   int32_t trace_cap;    // records per CTA
   int32_t debug_skip_signal;  // CTA index that withholds its Signal (tests), -1 off
   uint64_t timeout_ns;
+  int32_t pdl;  // launched with programmatic stream serialization (host side only)
 };
 
 }  // namespace sk

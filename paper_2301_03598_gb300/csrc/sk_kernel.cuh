@@ -31,9 +31,10 @@
 
 namespace sk {
 
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;  // two warps per TMEM lane quarter, splitting the columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kEpiWarp0 = 2;
-constexpr int kEpiThreads = 128;
+constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 
 #ifndef SK_STAGES_BN128
@@ -50,11 +51,11 @@ struct Cfg {
   static constexpr int kBBytes = BN * kBlkK * 2;
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kTmemCols = 2 * BN;  // two FP32 accumulators of BN columns
-  // Output staging for TMA stores: per epilogue warp two buffers of 32 rows x
+  // Output staging for TMA stores: per epilogue warp one buffer of 32 rows x
   // 128 B, 128-byte swizzled (1 KiB aligned).
   static constexpr int kStagingOffset = kStages * kStageBytes;
-  static constexpr int kStagingBytesPerWarp = 2 * 32 * 128;
-  static constexpr int kStagingBytes = 4 * kStagingBytesPerWarp;
+  static constexpr int kStagingBytesPerWarp = 32 * 128;
+  static constexpr int kStagingBytes = kEpiWarps * kStagingBytesPerWarp;
   static constexpr int kBarOffset = kStagingOffset + kStagingBytes;
   static constexpr int kNumBars = 2 * kStages + 5;
   static constexpr int kSmemBytes = kBarOffset + 256 + 1024;  // + barriers, + 1 KiB alignment
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf_bar(b), 1);
-      mbar_init(acce_bar(b), kEpiThreads / 32);
+      mbar_init(acce_bar(b), kEpiWarps);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -372,6 +373,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // Everything above overlaps the previous kernel under programmatic
+  // dependent launch; global memory is touched only after this point.
+  grid_dependency_wait();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -461,6 +465,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         acc ^= 1;
         if (acc == 0) acc_phase ^= 1u;
       }
+      // All MMAs are issued: the next kernel in the stream may start launching
+      // (it runs its prologue and then waits for this grid to complete).
+      grid_launch_dependents();
       // Drain: every MMA issued above completes before TMEM is released.
       mma_commit(drain_bar);
       const uint64_t t0 = globaltimer_ns();
@@ -469,7 +476,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // -------------------------------------------------------------- epilogue
-    const int quarter = warp & 3;  // TMEM lanes this warp may access
+    const int quarter = warp & 3;                     // TMEM lanes this warp may access
+    const int col_half = (warp - kEpiWarp0) >> 2;     // which interleaved column units
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
     const int ipt = a.iters_per_tile;
@@ -480,7 +488,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* const my_slot = a.partials + static_cast<size_t>(x) * (kBlkM * BN);
     const uint32_t staging = base + static_cast<uint32_t>(C_::kStagingOffset +
                                                          (warp - kEpiWarp0) * C_::kStagingBytesPerWarp);
-    int nstores = 0;  // TMA stores this warp has issued
     const bool tracer = a.trace != nullptr && warp == kEpiWarp0 && lane == 0;
     int32_t* const tb =
         a.trace + static_cast<size_t>(x) * (kTraceHeaderInts + a.trace_cap * kTraceRecordInts);
@@ -516,92 +523,120 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(acc * BN);
       const int grow = tm * kBlkM + row;
       const int col0 = tn * BN;
-      // Only the chunks holding columns < n are read, spilled, fixed up and stored.
+      // Column units of 128 output bytes (32 FP32 or 64 16-bit columns); the
+      // two warps of a lane quarter take alternate units.  Only units holding
+      // columns < n are read, spilled, fixed up and stored.
+      constexpr int kCpu = (sizeof(TC) == 4) ? 1 : 2;  // 32-column chunks per unit
       const int nchunks = (min(BN, a.n - col0) + 31) / 32;
+      const int nunits = (nchunks + kCpu - 1) / kCpu;
+      const int my_last_unit = (nunits - 1 - col_half) >= 0 ? nunits - 1 - ((nunits - 1 - col_half) & 1) : -1;
+      if (my_last_unit < 0) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce_bar(acc));
+      }
 #pragma unroll 1
-      for (int c = 0; c < nchunks; ++c) {
-        uint32_t r[32];
-        tmem_ld_x32(tbase + static_cast<uint32_t>(c * 32), r);
-        tmem_wait_ld();
-        if (c == nchunks - 1) {
-          // all of this warp's TMEM reads are done: hand the buffer back to the MMA warp
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(acce_bar(acc));
-        }
-        float v[32];
+      for (int u = col_half; u < nunits; u += 2) {
+#pragma unroll 1
+        for (int cc = 0; cc < kCpu; ++cc) {
+          const int c = u * kCpu + cc;
+          if (c >= nchunks) break;
+          uint32_t r[32];
+          tmem_ld_x32(tbase + static_cast<uint32_t>(c * 32), r);
+          tmem_wait_ld();
+          if (u == my_last_unit && (cc == kCpu - 1 || c == nchunks - 1)) {
+            // all of this warp's TMEM reads are done: hand the buffer back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce_bar(acc));
+          }
+          float v[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-        // Workspace slot layout: [c][j][row] float4, so a warp's 16-byte
-        // accesses are contiguous.
-        if (role == kRolePartial) {
-          float4* dst = reinterpret_cast<float4*>(my_slot) + (c * 8) * kBlkM + row;
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+          // Workspace slot layout: [c][j][row] float4, so a warp's 16-byte
+          // accesses are contiguous.
+          if (role == kRolePartial) {
+            float4* dst = reinterpret_cast<float4*>(my_slot) + (c * 8) * kBlkM + row;
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            __stcg(dst + j * kBlkM, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
-          continue;
-        }
-        if (role == kRoleOwner) {
-          for (int y = peer_first; y <= peer_last; ++y) {
-            const float4* src = reinterpret_cast<const float4*>(
-                                    a.partials + static_cast<size_t>(y) * (kBlkM * BN)) +
-                                (c * 8) * kBlkM + row;
+            for (int j = 0; j < 8; ++j)
+              __stcg(dst + j * kBlkM, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+            continue;
+          }
+          if (role == kRoleOwner) {
+            // acc + P[x+1] + P[x+2] + ... in increasing CTA order; two peers'
+            // loads are in flight at a time.
+            for (int y = peer_first; y <= peer_last; y += 2) {
+              const float4* s0 = reinterpret_cast<const float4*>(
+                                     a.partials + static_cast<size_t>(y) * (kBlkM * BN)) +
+                                 (c * 8) * kBlkM + row;
+              const bool two = y + 1 <= peer_last;
+              const float4* s1 = two ? s0 + (kBlkM * BN) / 4 : s0;
+              float4 p0[8], p1[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float4 p = __ldcg(src + j * kBlkM);
-              v[4 * j] += p.x;
-              v[4 * j + 1] += p.y;
-              v[4 * j + 2] += p.z;
-              v[4 * j + 3] += p.w;
+              for (int j = 0; j < 8; ++j) p0[j] = __ldcg(s0 + j * kBlkM);
+              if (two) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) p1[j] = __ldcg(s1 + j * kBlkM);
+              }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                v[4 * j] += p0[j].x;
+                v[4 * j + 1] += p0[j].y;
+                v[4 * j + 2] += p0[j].z;
+                v[4 * j + 3] += p0[j].w;
+              }
+              if (two) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  v[4 * j] += p1[j].x;
+                  v[4 * j + 1] += p1[j].y;
+                  v[4 * j + 2] += p1[j].z;
+                  v[4 * j + 3] += p1[j].w;
+                }
+              }
             }
           }
-        }
-        if (!a.c_tma) {
-          store_row32<TC>(a, grow, col0 + c * 32, v);
-          continue;
-        }
-        // StoreTile through a swizzled staging row and a TMA tensor store of
-        // 32 rows x 128 B (32 FP32 or 64 16-bit columns).
-        const float alpha = a.alpha, beta = a.beta;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] *= alpha;
-        if (beta != 0.0f) add_beta_c<TC>(a, grow, col0 + c * 32, v);
-        constexpr int kChunksPerStore = (sizeof(TC) == 4) ? 1 : 2;
-        const int half = (kChunksPerStore == 2) ? (c & 1) : 0;
-        const int buf = nstores & 1;  // alternate buffers across stores (and tiles)
-        const uint32_t srow = staging + static_cast<uint32_t>(buf * 4096 + lane * 128);
-        if (half == 0) {
-          // the store that last used this buffer has finished reading it
-          if (lane == 0) bulk_wait_group_read<1>();
-          __syncwarp();
-        }
-        if constexpr (sizeof(TC) == 4) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)), __float_as_uint(v[4 * j]),
-                         __float_as_uint(v[4 * j + 1]), __float_as_uint(v[4 * j + 2]),
-                         __float_as_uint(v[4 * j + 3]));
-        } else {
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const int j = half * 4 + jj;
-            st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)),
-                         pack2(v[8 * jj], v[8 * jj + 1], static_cast<TC*>(nullptr)),
-                         pack2(v[8 * jj + 2], v[8 * jj + 3], static_cast<TC*>(nullptr)),
-                         pack2(v[8 * jj + 4], v[8 * jj + 5], static_cast<TC*>(nullptr)),
-                         pack2(v[8 * jj + 6], v[8 * jj + 7], static_cast<TC*>(nullptr)));
+          if (!a.c_tma) {
+            store_row32<TC>(a, grow, col0 + c * 32, v);
+            continue;
           }
-        }
-        if (half == kChunksPerStore - 1 || c == nchunks - 1) {
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) {
-            tma_store_2d(&tmC, staging + static_cast<uint32_t>(buf * 4096),
-                         col0 + (c / kChunksPerStore) * (32 * kChunksPerStore),
-                         tm * kBlkM + quarter * 32);
-            bulk_commit_group();
+          // StoreTile through a swizzled staging row and a TMA tensor store of
+          // 32 rows x 128 B.
+          const float alpha = a.alpha, beta = a.beta;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] *= alpha;
+          if (beta != 0.0f) add_beta_c<TC>(a, grow, col0 + c * 32, v);
+          const uint32_t srow = staging + static_cast<uint32_t>(lane * 128);
+          if (cc == 0) {
+            // the previous store from this buffer has finished reading it
+            if (lane == 0) bulk_wait_group_read<0>();
+            __syncwarp();
           }
-          ++nstores;
+          if constexpr (sizeof(TC) == 4) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)),
+                           __float_as_uint(v[4 * j]), __float_as_uint(v[4 * j + 1]),
+                           __float_as_uint(v[4 * j + 2]), __float_as_uint(v[4 * j + 3]));
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int j = cc * 4 + jj;
+              st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)),
+                           pack2(v[8 * jj], v[8 * jj + 1], static_cast<TC*>(nullptr)),
+                           pack2(v[8 * jj + 2], v[8 * jj + 3], static_cast<TC*>(nullptr)),
+                           pack2(v[8 * jj + 4], v[8 * jj + 5], static_cast<TC*>(nullptr)),
+                           pack2(v[8 * jj + 6], v[8 * jj + 7], static_cast<TC*>(nullptr)));
+            }
+          }
+          if (cc == kCpu - 1 || c == nchunks - 1) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(&tmC, staging, col0 + u * (32 * kCpu), tm * kBlkM + quarter * 32);
+              bulk_commit_group();
+            }
+          }
         }
       }
       if (role == kRolePartial) {

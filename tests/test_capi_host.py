@@ -63,8 +63,9 @@ def test_hybrid_regions_match_oracle(t_m, t_n, ipt, p):
 
 def test_describe_config_shapes():
     d = sk.sk_plan_describe(384, 384, 4096)
-    assert (d["tile_n"], d["tiles"], d["iters_per_tile"], d["mode_name"]) == (256, 6, 64, "sk")
-    assert 6 <= d["grid"] <= 148 and d["workspace_bytes"] > 0
+    assert d["tile_n"] in (128, 256) and d["tiles"] == 3 * (-(-384 // d["tile_n"]))
+    assert (d["iters_per_tile"], d["mode_name"]) == (64, "sk")
+    assert d["tiles"] <= d["grid"] <= 148 and d["workspace_bytes"] > 0
     d = sk.sk_plan_describe(384, 384, 4096, tile_n=128)
     assert (d["tile_n"], d["tiles"]) == (128, 9)
     d = sk.sk_plan_describe(4096, 128, 4096)
