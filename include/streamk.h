@@ -70,7 +70,8 @@ typedef enum {
 /* Plan attributes (sk_plan_set / sk_plan_get).  Settable ones re-plan. */
 typedef enum {
   SK_ATTR_TILE_N = 1,        /* set/get: BLK_N, 128 or 256; set 0 for automatic */
-  SK_ATTR_GRID = 2,          /* set: grid size g for SK_MODE_SK (0 = model); get: the g in use */
+  SK_ATTR_GRID = 2,          /* set: grid size g (in cluster units) for SK_MODE_SK (0 = model);
+                                get: the g in use */
   SK_ATTR_RASTER_GROUP = 3,  /* set/get: tile-raster band height in tiles (0 = automatic) */
   SK_ATTR_TIMEOUT_NS = 4,    /* set/get: limit of every device-side wait, nanoseconds */
   SK_ATTR_LDA = 5,           /* set/get: leading dimension of A in elements (default dense) */
@@ -79,6 +80,9 @@ typedef enum {
   SK_ATTR_DEBUG_SKIP_SIGNAL = 8, /* set: a CTA index that withholds its fixup Signal, so the
                                     owner's bounded Wait must expire (failure-detection
                                     tests); -1 = off */
+  SK_ATTR_CLUSTER_M = 10,    /* set/get: CTAs per cluster along M, 1 or 2 (0 = automatic);
+                                with 2, CTA pairs compute 256-row tiles and share each B
+                                tile by TMA multicast */
   SK_ATTR_PDL = 9,           /* set/get: 1 (default) = launch with programmatic dependent
                                 launch, so the kernel's set-up overlaps the previous kernel
                                 in the stream; it touches global memory only after that
@@ -95,12 +99,16 @@ typedef enum {
   SK_ATTR_WORKSPACE_BYTES = 29, /* get: device workspace this plan needs (partials + flags) */
   SK_ATTR_NUM_SMS = 30,      /* get: SM count p of the plan's device */
   SK_ATTR_TRACE_INTS = 31,   /* get: int32 entries sk_gemm_traced needs */
-  SK_ATTR_TRACE_CAP = 32     /* get: trace records per CTA */
+  SK_ATTR_TRACE_CAP = 32,    /* get: trace records per CTA */
+  SK_ATTR_CTAS = 33          /* get: CTAs launched (grid * cluster_m) */
 } sk_attr;
 
 typedef struct sk_plan_s* sk_plan_t;
 
-/* Host-only description of a schedule (sk_plan_describe). */
+/* Host-only description of a schedule (sk_plan_describe).  The schedule's
+ * unit is a cluster of cluster_m CTAs computing a tile_m x tile_n tile
+ * (tile_m = 128 * cluster_m); tiles, grid and the regions count such units,
+ * the paper's p being the SM count divided by cluster_m. */
 typedef struct {
   int32_t mode;            /* resolved sk_mode */
   int32_t tile_m, tile_n, tile_k;
@@ -113,7 +121,9 @@ typedef struct {
   int64_t sk_iters;        /* sk_tiles * iters_per_tile */
   int32_t raster_group;    /* tile raster band height */
   int32_t max_segments;    /* most tile segments any CTA processes */
-  int64_t workspace_bytes; /* partials (grid x BLK_M x BLK_N x 4 B) + flags, 0 when no split */
+  int64_t workspace_bytes; /* flags + one 128 x BLK_N FP32 partial slot per CTA, 0 when no split */
+  int32_t cluster_m;       /* CTAs per unit along M: 1, or 2 (a pair shares the B tile) */
+  int32_t ctas;            /* CTAs launched: grid * cluster_m */
 } sk_schedule_info;
 
 /*
@@ -189,11 +199,11 @@ int sk_plan_attach_workspace(sk_plan_t plan, void* ws, size_t bytes);
 
 /*
  * Host-only planning, no GPU needed: the schedule sk_plan would choose for
- * this shape on a device with `num_sms` SMs.  tile_n / grid / raster_group as
- * the attributes above (0 = automatic).
+ * this shape on a device with `num_sms` SMs.  tile_n / grid / raster_group /
+ * cluster_m as the attributes above (0 = automatic).
  */
 int sk_plan_describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid,
-                     int raster_group, int num_sms, sk_schedule_info* out);
+                     int raster_group, int cluster_m, int num_sms, sk_schedule_info* out);
 
 /*
  * The grid-size model of Appendix A.1, host only: the g in [1, p] minimising

@@ -270,6 +270,27 @@ class Schedule:
         return out
 
 
+def cluster_trace(sched: Schedule, cluster_m: int) -> List[Tuple[int, ...]]:
+    """The trace of a schedule whose unit of work is a cluster of cluster_m
+    CTAs: unit x's segments are executed by CTAs x*cluster_m + r, each on its
+    own 128-row block (tile row tm*cluster_m + r) of the unit's tile, and the
+    peers of CTA x*cluster_m + r are the CTAs with the same r.  (The paper's
+    schedules are the cluster_m = 1 case.)"""
+    if cluster_m == 1:
+        return sched.trace()
+    by_unit = {}
+    for rec in sched.trace():
+        by_unit.setdefault(rec[0], []).append(rec)
+    out = []
+    for x in range(sched.g):
+        for r in range(cluster_m):
+            for (_, tile, tm, tn, k0, k1, role, pf, pl) in by_unit.get(x, []):
+                out.append((x * cluster_m + r, tile, tm * cluster_m + r, tn, k0, k1, role,
+                            pf * cluster_m + r if pf >= 0 else -1,
+                            pl * cluster_m + r if pl >= 0 else -1))
+    return out
+
+
 def persistent_schedule(prob: Problem, g: int, sk_tiles: int, group_m: int) -> Schedule:
     """Stream-K (Algorithm 5) over tiles [0, sk_tiles) with g CTAs, followed by
     the data-parallel tiles [sk_tiles, t) with tile sk_tiles + x + j*g going to

@@ -84,7 +84,7 @@ struct sk_plan_s {
   int a_type, b_type, c_type;
   int a_layout, b_layout, c_layout;
   int mode_req;
-  int tile_n_req = 0, grid_req = 0, group_req = 0;
+  int tile_n_req = 0, grid_req = 0, group_req = 0, cluster_req = 0;
   int64_t lda, ldb, ldc;
   // problem as the kernel runs it (C column-major runs C^T = B^T A^T)
   bool swap = false;
@@ -127,7 +127,7 @@ int replan(sk_plan_s* p) {
   const int64_t n = p->swap ? p->m : p->n;
   sk_schedule_info s;
   int st = sk::describe(m, n, p->k, p->mode_req, p->tile_n_req, p->grid_req, p->group_req,
-                        p->num_sms, &s);
+                        p->cluster_req, p->num_sms, &s);
   if (st != SK_OK) return st;
   if (s.workspace_bytes > 0 && static_cast<size_t>(s.workspace_bytes) > p->ws_bytes) {
     if (!p->ws_owned) return SK_ERR_INVALID;  // attached buffer too small for the new schedule
@@ -230,7 +230,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
       (reinterpret_cast<uintptr_t>(B) & 15u))
     return SK_ERR_INVALID;
   if (trace != nullptr) {
-    const int64_t need = static_cast<int64_t>(s.grid) *
+    const int64_t need = static_cast<int64_t>(s.ctas) *
                          (sk::kTraceHeaderInts + static_cast<int64_t>(s.max_segments) *
                                                      sk::kTraceRecordInts);
     if (trace_ints < need) return SK_ERR_INVALID;
@@ -249,7 +249,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
     p->cached_a = ka;
   }
   if (kb != p->cached_b) {
-    int st = encode_operand(&p->tm_b, kb, p->b_type, kn, p->k, kldb, s.tile_n);
+    int st = encode_operand(&p->tm_b, kb, p->b_type, kn, p->k, kldb, s.tile_n / s.cluster_m);
     if (st != SK_OK) return st;
     p->cached_b = kb;
   }
@@ -291,8 +291,10 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   a.pdl = p->pdl ? 1 : 0;
 
   cudaError_t e = s.tile_n == 256
-                      ? sk::launch_bn256(p->c_type, p->tm_a, p->tm_b, p->tm_c, a, split, stream)
-                      : sk::launch_bn128(p->c_type, p->tm_a, p->tm_b, p->tm_c, a, split, stream);
+                      ? sk::launch_bn256(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, a, split,
+                                         stream)
+                      : sk::launch_bn128(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, a, split,
+                                         stream);
   return cuda_status(e);
 }
 
@@ -475,6 +477,17 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
       if (v != 0 && v != 1) return SK_ERR_INVALID;
       p->pdl = v != 0;
       return SK_OK;
+    case SK_ATTR_CLUSTER_M: {
+      if (v != 0 && v != 1 && v != 2) return SK_ERR_UNSUPPORTED;
+      const int old = p->cluster_req;
+      p->cluster_req = static_cast<int>(v);
+      int st = replan(p);
+      if (st != SK_OK) {
+        p->cluster_req = old;
+        replan(p);
+      }
+      return st;
+    }
     default:
       return SK_ERR_INVALID;
   }
@@ -493,6 +506,8 @@ int sk_plan_get(sk_plan_t p, int attr, int64_t* v) {
     case SK_ATTR_LDC: *v = p->ldc; return SK_OK;
     case SK_ATTR_DEBUG_SKIP_SIGNAL: *v = p->debug_skip_signal; return SK_OK;
     case SK_ATTR_PDL: *v = p->pdl ? 1 : 0; return SK_OK;
+    case SK_ATTR_CLUSTER_M: *v = s.cluster_m; return SK_OK;
+    case SK_ATTR_CTAS: *v = s.ctas; return SK_OK;
     case SK_ATTR_MODE: *v = s.mode; return SK_OK;
     case SK_ATTR_TILE_M: *v = s.tile_m; return SK_OK;
     case SK_ATTR_TILE_K: *v = s.tile_k; return SK_OK;
@@ -506,7 +521,7 @@ int sk_plan_get(sk_plan_t p, int attr, int64_t* v) {
     case SK_ATTR_NUM_SMS: *v = p->num_sms; return SK_OK;
     case SK_ATTR_TRACE_CAP: *v = s.max_segments; return SK_OK;
     case SK_ATTR_TRACE_INTS:
-      *v = static_cast<int64_t>(s.grid) *
+      *v = static_cast<int64_t>(s.ctas) *
            (sk::kTraceHeaderInts + static_cast<int64_t>(s.max_segments) * sk::kTraceRecordInts);
       return SK_OK;
     default:
@@ -635,7 +650,7 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
         (reinterpret_cast<uintptr_t>(B) & 15u))
       return SK_ERR_INVALID;
     sk_schedule_info s;
-    int st = sk::describe(m, n, k, mode, 128, 0, 0, d->num_sms, &s);
+    int st = sk::describe(m, n, k, mode, 128, 0, 0, 1, d->num_sms, &s);
     if (st != SK_OK) return st;
     const bool split = s.workspace_bytes > 0;
     const size_t partial_bytes = static_cast<size_t>(s.grid) * sk::kBlkM * 128 * 4;
@@ -678,7 +693,7 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     a.debug_skip_signal = -1;
     a.timeout_ns = kDefaultTimeoutNs;
     a.pdl = 1;
-    e = sk::launch_bn128(c_type, tma, tmb, tmc, a, split, stream);
+    e = sk::launch_bn128(c_type, 1, tma, tmb, tmc, a, split, stream);
   }
   if (e != cudaSuccess) return cuda_status(e);
   if (device_status != nullptr) {

@@ -8,17 +8,24 @@
 
 namespace sk {
 
-template <typename TC>
+template <int CM, typename TC>
 static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
-                              const CUtensorMap& tc, const SkArgs& args,
-                              bool cooperative, cudaStream_t stream) {
+                              const CUtensorMap& tc, const SkArgs& args, bool cooperative,
+                              cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>(args.grid));
+  cfg.gridDim = dim3(static_cast<unsigned>(args.grid * CM));
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = Cfg<256>::kSmemBytes;
   cfg.stream = stream;
-  cudaLaunchAttribute attr[2];
+  cudaLaunchAttribute attr[3];
   unsigned na = 0;
+  if (CM > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = CM;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
   if (cooperative) {
     attr[na].id = cudaLaunchAttributeCooperative;
     attr[na].val.cooperative = 1;
@@ -31,37 +38,47 @@ static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<256, TC>, ta, tb, tc, args);
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<256, CM, TC>, ta, tb, tc, args);
 }
 
-cudaError_t launch_bn256(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
-                         const CUtensorMap& tc, const SkArgs& args, bool cooperative,
-                         cudaStream_t stream) {
+template <int CM>
+static cudaError_t launch_cm(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
+                             const CUtensorMap& tc, const SkArgs& args, bool cooperative,
+                             cudaStream_t stream) {
   switch (c_dtype) {
     case SK_F32:
-      return launch_one<float>(ta, tb, tc, args, cooperative, stream);
+      return launch_one<CM, float>(ta, tb, tc, args, cooperative, stream);
     case SK_BF16:
-      return launch_one<__nv_bfloat16>(ta, tb, tc, args, cooperative, stream);
+      return launch_one<CM, __nv_bfloat16>(ta, tb, tc, args, cooperative, stream);
     case SK_F16:
-      return launch_one<__half>(ta, tb, tc, args, cooperative, stream);
+      return launch_one<CM, __half>(ta, tb, tc, args, cooperative, stream);
     default:
       return cudaErrorInvalidValue;
   }
 }
 
+cudaError_t launch_bn256(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
+                         const CUtensorMap& tc, const SkArgs& args, bool cooperative,
+                         cudaStream_t stream) {
+  return cluster_m == 2 ? launch_cm<2>(c_dtype, ta, tb, tc, args, cooperative, stream)
+                        : launch_cm<1>(c_dtype, ta, tb, tc, args, cooperative, stream);
+}
+
+template <int CM, typename TC>
+static cudaError_t set_smem() {
+  return cudaFuncSetAttribute(sk_gemm_kernel<256, CM, TC>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<256>::kSmemBytes);
+}
+
 cudaError_t prepare_bn256(size_t* smem_bytes) {
-  const int bytes = Cfg<256>::kSmemBytes;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(sk_gemm_kernel<256, float>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(sk_gemm_kernel<256, __nv_bfloat16>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(sk_gemm_kernel<256, __half>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
-    return e;
-  *smem_bytes = static_cast<size_t>(bytes);
+  if ((e = set_smem<1, float>()) != cudaSuccess) return e;
+  if ((e = set_smem<1, __nv_bfloat16>()) != cudaSuccess) return e;
+  if ((e = set_smem<1, __half>()) != cudaSuccess) return e;
+  if ((e = set_smem<2, float>()) != cudaSuccess) return e;
+  if ((e = set_smem<2, __nv_bfloat16>()) != cudaSuccess) return e;
+  if ((e = set_smem<2, __half>()) != cudaSuccess) return e;
+  *smem_bytes = static_cast<size_t>(Cfg<256>::kSmemBytes);
   return cudaSuccess;
 }
 

@@ -7,12 +7,13 @@
 
 namespace sk {
 
-// c_dtype: SK_F32 / SK_BF16 / SK_F16.  cooperative: CTAs wait on one another,
-// so the launch must guarantee co-residency.
-cudaError_t launch_bn128(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
+// c_dtype: SK_F32 / SK_BF16 / SK_F16.  cluster_m: 1, or 2 for CTA pairs along M
+// (the grid is args.grid units of cluster_m CTAs).  cooperative: CTAs wait on
+// one another, so the launch must guarantee co-residency.
+cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
                          const CUtensorMap& tc, const SkArgs& args, bool cooperative,
                          cudaStream_t stream);
-cudaError_t launch_bn256(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
+cudaError_t launch_bn256(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
                          const CUtensorMap& tc, const SkArgs& args, bool cooperative,
                          cudaStream_t stream);
 // Dynamic shared memory of one CTA; also sets the kernels' opt-in limit.

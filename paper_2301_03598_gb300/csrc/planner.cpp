@@ -64,10 +64,20 @@ static int auto_tile_n(int64_t m, int64_t n, int64_t /*k*/, int num_sms) {
   return t128 <= num_sms ? 128 : 256;
 }
 
+// CTA pairs along M (clusters of 2 sharing the B tile by multicast) halve
+// the L2 -> SM traffic of B; they pay off once the problem fills the GPU with
+// 128 x 256 tiles, and need at least two 128-row blocks.
+static int auto_cluster_m(int64_t m, int64_t n, int tile_n, int num_sms) {
+  const int64_t tm = cdiv(m, kTileM);
+  if (tile_n != 256 || tm < 2 || num_sms < 2) return 1;
+  return tm * cdiv(n, 256) >= num_sms ? 2 : 1;
+}
+
 int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
-             int num_sms, sk_schedule_info* out) {
+             int cluster_m, int num_sms, sk_schedule_info* out) {
   if (out == nullptr || m < 0 || n < 0 || k < 0 || num_sms < 1 || grid < 0 || raster_group < 0)
     return SK_ERR_INVALID;
+  if (cluster_m != 0 && cluster_m != 1 && cluster_m != 2) return SK_ERR_UNSUPPORTED;
   if (num_sms > kMaxGrid || grid > num_sms) return SK_ERR_INVALID;
   if (mode < SK_MODE_AUTO || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
   if (tile_n != 0 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
@@ -76,9 +86,14 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
     return SK_ERR_INVALID;
 
   sk_schedule_info s{};
-  s.tile_m = kTileM;
   s.tile_k = kTileK;
   s.tile_n = tile_n ? tile_n : auto_tile_n(m, n, k, num_sms);
+  s.cluster_m = cluster_m ? cluster_m : auto_cluster_m(m, n, s.tile_n, num_sms);
+  // The schedule's unit is a cluster: cluster_m CTAs computing a
+  // (128 * cluster_m) x BLK_N tile; the paper's p is the number of such units.
+  s.tile_m = kTileM * s.cluster_m;
+  num_sms /= s.cluster_m;
+  if (grid > num_sms) return SK_ERR_INVALID;
   s.tiles_m = static_cast<int32_t>(cdiv(m, s.tile_m));
   s.tiles_n = static_cast<int32_t>(cdiv(n, s.tile_n));
   s.tiles = static_cast<int64_t>(s.tiles_m) * s.tiles_n;
@@ -126,6 +141,23 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
       }
       case SK_MODE_HYBRID:
       case SK_MODE_HYBRID_ONE_TILE: {
+        if (mode == SK_MODE_AUTO && w >= 1 && rem != 0) {
+          // The two-tile hybrid pays one spill and one fixup per split tile;
+          // with few iterations per tile that can cost more than the partial
+          // wave it removes.  Compare both with the model's terms: the spill
+          // and fixup are exposed when no data-parallel wave follows the
+          // Stream-K region (w == 1) and mostly hidden behind it otherwise.
+          const double split_us = (coef[1] + coef[3]) * (w == 1 ? 1.0 : 0.1);
+          const double dp_us = coef[0] + coef[2] * static_cast<double>(ipt * ((t + p - 1) / p));
+          const double sk_us =
+              coef[0] + split_us + coef[2] * static_cast<double>((t * ipt + p - 1) / p);
+          if (dp_us <= sk_us) {
+            s.mode = SK_MODE_DP;
+            s.sk_tiles = 0;
+            s.grid = static_cast<int32_t>(std::min<int64_t>(t, p));
+            break;
+          }
+        }
         if (rem == 0) {  // perfect quantization: full waves only
           s.sk_tiles = 0;
           s.grid = static_cast<int32_t>(std::min<int64_t>(t, p));
@@ -171,7 +203,8 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
       if (begin % ipt != 0) split = true;
     }
   }
-  s.workspace_bytes = split ? workspace_bytes_for(s.grid, s.tile_n) : 0;
+  s.ctas = s.grid * s.cluster_m;
+  s.workspace_bytes = split ? workspace_bytes_for(s.ctas, s.tile_n) : 0;
   *out = s;
   return SK_OK;
 }
@@ -183,8 +216,9 @@ int64_t workspace_bytes_for(int grid, int tile_n) {
 }  // namespace sk
 
 extern "C" int sk_plan_describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid,
-                                int raster_group, int num_sms, sk_schedule_info* out) {
-  return sk::describe(m, n, k, mode, tile_n, grid, raster_group, num_sms, out);
+                                int raster_group, int cluster_m, int num_sms,
+                                sk_schedule_info* out) {
+  return sk::describe(m, n, k, mode, tile_n, grid, raster_group, cluster_m, num_sms, out);
 }
 
 extern "C" int sk_grid_model(int64_t m, int64_t n, int64_t k, int bm, int bn, int bk, int p,

@@ -321,10 +321,15 @@ __device__ __forceinline__ void add_beta_c(const SkArgs& a, int grow, int gcol, 
   }
 }
 
-template <int BN, typename TC>
+// CM = CTAs per cluster along M (1 or 2).  With CM = 2 the two CTAs of a
+// cluster compute the two 128-row halves of a 256 x BN tile: the schedule's
+// unit is that tile and its CTA pair, each CTA loads its own A rows and half
+// of the B tile, multicasting that half to both CTAs.
+template <int BN, int CM, typename TC>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ SkArgs a) {
+  static_assert(CM == 1 || CM == 2, "cluster size along M");
   using C_ = Cfg<BN>;
   constexpr int S = C_::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -345,12 +350,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int x = blockIdx.x;
+  const int cta = blockIdx.x;                                 // this CTA (flags, partials, trace)
+  const int rank = CM == 2 ? static_cast<int>(cluster_ctarank()) : 0;
+  const int x = cta / CM;                                     // schedule unit (CTA pair)
+  constexpr uint16_t kPairMask = 0x3;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 1);
+      mbar_init(empty_bar(s), CM);  // released by the MMA of every CTA that reads the stage
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf_bar(b), 1);
@@ -371,6 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CM == 2) cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // Everything above overlaps the previous kernel under programmatic
@@ -390,6 +399,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       while (ok && w.next(a, tile, kb0, kb1)) {
         int tm, tn;
         tile_coords(a, tile, tm, tn);
+        tm = tm * CM + rank;  // this CTA's 128-row block
         for (int kb = kb0; kb < kb1; ++kb) {
           if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) {
             ok = false;
@@ -397,7 +407,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mbar_arrive_expect_tx(full_bar(stage), C_::kStageBytes);
           tma_load_2d(stage_a(stage), &tmA, full_bar(stage), kb * kBlkK, tm * kBlkM);
-          tma_load_2d(stage_b(stage), &tmB, full_bar(stage), kb * kBlkK, tn * BN);
+          if constexpr (CM == 2) {
+            // this CTA's half of the B tile, into both CTAs of the pair
+            tma_load_2d_multicast(stage_b(stage) + static_cast<uint32_t>(rank * (BN / 2) * 128), &tmB,
+                                  full_bar(stage), kb * kBlkK, tn * BN + rank * (BN / 2), kPairMask);
+          } else {
+            tma_load_2d(stage_b(stage), &tmB, full_bar(stage), kb * kBlkK, tn * BN);
+          }
           ++issued;
           if (++stage == S) {
             stage = 0;
@@ -454,7 +470,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
                     (kb > kb0 || kk > 0) ? 1u : 0u);
           }
-          mma_commit(empty_bar(stage));  // frees the stage once these MMAs finish
+          // frees the stage (in both CTAs of a pair) once these MMAs finish
+          if constexpr (CM == 2)
+            mma_commit_multicast(empty_bar(stage), kPairMask);
+          else
+            mma_commit(empty_bar(stage));
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -485,12 +505,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     w.init(a, x);
     int tile, kb0, kb1, acc = 0, nrec = 0;
     uint32_t acc_phase = 0;
-    float* const my_slot = a.partials + static_cast<size_t>(x) * (kBlkM * BN);
+    float* const my_slot = a.partials + static_cast<size_t>(cta) * (kBlkM * BN);
     const uint32_t staging = base + static_cast<uint32_t>(C_::kStagingOffset +
                                                          (warp - kEpiWarp0) * C_::kStagingBytesPerWarp);
     const bool tracer = a.trace != nullptr && warp == kEpiWarp0 && lane == 0;
     int32_t* const tb =
-        a.trace + static_cast<size_t>(x) * (kTraceHeaderInts + a.trace_cap * kTraceRecordInts);
+        a.trace + static_cast<size_t>(cta) * (kTraceHeaderInts + a.trace_cap * kTraceRecordInts);
     if (tracer) {
       const uint64_t t = globaltimer_ns();
       tb[0] = 0;
@@ -502,20 +522,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool started = kb0 == 0;
       const bool ended = kb1 == ipt;
       const int role = !started ? kRolePartial : (!ended ? kRoleOwner : kRoleWhole);
+      // Peers as CTA indices: the same half (rank) of each contributing unit.
       int peer_first = -1, peer_last = -1;
       if (role == kRoleOwner) {
-        peer_first = x + 1;
-        peer_last = cta_of_iter(a, static_cast<int64_t>(tile) * ipt + ipt - 1);
+        peer_first = (x + 1) * CM + rank;
+        peer_last = cta_of_iter(a, static_cast<int64_t>(tile) * ipt + ipt - 1) * CM + rank;
       }
       int tm, tn;
       tile_coords(a, tile, tm, tn);
+      tm = tm * CM + rank;
 
       bool fail = !wait_bar(accf_bar(acc), acc_phase, abort_flag, a, kAtEpiAccFull);
       if (epi_any(fail)) break;
       tc_fence_after();
       const uint64_t t_acc = tracer ? globaltimer_ns() : 0;
       if (role == kRoleOwner) {
-        for (int y = peer_first; y <= peer_last && !fail; ++y) fail = !wait_flag(&a.flags[y], abort_flag, a);
+        for (int y = peer_first; y <= peer_last && !fail; y += CM)
+          fail = !wait_flag(&a.flags[y], abort_flag, a);
         if (epi_any(fail)) break;
       }
       const uint64_t t_fix = tracer ? globaltimer_ns() : 0;
@@ -537,40 +560,54 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
 #pragma unroll 1
       for (int u = col_half; u < nunits; u += 2) {
-#pragma unroll 1
-        for (int cc = 0; cc < kCpu; ++cc) {
-          const int c = u * kCpu + cc;
-          if (c >= nchunks) break;
-          uint32_t r[32];
-          tmem_ld_x32(tbase + static_cast<uint32_t>(c * 32), r);
+        // One TMEM load per unit (32 or 64 FP32 columns), then one wait.
+        float v[kCpu][32];
+        {
+          uint32_t r[32 * kCpu];
+          if constexpr (kCpu == 2)
+            tmem_ld_x64(tbase + static_cast<uint32_t>(u * 64), r);
+          else
+            tmem_ld_x32(tbase + static_cast<uint32_t>(u * 32), r);
           tmem_wait_ld();
-          if (u == my_last_unit && (cc == kCpu - 1 || c == nchunks - 1)) {
+          if (u == my_last_unit) {
             // all of this warp's TMEM reads are done: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce_bar(acc));
           }
-          float v[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-          // Workspace slot layout: [c][j][row] float4, so a warp's 16-byte
-          // accesses are contiguous.
-          if (role == kRolePartial) {
-            float4* dst = reinterpret_cast<float4*>(my_slot) + (c * 8) * kBlkM + row;
+          for (int cc = 0; cc < kCpu; ++cc)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[cc][j] = __uint_as_float(r[cc * 32 + j]);
+        }
+        const int cvalid = min(kCpu, nchunks - u * kCpu);  // 32-column chunks inside n
+        // Workspace slot layout: [chunk][j][row] float4, so a warp's 16-byte
+        // accesses are contiguous.
+        if (role == kRolePartial) {
+#pragma unroll
+          for (int cc = 0; cc < kCpu; ++cc) {
+            if (cc >= cvalid) break;
+            float4* dst = reinterpret_cast<float4*>(my_slot) + ((u * kCpu + cc) * 8) * kBlkM + row;
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-              __stcg(dst + j * kBlkM, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
-            continue;
+              __stcg(dst + j * kBlkM, make_float4(v[cc][4 * j], v[cc][4 * j + 1], v[cc][4 * j + 2],
+                                                  v[cc][4 * j + 3]));
           }
-          if (role == kRoleOwner) {
-            // acc + P[x+1] + P[x+2] + ... in increasing CTA order; two peers'
-            // loads are in flight at a time.
-            for (int y = peer_first; y <= peer_last; y += 2) {
+          continue;
+        }
+        if (role == kRoleOwner) {
+          // acc + P[x+1] + P[x+2] + ... in increasing CTA order; two peers'
+          // loads are in flight at a time.
+#pragma unroll
+          for (int cc = 0; cc < kCpu; ++cc) {
+            if (cc >= cvalid) break;
+            const int c = u * kCpu + cc;
+            for (int y = peer_first; y <= peer_last; y += 2 * CM) {
               const float4* s0 = reinterpret_cast<const float4*>(
                                      a.partials + static_cast<size_t>(y) * (kBlkM * BN)) +
                                  (c * 8) * kBlkM + row;
-              const bool two = y + 1 <= peer_last;
-              const float4* s1 = two ? s0 + (kBlkM * BN) / 4 : s0;
+              const bool two = y + CM <= peer_last;
+              const float4* s1 = two ? s0 + CM * (kBlkM * BN) / 4 : s0;
               float4 p0[8], p1[8];
 #pragma unroll
               for (int j = 0; j < 8; ++j) p0[j] = __ldcg(s0 + j * kBlkM);
@@ -580,82 +617,83 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
-                v[4 * j] += p0[j].x;
-                v[4 * j + 1] += p0[j].y;
-                v[4 * j + 2] += p0[j].z;
-                v[4 * j + 3] += p0[j].w;
+                v[cc][4 * j] += p0[j].x;
+                v[cc][4 * j + 1] += p0[j].y;
+                v[cc][4 * j + 2] += p0[j].z;
+                v[cc][4 * j + 3] += p0[j].w;
               }
               if (two) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                  v[4 * j] += p1[j].x;
-                  v[4 * j + 1] += p1[j].y;
-                  v[4 * j + 2] += p1[j].z;
-                  v[4 * j + 3] += p1[j].w;
+                  v[cc][4 * j] += p1[j].x;
+                  v[cc][4 * j + 1] += p1[j].y;
+                  v[cc][4 * j + 2] += p1[j].z;
+                  v[cc][4 * j + 3] += p1[j].w;
                 }
               }
             }
           }
-          if (!a.c_tma) {
-            store_row32<TC>(a, grow, col0 + c * 32, v);
-            continue;
-          }
-          // StoreTile through a swizzled staging row and a TMA tensor store of
-          // 32 rows x 128 B.
-          const float alpha = a.alpha, beta = a.beta;
+        }
+        if (!a.c_tma) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] *= alpha;
-          if (beta != 0.0f) add_beta_c<TC>(a, grow, col0 + c * 32, v);
-          const uint32_t srow = staging + static_cast<uint32_t>(lane * 128);
-          if (cc == 0) {
-            // the previous store from this buffer has finished reading it
-            if (lane == 0) bulk_wait_group_read<0>();
-            __syncwarp();
-          }
-          if constexpr (sizeof(TC) == 4) {
+          for (int cc = 0; cc < kCpu; ++cc)
+            if (cc < cvalid) store_row32<TC>(a, grow, col0 + (u * kCpu + cc) * 32, v[cc]);
+          continue;
+        }
+        // StoreTile through a swizzled staging row and one TMA tensor store of
+        // 32 rows x 128 B.
+        const float alpha = a.alpha, beta = a.beta;
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-              st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)),
-                           __float_as_uint(v[4 * j]), __float_as_uint(v[4 * j + 1]),
-                           __float_as_uint(v[4 * j + 2]), __float_as_uint(v[4 * j + 3]));
-          } else {
+        for (int cc = 0; cc < kCpu; ++cc) {
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              const int j = cc * 4 + jj;
-              st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)),
-                           pack2(v[8 * jj], v[8 * jj + 1], static_cast<TC*>(nullptr)),
-                           pack2(v[8 * jj + 2], v[8 * jj + 3], static_cast<TC*>(nullptr)),
-                           pack2(v[8 * jj + 4], v[8 * jj + 5], static_cast<TC*>(nullptr)),
-                           pack2(v[8 * jj + 6], v[8 * jj + 7], static_cast<TC*>(nullptr)));
-            }
+          for (int j = 0; j < 32; ++j) v[cc][j] *= alpha;
+          if (beta != 0.0f && cc < cvalid) add_beta_c<TC>(a, grow, col0 + (u * kCpu + cc) * 32, v[cc]);
+        }
+        const uint32_t srow = staging + static_cast<uint32_t>(lane * 128);
+        // the previous store from this buffer has finished reading it
+        if (lane == 0) bulk_wait_group_read<0>();
+        __syncwarp();
+        if constexpr (sizeof(TC) == 4) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)),
+                         __float_as_uint(v[0][4 * j]), __float_as_uint(v[0][4 * j + 1]),
+                         __float_as_uint(v[0][4 * j + 2]), __float_as_uint(v[0][4 * j + 3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int cc = j >> 2, jj = j & 3;
+            st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)),
+                         pack2(v[cc][8 * jj], v[cc][8 * jj + 1], static_cast<TC*>(nullptr)),
+                         pack2(v[cc][8 * jj + 2], v[cc][8 * jj + 3], static_cast<TC*>(nullptr)),
+                         pack2(v[cc][8 * jj + 4], v[cc][8 * jj + 5], static_cast<TC*>(nullptr)),
+                         pack2(v[cc][8 * jj + 6], v[cc][8 * jj + 7], static_cast<TC*>(nullptr)));
           }
-          if (cc == kCpu - 1 || c == nchunks - 1) {
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-              tma_store_2d(&tmC, staging, col0 + u * (32 * kCpu), tm * kBlkM + quarter * 32);
-              bulk_commit_group();
-            }
-          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&tmC, staging, col0 + u * (32 * kCpu), tm * kBlkM + quarter * 32);
+          bulk_commit_group();
         }
       }
       if (role == kRolePartial) {
         // Signal(flags[x]): all 128 threads' partial stores before the release.
         __threadfence();
         named_bar_sync(kEpiBarrier, kEpiThreads);
-        if (warp == kEpiWarp0 && lane == 0 && x != a.debug_skip_signal)
-          st_release_gpu(&a.flags[x], a.epoch);
+        if (warp == kEpiWarp0 && lane == 0 && cta != a.debug_skip_signal)
+          st_release_gpu(&a.flags[cta], a.epoch);
       } else if (role == kRoleOwner && warp == kEpiWarp0 && lane == 0) {
         // Every partial has exactly one consumer: clear the peers' flags so the
         // next launch (even a graph replay carrying the same epoch) starts clean.
         // All epilogue threads passed their Waits before the last vote.
-        for (int y = peer_first; y <= peer_last; ++y) a.flags[y] = 0u;
+        for (int y = peer_first; y <= peer_last; y += CM) a.flags[y] = 0u;
       }
       if (tracer) {
         const uint64_t t_done = globaltimer_ns();
         if (nrec < a.trace_cap) {
           int32_t* rec = tb + kTraceHeaderInts + nrec * kTraceRecordInts;
-          rec[0] = x;
+          rec[0] = cta;
           rec[1] = tile;
           rec[2] = tm;
           rec[3] = tn;
@@ -685,6 +723,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncwarp();  // reconverge the producer / MMA warps (one lane worked)
   tc_fence_before();
   __syncthreads();
+  // Neither CTA of a pair leaves while the other may still multicast into it
+  // or arrive on its barriers.
+  if constexpr (CM == 2) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, C_::kTmemCols);

@@ -23,9 +23,9 @@ MODES = {"auto": 0, "dp": 1, "sk": 2, "hybrid": 3, "hybrid1": 4}
 MODE_NAMES = {v: k for k, v in MODES.items()}
 ATTRS = {
     "tile_n": 1, "grid": 2, "raster_group": 3, "timeout_ns": 4, "lda": 5, "ldb": 6, "ldc": 7,
-    "debug_skip_signal": 8, "pdl": 9, "mode": 20, "tile_m": 21, "tile_k": 22, "tiles_m": 23,
+    "debug_skip_signal": 8, "pdl": 9, "cluster_m": 10, "mode": 20, "tile_m": 21, "tile_k": 22, "tiles_m": 23,
     "tiles_n": 24, "tiles": 25, "iters_per_tile": 26, "sk_tiles": 27, "dp_tiles": 28,
-    "workspace_bytes": 29, "num_sms": 30, "trace_ints": 31, "trace_cap": 32,
+    "workspace_bytes": 29, "num_sms": 30, "trace_ints": 31, "trace_cap": 32, "ctas": 33,
 }
 TRACE_FIELDS = 9
 TRACE_HEADER = 4
@@ -45,7 +45,8 @@ class sk_schedule_info(ctypes.Structure):
                 ("iters_per_tile", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("sk_tiles", ctypes.c_int64), ("dp_tiles", ctypes.c_int64),
                 ("sk_iters", ctypes.c_int64), ("raster_group", ctypes.c_int32),
-                ("max_segments", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
+                ("max_segments", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
+                ("cluster_m", ctypes.c_int32), ("ctas", ctypes.c_int32)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -75,7 +76,7 @@ def lib() -> ctypes.CDLL:
     L.sk_plan_set.argtypes = [vp, i32, i64]
     L.sk_plan_get.argtypes = [vp, i32, ctypes.POINTER(i64)]
     L.sk_plan_attach_workspace.argtypes = [vp, vp, ctypes.c_size_t]
-    L.sk_plan_describe.argtypes = [i64, i64, i64, i32, i32, i32, i32, i32,
+    L.sk_plan_describe.argtypes = [i64, i64, i64, i32, i32, i32, i32, i32, i32,
                                    ctypes.POINTER(sk_schedule_info)]
     L.sk_grid_model.argtypes = [i64, i64, i64, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(i32)]
@@ -252,10 +253,11 @@ def sk_last_error(plan: Plan):
 
 
 def sk_plan_describe(m: int, n: int, k: int, mode="auto", tile_n: int = 0, grid: int = 0,
-                     raster_group: int = 0, num_sms: int = 148):
+                     raster_group: int = 0, num_sms: int = 148, cluster_m: int = 0):
     info = sk_schedule_info()
     _check(lib().sk_plan_describe(m, n, k, _code(MODES, mode, "mode"), tile_n, grid,
-                                  raster_group, num_sms, ctypes.byref(info)), "sk_plan_describe")
+                                  raster_group, cluster_m, num_sms, ctypes.byref(info)),
+           "sk_plan_describe")
     return info.as_dict()
 
 

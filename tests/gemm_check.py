@@ -114,7 +114,7 @@ class Problem:
             info = plan.info()
             trace_records = None
             if trace:
-                trace_records = sk.decode_trace(tr.cpu().tolist(), info["grid"],
+                trace_records = sk.decode_trace(tr.cpu().tolist(), info["ctas"],
                                                 info["trace_cap"])
             return outs, info, trace_records
         finally:

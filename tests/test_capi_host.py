@@ -70,11 +70,32 @@ def test_describe_config_shapes():
     assert (d["tile_n"], d["tiles"]) == (128, 9)
     d = sk.sk_plan_describe(4096, 128, 4096)
     assert d["tile_n"] == 128
-    d = sk.sk_plan_describe(8192, 8192, 8192)
+    d = sk.sk_plan_describe(8192, 8192, 8192, cluster_m=1)
     assert (d["tile_n"], d["tiles"], d["mode_name"]) == (256, 2048, "hybrid")
     assert d["sk_tiles"] == 2048 % 148 + 148 and d["dp_tiles"] % 148 == 0
+    # CTA pairs: 256 x 256 units on p = 74 pairs
+    d = sk.sk_plan_describe(8192, 8192, 8192)
+    assert (d["cluster_m"], d["tile_m"], d["tiles"], d["ctas"]) == (2, 256, 1024, 148)
+    assert d["sk_tiles"] == 1024 % 74 + 74 and d["dp_tiles"] % 74 == 0
     d = sk.sk_plan_describe(128 * 37, 256, 64)      # 37*2 tiles, below one wave
     assert d["mode_name"] == "sk"
+
+
+@pytest.mark.parametrize("m,n,k,mode", [(8192, 8192, 1024, "hybrid"), (4096, 2048, 512, "sk"),
+                                        (3000, 2000, 700, "auto"), (2000, 4000, 256, "dp")])
+def test_cluster_units_match_oracle(m, n, k, mode):
+    d = sk.sk_plan_describe(m, n, k, mode, tile_n=256, cluster_m=2, num_sms=152)
+    assert d["cluster_m"] == 2 and d["tile_m"] == 256 and d["ctas"] == 2 * d["grid"]
+    prob = S.Problem(m, n, k, 256, 256, 64)
+    assert d["tiles"] == prob.tiles and d["grid"] <= 76
+    if d["mode_name"] == "hybrid":
+        assert (d["sk_tiles"], d["dp_tiles"]) == S.hybrid_regions(prob.tiles, 76, S.HYBRID_TWO_TILE)
+    sched = S.persistent_schedule(prob, d["grid"], d["sk_tiles"], d["raster_group"])
+    assert max(len(c) for c in sched.ctas) <= d["max_segments"]
+    tr = S.cluster_trace(sched, 2)
+    assert {r[0] for r in tr} <= set(range(d["ctas"]))
+    if d["workspace_bytes"]:
+        assert d["workspace_bytes"] >= d["ctas"] * 128 * 256 * 4
 
 
 def test_max_segments_bounds_every_cta():

@@ -67,7 +67,7 @@ def test_two_tile_hybrid_with_dp_waves(tile_n):
     tiles_m = hybrid_shape(p, 2, 8)
     n = 8 * tile_n
     prob = Problem(tiles_m * 128, n, 256, "bf16", "bf16", "normal", seed=4, beta=0.5)
-    (C,), info, _ = prob.run(1.0, 0.5, "hybrid", plan_attrs={"tile_n": tile_n})
+    (C,), info, _ = prob.run(1.0, 0.5, "hybrid", plan_attrs={"tile_n": tile_n, "cluster_m": 1})
     t = tiles_m * 8
     want = S.hybrid_regions(t, p, S.HYBRID_TWO_TILE)
     assert info["tiles"] == t and (info["sk_tiles"], info["dp_tiles"]) == want
@@ -83,6 +83,25 @@ def test_one_tile_hybrid_with_dp_waves():
     want = S.hybrid_regions(tiles_m * 8, p, S.HYBRID_ONE_TILE)
     assert (info["sk_tiles"], info["dp_tiles"]) == want and 0 < want[0] < p
     prob.check(C, 1.0, 0.0, "one-tile hybrid")
+
+
+@pytest.mark.parametrize("m,n,k,mode,attrs", [
+    (4096, 4096, 1024, "hybrid", {}),
+    (1000, 1000, 1000, "sk", {"grid": 50}),
+    (1152, 2000, 520, "dp", {}),           # odd number of 128-row blocks: the last pair is half empty
+    (130, 520, 4096, "sk", {"grid": 20}),
+    (384, 384, 4096, "sk", {"tile_n": 128, "grid": 30}),
+    (2944, 1536, 136, "auto", {}),
+])
+@pytest.mark.parametrize("c_type", ["bf16", "f32"])
+def test_cta_pairs(m, n, k, mode, attrs, c_type):
+    prob = Problem(m, n, k, "bf16", c_type, "normal", seed=m + k, beta=0.5 if c_type == "f32" else 0.0)
+    beta = 0.5 if c_type == "f32" else 0.0
+    attrs = dict({"tile_n": 256}, **attrs)
+    attrs["cluster_m"] = 2
+    (C,), info, _ = prob.run(1.0, beta, mode, plan_attrs=attrs)
+    assert info["cluster_m"] == 2 and info["ctas"] == 2 * info["grid"]
+    prob.check(C, 1.0, beta, f"pairs {m}x{n}x{k} {mode} g={info['grid']}")
 
 
 def test_column_major_c():

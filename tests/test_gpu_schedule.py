@@ -17,7 +17,7 @@ def model_trace(info, m, n, k):
     prob = S.Problem(m, n, k, info["tile_m"], info["tile_n"], info["tile_k"])
     assert prob.tiles == info["tiles"] and prob.iters_per_tile == info["iters_per_tile"]
     sched = S.persistent_schedule(prob, info["grid"], info["sk_tiles"], info["raster_group"])
-    return sched.trace()
+    return S.cluster_trace(sched, info["cluster_m"])
 
 
 @pytest.mark.parametrize("m,n,k,mode,attrs", [
@@ -33,6 +33,11 @@ def model_trace(info, m, n, k):
     ("2p+8", 1024, 256, "hybrid", {"tile_n": 128, "raster_group": 5}),
     ("2p+8", 2048, 192, "hybrid", {"tile_n": 256}),
     ("2p+8", 1024, 320, "hybrid1", {"tile_n": 128}),
+    # CTA pairs (clusters of 2 along M sharing B by multicast)
+    (4096, 4096, 512, "hybrid", {"tile_n": 256, "cluster_m": 2}),
+    (1000, 3000, 640, "sk", {"tile_n": 256, "cluster_m": 2}),
+    (384, 384, 4096, "sk", {"tile_n": 128, "cluster_m": 2, "grid": 30}),
+    (2432, 2048, 192, "dp", {"tile_n": 256, "cluster_m": 2, "raster_group": 3}),
 ])
 def test_device_trace_matches_model(m, n, k, mode, attrs):
     if m == "2p+8":
@@ -44,7 +49,7 @@ def test_device_trace_matches_model(m, n, k, mode, attrs):
     # and per CTA, in processing order
     assert recs == want
     # the hybrid's owners have exactly one peer (Section 5.2)
-    if info["mode"] == sk.MODES["hybrid"] and info["sk_tiles"] > info["num_sms"]:
+    if info["mode"] == sk.MODES["hybrid"] and info["sk_tiles"] > info["num_sms"] // info["cluster_m"]:
         assert all(r[8] - r[7] == 0 for r in recs if r[6] == S.ROLE_OWNER)
     prob.check(C, 1.0, 0.0, f"traced {mode}")
 
