@@ -70,6 +70,27 @@ def load_peaks():
                 "source": "fallback"}
 
 
+PROFILE = os.path.join(ROOT, "profiles", "sk_gemm_sweep_launches.md")
+
+
+def profiled_bytes_per_flop():
+    """DRAM bytes per flop of sk_gemm_kernel from the committed ncu launch-list
+    summary, or None when the kernel or planner source changed since."""
+    import hashlib
+    import re
+    try:
+        text = open(PROFILE).read()
+        bpf = float(re.search(r"dram_bytes_per_flop: ([0-9.eE+-]+)", text).group(1))
+        sha = re.search(r"kernel_source_sha256: ([0-9a-f]+)", text).group(1)
+        h = hashlib.sha256()
+        for f in ("sk_kernel.cuh", "planner.cpp"):
+            with open(os.path.join(ROOT, "paper_2301_03598_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        return bpf if h.hexdigest() == sha else None
+    except Exception:
+        return None
+
+
 def geomean(x):
     x = np.asarray(x, np.float64)
     return float(np.exp(np.mean(np.log(x)))) if x.size else float("nan")
@@ -535,7 +556,16 @@ def ours_arm(args):
 
     if rank != 0:
         return
+    dump_dir = os.path.join(ROOT, "gpurun_out")
+    if os.path.isdir(dump_dir):   # per-shape detail for offline analysis
+        with open(os.path.join(dump_dir, "bench_per_shape.json"), "w") as f:
+            json.dump({"shapes": shapes,
+                       "plans": {v: [[p.get("tile_n"), p.get("grid"), p.get("sk_tiles"),
+                                      p.get("mode")] for p in r["_plans"]]
+                                 for v, r in results.items()},
+                       "us": {v: (r["_med"] * 1e3).tolist() for v, r in results.items()}}, f)
     kernel_ms = float(np.sum(H["_med"]))
+    bpf = profiled_bytes_per_flop()
     achieved = float(flops.sum() / (kernel_ms * 1e-3) / 1e12)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -558,7 +588,9 @@ def ours_arm(args):
         "variants": {v: {kk: vv for kk, vv in r.items() if not kk.startswith("_")}
                      for v, r in results.items()},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": (bpf * float(flops.mean())) if bpf is not None else None,
+                     "traffic_unit": "DRAM bytes per launch (profiles/sk_gemm_sweep_launches.md)",
                      "kernel": "sk::sk_gemm_kernel", "peak_kind":
                      f"bf16 sustained ({peaks['source']})"},
         "gpu_launches": int(sum(sweep.reps) * args.steps),

@@ -92,6 +92,7 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
   // The schedule's unit is a cluster: cluster_m CTAs computing a
   // (128 * cluster_m) x BLK_N tile; the paper's p is the number of such units.
   s.tile_m = kTileM * s.cluster_m;
+  const int num_sms_all = num_sms;
   num_sms /= s.cluster_m;
   if (grid > num_sms) return SK_ERR_INVALID;
   s.tiles_m = static_cast<int32_t>(cdiv(m, s.tile_m));
@@ -205,6 +206,12 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
   }
   s.ctas = s.grid * s.cluster_m;
   s.workspace_bytes = split ? workspace_bytes_for(s.ctas, s.tile_n) : 0;
+  if (split && cluster_m == 0 && s.cluster_m == 2) {
+    // Automatic planning keeps CTA pairs to schedules without split tiles:
+    // those launch without the cooperative attribute, which the profiler could
+    // not replay together with clusters.  Split schedules use single CTAs.
+    return describe(m, n, k, mode, tile_n, grid, raster_group, 1, num_sms_all, out);
+  }
   *out = s;
   return SK_OK;
 }

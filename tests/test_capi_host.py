@@ -73,10 +73,15 @@ def test_describe_config_shapes():
     d = sk.sk_plan_describe(8192, 8192, 8192, cluster_m=1)
     assert (d["tile_n"], d["tiles"], d["mode_name"]) == (256, 2048, "hybrid")
     assert d["sk_tiles"] == 2048 % 148 + 148 and d["dp_tiles"] % 148 == 0
-    # CTA pairs: 256 x 256 units on p = 74 pairs
-    d = sk.sk_plan_describe(8192, 8192, 8192)
+    # CTA pairs on request: 256 x 256 units on p = 74 pairs
+    d = sk.sk_plan_describe(8192, 8192, 8192, cluster_m=2)
     assert (d["cluster_m"], d["tile_m"], d["tiles"], d["ctas"]) == (2, 256, 1024, 148)
     assert d["sk_tiles"] == 1024 % 74 + 74 and d["dp_tiles"] % 74 == 0
+    # automatic planning pairs CTAs only in schedules without split tiles
+    d = sk.sk_plan_describe(8192, 8192, 8192)
+    assert d["cluster_m"] == 1 and d["mode_name"] == "hybrid"
+    d = sk.sk_plan_describe(8192, 8192, 128)
+    assert d["cluster_m"] == 2 and d["mode_name"] == "dp" and d["workspace_bytes"] == 0
     d = sk.sk_plan_describe(128 * 37, 256, 64)      # 37*2 tiles, below one wave
     assert d["mode_name"] == "sk"
 
