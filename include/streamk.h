@@ -226,11 +226,11 @@ int sk_grid_model(int64_t m, int64_t n, int64_t k, int bm, int bn, int bk, int p
  *
  * No plan, no cudaMalloc/cudaFree and no allocating library call: the
  * schedule is planned on the host stack for this call, with BLK_N = 128, and
- * the fixup scratch (flags, status words and up to 12 MiB - 8 KiB of FP32
- * partial tiles) is one fixed 12 MiB device array inside the library, which
- * every GPU that loads the library keeps until the process exits.  A schedule
- * that would need more partial-tile scratch than that (more than 191 CTAs)
- * returns SK_ERR_INVALID.
+ * the fixup scratch (128 KiB of flags, status words and up to 12 MiB - 132 KiB
+ * of FP32 partial tiles) is one fixed 12 MiB device array inside the library,
+ * which every GPU that loads the library keeps until the process exits.  A
+ * schedule that would need more partial-tile scratch than that (more than 189
+ * CTAs) returns SK_ERR_INVALID.
  *
  *   A: m x k row-major, lda >= k; B: k x n column-major (an n x k row-major
  *   array), ldb >= k; both device pointers 16-byte aligned with lda*2 and

@@ -8,10 +8,12 @@ namespace sk {
 
 constexpr int kTileM = 128;
 constexpr int kTileK = 64;
-// Workspace layout: kFlagBytes of flags (one uint32 per CTA, at most
-// kMaxGrid CTAs) at offset 0, then one BLK_M x BLK_N FP32 partial slot per CTA.
+// Workspace layout: kFlagBytes of flags at offset 0 (kFlagsPerCta uint32 per
+// CTA, one per 32-row x 128-byte unit of its partial tile, at most kMaxGrid
+// CTAs), then one BLK_M x BLK_N FP32 partial slot per CTA.
 constexpr int kMaxGrid = 1024;
-constexpr int64_t kFlagBytes = kMaxGrid * 4;
+constexpr int kFlagsPerCta = 32;
+constexpr int64_t kFlagBytes = static_cast<int64_t>(kMaxGrid) * kFlagsPerCta * 4;
 
 int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
              int cluster_m, int num_sms, sk_schedule_info* out);

@@ -13,6 +13,10 @@ constexpr int kRoleWhole = 0;    // tile_started && tile_ended: store the tile
 constexpr int kRolePartial = 1;  // !tile_started: spill FP32 partials, then Signal
 constexpr int kRoleOwner = 2;    // tile_started && !tile_ended: Wait peers, fix up, store
 
+// Fixup flags per CTA: one per (TMEM lane quarter, output unit) of its
+// partial tile, so the owner can consume a unit as soon as it is written.
+constexpr int kFlagsPerCtaDev = 32;
+
 constexpr int kTraceFields = 9;  // cta, tile, tm, tn, kb0, kb1, role, peer_first, peer_last
 // Trace layout per CTA: a header of kTraceHeaderInts int32 (record count,
 // reserved, u64 global-timer ns at kernel start) then records of

@@ -101,7 +101,7 @@ __device__ __forceinline__ bool wait_flag(const uint32_t* flag, volatile int* ab
   if (ld_acquire_gpu(flag) == a.epoch) return true;
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t i = 1;; ++i) {
-    __nanosleep(64);
+    if (i > 256) __nanosleep(64);  // spin tightly first: the peer is usually about to publish
     if (ld_acquire_gpu(flag) == a.epoch) return true;
     if ((i & 31u) == 0) {
       if (*abort_flag) return false;
@@ -536,12 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (epi_any(fail)) break;
       tc_fence_after();
       const uint64_t t_acc = tracer ? globaltimer_ns() : 0;
-      if (role == kRoleOwner) {
-        for (int y = peer_first; y <= peer_last && !fail; y += CM)
-          fail = !wait_flag(&a.flags[y], abort_flag, a);
-        if (epi_any(fail)) break;
-      }
-      const uint64_t t_fix = tracer ? globaltimer_ns() : 0;
+      uint64_t t_fix = t_acc;
 
       const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(acc * BN);
       const int grow = tm * kBlkM + row;
@@ -581,21 +576,38 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int j = 0; j < 32; ++j) v[cc][j] = __uint_as_float(r[cc * 32 + j]);
         }
         const int cvalid = min(kCpu, nchunks - u * kCpu);  // 32-column chunks inside n
-        // Workspace slot layout: [chunk][j][row] float4, so a warp's 16-byte
-        // accesses are contiguous.
+        // Workspace slot layout: [chunk][quarter][j][lane] float4, so the 32
+        // rows x 32 columns of a (chunk, quarter) are one contiguous 4 KiB block.
         if (role == kRolePartial) {
 #pragma unroll
           for (int cc = 0; cc < kCpu; ++cc) {
             if (cc >= cvalid) break;
-            float4* dst = reinterpret_cast<float4*>(my_slot) + ((u * kCpu + cc) * 8) * kBlkM + row;
+            float4* dst =
+                reinterpret_cast<float4*>(my_slot) + ((u * kCpu + cc) * 4 + quarter) * 256 + lane;
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-              __stcg(dst + j * kBlkM, make_float4(v[cc][4 * j], v[cc][4 * j + 1], v[cc][4 * j + 2],
-                                                  v[cc][4 * j + 3]));
+              __stcg(dst + j * 32, make_float4(v[cc][4 * j], v[cc][4 * j + 1], v[cc][4 * j + 2],
+                                               v[cc][4 * j + 3]));
+          }
+          // Signal(flags[cta][quarter][u]): this warp's part of the partial is
+          // written; the release is cumulative over the warp's stores.
+          __syncwarp();
+          if (lane == 0 && cta != a.debug_skip_signal) {
+            __threadfence();
+            st_release_gpu(&a.flags[cta * kFlagsPerCtaDev + quarter * 8 + u], a.epoch);
           }
           continue;
         }
         if (role == kRoleOwner) {
+          // Wait(flags[y][quarter][u]) for every peer y: the unit this warp
+          // adds next, so the fixup overlaps the peers' remaining spills.
+          for (int y = peer_first; y <= peer_last && !fail; y += CM)
+            fail = !wait_flag(&a.flags[y * kFlagsPerCtaDev + quarter * 8 + u], abort_flag, a);
+          if (__any_sync(0xffffffffu, fail)) {
+            fail = true;
+            break;
+          }
+          if (tracer && u == col_half) t_fix = globaltimer_ns();
           // acc + P[x+1] + P[x+2] + ... in increasing CTA order; two peers'
           // loads are in flight at a time.
 #pragma unroll
@@ -605,15 +617,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int y = peer_first; y <= peer_last; y += 2 * CM) {
               const float4* s0 = reinterpret_cast<const float4*>(
                                      a.partials + static_cast<size_t>(y) * (kBlkM * BN)) +
-                                 (c * 8) * kBlkM + row;
+                                 (c * 4 + quarter) * 256 + lane;
               const bool two = y + CM <= peer_last;
               const float4* s1 = two ? s0 + CM * (kBlkM * BN) / 4 : s0;
               float4 p0[8], p1[8];
 #pragma unroll
-              for (int j = 0; j < 8; ++j) p0[j] = __ldcg(s0 + j * kBlkM);
+              for (int j = 0; j < 8; ++j) p0[j] = __ldcg(s0 + j * 32);
               if (two) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) p1[j] = __ldcg(s1 + j * kBlkM);
+                for (int j = 0; j < 8; ++j) p1[j] = __ldcg(s1 + j * 32);
               }
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
@@ -677,17 +689,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           bulk_commit_group();
         }
       }
-      if (role == kRolePartial) {
-        // Signal(flags[x]): all 128 threads' partial stores before the release.
-        __threadfence();
-        named_bar_sync(kEpiBarrier, kEpiThreads);
-        if (warp == kEpiWarp0 && lane == 0 && cta != a.debug_skip_signal)
-          st_release_gpu(&a.flags[cta], a.epoch);
-      } else if (role == kRoleOwner && warp == kEpiWarp0 && lane == 0) {
-        // Every partial has exactly one consumer: clear the peers' flags so the
-        // next launch (even a graph replay carrying the same epoch) starts clean.
-        // All epilogue threads passed their Waits before the last vote.
-        for (int y = peer_first; y <= peer_last; y += CM) a.flags[y] = 0u;
+      if (epi_any(fail)) break;
+      if (role == kRoleOwner && lane == 0) {
+        // Every unit flag has exactly one consumer, this warp: clear the ones
+        // it consumed so the next launch (even a graph replay carrying the
+        // same epoch) starts clean.
+        for (int u = col_half; u < nunits; u += 2)
+          for (int y = peer_first; y <= peer_last; y += CM)
+            a.flags[y * kFlagsPerCtaDev + quarter * 8 + u] = 0u;
       }
       if (tracer) {
         const uint64_t t_done = globaltimer_ns();
