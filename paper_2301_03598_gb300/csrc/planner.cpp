@@ -35,21 +35,22 @@ int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]) {
 }
 
 // Model constants of Appendix A.1 for this kernel family on GB300, in
-// microseconds, fitted by least squares to measured times of basic Stream-K
-// over grid sizes g in [t, p] (12 shapes with t < p, each tile width): a =
-// fixed per-launch cost, b = a CTA spilling partial sums, c = one MAC-loop
-// iteration (BLK_M x BLK_N x 64), d = reading and adding one peer's partials.
+// microseconds, fitted by relative least squares to measured times of basic
+// Stream-K over grid sizes g in [t, p] for 70 shapes drawn like the
+// log-uniform shape sweep (t < p), each tile width: a = fixed per-launch
+// cost, b = a CTA spilling partial sums, c = one MAC-loop iteration
+// (BLK_M x BLK_N x 64), d = reading and adding one peer's partials.
 void model_coefficients(int tile_n, double out[4]) {
   if (tile_n == 256) {
-    out[0] = 4.71;
-    out[1] = 6.53;
-    out[2] = 0.263;
-    out[3] = 1.075;
+    out[0] = 5.45;
+    out[1] = 4.10;
+    out[2] = 0.295;
+    out[3] = 1.719;
   } else {
-    out[0] = 6.11;
-    out[1] = 0.85;
-    out[2] = 0.256;
-    out[3] = 0.873;
+    out[0] = 5.51;
+    out[1] = 1.68;
+    out[2] = 0.261;
+    out[3] = 0.943;
   }
 }
 

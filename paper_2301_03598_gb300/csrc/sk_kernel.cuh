@@ -689,7 +689,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           bulk_commit_group();
         }
       }
-      if (epi_any(fail)) break;
+      // Only owners wait inside the segment; their failure decision must be
+      // the same in every epilogue warp.
+      if (role == kRoleOwner && epi_any(fail)) break;
       if (role == kRoleOwner && lane == 0) {
         // Every unit flag has exactly one consumer, this warp: clear the ones
         // it consumed so the next launch (even a graph replay carrying the

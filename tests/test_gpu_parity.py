@@ -190,3 +190,67 @@ def test_invalid_arguments_on_device():
     assert e.value.status == sk.SK_ERR_UNSUPPORTED
     with pytest.raises(sk.StreamKError):
         sk.sk_plan(64, 64, 64, a_layout="col")
+
+
+def _sampled_check(m, n, k, alpha, beta, mode, seed, attrs=None, samples=4096):
+    """A full-size GEMM on the device, checked on a seeded sample of entries plus
+    whole rows and columns along tile edges (where Stream-K seams and ragged
+    tiles are), against the oracle computed entry by entry."""
+    import numpy as np
+    import oracle
+    from gemm_check import bound, check_bound
+    from paper_2301_03598_gb300 import inputs, streamk as sk
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    A = torch.randn(m, k, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(n, k, device="cuda", generator=g).to(torch.bfloat16)
+    C = torch.randn(m, n, device="cuda", generator=g).to(torch.bfloat16)
+    Cin = C.clone()
+    plan = sk.sk_plan(m, n, k, "bf16", "bf16", "bf16", "f32", "row", "col", "row", mode)
+    try:
+        for key, v in (attrs or {}).items():
+            plan.set(key, v)
+        info = plan.info()
+        sk.sk_gemm(plan, A, B, C, alpha, beta)
+        st, dev = sk.sk_last_error(plan)
+        assert st == sk.SK_OK, (st, dev)
+    finally:
+        plan.destroy()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rows = list(rng.integers(0, m, size=samples))
+    cols = list(rng.integers(0, n, size=samples))
+    for r in sorted({0, 127, 128, 255, 256, m - 1} & set(range(m))):   # seams along m
+        cs = rng.integers(0, n, size=64)
+        rows += [r] * len(cs)
+        cols += list(cs)
+    for c in sorted({0, 127, 128, 255, 256, n - 1} & set(range(n))):   # seams along n
+        rs = rng.integers(0, m, size=64)
+        rows += list(rs)
+        cols += [c] * len(rs)
+    rows = np.array(rows, np.int64)
+    cols = np.array(cols, np.int64)
+    ur, ri = np.unique(rows, return_inverse=True)
+    uc, ci = np.unique(cols, return_inverse=True)
+    A64 = inputs.widen(A[torch.from_numpy(ur).cuda()].cpu())
+    B64 = inputs.widen(B[torch.from_numpy(uc).cuda()].cpu())
+    C64in = inputs.widen(Cin[torch.from_numpy(ur).cuda()][:, torch.from_numpy(uc).cuda()].cpu())
+    want, absAB = oracle.gemm_entries(ri, ci, A64, B64.T, alpha, beta, C64in)
+    got = inputs.widen(C.cpu())[rows, cols]
+    cin = C64in[ri, ci]
+    check_bound(got, want, bound(k, alpha, beta, absAB, want, cin, "bf16"),
+                f"{m}x{n}x{k} {mode} sampled ({info['mode']}, tile_n {info['tile_n']}, g {info['grid']})")
+
+
+# The extreme-quantisation workloads at full size: BF16 in, FP32 accumulate,
+# BF16 out, alpha = 1, beta = 0.5 with random C (sampled entries).
+@pytest.mark.parametrize("m,n,k", [(8192, 8192, 8192), (256, 256, 65536), (8192, 128, 4096),
+                                   (1536, 1536, 1536), (1664, 1664, 1664)])
+@pytest.mark.parametrize("mode", ["auto", "dp", "sk"])
+def test_extreme_shapes_full_size_sampled(m, n, k, mode):
+    _sampled_check(m, n, k, 1.0, 0.5, mode, seed=m * 7 + k)
+
+
+@pytest.mark.parametrize("m,n,k,attrs", [(8192, 8192, 8192, {"cluster_m": 2}),
+                                         (4096, 4096, 4096, {"cluster_m": 2, "raster_group": 4})])
+def test_large_pairs_full_size_sampled(m, n, k, attrs):
+    _sampled_check(m, n, k, 1.0, 0.5, "hybrid", seed=11, attrs=attrs)
