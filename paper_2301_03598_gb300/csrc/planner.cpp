@@ -150,9 +150,10 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
           // The two-tile hybrid pays one spill and one fixup per split tile;
           // with few iterations per tile that can cost more than the partial
           // wave it removes.  Compare both with the model's terms: the spill
-          // and fixup are exposed when no data-parallel wave follows the
-          // Stream-K region (w == 1) and mostly hidden behind it otherwise.
-          const double split_us = (coef[1] + coef[3]) * (w == 1 ? 1.0 : 0.1);
+          // and fixup overlap the (w - 1) data-parallel tiles that follow the
+          // Stream-K region, and whatever those do not cover is exposed.
+          const double split_us = std::max(
+              0.0, coef[1] + coef[3] - coef[2] * static_cast<double>((w - 1) * ipt));
           const double dp_us = coef[0] + coef[2] * static_cast<double>(ipt * ((t + p - 1) / p));
           const double sk_us =
               coef[0] + split_us + coef[2] * static_cast<double>((t * ipt + p - 1) / p);
