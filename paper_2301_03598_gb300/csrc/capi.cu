@@ -188,14 +188,14 @@ bool encode_output(CUtensorMap* tm, void* ptr, int c_type, int64_t rows, int64_t
 
 // tcgen05 kind::f16 instruction descriptor: FP32 accumulator, A/B format,
 // both operands K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-uint32_t make_idesc(int in_dtype, int tile_n) {
+uint32_t make_idesc(int in_dtype, int tile_n, int cluster_m) {
   const uint32_t fmt = in_dtype == SK_BF16 ? 1u : 0u;
   uint32_t d = 0;
   d |= 1u << 4;                                         // D: F32
   d |= fmt << 7;                                        // A: F16 / BF16
   d |= fmt << 10;                                       // B: F16 / BF16
   d |= static_cast<uint32_t>(tile_n >> 3) << 17;        // N
-  d |= static_cast<uint32_t>(sk::kBlkM >> 4) << 24;     // M
+  d |= static_cast<uint32_t>((sk::kBlkM * cluster_m) >> 4) << 24;  // M (256 for a CTA pair)
   return d;
 }
 
@@ -272,7 +272,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   a.grid = s.grid;
   a.sk_q = static_cast<int32_t>(s.sk_iters / s.grid);
   a.sk_r = static_cast<int32_t>(s.sk_iters % s.grid);
-  a.idesc = make_idesc(p->a_type, s.tile_n);
+  a.idesc = make_idesc(p->a_type, s.tile_n, s.cluster_m);
   a.C = C;
   a.ldc = p->ldc;
   a.c_vec = (p->ldc * static_cast<int64_t>(dtype_size(p->c_type))) % 16 == 0 ? 1 : 0;
@@ -677,7 +677,7 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     a.grid = s.grid;
     a.sk_q = static_cast<int32_t>(s.sk_iters / s.grid);
     a.sk_r = static_cast<int32_t>(s.sk_iters % s.grid);
-    a.idesc = make_idesc(ab_type, 128);
+    a.idesc = make_idesc(ab_type, 128, 1);
     a.C = C;
     a.ldc = ldc;
     a.c_vec = (ldc * static_cast<int64_t>(dtype_size(c_type))) % 16 == 0 ? 1 : 0;

@@ -15,7 +15,7 @@ static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(args.grid * CM));
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = Cfg<128>::kSmemBytes;
+  cfg.dynamicSmemBytes = Cfg<128, CM>::kSmemBytes;
   cfg.stream = stream;
   cudaLaunchAttribute attr[3];
   unsigned na = 0;
@@ -67,7 +67,7 @@ cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, cons
 template <int CM, typename TC>
 static cudaError_t set_smem() {
   return cudaFuncSetAttribute(sk_gemm_kernel<128, CM, TC>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128>::kSmemBytes);
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128, CM>::kSmemBytes);
 }
 
 cudaError_t prepare_bn128(size_t* smem_bytes) {
@@ -78,7 +78,8 @@ cudaError_t prepare_bn128(size_t* smem_bytes) {
   if ((e = set_smem<2, float>()) != cudaSuccess) return e;
   if ((e = set_smem<2, __nv_bfloat16>()) != cudaSuccess) return e;
   if ((e = set_smem<2, __half>()) != cudaSuccess) return e;
-  *smem_bytes = static_cast<size_t>(Cfg<128>::kSmemBytes);
+  static_assert(Cfg<128, 1>::kSmemBytes == Cfg<128, 2>::kSmemBytes, "one size for both");
+  *smem_bytes = static_cast<size_t>(Cfg<128, 1>::kSmemBytes);
   return cudaSuccess;
 }
 

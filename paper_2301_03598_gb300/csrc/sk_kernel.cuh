@@ -6,13 +6,13 @@
 // sk_tiles tiles followed by full data-parallel waves).  The schedule is a pure
 // function of (blockIdx.x, SkArgs) that all three warp roles walk in lockstep.
 //
-// Roles (192 threads, one CTA per SM):
+// Roles (320 threads, one CTA per SM):
 //   warp 0      TMA producer: streams the A and B fragments of every MAC-loop
 //               iteration (Algorithm 3's LoadFragment) into an S-stage ring of
 //               128-byte-swizzled shared-memory tiles.
 //   warp 1      TMEM allocator and MMA issuer: one thread issues BLK_K/16
 //               tcgen05.mma per iteration into one of two TMEM accumulators.
-//   warps 2..5  epilogue: per tile segment, either spill the FP32 partial sums
+//   warps 2..9  epilogue: per tile segment, either spill the FP32 partial sums
 //               to this CTA's workspace slot and Signal (segment does not start
 //               the tile), or Wait for the contributing CTAs in increasing order
 //               and add their partials (tile started here, not finished here),
@@ -37,19 +37,13 @@ constexpr int kEpiWarp0 = 2;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 
-#ifndef SK_STAGES_BN128
-#define SK_STAGES_BN128 6
-#endif
-#ifndef SK_STAGES_BN256
-#define SK_STAGES_BN256 4
-#endif
-
-template <int BN>
+// Shared-memory stage ring per CTA: 192 KiB of operand stages.
+template <int BN, int CM>
 struct Cfg {
-  static constexpr int kStages = (BN == 256) ? SK_STAGES_BN256 : SK_STAGES_BN128;
-  static constexpr int kABytes = kBlkM * kBlkK * 2;
-  static constexpr int kBBytes = BN * kBlkK * 2;
+  static constexpr int kABytes = kBlkM * kBlkK * 2;       // this CTA's 128 rows of A
+  static constexpr int kBBytes = (BN / CM) * kBlkK * 2;   // this CTA's BN/CM rows of B
   static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kStages = (192 * 1024) / kStageBytes;  // 6, 4 (single); 8, 6 (pair)
   static constexpr int kTmemCols = 2 * BN;  // two FP32 accumulators of BN columns
   // Output staging for TMA stores: per epilogue warp one buffer of 32 rows x
   // 128 B, 128-byte swizzled (1 KiB aligned).
@@ -322,15 +316,17 @@ __device__ __forceinline__ void add_beta_c(const SkArgs& a, int grow, int gcol, 
 }
 
 // CM = CTAs per cluster along M (1 or 2).  With CM = 2 the two CTAs of a
-// cluster compute the two 128-row halves of a 256 x BN tile: the schedule's
-// unit is that tile and its CTA pair, each CTA loads its own A rows and half
-// of the B tile, multicasting that half to both CTAs.
+// cluster form a tcgen05 CTA pair computing one 256 x BN tile: the schedule's
+// unit is that tile.  Each CTA loads its own 128 rows of A and BN/2 rows of B
+// per k-block, the even CTA issues the pair MMAs (M = 256), and each CTA's
+// TMEM receives its own 128 rows of the accumulator, which its epilogue
+// spills, fixes up and stores exactly as a single CTA does.
 template <int BN, int CM, typename TC>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ SkArgs a) {
   static_assert(CM == 1 || CM == 2, "cluster size along M");
-  using C_ = Cfg<BN>;
+  using C_ = Cfg<BN, CM>;
   constexpr int S = C_::kStages;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -353,16 +349,29 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int cta = blockIdx.x;                                 // this CTA (flags, partials, trace)
   const int rank = CM == 2 ? static_cast<int>(cluster_ctarank()) : 0;
   const int x = cta / CM;                                     // schedule unit (CTA pair)
+  constexpr bool kPair = CM == 2;
   constexpr uint16_t kPairMask = 0x3;
+  // In a pair the even CTA's full and acce barriers gather both CTAs: the
+  // shared::cluster addresses of the even CTA's copies.
+  const uint32_t full0 = kPair ? mapa_shared(full_bar(0), 0) : full_bar(0);
+  const uint32_t acce0 = kPair ? mapa_shared(acce_bar(0), 0) : acce_bar(0);
+  const bool issuer = !kPair || rank == 0;  // this CTA issues the MMAs
+  // An epilogue warp has read accumulator b: tell the issuer it may reuse it.
+  auto release_acc = [&](int b) {
+    if constexpr (kPair)
+      mbar_arrive_cluster(acce0 + 8u * b);
+    else
+      mbar_arrive(acce_bar(b));
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), CM);  // released by the MMA of every CTA that reads the stage
+      mbar_init(full_bar(s), 1);   // the issuer's producer arrives with both CTAs' bytes
+      mbar_init(empty_bar(s), 1);  // released by the issuer's commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf_bar(b), 1);
-      mbar_init(acce_bar(b), kEpiWarps);
+      mbar_init(acce_bar(b), CM * kEpiWarps);  // every epilogue warp of the pair
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -374,16 +383,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (a.c_tma) tma_prefetch_desc(&tmC);
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), C_::kTmemCols);
-    tmem_relinquish();
+    if constexpr (kPair) {
+      tmem_alloc_pair(smem_u32(tmem_slot), C_::kTmemCols);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_slot), C_::kTmemCols);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (CM == 2) cluster_sync();  // the peer's barriers exist before any multicast
+  if constexpr (kPair) cluster_sync();  // both CTAs' barriers exist before either signals them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // Everything above overlaps the previous kernel under programmatic
-  // dependent launch; global memory is touched only after this point.
+  // dependent launch; nothing is loaded into shared memory or written to
+  // global memory before this point.
   grid_dependency_wait();
 
   if (warp == 0) {
@@ -405,13 +420,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(full_bar(stage), C_::kStageBytes);
-          tma_load_2d(stage_a(stage), &tmA, full_bar(stage), kb * kBlkK, tm * kBlkM);
-          if constexpr (CM == 2) {
-            // this CTA's half of the B tile, into both CTAs of the pair
-            tma_load_2d_multicast(stage_b(stage) + static_cast<uint32_t>(rank * (BN / 2) * 128), &tmB,
-                                  full_bar(stage), kb * kBlkK, tn * BN + rank * (BN / 2), kPairMask);
+          if constexpr (kPair) {
+            // this CTA's A rows and half of the B tile, completing on the
+            // issuer's full barrier, which expects both CTAs' bytes
+            const uint32_t fb = full0 + 8u * stage;
+            if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C_::kStageBytes);
+            tma_load_2d_pair(stage_a(stage), &tmA, fb, kb * kBlkK, tm * kBlkM);
+            tma_load_2d_pair(stage_b(stage), &tmB, fb, kb * kBlkK, tn * BN + rank * (BN / 2));
           } else {
+            mbar_arrive_expect_tx(full_bar(stage), C_::kStageBytes);
+            tma_load_2d(stage_a(stage), &tmA, full_bar(stage), kb * kBlkK, tm * kBlkM);
             tma_load_2d(stage_b(stage), &tmB, full_bar(stage), kb * kBlkK, tn * BN);
           }
           ++issued;
@@ -432,19 +450,29 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       } else {
-        // Unwind: let the loads already issued land before shared memory goes away.
-        const int64_t first = issued > S ? issued - S : 0;
-        for (int64_t j = first; j < issued; ++j) {
-          const int s = static_cast<int>(j % S);
-          const uint32_t par = static_cast<uint32_t>((j / S) & 1);
-          const uint64_t t0 = globaltimer_ns();
-          while (!mbar_try_wait(full_bar(s), par) && globaltimer_ns() - t0 < a.timeout_ns) {
+        // Unwind: let the loads already issued land before shared memory
+        // goes away.  They complete within microseconds; the waits share one
+        // bound.  A pair's odd CTA cannot observe its loads (they complete on
+        // the even CTA's barriers), so it waits out a fixed interval.
+        constexpr uint64_t kUnwindNs = 1000000;
+        const uint64_t t0 = globaltimer_ns();
+        if (issuer) {
+          const int64_t first = issued > S ? issued - S : 0;
+          for (int64_t j = first; j < issued; ++j) {
+            const int s = static_cast<int>(j % S);
+            const uint32_t par = static_cast<uint32_t>((j / S) & 1);
+            while (!mbar_try_wait(full_bar(s), par) && globaltimer_ns() - t0 < kUnwindNs) {
+            }
+          }
+        } else {
+          while (globaltimer_ns() - t0 < kUnwindNs / 20) {
           }
         }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && !issuer) grid_launch_dependents();  // a pair's odd CTA issues nothing
+    if (lane == 0 && issuer) {
       // ------------------------------------------------------------ MMA issuer
       Walker w;
       w.init(a, x);
@@ -467,12 +495,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int kk = 0; kk < kBlkK / 16; ++kk) {
             // advance 16 elements (32 B) along K inside the swizzle atom
-            mma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
-                    (kb > kb0 || kk > 0) ? 1u : 0u);
+            if constexpr (kPair)
+              mma_f16_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
+                           (kb > kb0 || kk > 0) ? 1u : 0u);
+            else
+              mma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
+                      (kb > kb0 || kk > 0) ? 1u : 0u);
           }
           // frees the stage (in both CTAs of a pair) once these MMAs finish
-          if constexpr (CM == 2)
-            mma_commit_multicast(empty_bar(stage), kPairMask);
+          if constexpr (kPair)
+            mma_commit_pair_multicast(empty_bar(stage), kPairMask);
           else
             mma_commit(empty_bar(stage));
           if (++stage == S) {
@@ -481,7 +513,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (!ok) break;
-        mma_commit(accf_bar(acc));  // accumulator complete
+        // accumulator complete (in both CTAs' TMEM for a pair)
+        if constexpr (kPair)
+          mma_commit_pair_multicast(accf_bar(acc), kPairMask);
+        else
+          mma_commit(accf_bar(acc));
         acc ^= 1;
         if (acc == 0) acc_phase ^= 1u;
       }
@@ -489,7 +525,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       // (it runs its prologue and then waits for this grid to complete).
       grid_launch_dependents();
       // Drain: every MMA issued above completes before TMEM is released.
-      mma_commit(drain_bar);
+      if constexpr (kPair)
+        mma_commit_pair_multicast(drain_bar, 0x1);
+      else
+        mma_commit(drain_bar);
       const uint64_t t0 = globaltimer_ns();
       while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < a.timeout_ns) {
       }
@@ -551,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (my_last_unit < 0) {
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(acce_bar(acc));
+        if (lane == 0) release_acc(acc);
       }
 #pragma unroll 1
       for (int u = col_half; u < nunits; u += 2) {
@@ -568,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // all of this warp's TMEM reads are done: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acce_bar(acc));
+            if (lane == 0) release_acc(acc);
           }
 #pragma unroll
           for (int cc = 0; cc < kCpu; ++cc)
@@ -726,20 +765,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1u;
     }
-    // The output tiles must be written before the kernel ends.
-    if (lane == 0) bulk_wait_group<0>();
+    // The staging buffers are read before the CTA's shared memory goes away;
+    // the global writes themselves complete with the grid.
+    if (lane == 0) bulk_wait_group_read<0>();
     __syncwarp();
   }
 
   __syncwarp();  // reconverge the producer / MMA warps (one lane worked)
   tc_fence_before();
   __syncthreads();
-  // Neither CTA of a pair leaves while the other may still multicast into it
-  // or arrive on its barriers.
-  if constexpr (CM == 2) cluster_sync();
+  // Neither CTA of a pair leaves while the other may still signal its
+  // barriers; the issuer's drain above covers every pair MMA writing the odd
+  // CTA's TMEM.
+  if constexpr (kPair) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, C_::kTmemCols);
+    if constexpr (kPair)
+      tmem_dealloc_pair(tmem_base, C_::kTmemCols);
+    else
+      tmem_dealloc(tmem_base, C_::kTmemCols);
   }
 }
 
