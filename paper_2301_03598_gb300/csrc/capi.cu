@@ -186,6 +186,20 @@ bool encode_output(CUtensorMap* tm, void* ptr, int c_type, int64_t rows, int64_t
   return r == CUDA_SUCCESS;
 }
 
+// The walk's precomputed divisors (see FastDiv in sk_args.h).
+void set_divisors(sk::SkArgs& a, const sk_schedule_info& s) {
+  const int32_t group = std::max(1, s.raster_group);
+  const int32_t nbands = (s.tiles_m + group - 1) / group;
+  const int32_t rows_last = std::max(1, s.tiles_m - (nbands - 1) * group);
+  a.div_ipt = sk::make_fastdiv(static_cast<uint32_t>(std::max(1, s.iters_per_tile)));
+  a.div_q1 = sk::make_fastdiv(static_cast<uint32_t>(a.sk_q + 1));
+  a.div_q = sk::make_fastdiv(static_cast<uint32_t>(std::max(1, a.sk_q)));
+  a.div_band = sk::make_fastdiv(static_cast<uint32_t>(std::max<int64_t>(1, int64_t(group) * s.tiles_n)));
+  a.div_rows = sk::make_fastdiv(static_cast<uint32_t>(group));
+  a.div_rows_last = sk::make_fastdiv(static_cast<uint32_t>(rows_last));
+  a.fast_iters = s.sk_iters < (int64_t(1) << 31) ? 1 : 0;
+}
+
 // tcgen05 kind::f16 instruction descriptor: FP32 accumulator, A/B format,
 // both operands K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 uint32_t make_idesc(int in_dtype, int tile_n, int cluster_m) {
@@ -272,6 +286,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   a.grid = s.grid;
   a.sk_q = static_cast<int32_t>(s.sk_iters / s.grid);
   a.sk_r = static_cast<int32_t>(s.sk_iters % s.grid);
+  set_divisors(a, s);
   a.idesc = make_idesc(p->a_type, s.tile_n, s.cluster_m);
   a.C = C;
   a.ldc = p->ldc;
@@ -290,11 +305,19 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   a.timeout_ns = p->timeout_ns;
   a.pdl = p->pdl ? 1 : 0;
 
+  // Split schedules need every CTA resident at once.  Single CTAs ask the
+  // launch to guarantee it (cooperative attribute).  Clustered launches go
+  // without it: their grid is at most one CTA per SM and nothing of this
+  // stream can hold an SM while they wait (a preceding kernel finishes on its
+  // own, a following one starts only after every CTA here has started), so
+  // all CTAs become resident; the bounded waits turn anything else into an
+  // error status.
+  const bool cooperative = split && s.cluster_m == 1;
   cudaError_t e = s.tile_n == 256
-                      ? sk::launch_bn256(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, a, split,
-                                         stream)
-                      : sk::launch_bn128(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, a, split,
-                                         stream);
+                      ? sk::launch_bn256(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, a,
+                                         cooperative, stream)
+                      : sk::launch_bn128(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, a,
+                                         cooperative, stream);
   return cuda_status(e);
 }
 
@@ -677,6 +700,7 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     a.grid = s.grid;
     a.sk_q = static_cast<int32_t>(s.sk_iters / s.grid);
     a.sk_r = static_cast<int32_t>(s.sk_iters % s.grid);
+    set_divisors(a, s);
     a.idesc = make_idesc(ab_type, 128, 1);
     a.C = C;
     a.ldc = ldc;

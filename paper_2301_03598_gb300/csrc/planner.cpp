@@ -34,48 +34,90 @@ int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]) {
   return best;
 }
 
-// Model constants of Appendix A.1 for this kernel family on GB300, in
-// microseconds, fitted by relative least squares to measured times of basic
-// Stream-K over grid sizes g in [t, p] for 70 shapes drawn like the
-// log-uniform shape sweep (t < p), each tile width: a = fixed per-launch
-// cost, b = a CTA spilling partial sums, c = one MAC-loop iteration
-// (BLK_M x BLK_N x 64), d = reading and adding one peer's partials.
-void model_coefficients(int tile_n, double out[4]) {
-  if (tile_n == 256) {
-    out[0] = 5.45;
-    out[1] = 4.10;
-    out[2] = 0.295;
-    out[3] = 1.719;
-  } else {
-    out[0] = 5.51;
-    out[1] = 1.68;
-    out[2] = 0.261;
-    out[3] = 0.943;
-  }
+// Model constants for this kernel family on GB300, in microseconds, per tile
+// configuration (BLK_N, CTAs per cluster along M).  The first four are the
+// terms of Appendix A.1: a = fixed per-launch cost, b = a schedule with split
+// tiles (spill, signal, wait), c = one MAC-loop iteration of a unit
+// (BLK_M x BLK_N x 64), d = reading and adding one more peer's partials.  The
+// fifth, e, is the per-segment cost (one accumulator through the epilogue),
+// which the paper's model folds into c.  Fitted by relative least squares to
+// the measured times of the 2,000-shape log-uniform sweep planned with each
+// configuration forced.
+void model_coefficients(int tile_n, int cluster_m, double out[5]) {
+  static const double k128x1[5] = {3.678, 4.167, 0.2896, 0.585, 0.263};
+  static const double k256x1[5] = {4.456, 6.667, 0.4028, 0.769, 0.131};
+  static const double k128x2[5] = {3.872, 5.024, 0.2864, 0.484, 0.526};
+  static const double k256x2[5] = {5.272, 8.645, 0.3168, 0.235, 0.329};
+  const double* c = cluster_m == 2 ? (tile_n == 256 ? k256x2 : k128x2)
+                                   : (tile_n == 256 ? k256x1 : k128x1);
+  for (int i = 0; i < 5; ++i) out[i] = c[i];
 }
 
-// BLK_N = 256 is the ideal blocking factor for throughput: an M=128 MMA with
-// N=128 takes as long as one with N=256.  When the 128-wide tiling fits in one
-// wave, the extra parallelism of the narrower tile (and its half-size partial
-// sums) measured faster, so it is used there and for outputs of at most 128
-// columns.
-static int auto_tile_n(int64_t m, int64_t n, int64_t /*k*/, int num_sms) {
-  if (n <= 128) return 128;
-  const int64_t t128 = cdiv(m, kTileM) * cdiv(n, 128);
-  return t128 <= num_sms ? 128 : 256;
+// Modelled time of a resolved schedule: the Appendix A.1 terms evaluated on
+// the busiest unit (its Stream-K share plus its data-parallel tiles), plus the
+// per-segment epilogue term.
+static double predict_us(const sk_schedule_info& s, const double c[5]) {
+  const int64_t ipt = s.iters_per_tile, g = std::max<int64_t>(1, s.grid);
+  if (s.tiles == 0 || ipt == 0) return c[0];
+  const int64_t sk_iters = s.sk_tiles * ipt;
+  const int64_t q = sk_iters / g;
+  const int64_t iters_per_unit = cdiv(sk_iters, g) + cdiv(s.dp_tiles, g) * ipt;
+  const double split = s.workspace_bytes > 0 ? 1.0 : 0.0;
+  const int64_t peers = s.sk_tiles ? cdiv(ipt, std::max<int64_t>(q, 1)) : 1;
+  const int64_t segs = (s.sk_tiles ? cdiv(q + 1, ipt) + 1 : 0) + cdiv(s.dp_tiles, g);
+  return c[0] + c[1] * split + c[2] * static_cast<double>(iters_per_unit) +
+         c[3] * static_cast<double>(peers - 1) * split + c[4] * static_cast<double>(segs);
 }
 
-// CTA pairs along M (clusters of 2 sharing the B tile by multicast) halve
-// the L2 -> SM traffic of B; they pay off once the problem fills the GPU with
-// 128 x 256 tiles, and need at least two 128-row blocks.
-static int auto_cluster_m(int64_t m, int64_t n, int tile_n, int num_sms) {
-  const int64_t tm = cdiv(m, kTileM);
-  if (tile_n != 256 || tm < 2 || num_sms < 2) return 1;
-  return tm * cdiv(n, 256) >= num_sms ? 2 : 1;
-}
+static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid,
+                          int raster_group, int cluster_m, int num_sms, sk_schedule_info* out);
 
+// With the tile width or the cluster size left to the planner (0), every
+// candidate configuration is planned and the one the model predicts fastest
+// is kept (ties: the first candidate, i.e. the narrower tile and single CTAs).
 int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
              int cluster_m, int num_sms, sk_schedule_info* out) {
+  if (out == nullptr || num_sms < 1) return SK_ERR_INVALID;
+  if (cluster_m != 0 && cluster_m != 1 && cluster_m != 2) return SK_ERR_UNSUPPORTED;
+  if (tile_n != 0 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  int tns[2], ntn = 0, cms[2], ncm = 0;
+  if (tile_n) {
+    tns[ntn++] = tile_n;
+  } else {
+    tns[ntn++] = 128;
+    if (n > 128) tns[ntn++] = 256;  // a 256-wide tile over <= 128 columns only wastes work
+  }
+  if (cluster_m) {
+    cms[ncm++] = cluster_m;
+  } else {
+    cms[ncm++] = 1;
+    if (m > kTileM && num_sms >= 2) cms[ncm++] = 2;  // a pair needs two 128-row blocks
+  }
+  int status = SK_ERR_INVALID;
+  double best_us = 0.0;
+  for (int i = 0; i < ntn; ++i) {
+    for (int j = 0; j < ncm; ++j) {
+      sk_schedule_info s{};
+      const int st = describe_fixed(m, n, k, mode, tns[i], grid, raster_group, cms[j], num_sms, &s);
+      if (st != SK_OK) {
+        if (status != SK_OK) status = st;
+        continue;
+      }
+      double c[5];
+      model_coefficients(s.tile_n, s.cluster_m, c);
+      const double us = predict_us(s, c);
+      if (status != SK_OK || us < best_us) {
+        *out = s;
+        best_us = us;
+        status = SK_OK;
+      }
+    }
+  }
+  return status;
+}
+
+static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid,
+                          int raster_group, int cluster_m, int num_sms, sk_schedule_info* out) {
   if (out == nullptr || m < 0 || n < 0 || k < 0 || num_sms < 1 || grid < 0 || raster_group < 0)
     return SK_ERR_INVALID;
   if (cluster_m != 0 && cluster_m != 1 && cluster_m != 2) return SK_ERR_UNSUPPORTED;
@@ -88,13 +130,13 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
 
   sk_schedule_info s{};
   s.tile_k = kTileK;
-  s.tile_n = tile_n ? tile_n : auto_tile_n(m, n, k, num_sms);
-  s.cluster_m = cluster_m ? cluster_m : auto_cluster_m(m, n, s.tile_n, num_sms);
+  s.tile_n = tile_n;
+  s.cluster_m = cluster_m;
   // The schedule's unit is a cluster: cluster_m CTAs computing a
   // (128 * cluster_m) x BLK_N tile; the paper's p is the number of such units.
   s.tile_m = kTileM * s.cluster_m;
-  const int num_sms_all = num_sms;
   num_sms /= s.cluster_m;
+  if (num_sms < 1) return SK_ERR_INVALID;
   if (grid > num_sms) return SK_ERR_INVALID;
   s.tiles_m = static_cast<int32_t>(cdiv(m, s.tile_m));
   s.tiles_n = static_cast<int32_t>(cdiv(n, s.tile_n));
@@ -111,8 +153,8 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
   const int64_t t = s.tiles;
   const int64_t ipt = s.iters_per_tile;
   const int p = num_sms;
-  double coef[4];
-  model_coefficients(s.tile_n, coef);
+  double coef[5];
+  model_coefficients(s.tile_n, s.cluster_m, coef);
 
   if (t == 0 || ipt == 0) {
     // Nothing to multiply: no MAC loop, C = beta * C handled by the launcher.
@@ -211,12 +253,6 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
   }
   s.ctas = s.grid * s.cluster_m;
   s.workspace_bytes = split ? workspace_bytes_for(s.ctas, s.tile_n) : 0;
-  if (split && cluster_m == 0 && s.cluster_m == 2) {
-    // Automatic planning keeps CTA pairs to schedules without split tiles:
-    // those launch without the cooperative attribute, which the profiler could
-    // not replay together with clusters.  Split schedules use single CTAs.
-    return describe(m, n, k, mode, tile_n, grid, raster_group, 1, num_sms_all, out);
-  }
   *out = s;
   return SK_OK;
 }

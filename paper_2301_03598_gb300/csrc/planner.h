@@ -18,7 +18,7 @@ constexpr int64_t kFlagBytes = static_cast<int64_t>(kMaxGrid) * kFlagsPerCta * 4
 int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
              int cluster_m, int num_sms, sk_schedule_info* out);
 int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]);
-void model_coefficients(int tile_n, double out[4]);
+void model_coefficients(int tile_n, int cluster_m, double out[5]);
 int64_t workspace_bytes_for(int grid, int tile_n);
 
 }  // namespace sk

@@ -32,6 +32,29 @@ constexpr int kDevTimeoutPipeline = 1;  // an mbarrier wait ran out
 constexpr int kDevTimeoutFlag = 2;      // a fixup wait on a peer's flag ran out
 constexpr int kDevAborted = 3;          // gave up because another CTA reported an error
 
+// Division by a launch-invariant divisor d >= 1 for dividends n < 2^31 with
+// one widening multiply (the round-up method of Granlund and Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994): with
+// l = ceil(log2 d) and m = ceil(2^(31+l) / d), m < 2^32 and
+// floor(n / d) = (n * m) >> (31 + l), because m*d - 2^(31+l) < d <= 2^l.
+struct FastDiv {
+  uint32_t m;
+  uint32_t shift;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((uint64_t(1) << l) < d) ++l;
+  const uint64_t m = ((uint64_t(1) << (31 + l)) + d - 1) / d;
+  return FastDiv{static_cast<uint32_t>(m), 31 + l};
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, FastDiv f) {
+  return static_cast<uint32_t>((static_cast<uint64_t>(n) * f.m) >> f.shift);
+}
+#endif
+
 struct SkArgs {
   // problem
   int32_t m, n, k;
@@ -43,6 +66,12 @@ struct SkArgs {
   int32_t sk_tiles;
   int32_t sk_q, sk_r;
   int32_t grid;  // g, persistent CTAs; data-parallel tiles sk_tiles + x + j*g
+  // Divisors of the walk, precomputed: iterations per tile, q + 1 and q (the
+  // Stream-K shares), the raster band's tiles and its height (a full band
+  // and the last one).  fast_iters: the Stream-K iteration space is below
+  // 2^31, so iteration indices use them; tile indices always do.
+  FastDiv div_ipt, div_q1, div_q, div_band, div_rows, div_rows_last;
+  int32_t fast_iters;
   // MMA instruction descriptor (input format bits, N, M)
   uint32_t idesc;
   // epilogue

@@ -144,7 +144,8 @@ struct Walker {
   __device__ __forceinline__ bool next(const SkArgs& a, int& tile, int& kb0, int& kb1) {
     if (it < it_end) {
       const int64_t ipt = a.iters_per_tile;
-      tile = static_cast<int>(it / ipt);
+      tile = a.fast_iters ? static_cast<int>(fast_div(static_cast<uint32_t>(it), a.div_ipt))
+                          : static_cast<int>(it / ipt);
       const int64_t tile_iter = static_cast<int64_t>(tile) * ipt;
       const int64_t tile_iter_end = tile_iter + ipt;
       kb0 = static_cast<int>(it - tile_iter);
@@ -165,6 +166,12 @@ struct Walker {
 
 // The CTA whose Stream-K range holds global iteration i.
 __device__ __forceinline__ int cta_of_iter(const SkArgs& a, int64_t i) {
+  if (a.fast_iters) {
+    const uint32_t i32 = static_cast<uint32_t>(i);
+    const uint32_t big = static_cast<uint32_t>(a.sk_r) * static_cast<uint32_t>(a.sk_q + 1);
+    return static_cast<int>(i32 < big ? fast_div(i32, a.div_q1)
+                                      : static_cast<uint32_t>(a.sk_r) + fast_div(i32 - big, a.div_q));
+  }
   const int64_t q = a.sk_q, r = a.sk_r;
   const int64_t big = r * (q + 1);
   if (i < big) return static_cast<int>(i / (q + 1));
@@ -174,12 +181,13 @@ __device__ __forceinline__ int cta_of_iter(const SkArgs& a, int64_t i) {
 // Tile raster: m fastest within bands of group_m tile rows.
 __device__ __forceinline__ void tile_coords(const SkArgs& a, int tile, int& tm, int& tn) {
   const int band_tiles = a.group_m * a.tiles_n;
-  const int band = tile / band_tiles;
+  const int band = static_cast<int>(fast_div(static_cast<uint32_t>(tile), a.div_band));
   const int first_m = band * a.group_m;
   const int rows = min(a.group_m, a.tiles_m - first_m);
   const int local = tile - band * band_tiles;
-  tm = first_m + local % rows;
-  tn = local / rows;
+  tn = static_cast<int>(
+      fast_div(static_cast<uint32_t>(local), rows == a.group_m ? a.div_rows : a.div_rows_last));
+  tm = first_m + local - tn * rows;
 }
 
 template <typename TC>

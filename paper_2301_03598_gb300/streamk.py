@@ -217,8 +217,11 @@ def sk_plan_get(plan: Plan, attr) -> int:
 
 
 def sk_plan_attach_workspace(plan: Plan, ws, nbytes: int) -> None:
+    """Attach caller memory as the plan's workspace.  The plan object keeps a
+    reference to ``ws`` so the memory outlives every launch that uses it."""
     _check(lib().sk_plan_attach_workspace(plan.handle, _ptr(ws), nbytes),
            "sk_plan_attach_workspace")
+    plan._workspace = ws
 
 
 def sk_gemm(plan: Plan, A, B, C, alpha: float = 1.0, beta: float = 0.0, stream=None) -> None:

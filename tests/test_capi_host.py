@@ -51,39 +51,47 @@ def test_hybrid_regions_match_oracle(t_m, t_n, ipt, p):
     m, n, k = t_m * 128, t_n * 128, ipt * 64
     t = t_m * t_n
     for mode, variant in (("hybrid", S.HYBRID_TWO_TILE), ("hybrid1", S.HYBRID_ONE_TILE)):
-        d = sk.sk_plan_describe(m, n, k, mode, tile_n=128, num_sms=p)
+        d = sk.sk_plan_describe(m, n, k, mode, tile_n=128, cluster_m=1, num_sms=p)
         sk_tiles, dp_tiles = S.hybrid_regions(t, p, variant)
         assert (d["sk_tiles"], d["dp_tiles"]) == (sk_tiles, dp_tiles)
         assert d["tiles"] == t and d["iters_per_tile"] == ipt
         if 0 < sk_tiles < t:
             assert d["grid"] == p
-    d = sk.sk_plan_describe(m, n, k, "dp", tile_n=128, num_sms=p)
+    d = sk.sk_plan_describe(m, n, k, "dp", tile_n=128, cluster_m=1, num_sms=p)
     assert d["sk_tiles"] == 0 and d["grid"] == min(t, p) and d["workspace_bytes"] == 0
 
 
 def test_describe_config_shapes():
-    d = sk.sk_plan_describe(384, 384, 4096)
-    assert d["tile_n"] in (128, 256) and d["tiles"] == 3 * (-(-384 // d["tile_n"]))
-    assert (d["iters_per_tile"], d["mode_name"]) == (64, "sk")
-    assert d["tiles"] <= d["grid"] <= 148 and d["workspace_bytes"] > 0
-    d = sk.sk_plan_describe(384, 384, 4096, tile_n=128)
-    assert (d["tile_n"], d["tiles"]) == (128, 9)
-    d = sk.sk_plan_describe(4096, 128, 4096)
-    assert d["tile_n"] == 128
-    d = sk.sk_plan_describe(8192, 8192, 8192, cluster_m=1)
+    d = sk.sk_plan_describe(384, 384, 4096, tile_n=128, cluster_m=1)
+    assert (d["tile_n"], d["tiles"], d["iters_per_tile"]) == (128, 9, 64)
+    assert d["mode_name"] == "sk" and 9 <= d["grid"] <= 148 and d["workspace_bytes"] > 0
+    d = sk.sk_plan_describe(8192, 8192, 8192, tile_n=256, cluster_m=1)
     assert (d["tile_n"], d["tiles"], d["mode_name"]) == (256, 2048, "hybrid")
     assert d["sk_tiles"] == 2048 % 148 + 148 and d["dp_tiles"] % 148 == 0
-    # CTA pairs on request: 256 x 256 units on p = 74 pairs
-    d = sk.sk_plan_describe(8192, 8192, 8192, cluster_m=2)
+    # CTA pairs: 256 x 256 units on p = 74 pairs
+    d = sk.sk_plan_describe(8192, 8192, 8192, tile_n=256, cluster_m=2)
     assert (d["cluster_m"], d["tile_m"], d["tiles"], d["ctas"]) == (2, 256, 1024, 148)
     assert d["sk_tiles"] == 1024 % 74 + 74 and d["dp_tiles"] % 74 == 0
-    # automatic planning pairs CTAs only in schedules without split tiles
-    d = sk.sk_plan_describe(8192, 8192, 8192)
-    assert d["cluster_m"] == 1 and d["mode_name"] == "hybrid"
-    d = sk.sk_plan_describe(8192, 8192, 128)
-    assert d["cluster_m"] == 2 and d["mode_name"] == "dp" and d["workspace_bytes"] == 0
-    d = sk.sk_plan_describe(128 * 37, 256, 64)      # 37*2 tiles, below one wave
+    d = sk.sk_plan_describe(128 * 37, 256, 64, tile_n=256, cluster_m=1)  # 37 tiles, below one wave
     assert d["mode_name"] == "sk"
+
+
+@pytest.mark.parametrize("m,n,k", [(384, 384, 4096), (4096, 128, 4096), (8192, 8192, 8192),
+                                   (8192, 8192, 128), (128, 8192, 1024), (1000, 3000, 700),
+                                   (256, 256, 65536), (8192, 128, 4096), (1536, 1536, 1536)])
+def test_auto_configuration_is_a_candidate(m, n, k):
+    """With tile width and cluster size left open the planner returns one of
+    the fixed-configuration plans: BLK_N 256 only for n > 128, CTA pairs only
+    for m > 128."""
+    d = sk.sk_plan_describe(m, n, k, num_sms=152)
+    assert d["tile_n"] in ((128, 256) if n > 128 else (128,))
+    assert d["cluster_m"] in ((1, 2) if m > 128 else (1,))
+    fixed = sk.sk_plan_describe(m, n, k, tile_n=d["tile_n"], cluster_m=d["cluster_m"], num_sms=152)
+    assert fixed == d
+    # a fixed tile width leaves only the cluster size open, and vice versa
+    for tn in ((128, 256) if n > 128 else (128,)):
+        assert sk.sk_plan_describe(m, n, k, tile_n=tn, num_sms=152)["tile_n"] == tn
+    assert sk.sk_plan_describe(m, n, k, cluster_m=1, num_sms=152)["cluster_m"] == 1
 
 
 @pytest.mark.parametrize("m,n,k,mode", [(8192, 8192, 1024, "hybrid"), (4096, 2048, 512, "sk"),
@@ -106,7 +114,7 @@ def test_cluster_units_match_oracle(m, n, k, mode):
 def test_max_segments_bounds_every_cta():
     for (m, n, k, mode, g) in [(384, 384, 4096, "sk", 148), (19 * 128, 2048, 256, "hybrid", 0),
                                (1000, 3000, 64, "auto", 0), (128, 128, 64 * 7, "sk", 5)]:
-        d = sk.sk_plan_describe(m, n, k, mode, tile_n=128, grid=g)
+        d = sk.sk_plan_describe(m, n, k, mode, tile_n=128, grid=g, cluster_m=1)
         prob = S.Problem(m, n, k, 128, 128, 64)
         sched = S.persistent_schedule(prob, d["grid"], d["sk_tiles"], d["raster_group"])
         assert max(len(c) for c in sched.ctas) <= d["max_segments"]
