@@ -42,12 +42,13 @@ int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]) {
 // fifth, e, is the per-segment cost (one accumulator through the epilogue),
 // which the paper's model folds into c.  Fitted by relative least squares to
 // the measured times of the 2,000-shape log-uniform sweep planned with each
-// configuration forced.
+// configuration and each of data-parallel, two-tile hybrid and basic Stream-K
+// forced (12 plans per shape).
 void model_coefficients(int tile_n, int cluster_m, double out[5]) {
-  static const double k128x1[5] = {3.678, 4.167, 0.2896, 0.585, 0.263};
-  static const double k256x1[5] = {4.456, 6.667, 0.4028, 0.769, 0.131};
-  static const double k128x2[5] = {3.872, 5.024, 0.2864, 0.484, 0.526};
-  static const double k256x2[5] = {5.272, 8.645, 0.3168, 0.235, 0.329};
+  static const double k128x1[5] = {3.696, 4.277, 0.2877, 0.450, 0.199};
+  static const double k256x1[5] = {4.292, 8.193, 0.3922, 0.708, 0.143};
+  static const double k128x2[5] = {4.378, 4.794, 0.2845, 0.590, 0.289};
+  static const double k256x2[5] = {5.503, 10.217, 0.3013, 0.783, 0.195};
   const double* c = cluster_m == 2 ? (tile_n == 256 ? k256x2 : k128x2)
                                    : (tile_n == 256 ? k256x1 : k128x1);
   for (int i = 0; i < 5; ++i) out[i] = c[i];
@@ -72,15 +73,18 @@ static double predict_us(const sk_schedule_info& s, const double c[5]) {
 static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid,
                           int raster_group, int cluster_m, int num_sms, sk_schedule_info* out);
 
-// With the tile width or the cluster size left to the planner (0), every
-// candidate configuration is planned and the one the model predicts fastest
-// is kept (ties: the first candidate, i.e. the narrower tile and single CTAs).
+// Planning with choices left open: a tile width or cluster size of 0 tries
+// each candidate configuration, SK_MODE_AUTO tries data-parallel tiling, the
+// two-tile hybrid and basic Stream-K (the latter at every grid size g), and
+// the schedule with the smallest modelled time is kept (ties: the earliest
+// candidate, i.e. narrower tiles, single CTAs, data-parallel, smaller g).
 int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
              int cluster_m, int num_sms, sk_schedule_info* out) {
   if (out == nullptr || num_sms < 1) return SK_ERR_INVALID;
   if (cluster_m != 0 && cluster_m != 1 && cluster_m != 2) return SK_ERR_UNSUPPORTED;
   if (tile_n != 0 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
-  int tns[2], ntn = 0, cms[2], ncm = 0;
+  if (mode < SK_MODE_AUTO || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
+  int tns[2], ntn = 0, cms[2], ncm = 0, modes[3], nmode = 0;
   if (tile_n) {
     tns[ntn++] = tile_n;
   } else {
@@ -93,23 +97,42 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
     cms[ncm++] = 1;
     if (m > kTileM && num_sms >= 2) cms[ncm++] = 2;  // a pair needs two 128-row blocks
   }
+  if (mode == SK_MODE_AUTO) {
+    modes[nmode++] = SK_MODE_DP;
+    modes[nmode++] = SK_MODE_HYBRID;
+    modes[nmode++] = SK_MODE_SK;
+  } else {
+    modes[nmode++] = mode;
+  }
   int status = SK_ERR_INVALID;
   double best_us = 0.0;
+  auto consider = [&](int md, int tn, int cm, int g) {
+    sk_schedule_info s{};
+    const int st = describe_fixed(m, n, k, md, tn, g, raster_group, cm, num_sms, &s);
+    if (st != SK_OK) {
+      if (status != SK_OK) status = st;
+      return;
+    }
+    double c[5];
+    model_coefficients(s.tile_n, s.cluster_m, c);
+    const double us = predict_us(s, c);
+    if (status != SK_OK || us < best_us) {
+      *out = s;
+      best_us = us;
+      status = SK_OK;
+    }
+  };
   for (int i = 0; i < ntn; ++i) {
     for (int j = 0; j < ncm; ++j) {
-      sk_schedule_info s{};
-      const int st = describe_fixed(m, n, k, mode, tns[i], grid, raster_group, cms[j], num_sms, &s);
-      if (st != SK_OK) {
-        if (status != SK_OK) status = st;
-        continue;
-      }
-      double c[5];
-      model_coefficients(s.tile_n, s.cluster_m, c);
-      const double us = predict_us(s, c);
-      if (status != SK_OK || us < best_us) {
-        *out = s;
-        best_us = us;
-        status = SK_OK;
+      for (int h = 0; h < nmode; ++h) {
+        if (mode == SK_MODE_AUTO && modes[h] == SK_MODE_SK && grid == 0) {
+          const int64_t units = num_sms / cms[j];
+          const int64_t iters = cdiv(m, int64_t(kTileM) * cms[j]) * cdiv(n, tns[i]) * cdiv(k, kTileK);
+          const int64_t g_max = std::min<int64_t>(units, std::max<int64_t>(iters, 1));
+          for (int64_t g = 1; g <= g_max; ++g) consider(SK_MODE_SK, tns[i], cms[j], static_cast<int>(g));
+        } else {
+          consider(modes[h], tns[i], cms[j], grid);
+        }
       }
     }
   }
@@ -120,10 +143,10 @@ static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n,
                           int raster_group, int cluster_m, int num_sms, sk_schedule_info* out) {
   if (out == nullptr || m < 0 || n < 0 || k < 0 || num_sms < 1 || grid < 0 || raster_group < 0)
     return SK_ERR_INVALID;
-  if (cluster_m != 0 && cluster_m != 1 && cluster_m != 2) return SK_ERR_UNSUPPORTED;
+  if (cluster_m != 1 && cluster_m != 2) return SK_ERR_UNSUPPORTED;
   if (num_sms > kMaxGrid || grid > num_sms) return SK_ERR_INVALID;
-  if (mode < SK_MODE_AUTO || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
-  if (tile_n != 0 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  if (mode < SK_MODE_DP || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
+  if (tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
   // Index arithmetic on the device is 32-bit for tiles and k-blocks.
   if (m > (int64_t(1) << 31) - 1 || n > (int64_t(1) << 31) - 1 || k > (int64_t(1) << 31) - 1)
     return SK_ERR_INVALID;
@@ -163,15 +186,7 @@ static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n,
     s.sk_tiles = 0;
     s.dp_tiles = t;
   } else {
-    int resolved = mode;
-    if (mode == SK_MODE_AUTO) {
-      if (t % p == 0)
-        resolved = SK_MODE_DP;
-      else if (t >= p)
-        resolved = SK_MODE_HYBRID;
-      else
-        resolved = SK_MODE_SK;
-    }
+    const int resolved = mode;
     s.mode = resolved;
     const int64_t w = t / p, rem = t % p;
     switch (resolved) {
@@ -188,24 +203,6 @@ static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n,
       }
       case SK_MODE_HYBRID:
       case SK_MODE_HYBRID_ONE_TILE: {
-        if (mode == SK_MODE_AUTO && w >= 1 && rem != 0) {
-          // The two-tile hybrid pays one spill and one fixup per split tile;
-          // with few iterations per tile that can cost more than the partial
-          // wave it removes.  Compare both with the model's terms: the spill
-          // and fixup overlap the (w - 1) data-parallel tiles that follow the
-          // Stream-K region, and whatever those do not cover is exposed.
-          const double split_us = std::max(
-              0.0, coef[1] + coef[3] - coef[2] * static_cast<double>((w - 1) * ipt));
-          const double dp_us = coef[0] + coef[2] * static_cast<double>(ipt * ((t + p - 1) / p));
-          const double sk_us =
-              coef[0] + split_us + coef[2] * static_cast<double>((t * ipt + p - 1) / p);
-          if (dp_us <= sk_us) {
-            s.mode = SK_MODE_DP;
-            s.sk_tiles = 0;
-            s.grid = static_cast<int32_t>(std::min<int64_t>(t, p));
-            break;
-          }
-        }
         if (rem == 0) {  // perfect quantization: full waves only
           s.sk_tiles = 0;
           s.grid = static_cast<int32_t>(std::min<int64_t>(t, p));

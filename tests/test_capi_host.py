@@ -62,18 +62,18 @@ def test_hybrid_regions_match_oracle(t_m, t_n, ipt, p):
 
 
 def test_describe_config_shapes():
-    d = sk.sk_plan_describe(384, 384, 4096, tile_n=128, cluster_m=1)
+    d = sk.sk_plan_describe(384, 384, 4096, "sk", tile_n=128, cluster_m=1)
     assert (d["tile_n"], d["tiles"], d["iters_per_tile"]) == (128, 9, 64)
     assert d["mode_name"] == "sk" and 9 <= d["grid"] <= 148 and d["workspace_bytes"] > 0
-    d = sk.sk_plan_describe(8192, 8192, 8192, tile_n=256, cluster_m=1)
+    d = sk.sk_plan_describe(8192, 8192, 8192, "hybrid", tile_n=256, cluster_m=1)
     assert (d["tile_n"], d["tiles"], d["mode_name"]) == (256, 2048, "hybrid")
     assert d["sk_tiles"] == 2048 % 148 + 148 and d["dp_tiles"] % 148 == 0
     # CTA pairs: 256 x 256 units on p = 74 pairs
-    d = sk.sk_plan_describe(8192, 8192, 8192, tile_n=256, cluster_m=2)
+    d = sk.sk_plan_describe(8192, 8192, 8192, "hybrid", tile_n=256, cluster_m=2)
     assert (d["cluster_m"], d["tile_m"], d["tiles"], d["ctas"]) == (2, 256, 1024, 148)
     assert d["sk_tiles"] == 1024 % 74 + 74 and d["dp_tiles"] % 74 == 0
-    d = sk.sk_plan_describe(128 * 37, 256, 64, tile_n=256, cluster_m=1)  # 37 tiles, below one wave
-    assert d["mode_name"] == "sk"
+    d = sk.sk_plan_describe(128 * 37, 256, 64, "hybrid", tile_n=256, cluster_m=1)
+    assert d["mode_name"] == "hybrid" and d["sk_tiles"] == 37   # below one wave: basic Stream-K
 
 
 @pytest.mark.parametrize("m,n,k", [(384, 384, 4096), (4096, 128, 4096), (8192, 8192, 8192),
