@@ -270,6 +270,84 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// ---------------------------------------------------------------- look-ahead probes
+// An issuing thread that blocks on an mbarrier probe loses the probe's
+// round-trip latency (about 130 SM cycles measured on sm_103a) every
+// pipeline stage, which is as long as a 128x128x16 MMA.  These fuse a
+// non-blocking probe of the *next* stage's barrier (mbarrier.test_wait) with
+// the current stage's last asynchronous instruction, so the latency overlaps
+// the issue; the returned flag says whether the probed phase had completed.
+
+// The last MMA of a k-block (single CTA) plus a probe of `bar` for `parity`.
+__device__ __forceinline__ bool mma_f16_probe(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                              uint32_t idesc, uint32_t accumulate, uint32_t bar,
+                                              uint32_t parity) {
+  uint32_t ready;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q, [%5], %6;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %3, %7, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(ready)
+      : "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(accumulate), "r"(bar), "r"(parity), "r"(idesc)
+      : "memory");
+  return ready != 0;
+}
+
+// The same for a pair MMA (cta_group::2).
+__device__ __forceinline__ bool mma_f16_pair_probe(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                                   uint32_t idesc, uint32_t accumulate, uint32_t bar,
+                                                   uint32_t parity) {
+  uint32_t ready;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q, [%5], %6;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%1], %2, %3, %7, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(ready)
+      : "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(accumulate), "r"(bar), "r"(parity), "r"(idesc)
+      : "memory");
+  return ready != 0;
+}
+
+// A 2-D tiled TMA load (as tma_load_2d) plus a probe of `probe_bar`.
+__device__ __forceinline__ bool tma_load_2d_probe(uint32_t dst, const void* tmap, uint32_t bar,
+                                                  int32_t x, int32_t y, uint32_t probe_bar,
+                                                  uint32_t parity) {
+  uint32_t ready;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q, [%6], %7;\n\t"
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%1], [%2, {%4, %5}], [%3];\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(ready)
+      : "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(bar), "r"(x), "r"(y), "r"(probe_bar),
+        "r"(parity)
+      : "memory");
+  return ready != 0;
+}
+
+// A pair TMA load (as tma_load_2d_pair) plus a probe of `probe_bar`.
+__device__ __forceinline__ bool tma_load_2d_pair_probe(uint32_t dst, const void* tmap, uint32_t bar,
+                                                       int32_t x, int32_t y, uint32_t probe_bar,
+                                                       uint32_t parity) {
+  uint32_t ready;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q, [%6], %7;\n\t"
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%1], [%2, {%4, %5}], [%3];\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(ready)
+      : "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(bar), "r"(x), "r"(y), "r"(probe_bar),
+        "r"(parity)
+      : "memory");
+  return ready != 0;
+}
+
 // ---------------------------------------------------------------- flags
 __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
   uint32_t v;

@@ -419,14 +419,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int64_t issued = 0;
       bool ok = true;
+      // ready: the current stage's empty barrier is known to have completed
+      // (probed while the previous stage's B load was issued).
+      bool ready = false;
       while (ok && w.next(a, tile, kb0, kb1)) {
         int tm, tn;
         tile_coords(a, tile, tm, tn);
         tm = tm * CM + rank;  // this CTA's 128-row block
         for (int kb = kb0; kb < kb1; ++kb) {
-          if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) {
+          if (!ready && !wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) {
             ok = false;
             break;
+          }
+          int next = stage + 1;
+          uint32_t next_phase = phase;
+          if (next == S) {
+            next = 0;
+            next_phase ^= 1u;
           }
           if constexpr (kPair) {
             // this CTA's A rows and half of the B tile, completing on the
@@ -434,17 +443,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t fb = full0 + 8u * stage;
             if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C_::kStageBytes);
             tma_load_2d_pair(stage_a(stage), &tmA, fb, kb * kBlkK, tm * kBlkM);
-            tma_load_2d_pair(stage_b(stage), &tmB, fb, kb * kBlkK, tn * BN + rank * (BN / 2));
+            ready = tma_load_2d_pair_probe(stage_b(stage), &tmB, fb, kb * kBlkK,
+                                           tn * BN + rank * (BN / 2), empty_bar(next),
+                                           next_phase ^ 1u);
           } else {
             mbar_arrive_expect_tx(full_bar(stage), C_::kStageBytes);
             tma_load_2d(stage_a(stage), &tmA, full_bar(stage), kb * kBlkK, tm * kBlkM);
-            tma_load_2d(stage_b(stage), &tmB, full_bar(stage), kb * kBlkK, tn * BN);
+            ready = tma_load_2d_probe(stage_b(stage), &tmB, full_bar(stage), kb * kBlkK, tn * BN,
+                                      empty_bar(next), next_phase ^ 1u);
           }
           ++issued;
-          if (++stage == S) {
-            stage = 0;
-            phase ^= 1u;
-          }
+          stage = next;
+          phase = next_phase;
         }
       }
       if (ok) {
@@ -488,20 +498,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0, acc = 0;
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
+      // ready: the current stage's full barrier is known to have completed
+      // (probed while the previous k-block's last MMA was issued).
+      bool ready = false;
       while (ok && w.next(a, tile, kb0, kb1)) {
         if (!wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
         for (int kb = kb0; kb < kb1; ++kb) {
-          if (!wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull)) {
+          if (!ready && !wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint64_t adesc = smem_desc_sw128(stage_a(stage));
           const uint64_t bdesc = smem_desc_sw128(stage_b(stage));
+          int next = stage + 1;
+          uint32_t next_phase = phase;
+          if (next == S) {
+            next = 0;
+            next_phase ^= 1u;
+          }
 #pragma unroll
-          for (int kk = 0; kk < kBlkK / 16; ++kk) {
+          for (int kk = 0; kk < kBlkK / 16 - 1; ++kk) {
             // advance 16 elements (32 B) along K inside the swizzle atom
             if constexpr (kPair)
               mma_f16_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
@@ -510,15 +529,21 @@ __global__ void __launch_bounds__(kThreads, 1)
               mma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
                       (kb > kb0 || kk > 0) ? 1u : 0u);
           }
+          // the last MMA of the k-block, fused with a probe of the next stage
+          constexpr uint32_t kLast = 2u * (kBlkK / 16 - 1);
+          if constexpr (kPair)
+            ready = mma_f16_pair_probe(d_tmem, adesc + kLast, bdesc + kLast, a.idesc, 1u,
+                                       full_bar(next), next_phase);
+          else
+            ready = mma_f16_probe(d_tmem, adesc + kLast, bdesc + kLast, a.idesc, 1u, full_bar(next),
+                                  next_phase);
           // frees the stage (in both CTAs of a pair) once these MMAs finish
           if constexpr (kPair)
             mma_commit_pair_multicast(empty_bar(stage), kPairMask);
           else
             mma_commit(empty_bar(stage));
-          if (++stage == S) {
-            stage = 0;
-            phase ^= 1u;
-          }
+          stage = next;
+          phase = next_phase;
         }
         if (!ok) break;
         // accumulator complete (in both CTAs' TMEM for a pair)
