@@ -107,6 +107,7 @@ struct sk_plan_s {
   const void* cached_b = nullptr;
   const void* cached_c = nullptr;
   CUtensorMap tm_a{}, tm_b{}, tm_c{};
+  CUtensorMap tm_a3{}, tm_b3{};  // 3-D views (two k-blocks per box) for BLK_K = 128 plans
   bool c_tma = false;
   cudaStream_t last_stream = nullptr;
   bool launched = false;
@@ -161,6 +162,30 @@ int encode_operand(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows, in
   CUtensorMapDataType dt =
       dtype == SK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   CUresult r = fn(tm, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SK_OK : SK_ERR_INVALID;
+}
+
+// The same operand viewed as {64, rows, k/64} with strides {ld, 128 B}: one
+// box {64, box_rows, 2} holds two consecutive 64-wide k-blocks.  Only the
+// k-blocks that lie entirely inside k are addressed through this view (the
+// innermost extent is 64 regardless of k); the kernel loads a tail k-block
+// through the 2-D map, which fills columns beyond k with zeros.
+int encode_operand_3d(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows, int64_t kdim,
+                      int64_t ld, int box_rows) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return SK_ERR_CUDA;
+  const int64_t kfull = kdim / sk::kBlkK;
+  if (kfull < 2) return SK_ERR_INVALID;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(sk::kBlkK), static_cast<cuuint64_t>(rows),
+                        static_cast<cuuint64_t>(kfull)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 2, static_cast<cuuint64_t>(sk::kBlkK) * 2};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(sk::kBlkK), static_cast<cuuint32_t>(box_rows), 2};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUtensorMapDataType dt =
+      dtype == SK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUresult r = fn(tm, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? SK_OK : SK_ERR_INVALID;
@@ -257,13 +282,18 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   const int64_t kn = p->swap ? p->m : p->n;
   const int64_t klda = p->swap ? p->ldb : p->lda;
   const int64_t kldb = p->swap ? p->lda : p->ldb;
+  const bool use3d = s.tile_k == 2 * sk::kBlkK && p->k / sk::kBlkK >= 2;
   if (ka != p->cached_a) {
     int st = encode_operand(&p->tm_a, ka, p->a_type, km, p->k, klda, sk::kBlkM);
+    if (st == SK_OK && use3d)
+      st = encode_operand_3d(&p->tm_a3, ka, p->a_type, km, p->k, klda, sk::kBlkM);
     if (st != SK_OK) return st;
     p->cached_a = ka;
   }
   if (kb != p->cached_b) {
     int st = encode_operand(&p->tm_b, kb, p->b_type, kn, p->k, kldb, s.tile_n / s.cluster_m);
+    if (st == SK_OK && use3d)
+      st = encode_operand_3d(&p->tm_b3, kb, p->b_type, kn, p->k, kldb, s.tile_n / s.cluster_m);
     if (st != SK_OK) return st;
     p->cached_b = kb;
   }
@@ -287,6 +317,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   a.sk_q = static_cast<int32_t>(s.sk_iters / s.grid);
   a.sk_r = static_cast<int32_t>(s.sk_iters % s.grid);
   set_divisors(a, s);
+  a.kfull64 = use3d ? static_cast<int32_t>(p->k / sk::kBlkK) : 0;
   a.idesc = make_idesc(p->a_type, s.tile_n, s.cluster_m);
   a.C = C;
   a.ldc = p->ldc;
@@ -313,11 +344,13 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   // all CTAs become resident; the bounded waits turn anything else into an
   // error status.
   const bool cooperative = split && s.cluster_m == 1;
+  const CUtensorMap& ta3 = use3d ? p->tm_a3 : p->tm_a;
+  const CUtensorMap& tb3 = use3d ? p->tm_b3 : p->tm_b;
   cudaError_t e = s.tile_n == 256
-                      ? sk::launch_bn256(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, a,
-                                         cooperative, stream)
-                      : sk::launch_bn128(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, a,
-                                         cooperative, stream);
+                      ? sk::launch_bn256(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3,
+                                         a, cooperative, stream)
+                      : sk::launch_bn128(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3,
+                                         a, cooperative, stream);
   return cuda_status(e);
 }
 
@@ -679,9 +712,16 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     const size_t partial_bytes = static_cast<size_t>(s.grid) * sk::kBlkM * 128 * 4;
     if (split && kNoAllocPartialsOffset + partial_bytes > kNoAllocScratchBytes)
       return SK_ERR_INVALID;  // needs more scratch than the fixed maximum
-    CUtensorMap tma, tmb, tmc;
+    CUtensorMap tma, tmb, tmc, tma3, tmb3;
     if ((st = encode_operand(&tma, A, ab_type, m, k, lda, sk::kBlkM)) != SK_OK) return st;
     if ((st = encode_operand(&tmb, B, ab_type, n, k, ldb, 128)) != SK_OK) return st;
+    const bool use3d = s.tile_k == 2 * sk::kBlkK && k / sk::kBlkK >= 2;
+    tma3 = tma;
+    tmb3 = tmb;
+    if (use3d) {
+      if ((st = encode_operand_3d(&tma3, A, ab_type, m, k, lda, sk::kBlkM)) != SK_OK) return st;
+      if ((st = encode_operand_3d(&tmb3, B, ab_type, n, k, ldb, 128)) != SK_OK) return st;
+    }
     const bool c_tma = encode_output(&tmc, C, c_type, m, n, ldc);
     if (split) {
       e = cudaMemsetAsync(scratch, 0, static_cast<size_t>(sk::kFlagBytes), stream);
@@ -701,6 +741,7 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     a.sk_q = static_cast<int32_t>(s.sk_iters / s.grid);
     a.sk_r = static_cast<int32_t>(s.sk_iters % s.grid);
     set_divisors(a, s);
+    a.kfull64 = use3d ? static_cast<int32_t>(k / sk::kBlkK) : 0;
     a.idesc = make_idesc(ab_type, 128, 1);
     a.C = C;
     a.ldc = ldc;
@@ -717,7 +758,7 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     a.debug_skip_signal = -1;
     a.timeout_ns = kDefaultTimeoutNs;
     a.pdl = 1;
-    e = sk::launch_bn128(c_type, 1, tma, tmb, tmc, a, split, stream);
+    e = sk::launch_bn128(c_type, 1, tma, tmb, tmc, tma3, tmb3, a, split, stream);
   }
   if (e != cudaSuccess) return cuda_status(e);
   if (device_status != nullptr) {

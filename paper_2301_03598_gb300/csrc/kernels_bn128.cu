@@ -10,8 +10,8 @@ namespace sk {
 
 template <int CM, typename TC>
 static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
-                              const CUtensorMap& tc, const SkArgs& args, bool cooperative,
-                              cudaStream_t stream) {
+                              const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
+                              const SkArgs& args, bool cooperative, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(args.grid * CM));
   cfg.blockDim = dim3(kThreads);
@@ -38,30 +38,30 @@ static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, CM, TC>, ta, tb, tc, args);
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, CM, TC>, ta, tb, tc, ta3, tb3, args);
 }
 
 template <int CM>
 static cudaError_t launch_cm(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
-                             const CUtensorMap& tc, const SkArgs& args, bool cooperative,
-                             cudaStream_t stream) {
+                             const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
+                             const SkArgs& args, bool cooperative, cudaStream_t stream) {
   switch (c_dtype) {
     case SK_F32:
-      return launch_one<CM, float>(ta, tb, tc, args, cooperative, stream);
+      return launch_one<CM, float>(ta, tb, tc, ta3, tb3, args, cooperative, stream);
     case SK_BF16:
-      return launch_one<CM, __nv_bfloat16>(ta, tb, tc, args, cooperative, stream);
+      return launch_one<CM, __nv_bfloat16>(ta, tb, tc, ta3, tb3, args, cooperative, stream);
     case SK_F16:
-      return launch_one<CM, __half>(ta, tb, tc, args, cooperative, stream);
+      return launch_one<CM, __half>(ta, tb, tc, ta3, tb3, args, cooperative, stream);
     default:
       return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
-                         const CUtensorMap& tc, const SkArgs& args, bool cooperative,
-                         cudaStream_t stream) {
-  return cluster_m == 2 ? launch_cm<2>(c_dtype, ta, tb, tc, args, cooperative, stream)
-                        : launch_cm<1>(c_dtype, ta, tb, tc, args, cooperative, stream);
+                         const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
+                         const SkArgs& args, bool cooperative, cudaStream_t stream) {
+  return cluster_m == 2 ? launch_cm<2>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream)
+                        : launch_cm<1>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream);
 }
 
 template <int CM, typename TC>

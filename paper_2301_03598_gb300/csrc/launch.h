@@ -8,14 +8,17 @@
 namespace sk {
 
 // c_dtype: SK_F32 / SK_BF16 / SK_F16.  cluster_m: 1, or 2 for CTA pairs along M
-// (the grid is args.grid units of cluster_m CTAs).  cooperative: CTAs wait on
-// one another, so the launch must guarantee co-residency.
+// (the grid is args.grid units of cluster_m CTAs).  ta/tb: 2-D operand maps
+// (boxes of one 64-wide k-block); ta3/tb3: the 3-D views whose boxes hold two
+// k-blocks, used by BLK_N = 128 (pass the 2-D maps when unused).
+// cooperative: CTAs wait on one another, so the launch must guarantee
+// co-residency.
 cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
-                         const CUtensorMap& tc, const SkArgs& args, bool cooperative,
-                         cudaStream_t stream);
+                         const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
+                         const SkArgs& args, bool cooperative, cudaStream_t stream);
 cudaError_t launch_bn256(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
-                         const CUtensorMap& tc, const SkArgs& args, bool cooperative,
-                         cudaStream_t stream);
+                         const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
+                         const SkArgs& args, bool cooperative, cudaStream_t stream);
 // Dynamic shared memory of one CTA; also sets the kernels' opt-in limit.
 cudaError_t prepare_bn128(size_t* smem_bytes);
 cudaError_t prepare_bn256(size_t* smem_bytes);

@@ -127,7 +127,8 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
       for (int h = 0; h < nmode; ++h) {
         if (mode == SK_MODE_AUTO && modes[h] == SK_MODE_SK && grid == 0) {
           const int64_t units = num_sms / cms[j];
-          const int64_t iters = cdiv(m, int64_t(kTileM) * cms[j]) * cdiv(n, tns[i]) * cdiv(k, kTileK);
+          const int64_t iters =
+              cdiv(m, int64_t(kTileM) * cms[j]) * cdiv(n, tns[i]) * cdiv(k, tile_k_for(tns[i]));
           const int64_t g_max = std::min<int64_t>(units, std::max<int64_t>(iters, 1));
           for (int64_t g = 1; g <= g_max; ++g) consider(SK_MODE_SK, tns[i], cms[j], static_cast<int>(g));
         } else {
@@ -152,7 +153,7 @@ static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n,
     return SK_ERR_INVALID;
 
   sk_schedule_info s{};
-  s.tile_k = kTileK;
+  s.tile_k = tile_k_for(tile_n);
   s.tile_n = tile_n;
   s.cluster_m = cluster_m;
   // The schedule's unit is a cluster: cluster_m CTAs computing a

@@ -7,7 +7,9 @@
 namespace sk {
 
 constexpr int kTileM = 128;
-constexpr int kTileK = 64;
+// BLK_K, the depth of one MAC-loop iteration: two 64-wide k-blocks for
+// BLK_N = 128 (one pipeline stage each, see the kernel's Cfg), one for 256.
+constexpr int tile_k_for(int tile_n) { return tile_n == 128 ? 128 : 64; }
 // Workspace layout: kFlagBytes of flags at offset 0 (kFlagsPerCta uint32 per
 // CTA, one per 32-row x 128-byte unit of its partial tile, at most kMaxGrid
 // CTAs), then one BLK_M x BLK_N FP32 partial slot per CTA.

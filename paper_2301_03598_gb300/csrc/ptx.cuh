@@ -92,6 +92,27 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const void* tmap,
       : "memory");
 }
 
+// 3-D tiled loads.  With a K-contiguous matrix viewed as {64, rows, k/64}
+// (strides: the row pitch, then 128 bytes), one box {64, rows, 2} is two
+// consecutive 64-wide k-blocks, landing as two 128-byte-swizzled 2-D tiles
+// back to back: half the TMA instructions per byte.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, uint32_t bar, int32_t x,
+                                            int32_t y, int32_t z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const void* tmap, uint32_t bar,
+                                                 int32_t x, int32_t y, int32_t z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
 // The shared::cluster address of the variable at shared::cta address `addr` in
 // the CTA of cluster rank `rank`.
 __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
@@ -344,6 +365,40 @@ __device__ __forceinline__ bool tma_load_2d_pair_probe(uint32_t dst, const void*
       : "=r"(ready)
       : "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(bar), "r"(x), "r"(y), "r"(probe_bar),
         "r"(parity)
+      : "memory");
+  return ready != 0;
+}
+
+// 3-D loads (as tma_load_3d / tma_load_3d_pair) plus a probe of `probe_bar`.
+__device__ __forceinline__ bool tma_load_3d_probe(uint32_t dst, const void* tmap, uint32_t bar,
+                                                  int32_t x, int32_t y, int32_t z,
+                                                  uint32_t probe_bar, uint32_t parity) {
+  uint32_t ready;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q, [%7], %8;\n\t"
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%1], [%2, {%4, %5, %6}], [%3];\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(ready)
+      : "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(bar), "r"(x), "r"(y), "r"(z),
+        "r"(probe_bar), "r"(parity)
+      : "memory");
+  return ready != 0;
+}
+__device__ __forceinline__ bool tma_load_3d_pair_probe(uint32_t dst, const void* tmap, uint32_t bar,
+                                                       int32_t x, int32_t y, int32_t z,
+                                                       uint32_t probe_bar, uint32_t parity) {
+  uint32_t ready;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q, [%7], %8;\n\t"
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%1], [%2, {%4, %5, %6}], [%3];\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(ready)
+      : "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(bar), "r"(x), "r"(y), "r"(z),
+        "r"(probe_bar), "r"(parity)
       : "memory");
   return ready != 0;
 }

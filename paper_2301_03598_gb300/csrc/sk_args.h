@@ -6,7 +6,7 @@
 namespace sk {
 
 constexpr int kBlkM = 128;  // BLK_M: one tcgen05 M=128 MMA covers the tile height
-constexpr int kBlkK = 64;   // BLK_K: 64 16-bit elements = one 128-byte swizzle row
+constexpr int kBlkK = 64;   // one k-block: 64 16-bit elements = one 128-byte swizzle row
 
 // Segment roles (the trace format; see include/streamk.h).
 constexpr int kRoleWhole = 0;    // tile_started && tile_ended: store the tile
@@ -72,6 +72,7 @@ struct SkArgs {
   // 2^31, so iteration indices use them; tile indices always do.
   FastDiv div_ipt, div_q1, div_q, div_band, div_rows, div_rows_last;
   int32_t fast_iters;
+  int32_t kfull64;  // k-blocks of 64 that lie entirely inside k (3-D loads need two of them)
   // MMA instruction descriptor (input format bits, N, M)
   uint32_t idesc;
   // epilogue

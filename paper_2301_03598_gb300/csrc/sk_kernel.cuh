@@ -37,13 +37,19 @@ constexpr int kEpiWarp0 = 2;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 
-// Shared-memory stage ring per CTA: 192 KiB of operand stages.
+// Shared-memory stage ring per CTA: 192 KiB of operand stages.  A stage
+// holds KD consecutive 64-wide k-blocks (one MAC-loop iteration of BLK_K =
+// 64 * KD): KD = 2 for BLK_N = 128, whose 2-D stages are too small for the
+// SM's TMA path (a stage costs about as much as its bytes), KD = 1 for 256.
 template <int BN, int CM>
 struct Cfg {
-  static constexpr int kABytes = kBlkM * kBlkK * 2;       // this CTA's 128 rows of A
-  static constexpr int kBBytes = (BN / CM) * kBlkK * 2;   // this CTA's BN/CM rows of B
+  static constexpr int KD = BN == 128 ? 2 : 1;
+  static constexpr int kSubA = kBlkM * kBlkK * 2;       // one k-block of this CTA's 128 A rows
+  static constexpr int kSubB = (BN / CM) * kBlkK * 2;   // one k-block of its BN/CM B rows
+  static constexpr int kABytes = KD * kSubA;
+  static constexpr int kBBytes = KD * kSubB;
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kStages = (192 * 1024) / kStageBytes;  // 6, 4 (single); 8, 6 (pair)
+  static constexpr int kStages = (192 * 1024) / kStageBytes;  // 3, 4 (BN 128); 4, 6 (BN 256)
   static constexpr int kTmemCols = 2 * BN;  // two FP32 accumulators of BN columns
   // Output staging for TMA stores: per epilogue warp one buffer of 32 rows x
   // 128 B, 128-byte swizzled (1 KiB aligned).
@@ -332,10 +338,12 @@ __device__ __forceinline__ void add_beta_c(const SkArgs& a, int grow, int gcol, 
 template <int BN, int CM, typename TC>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ SkArgs a) {
+                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmA3,
+                   const __grid_constant__ CUtensorMap tmB3, const __grid_constant__ SkArgs a) {
   static_assert(CM == 1 || CM == 2, "cluster size along M");
   using C_ = Cfg<BN, CM>;
   constexpr int S = C_::kStages;
+  constexpr int KD = C_::KD;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // 128-byte swizzle atoms need 1 KiB alignment
@@ -389,6 +397,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     tma_prefetch_desc(&tmA);
     tma_prefetch_desc(&tmB);
     if (a.c_tma) tma_prefetch_desc(&tmC);
+    if (KD == 2 && a.kfull64 >= 2) {
+      tma_prefetch_desc(&tmA3);
+      tma_prefetch_desc(&tmB3);
+    }
   }
   if (warp == 1) {
     if constexpr (kPair) {
@@ -437,20 +449,53 @@ __global__ void __launch_bounds__(kThreads, 1)
             next = 0;
             next_phase ^= 1u;
           }
+          // k-blocks k0 .. k0+KD-1 of this CTA's A rows and its BN/CM rows of
+          // B.  A KD = 2 stage of two full k-blocks is one 3-D box per
+          // operand; a stage reaching into the k tail loads its k-blocks as
+          // 2-D boxes, whose out-of-range columns TMA fills with zeros.
+          const int k0 = kb * KD;
+          const bool box3 = KD == 2 && k0 + 2 <= a.kfull64;
+          const int brow = tn * BN + rank * (BN / CM);
           if constexpr (kPair) {
-            // this CTA's A rows and half of the B tile, completing on the
-            // issuer's full barrier, which expects both CTAs' bytes
+            // completing on the issuer's full barrier, which expects both
+            // CTAs' bytes
             const uint32_t fb = full0 + 8u * stage;
             if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C_::kStageBytes);
-            tma_load_2d_pair(stage_a(stage), &tmA, fb, kb * kBlkK, tm * kBlkM);
-            ready = tma_load_2d_pair_probe(stage_b(stage), &tmB, fb, kb * kBlkK,
-                                           tn * BN + rank * (BN / 2), empty_bar(next),
-                                           next_phase ^ 1u);
+            if (box3) {
+              tma_load_3d_pair(stage_a(stage), &tmA3, fb, 0, tm * kBlkM, k0);
+              ready = tma_load_3d_pair_probe(stage_b(stage), &tmB3, fb, 0, brow, k0, empty_bar(next),
+                                             next_phase ^ 1u);
+            } else if constexpr (KD == 1) {
+              tma_load_2d_pair(stage_a(stage), &tmA, fb, k0 * kBlkK, tm * kBlkM);
+              ready = tma_load_2d_pair_probe(stage_b(stage), &tmB, fb, k0 * kBlkK, brow,
+                                             empty_bar(next), next_phase ^ 1u);
+            } else {
+#pragma unroll
+              for (int j = 0; j < KD; ++j) {
+                tma_load_2d_pair(stage_a(stage) + j * C_::kSubA, &tmA, fb, (k0 + j) * kBlkK, tm * kBlkM);
+                tma_load_2d_pair(stage_b(stage) + j * C_::kSubB, &tmB, fb, (k0 + j) * kBlkK, brow);
+              }
+              ready = false;
+            }
           } else {
-            mbar_arrive_expect_tx(full_bar(stage), C_::kStageBytes);
-            tma_load_2d(stage_a(stage), &tmA, full_bar(stage), kb * kBlkK, tm * kBlkM);
-            ready = tma_load_2d_probe(stage_b(stage), &tmB, full_bar(stage), kb * kBlkK, tn * BN,
-                                      empty_bar(next), next_phase ^ 1u);
+            const uint32_t fb = full_bar(stage);
+            mbar_arrive_expect_tx(fb, C_::kStageBytes);
+            if (box3) {
+              tma_load_3d(stage_a(stage), &tmA3, fb, 0, tm * kBlkM, k0);
+              ready = tma_load_3d_probe(stage_b(stage), &tmB3, fb, 0, brow, k0, empty_bar(next),
+                                        next_phase ^ 1u);
+            } else if constexpr (KD == 1) {
+              tma_load_2d(stage_a(stage), &tmA, fb, k0 * kBlkK, tm * kBlkM);
+              ready = tma_load_2d_probe(stage_b(stage), &tmB, fb, k0 * kBlkK, brow, empty_bar(next),
+                                        next_phase ^ 1u);
+            } else {
+#pragma unroll
+              for (int j = 0; j < KD; ++j) {
+                tma_load_2d(stage_a(stage) + j * C_::kSubA, &tmA, fb, (k0 + j) * kBlkK, tm * kBlkM);
+                tma_load_2d(stage_b(stage) + j * C_::kSubB, &tmB, fb, (k0 + j) * kBlkK, brow);
+              }
+              ready = false;
+            }
           }
           ++issued;
           stage = next;
@@ -511,8 +556,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint64_t adesc = smem_desc_sw128(stage_a(stage));
-          const uint64_t bdesc = smem_desc_sw128(stage_b(stage));
           int next = stage + 1;
           uint32_t next_phase = phase;
           if (next == S) {
@@ -520,23 +563,28 @@ __global__ void __launch_bounds__(kThreads, 1)
             next_phase ^= 1u;
           }
 #pragma unroll
-          for (int kk = 0; kk < kBlkK / 16 - 1; ++kk) {
-            // advance 16 elements (32 B) along K inside the swizzle atom
-            if constexpr (kPair)
-              mma_f16_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
-                           (kb > kb0 || kk > 0) ? 1u : 0u);
-            else
-              mma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
-                      (kb > kb0 || kk > 0) ? 1u : 0u);
+          for (int j = 0; j < KD; ++j) {
+            const uint64_t adesc = smem_desc_sw128(stage_a(stage) + j * C_::kSubA);
+            const uint64_t bdesc = smem_desc_sw128(stage_b(stage) + j * C_::kSubB);
+#pragma unroll
+            for (int kk = 0; kk < kBlkK / 16; ++kk) {
+              // advance 16 elements (32 B) along K inside the swizzle atom
+              const uint32_t acc_flag = (kb > kb0 || j > 0 || kk > 0) ? 1u : 0u;
+              if (j == KD - 1 && kk == kBlkK / 16 - 1) {
+                // the stage's last MMA, fused with a probe of the next stage
+                if constexpr (kPair)
+                  ready = mma_f16_pair_probe(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
+                                             acc_flag, full_bar(next), next_phase);
+                else
+                  ready = mma_f16_probe(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, acc_flag,
+                                        full_bar(next), next_phase);
+              } else if constexpr (kPair) {
+                mma_f16_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, acc_flag);
+              } else {
+                mma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, acc_flag);
+              }
+            }
           }
-          // the last MMA of the k-block, fused with a probe of the next stage
-          constexpr uint32_t kLast = 2u * (kBlkK / 16 - 1);
-          if constexpr (kPair)
-            ready = mma_f16_pair_probe(d_tmem, adesc + kLast, bdesc + kLast, a.idesc, 1u,
-                                       full_bar(next), next_phase);
-          else
-            ready = mma_f16_probe(d_tmem, adesc + kLast, bdesc + kLast, a.idesc, 1u, full_bar(next),
-                                  next_phase);
           // frees the stage (in both CTAs of a pair) once these MMAs finish
           if constexpr (kPair)
             mma_commit_pair_multicast(empty_bar(stage), kPairMask);

@@ -48,7 +48,7 @@ def test_grid_model_matches_oracle(m, n, k, coef):
                                          (38, 8, 3), (12, 12, 24), (2, 2, 1024)])
 @pytest.mark.parametrize("p", [148, 132, 4])
 def test_hybrid_regions_match_oracle(t_m, t_n, ipt, p):
-    m, n, k = t_m * 128, t_n * 128, ipt * 64
+    m, n, k = t_m * 128, t_n * 128, ipt * 128   # BLK_N = 128 plans iterate BLK_K = 128
     t = t_m * t_n
     for mode, variant in (("hybrid", S.HYBRID_TWO_TILE), ("hybrid1", S.HYBRID_ONE_TILE)):
         d = sk.sk_plan_describe(m, n, k, mode, tile_n=128, cluster_m=1, num_sms=p)
@@ -63,7 +63,7 @@ def test_hybrid_regions_match_oracle(t_m, t_n, ipt, p):
 
 def test_describe_config_shapes():
     d = sk.sk_plan_describe(384, 384, 4096, "sk", tile_n=128, cluster_m=1)
-    assert (d["tile_n"], d["tiles"], d["iters_per_tile"]) == (128, 9, 64)
+    assert (d["tile_n"], d["tile_k"], d["tiles"], d["iters_per_tile"]) == (128, 128, 9, 32)
     assert d["mode_name"] == "sk" and 9 <= d["grid"] <= 148 and d["workspace_bytes"] > 0
     d = sk.sk_plan_describe(8192, 8192, 8192, "hybrid", tile_n=256, cluster_m=1)
     assert (d["tile_n"], d["tiles"], d["mode_name"]) == (256, 2048, "hybrid")
@@ -115,7 +115,7 @@ def test_max_segments_bounds_every_cta():
     for (m, n, k, mode, g) in [(384, 384, 4096, "sk", 148), (19 * 128, 2048, 256, "hybrid", 0),
                                (1000, 3000, 64, "auto", 0), (128, 128, 64 * 7, "sk", 5)]:
         d = sk.sk_plan_describe(m, n, k, mode, tile_n=128, grid=g, cluster_m=1)
-        prob = S.Problem(m, n, k, 128, 128, 64)
+        prob = S.Problem(m, n, k, 128, 128, d["tile_k"])
         sched = S.persistent_schedule(prob, d["grid"], d["sk_tiles"], d["raster_group"])
         assert max(len(c) for c in sched.ctas) <= d["max_segments"]
 

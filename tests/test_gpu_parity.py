@@ -92,6 +92,8 @@ def test_one_tile_hybrid_with_dp_waves():
     (130, 520, 4096, "sk", {"grid": 20}),
     (384, 384, 4096, "sk", {"tile_n": 128, "grid": 30}),
     (2944, 1536, 136, "auto", {}),
+    (1000, 1000, 1000, "sk", {"tile_n": 128, "grid": 50}),   # 128-deep iterations, ragged k tail
+    (520, 640, 192, "dp", {"tile_n": 128}),                  # last iteration: one k-block, one empty
 ])
 @pytest.mark.parametrize("c_type", ["bf16", "f32"])
 def test_cta_pairs(m, n, k, mode, attrs, c_type):
