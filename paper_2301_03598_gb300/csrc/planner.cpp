@@ -38,17 +38,17 @@ int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]) {
 // configuration (BLK_N, CTAs per cluster along M).  The first four are the
 // terms of Appendix A.1: a = fixed per-launch cost, b = a schedule with split
 // tiles (spill, signal, wait), c = one MAC-loop iteration of a unit
-// (BLK_M x BLK_N x 64), d = reading and adding one more peer's partials.  The
+// (BLK_M x BLK_N x BLK_K), d = reading and adding one more peer's partials.  The
 // fifth, e, is the per-segment cost (one accumulator through the epilogue),
 // which the paper's model folds into c.  Fitted by relative least squares to
 // the measured times of the 2,000-shape log-uniform sweep planned with each
 // configuration and each of data-parallel, two-tile hybrid and basic Stream-K
 // forced (12 plans per shape).
 void model_coefficients(int tile_n, int cluster_m, double out[5]) {
-  static const double k128x1[5] = {3.696, 4.277, 0.2877, 0.450, 0.199};
-  static const double k256x1[5] = {4.292, 8.193, 0.3922, 0.708, 0.143};
-  static const double k128x2[5] = {4.378, 4.794, 0.2845, 0.590, 0.289};
-  static const double k256x2[5] = {5.503, 10.217, 0.3013, 0.783, 0.195};
+  static const double k128x1[5] = {3.782, 3.548, 0.5514, 0.726, 0.157};
+  static const double k256x1[5] = {4.349, 8.006, 0.3922, 0.839, 0.144};
+  static const double k128x2[5] = {4.501, 4.326, 0.4446, 0.508, 0.309};
+  static const double k256x2[5] = {5.622, 9.815, 0.2957, 0.474, 0.203};
   const double* c = cluster_m == 2 ? (tile_n == 256 ? k256x2 : k128x2)
                                    : (tile_n == 256 ? k256x1 : k128x1);
   for (int i = 0; i < 5; ++i) out[i] = c[i];
