@@ -81,15 +81,20 @@ typedef enum {
                                     owner's bounded Wait must expire (failure-detection
                                     tests); -1 = off */
   SK_ATTR_CLUSTER_M = 10,    /* set/get: CTAs per cluster along M, 1 or 2 (0 = automatic);
-                                with 2, CTA pairs compute 256-row tiles and share each B
-                                tile by TMA multicast */
+                                with 2, a tcgen05 CTA pair computes each 256-row tile with
+                                two-SM MMAs, each CTA holding half of the B tile */
+  SK_ATTR_STORE = 11,        /* set/get: how the epilogue writes C when C's rows are 16-byte
+                                aligned: 0 = automatic, 1 = TMA tensor stores, 2 = coalesced
+                                global stores from the same staging buffer.  Unaligned C is
+                                always written row by row. */
   SK_ATTR_PDL = 9,           /* set/get: 1 (default) = launch with programmatic dependent
                                 launch, so the kernel's set-up overlaps the previous kernel
                                 in the stream; it touches global memory only after that
                                 kernel has completed.  0 = plain stream serialisation. */
   SK_ATTR_MODE = 20,         /* get: resolved sk_mode */
   SK_ATTR_TILE_M = 21,       /* get: BLK_M (128) */
-  SK_ATTR_TILE_K = 22,       /* get: BLK_K (64) */
+  SK_ATTR_TILE_K = 22,       /* get: BLK_K, the depth of one MAC-loop iteration (128 for
+                                BLK_N = 128, 64 for BLK_N = 256) */
   SK_ATTR_TILES_M = 23,      /* get: ceil(m / BLK_M) */
   SK_ATTR_TILES_N = 24,      /* get: ceil(n / BLK_N) */
   SK_ATTR_TILES = 25,        /* get: t */
@@ -100,10 +105,12 @@ typedef enum {
   SK_ATTR_NUM_SMS = 30,      /* get: SM count p of the plan's device */
   SK_ATTR_TRACE_INTS = 31,   /* get: int32 entries sk_gemm_traced needs */
   SK_ATTR_TRACE_CAP = 32,    /* get: trace records per CTA */
-  SK_ATTR_CTAS = 33          /* get: CTAs launched (grid * cluster_m) */
+  SK_ATTR_CTAS = 33,         /* get: CTAs launched (grid * cluster_m) */
+  SK_ATTR_SEGMENTS = 34      /* get (grouped plans): segment records of the schedule */
 } sk_attr;
 
 typedef struct sk_plan_s* sk_plan_t;
+typedef struct sk_grouped_s* sk_grouped_t;
 
 /* Host-only description of a schedule (sk_plan_describe).  The schedule's
  * unit is a cluster of cluster_m CTAs computing a tile_m x tile_n tile
@@ -255,6 +262,68 @@ int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type, sk_dtype 
 
 /* Human-readable name of an sk_status. */
 const char* sk_status_string(int status);
+
+/* ---------------------------------------------------------------- grouped GEMM
+ * Stream-K across a group of independent problems in one persistent launch
+ * (the paper's Conclusion, Section 7, names other GEMM-like workloads that
+ * suffer the same quantization as future work).  The problems' MAC-loop
+ * iterations are laid end to end, problem after problem and tile after tile
+ * in each problem's raster, and that single iteration space is scheduled like
+ * one GEMM's: Algorithm 5's within-one split over g CTAs, the two-tile hybrid
+ * of Section 5.2 over the concatenated tile list, or data-parallel waves.
+ * Problem i is C_i = alpha_i * A_i * B_i + beta_i * C_i with A_i row-major
+ * m_i x k_i, B_i column-major k_i x n_i (an n_i x k_i row-major array), C_i
+ * row-major m_i x n_i, all dense, one input type and one output type for the
+ * group, FP32 accumulation.  All problems use one tile width (BLK_N);
+ * schedules use single CTAs.
+ *
+ * sk_grouped_plan: count >= 1 problems, m/n/k host arrays of count entries
+ *   (each >= 1, k a multiple of 8 so that dense 16-bit rows are 16-byte
+ *   multiples as TMA requires); mode SK_MODE_AUTO (the model picks data-parallel, the
+ *   two-tile hybrid or basic Stream-K, and the tile width), SK_MODE_DP,
+ *   SK_MODE_SK or SK_MODE_HYBRID.  The plan owns its device schedule (one
+ *   32-byte record per segment), problem table, workspace and status words.
+ *   Returns SK_ERR_INVALID / SK_ERR_UNSUPPORTED for bad arguments,
+ *   SK_ERR_DEVICE off sm_103a, SK_ERR_CUDA / SK_ERR_NOMEM on allocation.
+ * sk_grouped_gemm: A, B, C are host arrays of count device pointers (16-byte
+ *   aligned); alpha / beta host arrays of count values or NULL (1 and 0).
+ *   Asynchronous on `stream`; tensor maps are re-encoded, and the problem
+ *   table re-uploaded, only for problems whose pointers or scalars changed
+ *   since the previous launch (the upload is stream-ordered).  One plan must
+ *   not be launched on two streams at once.
+ * sk_grouped_gemm_traced: as sk_grouped_gemm, recording the schedule as
+ *   sk_gemm_traced does (field 9 of each record holds the problem index);
+ *   trace_ints >= SK_ATTR_TRACE_INTS.
+ * sk_grouped_last_error: as sk_last_error.
+ * sk_grouped_set: SK_ATTR_TILE_N, SK_ATTR_GRID, SK_ATTR_MODE (replan),
+ *   SK_ATTR_TIMEOUT_NS, SK_ATTR_PDL, SK_ATTR_STORE.
+ * sk_grouped_get: SK_ATTR_MODE, TILE_M, TILE_N, TILE_K, GRID, CTAS, TILES,
+ *   SK_TILES, DP_TILES, WORKSPACE_BYTES, NUM_SMS, TRACE_CAP, TRACE_INTS,
+ *   TIMEOUT_NS, PDL, STORE, SEGMENTS.
+ * sk_grouped_schedule: the host copy of the schedule, 10 int32 per segment
+ *   (cta, problem, tile, tm, tn, kb0, kb1, role, peer_first, peer_last), CTA
+ *   by CTA in processing order; *count receives the number of segments; with
+ *   records == NULL only the count is returned; capacity in int32.
+ */
+int sk_grouped_plan(sk_grouped_t* out, int count, const int64_t* m, const int64_t* n,
+                    const int64_t* k, sk_dtype ab_type, sk_dtype c_type, int mode);
+int sk_grouped_gemm(sk_grouped_t plan, const void* const* A, const void* const* B,
+                    void* const* C, const float* alpha, const float* beta, void* stream);
+int sk_grouped_gemm_traced(sk_grouped_t plan, const void* const* A, const void* const* B,
+                           void* const* C, const float* alpha, const float* beta, int32_t* trace,
+                           int64_t trace_ints, void* stream);
+int sk_grouped_last_error(sk_grouped_t plan, int* device_status);
+int sk_grouped_set(sk_grouped_t plan, int attr, int64_t value);
+int sk_grouped_get(sk_grouped_t plan, int attr, int64_t* value);
+int sk_grouped_schedule(sk_grouped_t plan, int32_t* records, int64_t capacity, int64_t* count);
+int sk_grouped_destroy(sk_grouped_t plan);
+/* Host-only planning of a grouped launch for num_sms SMs (no device needed):
+ * summary receives 8 int64 (mode, tile_n, tile_k, grid, tiles, sk_tiles,
+ * workspace_bytes, max_segments) when non-NULL; records and *nrec as in
+ * sk_grouped_schedule.  tile_n 0 / grid 0 = automatic. */
+int sk_grouped_plan_describe(int count, const int64_t* m, const int64_t* n, const int64_t* k,
+                             int mode, int tile_n, int grid, int num_sms, int64_t* summary,
+                             int32_t* records, int64_t capacity, int64_t* nrec);
 
 #ifdef __cplusplus
 }

@@ -356,3 +356,99 @@ def stream_k_utilization(total_iters: int, g: int, p: Optional[int] = None) -> f
     per_cta = max(cta_iter_range(x, total_iters, g)[1] - cta_iter_range(x, total_iters, g)[0]
                   for x in range(g))
     return total_iters / (p * per_cta)
+
+
+# ---------------------------------------------------------------------------
+# Stream-K across a group of problems (the Conclusion, Section 7, names other
+# GEMM-like workloads as future work): the problems' MAC-loop iteration spaces are laid
+# end to end, problem after problem and, inside a problem, tile after tile,
+# and Algorithm 5 splits that single space evenly over g CTAs.  Tiles of
+# different problems may have different iteration counts.
+# ---------------------------------------------------------------------------
+@dataclass
+class GroupSegment:
+    """MacLoop over local iterations [local_iter, local_iter_end) of tile
+    tile_idx of problem `problem`, with the CTA's role for that tile."""
+    problem: int
+    tile_idx: int
+    local_iter: int
+    local_iter_end: int
+    role: int
+    peers: Tuple[int, ...] = ()
+
+
+def group_offsets(probs: List[Problem]) -> Tuple[List[int], List[int]]:
+    """Prefix sums: first global tile and first global iteration of each
+    problem, each list one longer than probs."""
+    tile_off, iter_off = [0], [0]
+    for p in probs:
+        tile_off.append(tile_off[-1] + p.tiles)
+        iter_off.append(iter_off[-1] + p.tiles * p.iters_per_tile)
+    return tile_off, iter_off
+
+
+def group_tile(probs: List[Problem], tile_off: List[int], gtile: int) -> Tuple[int, int]:
+    """(problem, local tile) of global tile index gtile."""
+    for pi in range(len(probs)):
+        if tile_off[pi] <= gtile < tile_off[pi + 1]:
+            return pi, gtile - tile_off[pi]
+    raise ValueError("tile out of range")
+
+
+def grouped_schedule(probs: List[Problem], g: int, sk_tiles: int) -> List[List[GroupSegment]]:
+    """Stream-K (Algorithm 5) over the first sk_tiles global tiles with g CTAs,
+    then the remaining global tiles data-parallel, tile sk_tiles + x + j*g to
+    CTA x.  Returns each CTA's segments in processing order."""
+    tile_off, iter_off = group_offsets(probs)
+    t = tile_off[-1]
+    if not (0 <= sk_tiles <= t) or g < 1:
+        raise ValueError("bad grouped schedule")
+    # global iteration of the start of global tile j (tiles laid end to end)
+    def tile_iter(j: int) -> int:
+        pi, lt = (len(probs), 0) if j == t else group_tile(probs, tile_off, j)
+        return iter_off[pi] + lt * (probs[pi].iters_per_tile if pi < len(probs) else 0)
+    sk_iters = tile_iter(sk_tiles)
+    ctas: List[List[GroupSegment]] = [[] for _ in range(g)]
+    if sk_iters > 0:
+        for x in range(g):
+            it, it_end = cta_iter_range(x, sk_iters, g)
+            while it < it_end:
+                # the tile holding iteration it
+                pi = max(q for q in range(len(probs)) if iter_off[q] <= it)
+                ipt = probs[pi].iters_per_tile
+                lt = (it - iter_off[pi]) // ipt
+                start = iter_off[pi] + lt * ipt
+                end = start + ipt
+                seg = (pi, lt, it - start, min(it_end, end) - start)
+                if it != start:
+                    ctas[x].append(GroupSegment(*seg, ROLE_PARTIAL))
+                elif it_end < end:
+                    last = cta_of_iter(end - 1, sk_iters, g)
+                    ctas[x].append(GroupSegment(*seg, ROLE_OWNER, tuple(range(x + 1, last + 1))))
+                else:
+                    ctas[x].append(GroupSegment(*seg, ROLE_WHOLE))
+                it = end
+    for x in range(g):
+        j = sk_tiles + x
+        while j < t:
+            pi, lt = group_tile(probs, tile_off, j)
+            ctas[x].append(GroupSegment(pi, lt, 0, probs[pi].iters_per_tile, ROLE_WHOLE))
+            j += g
+    return ctas
+
+
+def grouped_trace(probs: List[Problem], ctas: List[List[GroupSegment]],
+                  group_m: List[int]) -> List[Tuple[int, ...]]:
+    """Records (cta, problem, tile_idx, tm, tn, local_iter, local_iter_end,
+    role, peer_first, peer_last), CTA by CTA in processing order, with each
+    problem's tile raster (reading 2) of band height group_m[problem]."""
+    out = []
+    for x, segs in enumerate(ctas):
+        for s in segs:
+            pr = probs[s.problem]
+            tm, tn = tile_coords(s.tile_idx, pr.tiles_m, pr.tiles_n, group_m[s.problem])
+            pf = s.peers[0] if s.peers else -1
+            pl = s.peers[-1] if s.peers else -1
+            out.append((x, s.problem, s.tile_idx, tm, tn, s.local_iter, s.local_iter_end, s.role,
+                        pf, pl))
+    return out

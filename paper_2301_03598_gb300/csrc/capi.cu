@@ -14,6 +14,7 @@
 #include <mutex>
 #include <new>
 #include <type_traits>
+#include <vector>
 
 #include "../../include/streamk.h"
 #include "launch.h"
@@ -102,6 +103,7 @@ struct sk_plan_s {
   uint64_t timeout_ns = kDefaultTimeoutNs;
   int debug_skip_signal = -1;
   bool pdl = true;
+  int store_req = 0;  // SK_ATTR_STORE
   // TMA descriptor cache
   const void* cached_a = nullptr;
   const void* cached_b = nullptr;
@@ -225,6 +227,10 @@ void set_divisors(sk::SkArgs& a, const sk_schedule_info& s) {
   a.fast_iters = s.sk_iters < (int64_t(1) << 31) ? 1 : 0;
 }
 
+// The epilogue's store path for an aligned C (SkArgs::c_tma): the requested
+// one, else the default.
+int store_path(int req) { return req == 1 ? 1 : req == 2 ? 2 : 1; }
+
 // tcgen05 kind::f16 instruction descriptor: FP32 accumulator, A/B format,
 // both operands K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 uint32_t make_idesc(int in_dtype, int tile_n, int cluster_m) {
@@ -322,7 +328,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   a.C = C;
   a.ldc = p->ldc;
   a.c_vec = (p->ldc * static_cast<int64_t>(dtype_size(p->c_type))) % 16 == 0 ? 1 : 0;
-  a.c_tma = p->c_tma ? 1 : 0;
+  a.c_tma = p->c_tma ? store_path(p->store_req) : 0;
   a.alpha = alpha;
   a.beta = beta;
   const bool split = s.workspace_bytes > 0;
@@ -533,6 +539,10 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
       if (v != 0 && v != 1) return SK_ERR_INVALID;
       p->pdl = v != 0;
       return SK_OK;
+    case SK_ATTR_STORE:
+      if (v < 0 || v > 2) return SK_ERR_INVALID;
+      p->store_req = static_cast<int>(v);
+      return SK_OK;
     case SK_ATTR_CLUSTER_M: {
       if (v != 0 && v != 1 && v != 2) return SK_ERR_UNSUPPORTED;
       const int old = p->cluster_req;
@@ -562,6 +572,7 @@ int sk_plan_get(sk_plan_t p, int attr, int64_t* v) {
     case SK_ATTR_LDC: *v = p->ldc; return SK_OK;
     case SK_ATTR_DEBUG_SKIP_SIGNAL: *v = p->debug_skip_signal; return SK_OK;
     case SK_ATTR_PDL: *v = p->pdl ? 1 : 0; return SK_OK;
+    case SK_ATTR_STORE: *v = p->store_req; return SK_OK;
     case SK_ATTR_CLUSTER_M: *v = s.cluster_m; return SK_OK;
     case SK_ATTR_CTAS: *v = s.ctas; return SK_OK;
     case SK_ATTR_MODE: *v = s.mode; return SK_OK;
@@ -746,7 +757,7 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
     a.C = C;
     a.ldc = ldc;
     a.c_vec = (ldc * static_cast<int64_t>(dtype_size(c_type))) % 16 == 0 ? 1 : 0;
-    a.c_tma = c_tma ? 1 : 0;
+    a.c_tma = c_tma ? store_path(0) : 0;
     a.alpha = alpha;
     a.beta = beta;
     a.flags = split ? reinterpret_cast<uint32_t*>(scratch) : nullptr;
@@ -767,3 +778,384 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
   }
   return SK_OK;
 }
+
+// ------------------------------------------------------------------ grouped GEMM
+struct sk_grouped_s {
+  int count = 0;
+  std::vector<int64_t> m, n, k;
+  int ab_type = 0, c_type = 0;
+  int mode_req = SK_MODE_AUTO, tile_n_req = 0, grid_req = 0;
+  int device = 0, num_sms = 0;
+  sk::GroupPlan plan;
+  // device
+  sk::GroupSeg* d_segs = nullptr;
+  int32_t* d_start = nullptr;
+  sk::GroupProblem* d_probs = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int32_t* err = nullptr;
+  // host copy of the problem table (pinned) and what it was encoded for
+  sk::GroupProblem* h_probs = nullptr;
+  cudaEvent_t copied = nullptr;
+  bool copy_pending = false;
+  bool table_valid = false;
+  std::vector<const void*> enc_a, enc_b;
+  std::vector<void*> enc_c;
+  std::vector<float> enc_alpha, enc_beta;
+  // knobs
+  uint64_t timeout_ns = kDefaultTimeoutNs;
+  bool pdl = true;
+  int store_req = 0;
+  cudaStream_t last_stream = nullptr;
+  bool launched = false;
+};
+
+namespace {
+
+void grouped_free_schedule(sk_grouped_s* g) {
+  if (g->d_segs) cudaFree(g->d_segs);
+  if (g->d_start) cudaFree(g->d_start);
+  g->d_segs = nullptr;
+  g->d_start = nullptr;
+}
+
+// Plan the group and upload its segment records; grow the workspace if the
+// schedule splits tiles.  Any cached problem table is re-encoded next launch
+// (the tile width sets the tensor-map boxes).
+int grouped_replan(sk_grouped_s* g) {
+  sk::GroupPlan gp;
+  int st = sk::describe_grouped(g->count, g->m.data(), g->n.data(), g->k.data(), g->mode_req,
+                                g->tile_n_req, g->grid_req, g->num_sms, &gp);
+  if (st != SK_OK) return st;
+  if (g->launched) {
+    cudaError_t e = cudaStreamSynchronize(g->last_stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (gp.workspace_bytes > 0 && static_cast<size_t>(gp.workspace_bytes) > g->ws_bytes) {
+    if (g->ws) cudaFree(g->ws);
+    g->ws = nullptr;
+    g->ws_bytes = 0;
+    void* w = nullptr;
+    cudaError_t e = cudaMalloc(&w, static_cast<size_t>(gp.workspace_bytes));
+    if (e == cudaSuccess) e = cudaMemset(w, 0, static_cast<size_t>(gp.workspace_bytes));
+    if (e != cudaSuccess) {
+      if (w) cudaFree(w);
+      return cuda_status(e);
+    }
+    g->ws = static_cast<char*>(w);
+    g->ws_bytes = static_cast<size_t>(gp.workspace_bytes);
+  }
+  grouped_free_schedule(g);
+  void *segs = nullptr, *start = nullptr;
+  const size_t seg_bytes = std::max<size_t>(1, gp.segs.size()) * sizeof(sk::GroupSeg);
+  cudaError_t e = cudaMalloc(&segs, seg_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&start, gp.start.size() * sizeof(int32_t));
+  if (e == cudaSuccess && !gp.segs.empty())
+    e = cudaMemcpy(segs, gp.segs.data(), gp.segs.size() * sizeof(sk::GroupSeg), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(start, gp.start.data(), gp.start.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (segs) cudaFree(segs);
+    if (start) cudaFree(start);
+    return cuda_status(e);
+  }
+  g->d_segs = static_cast<sk::GroupSeg*>(segs);
+  g->d_start = static_cast<int32_t*>(start);
+  g->plan = std::move(gp);
+  g->table_valid = false;
+  return SK_OK;
+}
+
+int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B, void* const* C,
+                 const float* alpha, const float* beta, int32_t* trace, int64_t trace_ints,
+                 void* stream_v) {
+  if (g == nullptr || A == nullptr || B == nullptr || C == nullptr) return SK_ERR_INVALID;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+  const sk::GroupPlan& gp = g->plan;
+  if (trace != nullptr) {
+    const int64_t need = static_cast<int64_t>(gp.grid) *
+                         (sk::kTraceHeaderInts + static_cast<int64_t>(gp.max_segments) * sk::kTraceRecordInts);
+    if (trace_ints < need) return SK_ERR_INVALID;
+  }
+  // Encode the problems whose operands changed since the table was built
+  // (all of them after a replan), after the previous upload of the pinned
+  // table has been read.
+  std::vector<char> changed(static_cast<size_t>(g->count), 0);
+  bool dirty = false;
+  for (int i = 0; i < g->count; ++i) {
+    const float al = alpha ? alpha[i] : 1.0f, be = beta ? beta[i] : 0.0f;
+    if (A[i] == nullptr || B[i] == nullptr || C[i] == nullptr ||
+        (reinterpret_cast<uintptr_t>(A[i]) & 15u) || (reinterpret_cast<uintptr_t>(B[i]) & 15u) ||
+        (reinterpret_cast<uintptr_t>(C[i]) & 15u))
+      return SK_ERR_INVALID;
+    changed[static_cast<size_t>(i)] =
+        !g->table_valid || A[i] != g->enc_a[i] || B[i] != g->enc_b[i] || C[i] != g->enc_c[i] ||
+        al != g->enc_alpha[i] || be != g->enc_beta[i];
+    dirty = dirty || changed[static_cast<size_t>(i)];
+  }
+  if (dirty && g->copy_pending) {
+    cudaError_t e = cudaEventSynchronize(g->copied);
+    if (e != cudaSuccess) return cuda_status(e);
+    g->copy_pending = false;
+  }
+  for (int i = 0; i < g->count; ++i) {
+    if (!changed[static_cast<size_t>(i)]) continue;
+    const float al = alpha ? alpha[i] : 1.0f, be = beta ? beta[i] : 0.0f;
+    sk::GroupProblem& pr = g->h_probs[i];
+    const int64_t m = g->m[i], n = g->n[i], k = g->k[i];
+    int st = encode_operand(&pr.tmA, A[i], g->ab_type, m, k, k, sk::kBlkM);
+    if (st == SK_OK) st = encode_operand(&pr.tmB, B[i], g->ab_type, n, k, k, gp.tile_n);
+    const bool use3d = gp.tile_k == 2 * sk::kBlkK && k / sk::kBlkK >= 2;
+    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmA3, A[i], g->ab_type, m, k, k, sk::kBlkM);
+    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmB3, B[i], g->ab_type, n, k, k, gp.tile_n);
+    if (st != SK_OK) {
+      g->table_valid = false;
+      return st;
+    }
+    if (!use3d) {
+      pr.tmA3 = pr.tmA;
+      pr.tmB3 = pr.tmB;
+    }
+    const bool c_tma = encode_output(&pr.tmC, C[i], g->c_type, m, n, n);
+    if (!c_tma) pr.tmC = pr.tmA;
+    pr.C = C[i];
+    pr.ldc = n;
+    pr.m = static_cast<int32_t>(m);
+    pr.n = static_cast<int32_t>(n);
+    pr.c_tma = c_tma ? store_path(g->store_req) : 0;
+    pr.c_vec = (n * static_cast<int64_t>(dtype_size(g->c_type))) % 16 == 0 ? 1 : 0;
+    pr.alpha = al;
+    pr.beta = be;
+    g->enc_a[i] = A[i];
+    g->enc_b[i] = B[i];
+    g->enc_c[i] = C[i];
+    g->enc_alpha[i] = al;
+    g->enc_beta[i] = be;
+  }
+  if (dirty) {
+    cudaError_t e = cudaMemcpyAsync(g->d_probs, g->h_probs,
+                                    static_cast<size_t>(g->count) * sizeof(sk::GroupProblem),
+                                    cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(g->copied, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    g->copy_pending = true;
+    g->table_valid = true;
+  }
+  sk::SkArgs a{};
+  a.grid = gp.grid;
+  a.idesc = make_idesc(g->ab_type, gp.tile_n, 1);
+  a.c_tma = 0;
+  const bool split = gp.workspace_bytes > 0;
+  a.flags = split ? reinterpret_cast<uint32_t*>(g->ws) : nullptr;
+  a.partials = split ? reinterpret_cast<float*>(g->ws + sk::kFlagBytes) : nullptr;
+  a.epoch = next_epoch();
+  a.err = g->err;
+  a.trace = trace;
+  a.trace_cap = gp.max_segments;
+  a.debug_skip_signal = -1;
+  a.timeout_ns = g->timeout_ns;
+  a.pdl = g->pdl ? 1 : 0;
+  a.gsegs = g->d_segs;
+  a.gseg_start = g->d_start;
+  a.gprobs = g->d_probs;
+  const CUtensorMap& any = g->h_probs[0].tmA;
+  cudaError_t e = gp.tile_n == 256 ? sk::launch_grouped_bn256(g->c_type, any, a, split, stream)
+                                   : sk::launch_grouped_bn128(g->c_type, any, a, split, stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  g->last_stream = stream;
+  g->launched = true;
+  return SK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sk_grouped_plan(sk_grouped_t* out, int count, const int64_t* m, const int64_t* n,
+                    const int64_t* k, sk_dtype ab_type, sk_dtype c_type, int mode) {
+  if (out == nullptr) return SK_ERR_INVALID;
+  *out = nullptr;
+  if (count < 1 || count > (1 << 20) || m == nullptr || n == nullptr || k == nullptr)
+    return SK_ERR_INVALID;
+  if (!(ab_type == SK_F16 || ab_type == SK_BF16)) return SK_ERR_UNSUPPORTED;
+  if (!(c_type == SK_F32 || c_type == SK_BF16 || c_type == SK_F16)) return SK_ERR_UNSUPPORTED;
+  if (mode != SK_MODE_AUTO && mode != SK_MODE_DP && mode != SK_MODE_SK && mode != SK_MODE_HYBRID)
+    return SK_ERR_UNSUPPORTED;
+  for (int i = 0; i < count; ++i)  // dense rows of A and B must be 16-byte multiples (TMA)
+    if (k[i] < 1 || k[i] % 8 != 0) return SK_ERR_INVALID;
+  int dev = 0, major = 0, minor = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SK_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SK_ERR_CUDA;
+  if (major != 10 || minor != 3) return SK_ERR_DEVICE;
+  sk_grouped_s* g = new (std::nothrow) sk_grouped_s();
+  if (g == nullptr) return SK_ERR_NOMEM;
+  g->count = count;
+  g->m.assign(m, m + count);
+  g->n.assign(n, n + count);
+  g->k.assign(k, k + count);
+  g->ab_type = ab_type;
+  g->c_type = c_type;
+  g->mode_req = mode;
+  g->device = dev;
+  g->num_sms = sms;
+  g->enc_a.assign(count, nullptr);
+  g->enc_b.assign(count, nullptr);
+  g->enc_c.assign(count, nullptr);
+  g->enc_alpha.assign(count, 0.0f);
+  g->enc_beta.assign(count, 0.0f);
+  size_t s1 = 0, s2 = 0;
+  cudaError_t e = sk::prepare_bn128(&s1);
+  if (e == cudaSuccess) e = sk::prepare_bn256(&s2);
+  void *errw = nullptr, *probs = nullptr, *hprobs = nullptr;
+  const size_t table = static_cast<size_t>(count) * sizeof(sk::GroupProblem);
+  if (e == cudaSuccess) e = cudaMalloc(&errw, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(errw, 0, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&probs, table);
+  if (e == cudaSuccess) e = cudaMallocHost(&hprobs, table);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->copied, cudaEventDisableTiming);
+  g->err = static_cast<int32_t*>(errw);
+  g->d_probs = static_cast<sk::GroupProblem*>(probs);
+  g->h_probs = static_cast<sk::GroupProblem*>(hprobs);
+  if (e != cudaSuccess) {
+    sk_grouped_destroy(g);
+    return cuda_status(e);
+  }
+  std::memset(static_cast<void*>(g->h_probs), 0, table);
+  int st = grouped_replan(g);
+  if (st != SK_OK) {
+    sk_grouped_destroy(g);
+    return st;
+  }
+  *out = g;
+  return SK_OK;
+}
+
+int sk_grouped_destroy(sk_grouped_t g) {
+  if (g == nullptr) return SK_OK;
+  if (g->launched) cudaStreamSynchronize(g->last_stream);
+  grouped_free_schedule(g);
+  if (g->d_probs) cudaFree(g->d_probs);
+  if (g->h_probs) cudaFreeHost(g->h_probs);
+  if (g->copied) cudaEventDestroy(g->copied);
+  if (g->ws) cudaFree(g->ws);
+  if (g->err) cudaFree(g->err);
+  delete g;
+  return SK_OK;
+}
+
+int sk_grouped_gemm(sk_grouped_t g, const void* const* A, const void* const* B, void* const* C,
+                    const float* alpha, const float* beta, void* stream) {
+  return grouped_impl(g, A, B, C, alpha, beta, nullptr, 0, stream);
+}
+
+int sk_grouped_gemm_traced(sk_grouped_t g, const void* const* A, const void* const* B,
+                           void* const* C, const float* alpha, const float* beta, int32_t* trace,
+                           int64_t trace_ints, void* stream) {
+  if (trace == nullptr) return SK_ERR_INVALID;
+  return grouped_impl(g, A, B, C, alpha, beta, trace, trace_ints, stream);
+}
+
+int sk_grouped_last_error(sk_grouped_t g, int* device_status) {
+  if (g == nullptr) return SK_ERR_INVALID;
+  if (device_status) *device_status = 0;
+  cudaError_t e = g->launched ? cudaStreamSynchronize(g->last_stream) : cudaSuccess;
+  if (e != cudaSuccess) return SK_ERR_CUDA;
+  int32_t h[4] = {0, 0, 0, 0};
+  e = cudaMemcpy(h, g->err, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return SK_ERR_CUDA;
+  if (h[0] != 0 || h[3] != 0) {
+    e = cudaMemset(g->err, 0, 4 * sizeof(int32_t));
+    if (e == cudaSuccess && g->ws != nullptr) e = cudaMemset(g->ws, 0, static_cast<size_t>(sk::kFlagBytes));
+    if (e != cudaSuccess) return SK_ERR_CUDA;
+  }
+  if (device_status) *device_status = h[0];
+  return h[0] == 0 ? SK_OK : SK_ERR_TIMEOUT;
+}
+
+int sk_grouped_set(sk_grouped_t g, int attr, int64_t v) {
+  if (g == nullptr) return SK_ERR_INVALID;
+  switch (attr) {
+    case SK_ATTR_TILE_N:
+    case SK_ATTR_GRID:
+    case SK_ATTR_MODE: {
+      const int t = g->tile_n_req, gr = g->grid_req, md = g->mode_req;
+      if (attr == SK_ATTR_TILE_N) g->tile_n_req = static_cast<int>(v);
+      if (attr == SK_ATTR_GRID) g->grid_req = static_cast<int>(v);
+      if (attr == SK_ATTR_MODE) g->mode_req = static_cast<int>(v);
+      const int st = grouped_replan(g);
+      if (st != SK_OK) {
+        g->tile_n_req = t;
+        g->grid_req = gr;
+        g->mode_req = md;
+        grouped_replan(g);
+      }
+      return st;
+    }
+    case SK_ATTR_TIMEOUT_NS:
+      if (v <= 0) return SK_ERR_INVALID;
+      g->timeout_ns = static_cast<uint64_t>(v);
+      return SK_OK;
+    case SK_ATTR_PDL:
+      if (v != 0 && v != 1) return SK_ERR_INVALID;
+      g->pdl = v != 0;
+      return SK_OK;
+    case SK_ATTR_STORE:
+      if (v < 0 || v > 2) return SK_ERR_INVALID;
+      g->store_req = static_cast<int>(v);
+      g->table_valid = false;
+      return SK_OK;
+    default:
+      return SK_ERR_INVALID;
+  }
+}
+
+int sk_grouped_get(sk_grouped_t g, int attr, int64_t* v) {
+  if (g == nullptr || v == nullptr) return SK_ERR_INVALID;
+  const sk::GroupPlan& gp = g->plan;
+  switch (attr) {
+    case SK_ATTR_MODE: *v = gp.mode; return SK_OK;
+    case SK_ATTR_TILE_N: *v = gp.tile_n; return SK_OK;
+    case SK_ATTR_TILE_M: *v = sk::kBlkM; return SK_OK;
+    case SK_ATTR_TILE_K: *v = gp.tile_k; return SK_OK;
+    case SK_ATTR_GRID: *v = gp.grid; return SK_OK;
+    case SK_ATTR_CTAS: *v = gp.grid; return SK_OK;
+    case SK_ATTR_TILES: *v = gp.tiles; return SK_OK;
+    case SK_ATTR_SK_TILES: *v = gp.sk_tiles; return SK_OK;
+    case SK_ATTR_DP_TILES: *v = gp.tiles - gp.sk_tiles; return SK_OK;
+    case SK_ATTR_WORKSPACE_BYTES: *v = gp.workspace_bytes; return SK_OK;
+    case SK_ATTR_NUM_SMS: *v = g->num_sms; return SK_OK;
+    case SK_ATTR_TRACE_CAP: *v = gp.max_segments; return SK_OK;
+    case SK_ATTR_TRACE_INTS:
+      *v = static_cast<int64_t>(gp.grid) *
+           (sk::kTraceHeaderInts + static_cast<int64_t>(gp.max_segments) * sk::kTraceRecordInts);
+      return SK_OK;
+    case SK_ATTR_TIMEOUT_NS: *v = static_cast<int64_t>(g->timeout_ns); return SK_OK;
+    case SK_ATTR_PDL: *v = g->pdl ? 1 : 0; return SK_OK;
+    case SK_ATTR_STORE: *v = g->store_req; return SK_OK;
+    case SK_ATTR_SEGMENTS: *v = static_cast<int64_t>(gp.segs.size()); return SK_OK;
+    default: return SK_ERR_INVALID;
+  }
+}
+
+int sk_grouped_schedule(sk_grouped_t g, int32_t* records, int64_t capacity, int64_t* count) {
+  if (g == nullptr || count == nullptr) return SK_ERR_INVALID;
+  const sk::GroupPlan& gp = g->plan;
+  *count = static_cast<int64_t>(gp.segs.size());
+  if (records == nullptr) return SK_OK;
+  if (capacity < static_cast<int64_t>(gp.segs.size()) * 10) return SK_ERR_INVALID;
+  int64_t o = 0;
+  for (size_t x = 0; x + 1 < gp.start.size(); ++x) {
+    for (int32_t i = gp.start[x]; i < gp.start[x + 1]; ++i) {
+      const sk::GroupSeg& r = gp.segs[static_cast<size_t>(i)];
+      const int32_t f[10] = {static_cast<int32_t>(x), r.problem, r.tile, r.tm, r.tn,
+                             r.kb0, r.kb1, r.role, r.peer_first, r.peer_last};
+      for (int j = 0; j < 10; ++j) records[o++] = f[j];
+    }
+  }
+  return SK_OK;
+}
+
+}  // extern "C"

@@ -38,7 +38,7 @@ static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, CM, TC>, ta, tb, tc, ta3, tb3, args);
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, CM, TC, false>, ta, tb, tc, ta3, tb3, args);
 }
 
 template <int CM>
@@ -64,9 +64,54 @@ cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, cons
                         : launch_cm<1>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream);
 }
 
+// Grouped launches: single CTAs, segment records and problem table in args
+// (the tensor-map parameters are not read).
+template <typename TC>
+static cudaError_t launch_grouped_one(const CUtensorMap& tm, const SkArgs& args, bool cooperative,
+                                      cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(args.grid));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = Cfg<128, 1>::kSmemBytes;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[2];
+  unsigned na = 0;
+  if (cooperative) {
+    attr[na].id = cudaLaunchAttributeCooperative;
+    attr[na].val.cooperative = 1;
+    ++na;
+  }
+  if (args.pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, 1, TC, true>, tm, tm, tm, tm, tm, args);
+}
+
+cudaError_t launch_grouped_bn128(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
+                                bool cooperative, cudaStream_t stream) {
+  switch (c_dtype) {
+    case SK_F32:
+      return launch_grouped_one<float>(tm, args, cooperative, stream);
+    case SK_BF16:
+      return launch_grouped_one<__nv_bfloat16>(tm, args, cooperative, stream);
+    case SK_F16:
+      return launch_grouped_one<__half>(tm, args, cooperative, stream);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 template <int CM, typename TC>
 static cudaError_t set_smem() {
-  return cudaFuncSetAttribute(sk_gemm_kernel<128, CM, TC>,
+  cudaError_t e = cudaFuncSetAttribute(sk_gemm_kernel<128, CM, TC, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg<128, CM>::kSmemBytes);
+  if (e != cudaSuccess || CM != 1) return e;
+  return cudaFuncSetAttribute(sk_gemm_kernel<128, 1, TC, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128, CM>::kSmemBytes);
 }
 

@@ -19,6 +19,12 @@ cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, cons
 cudaError_t launch_bn256(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
                          const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
                          const SkArgs& args, bool cooperative, cudaStream_t stream);
+// A grouped launch (args.grid single CTAs walking args.gsegs); tm is any valid
+// tensor map (the kernel's tensor-map parameters are unused there).
+cudaError_t launch_grouped_bn128(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
+                                 bool cooperative, cudaStream_t stream);
+cudaError_t launch_grouped_bn256(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
+                                 bool cooperative, cudaStream_t stream);
 // Dynamic shared memory of one CTA; also sets the kernels' opt-in limit.
 cudaError_t prepare_bn128(size_t* smem_bytes);
 cudaError_t prepare_bn256(size_t* smem_bytes);

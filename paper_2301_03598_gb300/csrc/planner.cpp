@@ -277,3 +277,238 @@ extern "C" int sk_grid_model(int64_t m, int64_t n, int64_t k, int bm, int bn, in
   *g_out = sk::grid_model(tiles, ipt, p, coef);
   return SK_OK;
 }
+
+// ------------------------------------------------------------------ grouped
+namespace sk {
+
+namespace {
+
+struct GroupShape {
+  int64_t tiles_m, tiles_n, tiles, ipt, group_m, kfull64;
+};
+
+// The CTA whose share of `total` iterations (within-one split over g) holds i.
+int64_t owner_of(int64_t i, int64_t total, int64_t g) {
+  const int64_t q = total / g, r = total % g;
+  const int64_t big = r * (q + 1);
+  return i < big ? i / (q + 1) : r + (i - big) / q;
+}
+
+void raster(int64_t tile, const GroupShape& p, int64_t& tm, int64_t& tn) {
+  const int64_t band_tiles = p.group_m * p.tiles_n;
+  const int64_t band = tile / band_tiles;
+  const int64_t first_m = band * p.group_m;
+  const int64_t rows = std::min(p.group_m, p.tiles_m - first_m);
+  const int64_t local = tile - band * band_tiles;
+  tm = first_m + local % rows;
+  tn = local / rows;
+}
+
+// Lays out the schedule: Stream-K (Algorithm 5) over the first sk_tiles
+// global tiles of the concatenated problems, then the remaining tiles
+// data-parallel round-robin.  Returns false when a record field overflows.
+bool build_group(const std::vector<GroupShape>& ps, int64_t g, int64_t sk_tiles, GroupPlan* out) {
+  const size_t P = ps.size();
+  std::vector<int64_t> tile_off(P + 1, 0), iter_off(P + 1, 0);
+  for (size_t i = 0; i < P; ++i) {
+    tile_off[i + 1] = tile_off[i] + ps[i].tiles;
+    iter_off[i + 1] = iter_off[i] + ps[i].tiles * ps[i].ipt;
+  }
+  const int64_t t = tile_off[P];
+  // global iteration at which global tile sk_tiles starts
+  int64_t sk_iters = 0;
+  {
+    size_t pi = 0;
+    while (pi < P && tile_off[pi + 1] <= sk_tiles) ++pi;
+    sk_iters = pi < P ? iter_off[pi] + (sk_tiles - tile_off[pi]) * ps[pi].ipt : iter_off[P];
+  }
+  out->segs.clear();
+  out->start.assign(static_cast<size_t>(g) + 1, 0);
+  out->split = false;
+  out->sk_tiles = sk_tiles;
+  out->sk_iters = sk_iters;
+  out->tiles = t;
+  int max_segs = 0;
+  auto emit = [&](size_t pi, int64_t lt, int64_t kb0, int64_t kb1, int role, int64_t pf,
+                  int64_t pl) -> bool {
+    const GroupShape& p = ps[pi];
+    int64_t tm, tn;
+    raster(lt, p, tm, tn);
+    if (tm > 32767 || tn > 32767 || kb1 > 32767 || p.kfull64 > 32767 || lt > INT32_MAX)
+      return false;
+    GroupSeg r{};
+    r.problem = static_cast<int32_t>(pi);
+    r.tile = static_cast<int32_t>(lt);
+    r.tm = static_cast<int16_t>(tm);
+    r.tn = static_cast<int16_t>(tn);
+    r.kb0 = static_cast<int16_t>(kb0);
+    r.kb1 = static_cast<int16_t>(kb1);
+    r.role = static_cast<int16_t>(role);
+    r.kfull64 = static_cast<int16_t>(p.kfull64);
+    r.peer_first = static_cast<int16_t>(pf);
+    r.peer_last = static_cast<int16_t>(pl);
+    out->segs.push_back(r);
+    if (role != kRoleWhole) out->split = true;
+    return true;
+  };
+  for (int64_t x = 0; x < g; ++x) {
+    const size_t first = out->segs.size();
+    if (sk_iters > 0) {
+      const int64_t q = sk_iters / g, r = sk_iters % g;
+      int64_t it = x * q + std::min(x, r);
+      const int64_t it_end = it + q + (x < r ? 1 : 0);
+      size_t pi = 0;
+      while (it < it_end) {
+        while (iter_off[pi + 1] <= it) ++pi;
+        const int64_t ipt = ps[pi].ipt;
+        const int64_t lt = (it - iter_off[pi]) / ipt;
+        const int64_t start = iter_off[pi] + lt * ipt, end = start + ipt;
+        const int64_t kb0 = it - start, kb1 = std::min(it_end, end) - start;
+        bool ok;
+        if (it != start)
+          ok = emit(pi, lt, kb0, kb1, kRolePartial, -1, -1);
+        else if (it_end < end)
+          ok = emit(pi, lt, kb0, kb1, kRoleOwner, x + 1, owner_of(end - 1, sk_iters, g));
+        else
+          ok = emit(pi, lt, kb0, kb1, kRoleWhole, -1, -1);
+        if (!ok) return false;
+        it = end;
+      }
+    }
+    size_t pi = 0;
+    for (int64_t j = sk_tiles + x; j < t; j += g) {
+      while (tile_off[pi + 1] <= j) ++pi;
+      if (!emit(pi, j - tile_off[pi], 0, ps[pi].ipt, kRoleWhole, -1, -1)) return false;
+    }
+    out->start[static_cast<size_t>(x) + 1] = static_cast<int32_t>(out->segs.size());
+    max_segs = std::max(max_segs, static_cast<int>(out->segs.size() - first));
+  }
+  out->max_segments = std::max(max_segs, 1);
+  return true;
+}
+
+// Modelled time of a grouped schedule: the busiest CTA's iterations and
+// segments under the Appendix A.1 terms plus the per-segment term.
+double predict_group(const GroupPlan& gp, const double c[5]) {
+  double worst = 0.0;
+  int64_t peers_max = 1;
+  for (size_t x = 0; x + 1 < gp.start.size(); ++x) {
+    int64_t iters = 0, segs = 0;
+    for (int32_t i = gp.start[x]; i < gp.start[x + 1]; ++i) {
+      const GroupSeg& r = gp.segs[static_cast<size_t>(i)];
+      iters += r.kb1 - r.kb0;
+      ++segs;
+      if (r.role == kRoleOwner) peers_max = std::max<int64_t>(peers_max, r.peer_last - r.peer_first + 2);
+    }
+    worst = std::max(worst, c[2] * static_cast<double>(iters) + c[4] * static_cast<double>(segs));
+  }
+  const double split = gp.split ? 1.0 : 0.0;
+  return c[0] + c[1] * split + c[3] * static_cast<double>(peers_max - 1) * split + worst;
+}
+
+}  // namespace
+
+int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_t* k, int mode,
+                     int tile_n, int grid, int num_sms, GroupPlan* out) {
+  if (out == nullptr || count < 1 || m == nullptr || n == nullptr || k == nullptr || num_sms < 1 ||
+      num_sms > kMaxGrid || grid < 0 || grid > num_sms)
+    return SK_ERR_INVALID;
+  if (tile_n != 0 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  if (mode != SK_MODE_AUTO && mode != SK_MODE_DP && mode != SK_MODE_SK && mode != SK_MODE_HYBRID)
+    return SK_ERR_UNSUPPORTED;
+  int64_t max_n = 0;
+  for (int i = 0; i < count; ++i) {
+    if (m[i] < 1 || n[i] < 1 || k[i] < 1 || m[i] > INT32_MAX || n[i] > INT32_MAX || k[i] > INT32_MAX)
+      return SK_ERR_INVALID;
+    max_n = std::max(max_n, n[i]);
+  }
+  int tns[2], ntn = 0;
+  if (tile_n) {
+    tns[ntn++] = tile_n;
+  } else {
+    tns[ntn++] = 128;
+    if (max_n > 128) tns[ntn++] = 256;
+  }
+  int status = SK_ERR_INVALID;
+  double best_us = 0.0;
+  for (int i = 0; i < ntn; ++i) {
+    const int bn = tns[i];
+    const int bk = tile_k_for(bn);
+    std::vector<GroupShape> ps(static_cast<size_t>(count));
+    int64_t t = 0, total_iters = 0;
+    for (int j = 0; j < count; ++j) {
+      GroupShape& p = ps[static_cast<size_t>(j)];
+      p.tiles_m = cdiv(m[j], kTileM);
+      p.tiles_n = cdiv(n[j], bn);
+      p.tiles = p.tiles_m * p.tiles_n;
+      p.ipt = cdiv(k[j], bk);
+      p.group_m = std::min<int64_t>(p.tiles_m, 16);
+      p.kfull64 = bk == 128 && k[j] / 64 >= 2 ? k[j] / 64 : 0;
+      t += p.tiles;
+      total_iters += p.tiles * p.ipt;
+    }
+    if (t > INT32_MAX || total_iters > INT32_MAX) return SK_ERR_INVALID;
+    double c[5];
+    model_coefficients(bn, 1, c);
+    const int64_t p = num_sms;
+    // candidate (mode, sk_tiles, grid)
+    struct Cand { int mode; int64_t sk_tiles, g; };
+    std::vector<Cand> cands;
+    const int64_t g_all = grid ? grid : std::min<int64_t>(p, total_iters);
+    const int64_t g_dp = grid ? grid : std::min<int64_t>(p, t);
+    if (mode == SK_MODE_AUTO || mode == SK_MODE_DP) cands.push_back({SK_MODE_DP, 0, g_dp});
+    if (mode == SK_MODE_AUTO || mode == SK_MODE_SK) cands.push_back({SK_MODE_SK, t, g_all});
+    if (mode == SK_MODE_AUTO || mode == SK_MODE_HYBRID) {
+      const int64_t w = t / p, rem = t % p;
+      const int64_t skt = rem == 0 ? 0 : (w == 0 ? t : rem + p);
+      cands.push_back({SK_MODE_HYBRID, skt, skt == t ? g_all : (grid ? grid : p)});
+    }
+    for (const Cand& cd : cands) {
+      GroupPlan gp;
+      if (!build_group(ps, std::max<int64_t>(cd.g, 1), cd.sk_tiles, &gp)) return SK_ERR_INVALID;
+      const double us = predict_group(gp, c);
+      if (status != SK_OK || us < best_us) {
+        gp.mode = cd.mode;
+        gp.tile_n = bn;
+        gp.tile_k = bk;
+        gp.grid = static_cast<int32_t>(std::max<int64_t>(cd.g, 1));
+        gp.workspace_bytes = gp.split ? workspace_bytes_for(gp.grid, bn) : 0;
+        *out = std::move(gp);
+        best_us = us;
+        status = SK_OK;
+      }
+    }
+  }
+  return status;
+}
+
+}  // namespace sk
+
+// Host-only planning of a grouped launch (no device needed): the summary and
+// the segment records of sk_grouped_plan's schedule for num_sms SMs.
+extern "C" int sk_grouped_plan_describe(int count, const int64_t* m, const int64_t* n,
+                                        const int64_t* k, int mode, int tile_n, int grid,
+                                        int num_sms, int64_t* summary, int32_t* records,
+                                        int64_t capacity, int64_t* nrec) {
+  sk::GroupPlan gp;
+  const int st = sk::describe_grouped(count, m, n, k, mode, tile_n, grid, num_sms, &gp);
+  if (st != SK_OK) return st;
+  if (summary != nullptr) {
+    const int64_t sm[8] = {gp.mode, gp.tile_n, gp.tile_k, gp.grid, gp.tiles, gp.sk_tiles,
+                           gp.workspace_bytes, gp.max_segments};
+    for (int i = 0; i < 8; ++i) summary[i] = sm[i];
+  }
+  if (nrec != nullptr) *nrec = static_cast<int64_t>(gp.segs.size());
+  if (records == nullptr) return SK_OK;
+  if (capacity < static_cast<int64_t>(gp.segs.size()) * 10) return SK_ERR_INVALID;
+  int64_t o = 0;
+  for (size_t x = 0; x + 1 < gp.start.size(); ++x) {
+    for (int32_t i = gp.start[x]; i < gp.start[x + 1]; ++i) {
+      const sk::GroupSeg& r = gp.segs[static_cast<size_t>(i)];
+      const int32_t f[10] = {static_cast<int32_t>(x), r.problem, r.tile, r.tm, r.tn,
+                             r.kb0, r.kb1, r.role, r.peer_first, r.peer_last};
+      for (int j = 0; j < 10; ++j) records[o++] = f[j];
+    }
+  }
+  return SK_OK;
+}

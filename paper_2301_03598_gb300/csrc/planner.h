@@ -1,8 +1,10 @@
 // Host planner interface (see planner.cpp).
 #pragma once
 #include <cstdint>
+#include <vector>
 
 #include "../../include/streamk.h"
+#include "sk_args.h"
 
 namespace sk {
 
@@ -22,5 +24,18 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
 int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]);
 void model_coefficients(int tile_n, int cluster_m, double out[5]);
 int64_t workspace_bytes_for(int grid, int tile_n);
+
+// A grouped launch's schedule: per-CTA segment records (CTA x owns
+// segs[start[x] .. start[x+1])) over the problems' concatenated iteration
+// space, single CTAs, one tile width for all problems.
+struct GroupPlan {
+  int mode = 0, tile_n = 0, tile_k = 0, grid = 0, max_segments = 1;
+  int64_t tiles = 0, sk_tiles = 0, sk_iters = 0, workspace_bytes = 0;
+  bool split = false;
+  std::vector<GroupSeg> segs;
+  std::vector<int32_t> start;
+};
+int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_t* k, int mode,
+                     int tile_n, int grid, int num_sms, GroupPlan* out);
 
 }  // namespace sk

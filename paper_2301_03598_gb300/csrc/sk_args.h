@@ -3,6 +3,8 @@
 #pragma once
 #include <cstdint>
 
+#include <cuda.h>
+
 namespace sk {
 
 constexpr int kBlkM = 128;  // BLK_M: one tcgen05 M=128 MMA covers the tile height
@@ -55,6 +57,33 @@ __device__ __forceinline__ uint32_t fast_div(uint32_t n, FastDiv f) {
 }
 #endif
 
+// Grouped GEMM: one launch runs several problems as one Stream-K iteration
+// space.  The host planner lays the schedule out as per-CTA lists of segment
+// records; the kernel walks its list instead of deriving segments.
+struct alignas(16) GroupSeg {
+  int32_t problem;
+  int32_t tile;        // the problem's tile index (its raster order)
+  int16_t tm, tn;      // tile row (128 rows) and column (BLK_N columns) in the problem
+  int16_t kb0, kb1;    // MAC-loop iterations [kb0, kb1) of the tile
+  int16_t role;        // kRoleWhole / kRolePartial / kRoleOwner
+  int16_t kfull64;     // the problem's k-blocks of 64 entirely inside k
+  int16_t peer_first;  // owner: contributing CTAs, else -1
+  int16_t peer_last;
+  int32_t pad[2];
+};
+static_assert(sizeof(GroupSeg) == 32, "segment record size");
+
+// Per-problem operands of a grouped launch (device memory, 128-byte aligned
+// for the tensor maps, which TMA reads in place).
+struct alignas(128) GroupProblem {
+  CUtensorMap tmA, tmB, tmC, tmA3, tmB3;
+  void* C;
+  int64_t ldc;
+  int32_t m, n;
+  int32_t c_tma, c_vec;
+  float alpha, beta;
+};
+
 struct SkArgs {
   // problem
   int32_t m, n, k;
@@ -79,7 +108,8 @@ struct SkArgs {
   void* C;
   int64_t ldc;  // elements
   int32_t c_vec;  // rows of C start 16-byte aligned: 16-byte vector loads/stores allowed
-  int32_t c_tma;  // C is stored with TMA tensor stores (tensor map valid)
+  int32_t c_tma;  // 1: C through TMA tensor stores (tensor map valid); 2: coalesced
+                  // stores from the staging buffer; 0: row-wise stores (C not 16-byte aligned)
   float alpha, beta;
   // fixup workspace: grid slots of BLK_M x BLK_N FP32, plus one flag per slot
   float* partials;
@@ -92,6 +122,10 @@ struct SkArgs {
   int32_t debug_skip_signal;  // CTA index that withholds its Signal (tests), -1 off
   uint64_t timeout_ns;
   int32_t pdl;  // launched with programmatic stream serialization (host side only)
+  // grouped launches: CTA x walks gsegs[gseg_start[x] .. gseg_start[x+1])
+  const GroupSeg* gsegs;
+  const int32_t* gseg_start;
+  const GroupProblem* gprobs;
 };
 
 }  // namespace sk

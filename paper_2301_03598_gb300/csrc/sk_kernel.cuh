@@ -196,6 +196,65 @@ __device__ __forceinline__ void tile_coords(const SkArgs& a, int tile, int& tm, 
   tm = first_m + local - tn * rows;
 }
 
+// One segment of a CTA's walk, as every role sees it.  Peers are schedule
+// units (CTA pairs count once); the epilogue turns them into CTA indices.
+struct Seg {
+  int problem, tile, tm, tn, kb0, kb1, role, peer_first, peer_last, kfull64;
+};
+
+// A CTA's segments: derived from its Stream-K share and data-parallel tiles
+// (single GEMM), or read from the records the host laid out (grouped).
+template <bool GROUPED>
+struct SegCursor {
+  Walker w;
+  int idx, end, x;
+
+  __device__ __forceinline__ void init(const SkArgs& a, int unit) {
+    x = unit;
+    if constexpr (GROUPED) {
+      idx = a.gseg_start[unit];
+      end = a.gseg_start[unit + 1];
+    } else {
+      w.init(a, unit);
+    }
+  }
+
+  __device__ __forceinline__ bool next(const SkArgs& a, Seg& s) {
+    if constexpr (GROUPED) {
+      if (idx >= end) return false;
+      const GroupSeg r = a.gsegs[idx++];
+      s.problem = r.problem;
+      s.tile = r.tile;
+      s.tm = r.tm;
+      s.tn = r.tn;
+      s.kb0 = r.kb0;
+      s.kb1 = r.kb1;
+      s.role = r.role;
+      s.peer_first = r.peer_first;
+      s.peer_last = r.peer_last;
+      s.kfull64 = r.kfull64;
+      return true;
+    } else {
+      int tile, kb0, kb1;
+      if (!w.next(a, tile, kb0, kb1)) return false;
+      const int ipt = a.iters_per_tile;
+      s.problem = 0;
+      s.tile = tile;
+      s.kb0 = kb0;
+      s.kb1 = kb1;
+      s.role = kb0 != 0 ? kRolePartial : (kb1 != ipt ? kRoleOwner : kRoleWhole);
+      s.peer_first = s.peer_last = -1;
+      if (s.role == kRoleOwner) {
+        s.peer_first = x + 1;
+        s.peer_last = cta_of_iter(a, static_cast<int64_t>(tile) * ipt + ipt - 1);
+      }
+      tile_coords(a, tile, s.tm, s.tn);
+      s.kfull64 = a.kfull64;
+      return true;
+    }
+  }
+};
+
 template <typename TC>
 __device__ __forceinline__ float to_f32(TC v);
 template <>
@@ -231,14 +290,25 @@ __device__ __forceinline__ float2 unpack2(uint32_t u, __half*) {
   return __half22float2(h);
 }
 
+// Where and how a segment's output tile goes: the launch's C (single GEMM) or
+// the segment's problem's C (grouped).
+struct OutView {
+  void* C;
+  int64_t ldc;
+  int32_t m, n;
+  int32_t c_vec, c_tma;
+  float alpha, beta;
+  const CUtensorMap* tmC;
+};
+
 // StoreTile for one thread's 32 consecutive columns of one row:
 // C[row, col .. col+31] = alpha * v + beta * C[row, col .. col+31].
 template <typename TC>
-__device__ __forceinline__ void store_row32(const SkArgs& a, int grow, int gcol, const float (&v)[32]) {
-  if (grow >= a.m) return;
-  TC* crow = reinterpret_cast<TC*>(a.C) + static_cast<int64_t>(grow) * a.ldc + gcol;
-  const float alpha = a.alpha, beta = a.beta;
-  if (a.c_vec && gcol + 32 <= a.n) {
+__device__ __forceinline__ void store_row32(const OutView& o, int grow, int gcol, const float (&v)[32]) {
+  if (grow >= o.m) return;
+  TC* crow = reinterpret_cast<TC*>(o.C) + static_cast<int64_t>(grow) * o.ldc + gcol;
+  const float alpha = o.alpha, beta = o.beta;
+  if (o.c_vec && gcol + 32 <= o.n) {
     if constexpr (sizeof(TC) == 4) {
       float4* p = reinterpret_cast<float4*>(crow);
 #pragma unroll
@@ -282,7 +352,7 @@ __device__ __forceinline__ void store_row32(const SkArgs& a, int grow, int gcol,
   } else {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      if (gcol + j < a.n) {
+      if (gcol + j < o.n) {
         float o = alpha * v[j];
         if (beta != 0.0f) o = fmaf(beta, to_f32<TC>(crow[j]), o);
         crow[j] = from_f32<TC>(o);
@@ -291,13 +361,32 @@ __device__ __forceinline__ void store_row32(const SkArgs& a, int grow, int gcol,
   }
 }
 
+// 16 bytes of output (8 16-bit or 4 FP32 values, packed as stored) at
+// C[row, col ..]: one vector store when the chunk lies inside the matrix,
+// else element by element up to column n.
+template <typename TC>
+__device__ __forceinline__ void store_chunk16(const OutView& o, int grow, int gcol, uint32_t w0,
+                                              uint32_t w1, uint32_t w2, uint32_t w3) {
+  constexpr int kPer = 16 / static_cast<int>(sizeof(TC));
+  TC* dst = reinterpret_cast<TC*>(o.C) + static_cast<int64_t>(grow) * o.ldc + gcol;
+  if (gcol + kPer <= o.n) {
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w0, w1, w2, w3);
+  } else if (gcol < o.n) {
+    const uint32_t w[4] = {w0, w1, w2, w3};
+    const TC* vals = reinterpret_cast<const TC*>(w);
+#pragma unroll
+    for (int e = 0; e < kPer; ++e)
+      if (gcol + e < o.n) dst[e] = vals[e];
+  }
+}
+
 // v[j] += beta * C[row, col + j] for the columns of this chunk inside the matrix.
 template <typename TC>
-__device__ __forceinline__ void add_beta_c(const SkArgs& a, int grow, int gcol, float (&v)[32]) {
-  if (grow >= a.m) return;
-  const TC* crow = reinterpret_cast<const TC*>(a.C) + static_cast<int64_t>(grow) * a.ldc + gcol;
-  const float beta = a.beta;
-  if (a.c_vec && gcol + 32 <= a.n) {
+__device__ __forceinline__ void add_beta_c(const OutView& o, int grow, int gcol, float (&v)[32]) {
+  if (grow >= o.m) return;
+  const TC* crow = reinterpret_cast<const TC*>(o.C) + static_cast<int64_t>(grow) * o.ldc + gcol;
+  const float beta = o.beta;
+  if (o.c_vec && gcol + 32 <= o.n) {
     if constexpr (sizeof(TC) == 4) {
       const float4* p = reinterpret_cast<const float4*>(crow);
 #pragma unroll
@@ -325,7 +414,7 @@ __device__ __forceinline__ void add_beta_c(const SkArgs& a, int grow, int gcol, 
   } else {
 #pragma unroll
     for (int j = 0; j < 32; ++j)
-      if (gcol + j < a.n) v[j] = fmaf(beta, to_f32<TC>(crow[j]), v[j]);
+      if (gcol + j < o.n) v[j] = fmaf(beta, to_f32<TC>(crow[j]), v[j]);
   }
 }
 
@@ -335,12 +424,13 @@ __device__ __forceinline__ void add_beta_c(const SkArgs& a, int grow, int gcol, 
 // per k-block, the even CTA issues the pair MMAs (M = 256), and each CTA's
 // TMEM receives its own 128 rows of the accumulator, which its epilogue
 // spills, fixes up and stores exactly as a single CTA does.
-template <int BN, int CM, typename TC>
+template <int BN, int CM, typename TC, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmA3,
                    const __grid_constant__ CUtensorMap tmB3, const __grid_constant__ SkArgs a) {
   static_assert(CM == 1 || CM == 2, "cluster size along M");
+  static_assert(!GROUPED || CM == 1, "grouped launches use single CTAs");
   using C_ = Cfg<BN, CM>;
   constexpr int S = C_::kStages;
   constexpr int KD = C_::KD;
@@ -394,12 +484,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_barrier_init();
   }
   if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
-    if (a.c_tma) tma_prefetch_desc(&tmC);
-    if (KD == 2 && a.kfull64 >= 2) {
-      tma_prefetch_desc(&tmA3);
-      tma_prefetch_desc(&tmB3);
+    if constexpr (!GROUPED) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+      if (a.c_tma == 1) tma_prefetch_desc(&tmC);
+      if (KD == 2 && a.kfull64 >= 2) {
+        tma_prefetch_desc(&tmA3);
+        tma_prefetch_desc(&tmB3);
+      }
     }
   }
   if (warp == 1) {
@@ -424,9 +516,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ------------------------------------------------------------ producer
-      Walker w;
-      w.init(a, x);
-      int tile, kb0, kb1;
+      SegCursor<GROUPED> cur;
+      cur.init(a, x);
+      Seg sg;
+      int last_problem = -1;  // grouped: the problem whose tensor maps were last acquired
       int stage = 0;
       uint32_t phase = 0;
       int64_t issued = 0;
@@ -434,10 +527,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ready: the current stage's empty barrier is known to have completed
       // (probed while the previous stage's B load was issued).
       bool ready = false;
-      while (ok && w.next(a, tile, kb0, kb1)) {
-        int tm, tn;
-        tile_coords(a, tile, tm, tn);
-        tm = tm * CM + rank;  // this CTA's 128-row block
+      while (ok && cur.next(a, sg)) {
+        const int kb0 = sg.kb0, kb1 = sg.kb1;
+        const int tm = sg.tm * CM + rank;  // this CTA's 128-row block
+        const int tn = sg.tn;
+        const CUtensorMap *pA = &tmA, *pB = &tmB, *pA3 = &tmA3, *pB3 = &tmB3;
+        if constexpr (GROUPED) {
+          const GroupProblem* gp = a.gprobs + sg.problem;
+          pA = &gp->tmA;
+          pB = &gp->tmB;
+          pA3 = &gp->tmA3;
+          pB3 = &gp->tmB3;
+          if (sg.problem != last_problem) {
+            tensormap_acquire(pA);
+            tensormap_acquire(pB);
+            tensormap_acquire(pA3);
+            tensormap_acquire(pB3);
+            last_problem = sg.problem;
+          }
+        }
         for (int kb = kb0; kb < kb1; ++kb) {
           if (!ready && !wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) {
             ok = false;
@@ -454,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // operand; a stage reaching into the k tail loads its k-blocks as
           // 2-D boxes, whose out-of-range columns TMA fills with zeros.
           const int k0 = kb * KD;
-          const bool box3 = KD == 2 && k0 + 2 <= a.kfull64;
+          const bool box3 = KD == 2 && k0 + 2 <= sg.kfull64;
           const int brow = tn * BN + rank * (BN / CM);
           if constexpr (kPair) {
             // completing on the issuer's full barrier, which expects both
@@ -462,18 +570,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t fb = full0 + 8u * stage;
             if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C_::kStageBytes);
             if (box3) {
-              tma_load_3d_pair(stage_a(stage), &tmA3, fb, 0, tm * kBlkM, k0);
-              ready = tma_load_3d_pair_probe(stage_b(stage), &tmB3, fb, 0, brow, k0, empty_bar(next),
+              tma_load_3d_pair(stage_a(stage), pA3, fb, 0, tm * kBlkM, k0);
+              ready = tma_load_3d_pair_probe(stage_b(stage), pB3, fb, 0, brow, k0, empty_bar(next),
                                              next_phase ^ 1u);
             } else if constexpr (KD == 1) {
-              tma_load_2d_pair(stage_a(stage), &tmA, fb, k0 * kBlkK, tm * kBlkM);
-              ready = tma_load_2d_pair_probe(stage_b(stage), &tmB, fb, k0 * kBlkK, brow,
+              tma_load_2d_pair(stage_a(stage), pA, fb, k0 * kBlkK, tm * kBlkM);
+              ready = tma_load_2d_pair_probe(stage_b(stage), pB, fb, k0 * kBlkK, brow,
                                              empty_bar(next), next_phase ^ 1u);
             } else {
 #pragma unroll
               for (int j = 0; j < KD; ++j) {
-                tma_load_2d_pair(stage_a(stage) + j * C_::kSubA, &tmA, fb, (k0 + j) * kBlkK, tm * kBlkM);
-                tma_load_2d_pair(stage_b(stage) + j * C_::kSubB, &tmB, fb, (k0 + j) * kBlkK, brow);
+                tma_load_2d_pair(stage_a(stage) + j * C_::kSubA, pA, fb, (k0 + j) * kBlkK, tm * kBlkM);
+                tma_load_2d_pair(stage_b(stage) + j * C_::kSubB, pB, fb, (k0 + j) * kBlkK, brow);
               }
               ready = false;
             }
@@ -481,18 +589,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t fb = full_bar(stage);
             mbar_arrive_expect_tx(fb, C_::kStageBytes);
             if (box3) {
-              tma_load_3d(stage_a(stage), &tmA3, fb, 0, tm * kBlkM, k0);
-              ready = tma_load_3d_probe(stage_b(stage), &tmB3, fb, 0, brow, k0, empty_bar(next),
+              tma_load_3d(stage_a(stage), pA3, fb, 0, tm * kBlkM, k0);
+              ready = tma_load_3d_probe(stage_b(stage), pB3, fb, 0, brow, k0, empty_bar(next),
                                         next_phase ^ 1u);
             } else if constexpr (KD == 1) {
-              tma_load_2d(stage_a(stage), &tmA, fb, k0 * kBlkK, tm * kBlkM);
-              ready = tma_load_2d_probe(stage_b(stage), &tmB, fb, k0 * kBlkK, brow, empty_bar(next),
+              tma_load_2d(stage_a(stage), pA, fb, k0 * kBlkK, tm * kBlkM);
+              ready = tma_load_2d_probe(stage_b(stage), pB, fb, k0 * kBlkK, brow, empty_bar(next),
                                         next_phase ^ 1u);
             } else {
 #pragma unroll
               for (int j = 0; j < KD; ++j) {
-                tma_load_2d(stage_a(stage) + j * C_::kSubA, &tmA, fb, (k0 + j) * kBlkK, tm * kBlkM);
-                tma_load_2d(stage_b(stage) + j * C_::kSubB, &tmB, fb, (k0 + j) * kBlkK, brow);
+                tma_load_2d(stage_a(stage) + j * C_::kSubA, pA, fb, (k0 + j) * kBlkK, tm * kBlkM);
+                tma_load_2d(stage_b(stage) + j * C_::kSubB, pB, fb, (k0 + j) * kBlkK, brow);
               }
               ready = false;
             }
@@ -537,16 +645,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0 && !issuer) grid_launch_dependents();  // a pair's odd CTA issues nothing
     if (lane == 0 && issuer) {
       // ------------------------------------------------------------ MMA issuer
-      Walker w;
-      w.init(a, x);
-      int tile, kb0, kb1;
+      SegCursor<GROUPED> cur;
+      cur.init(a, x);
+      Seg sg;
       int stage = 0, acc = 0;
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
       // ready: the current stage's full barrier is known to have completed
       // (probed while the previous k-block's last MMA was issued).
       bool ready = false;
-      while (ok && w.next(a, tile, kb0, kb1)) {
+      while (ok && cur.next(a, sg)) {
+        const int kb0 = sg.kb0, kb1 = sg.kb1;
         if (!wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
@@ -620,11 +729,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int col_half = (warp - kEpiWarp0) >> 2;     // which interleaved column units
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
-    const int ipt = a.iters_per_tile;
-    Walker w;
-    w.init(a, x);
-    int tile, kb0, kb1, acc = 0, nrec = 0;
+    SegCursor<GROUPED> cur;
+    cur.init(a, x);
+    Seg sg;
+    int acc = 0, nrec = 0;
     uint32_t acc_phase = 0;
+    // the single GEMM's output; a grouped segment switches to its problem's
+    OutView out{a.C, a.ldc, a.m, a.n, a.c_vec, a.c_tma, a.alpha, a.beta, &tmC};
     float* const my_slot = a.partials + static_cast<size_t>(cta) * (kBlkM * BN);
     const uint32_t staging = base + static_cast<uint32_t>(C_::kStagingOffset +
                                                          (warp - kEpiWarp0) * C_::kStagingBytesPerWarp);
@@ -638,19 +749,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       tb[2] = static_cast<int32_t>(t & 0xffffffffu);
       tb[3] = static_cast<int32_t>(t >> 32);
     }
-    while (w.next(a, tile, kb0, kb1)) {
-      const bool started = kb0 == 0;
-      const bool ended = kb1 == ipt;
-      const int role = !started ? kRolePartial : (!ended ? kRoleOwner : kRoleWhole);
+    while (cur.next(a, sg)) {
+      const int tile = sg.tile, kb0 = sg.kb0, kb1 = sg.kb1, role = sg.role;
       // Peers as CTA indices: the same half (rank) of each contributing unit.
       int peer_first = -1, peer_last = -1;
       if (role == kRoleOwner) {
-        peer_first = (x + 1) * CM + rank;
-        peer_last = cta_of_iter(a, static_cast<int64_t>(tile) * ipt + ipt - 1) * CM + rank;
+        peer_first = sg.peer_first * CM + rank;
+        peer_last = sg.peer_last * CM + rank;
       }
-      int tm, tn;
-      tile_coords(a, tile, tm, tn);
-      tm = tm * CM + rank;
+      const int tm = sg.tm * CM + rank, tn = sg.tn;
+      if constexpr (GROUPED) {
+        const GroupProblem* gp = a.gprobs + sg.problem;
+        out = OutView{gp->C, gp->ldc, gp->m, gp->n, gp->c_vec, gp->c_tma, gp->alpha, gp->beta, &gp->tmC};
+        if (lane == 0 && out.c_tma == 1) tensormap_acquire(out.tmC);
+      }
 
       bool fail = !wait_bar(accf_bar(acc), acc_phase, abort_flag, a, kAtEpiAccFull);
       if (epi_any(fail)) break;
@@ -665,7 +777,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // two warps of a lane quarter take alternate units.  Only units holding
       // columns < n are read, spilled, fixed up and stored.
       constexpr int kCpu = (sizeof(TC) == 4) ? 1 : 2;  // 32-column chunks per unit
-      const int nchunks = (min(BN, a.n - col0) + 31) / 32;
+      const int nchunks = (min(BN, out.n - col0) + 31) / 32;
       const int nunits = (nchunks + kCpu - 1) / kCpu;
       const int my_last_unit = (nunits - 1 - col_half) >= 0 ? nunits - 1 - ((nunits - 1 - col_half) & 1) : -1;
       if (my_last_unit < 0) {
@@ -766,20 +878,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-        if (!a.c_tma) {
+        if (!out.c_tma) {
 #pragma unroll
           for (int cc = 0; cc < kCpu; ++cc)
-            if (cc < cvalid) store_row32<TC>(a, grow, col0 + (u * kCpu + cc) * 32, v[cc]);
+            if (cc < cvalid) store_row32<TC>(out, grow, col0 + (u * kCpu + cc) * 32, v[cc]);
           continue;
         }
         // StoreTile through a swizzled staging row and one TMA tensor store of
         // 32 rows x 128 B.
-        const float alpha = a.alpha, beta = a.beta;
+        const float alpha = out.alpha, beta = out.beta;
 #pragma unroll
         for (int cc = 0; cc < kCpu; ++cc) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[cc][j] *= alpha;
-          if (beta != 0.0f && cc < cvalid) add_beta_c<TC>(a, grow, col0 + (u * kCpu + cc) * 32, v[cc]);
+          if (beta != 0.0f && cc < cvalid) add_beta_c<TC>(out, grow, col0 + (u * kCpu + cc) * 32, v[cc]);
         }
         const uint32_t srow = staging + static_cast<uint32_t>(lane * 128);
         // the previous store from this buffer has finished reading it
@@ -802,11 +914,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                          pack2(v[cc][8 * jj + 6], v[cc][8 * jj + 7], static_cast<TC*>(nullptr)));
           }
         }
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-          tma_store_2d(&tmC, staging, col0 + u * (32 * kCpu), tm * kBlkM + quarter * 32);
-          bulk_commit_group();
+        if (out.c_tma == 1) {
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(out.tmC, staging, col0 + u * (32 * kCpu), tm * kBlkM + quarter * 32);
+            bulk_commit_group();
+          }
+        } else {
+          // The same 32 rows x 128 B through coalesced global stores: each
+          // instruction writes four whole 128-byte row segments.
+          __syncwarp();
+          const int chunk = lane & 7;
+          const int gcol = col0 + u * (32 * kCpu) + chunk * (16 / static_cast<int>(sizeof(TC)));
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int r = i * 4 + (lane >> 3);
+            const int grow_r = tm * kBlkM + quarter * 32 + r;
+            uint32_t w0, w1, w2, w3;
+            ld_shared_v4(staging + static_cast<uint32_t>(r * 128 + ((chunk ^ (r & 7)) * 16)), w0, w1, w2, w3);
+            if (grow_r < out.m) store_chunk16<TC>(out, grow_r, gcol, w0, w1, w2, w3);
+          }
+          __syncwarp();  // the staging buffer is read before the next unit overwrites it
         }
       }
       // Only owners wait inside the segment; their failure decision must be
@@ -833,7 +962,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           rec[6] = role;
           rec[7] = peer_first;
           rec[8] = peer_last;
-          rec[9] = 0;
+          rec[9] = sg.problem;
           const uint64_t ts[3] = {t_acc, t_fix, t_done};
           for (int i = 0; i < 3; ++i) {
             rec[10 + 2 * i] = static_cast<int32_t>(ts[i] & 0xffffffffu);

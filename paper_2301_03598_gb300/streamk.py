@@ -23,10 +23,12 @@ MODES = {"auto": 0, "dp": 1, "sk": 2, "hybrid": 3, "hybrid1": 4}
 MODE_NAMES = {v: k for k, v in MODES.items()}
 ATTRS = {
     "tile_n": 1, "grid": 2, "raster_group": 3, "timeout_ns": 4, "lda": 5, "ldb": 6, "ldc": 7,
-    "debug_skip_signal": 8, "pdl": 9, "cluster_m": 10, "mode": 20, "tile_m": 21, "tile_k": 22, "tiles_m": 23,
+    "debug_skip_signal": 8, "pdl": 9, "cluster_m": 10, "store": 11, "mode": 20, "tile_m": 21, "tile_k": 22, "tiles_m": 23,
     "tiles_n": 24, "tiles": 25, "iters_per_tile": 26, "sk_tiles": 27, "dp_tiles": 28,
     "workspace_bytes": 29, "num_sms": 30, "trace_ints": 31, "trace_cap": 32, "ctas": 33,
+    "segments": 34,
 }
+GROUPED_ONLY_ATTRS = ("segments",)
 TRACE_FIELDS = 9
 TRACE_HEADER = 4
 TRACE_RECORD = 16
@@ -82,11 +84,27 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(i32)]
     L.sk_gemm_noalloc.argtypes = [i64, i64, i64, i32, i32, vp, i64, vp, i64, vp, i64, f32, f32,
                                   i32, vp, vp]
+    vpp = ctypes.POINTER(vp)
+    i64p = ctypes.POINTER(i64)
+    f32p = ctypes.POINTER(f32)
+    L.sk_grouped_plan.argtypes = [ctypes.POINTER(vp), i32, i64p, i64p, i64p, i32, i32, i32]
+    L.sk_grouped_gemm.argtypes = [vp, vpp, vpp, vpp, f32p, f32p, vp]
+    L.sk_grouped_gemm_traced.argtypes = [vp, vpp, vpp, vpp, f32p, f32p, vp, i64, vp]
+    L.sk_grouped_last_error.argtypes = [vp, ctypes.POINTER(i32)]
+    L.sk_grouped_set.argtypes = [vp, i32, i64]
+    L.sk_grouped_get.argtypes = [vp, i32, i64p]
+    L.sk_grouped_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i64, i64p]
+    L.sk_grouped_destroy.argtypes = [vp]
+    L.sk_grouped_plan_describe.argtypes = [i32, i64p, i64p, i64p, i32, i32, i32, i32, i64p,
+                                           ctypes.POINTER(ctypes.c_int32), i64, i64p]
     L.sk_status_string.argtypes = [i32]
     L.sk_status_string.restype = ctypes.c_char_p
     for name in ("sk_plan", "sk_gemm", "sk_gemm_traced", "sk_last_error", "sk_plan_destroy",
                  "sk_plan_set", "sk_plan_get", "sk_plan_attach_workspace", "sk_plan_describe",
-                 "sk_grid_model", "sk_gemm_noalloc"):
+                 "sk_grid_model", "sk_gemm_noalloc", "sk_grouped_plan", "sk_grouped_gemm",
+                 "sk_grouped_gemm_traced", "sk_grouped_last_error", "sk_grouped_set",
+                 "sk_grouped_get", "sk_grouped_schedule", "sk_grouped_destroy",
+                 "sk_grouped_plan_describe"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -161,7 +179,7 @@ class Plan:
         sk_plan_set(self, attr, value)
 
     def info(self):
-        return {name: self.get(name) for name in ATTRS}
+        return {name: self.get(name) for name in ATTRS if name not in GROUPED_ONLY_ATTRS}
 
     def destroy(self):
         if self.handle:
@@ -297,3 +315,126 @@ def decode_trace(trace_host, grid: int, cap: int, with_times: bool = False):
             else:
                 out.append(fields)
     return out
+
+
+# ---------------------------------------------------------------- grouped GEMM
+class GroupedPlan:
+    """Owner of an sk_grouped_t handle (Stream-K across a group of problems)."""
+
+    def __init__(self, handle: int, shapes, a_type: str, c_type: str):
+        self.handle = handle
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        self.a_type, self.c_type = a_type, c_type
+
+    def get(self, attr) -> int:
+        v = ctypes.c_int64()
+        _check(lib().sk_grouped_get(self.handle, _code(ATTRS, attr, "attr"), ctypes.byref(v)),
+               "sk_grouped_get")
+        return v.value
+
+    def set(self, attr, value: int) -> None:
+        _check(lib().sk_grouped_set(self.handle, _code(ATTRS, attr, "attr"), int(value)),
+               "sk_grouped_set")
+
+    def info(self):
+        names = ("mode", "tile_m", "tile_n", "tile_k", "grid", "ctas", "tiles", "sk_tiles",
+                 "dp_tiles", "workspace_bytes", "num_sms", "trace_cap", "trace_ints", "segments")
+        return {name: self.get(name) for name in names}
+
+    def destroy(self):
+        if self.handle:
+            lib().sk_grouped_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sk_grouped_plan(shapes, ab_type="bf16", c_type="bf16", mode="auto") -> GroupedPlan:
+    """shapes: a sequence of (m, n, k)."""
+    cnt = len(shapes)
+    arr = lambda j: (ctypes.c_int64 * cnt)(*[int(s[j]) for s in shapes])
+    h = ctypes.c_void_p()
+    ab = _dtype_name(ab_type)
+    c = _dtype_name(c_type)
+    _check(lib().sk_grouped_plan(ctypes.byref(h), cnt, arr(0), arr(1), arr(2),
+                                 _code(DTYPES, ab, "dtype"), _code(DTYPES, c, "dtype"),
+                                 _code(MODES, mode, "mode")), "sk_grouped_plan")
+    return GroupedPlan(h.value, shapes, ab, c)
+
+
+def _ptr_array(xs):
+    return (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+
+
+def _f32_array(xs):
+    return None if xs is None else (ctypes.c_float * len(xs))(*[float(v) for v in xs])
+
+
+def sk_grouped_gemm(plan: GroupedPlan, As, Bs, Cs, alpha=None, beta=None, stream=None) -> None:
+    """C_i = alpha_i * A_i @ B_i + beta_i * C_i for every problem of the plan, in
+    one launch (A_i m x k row-major, B_i an n x k row-major tensor)."""
+    _check(lib().sk_grouped_gemm(plan.handle, _ptr_array(As), _ptr_array(Bs), _ptr_array(Cs),
+                                 _f32_array(alpha), _f32_array(beta), _stream(stream)),
+           "sk_grouped_gemm")
+
+
+def sk_grouped_gemm_traced(plan: GroupedPlan, As, Bs, Cs, alpha, beta, trace, stream=None) -> None:
+    _check(lib().sk_grouped_gemm_traced(plan.handle, _ptr_array(As), _ptr_array(Bs),
+                                        _ptr_array(Cs), _f32_array(alpha), _f32_array(beta),
+                                        _ptr(trace), trace.numel(), _stream(stream)),
+           "sk_grouped_gemm_traced")
+
+
+def sk_grouped_last_error(plan: GroupedPlan):
+    dev = ctypes.c_int(0)
+    st = lib().sk_grouped_last_error(plan.handle, ctypes.byref(dev))
+    return st, dev.value
+
+
+def sk_grouped_schedule(plan: GroupedPlan):
+    """The plan's schedule as records (cta, problem, tile, tm, tn, kb0, kb1,
+    role, peer_first, peer_last), CTA by CTA in processing order."""
+    cnt = ctypes.c_int64(0)
+    _check(lib().sk_grouped_schedule(plan.handle, None, 0, ctypes.byref(cnt)), "sk_grouped_schedule")
+    buf = (ctypes.c_int32 * (10 * max(1, cnt.value)))()
+    _check(lib().sk_grouped_schedule(plan.handle, buf, 10 * max(1, cnt.value), ctypes.byref(cnt)),
+           "sk_grouped_schedule")
+    vals = list(buf)
+    return [tuple(vals[10 * i:10 * i + 10]) for i in range(cnt.value)]
+
+
+def sk_grouped_destroy(plan: GroupedPlan) -> None:
+    plan.destroy()
+
+
+def sk_grouped_plan_describe(shapes, mode="auto", tile_n: int = 0, grid: int = 0,
+                             num_sms: int = 148):
+    """Host-only grouped planning: (summary dict, records) without a device."""
+    cnt = len(shapes)
+    arr = lambda j: (ctypes.c_int64 * cnt)(*[int(s[j]) for s in shapes])
+    m, n, k = arr(0), arr(1), arr(2)
+    summary = (ctypes.c_int64 * 8)()
+    nrec = ctypes.c_int64(0)
+    _check(lib().sk_grouped_plan_describe(cnt, m, n, k, _code(MODES, mode, "mode"), tile_n, grid,
+                                          num_sms, summary, None, 0, ctypes.byref(nrec)),
+           "sk_grouped_plan_describe")
+    buf = (ctypes.c_int32 * (10 * max(1, nrec.value)))()
+    _check(lib().sk_grouped_plan_describe(cnt, m, n, k, _code(MODES, mode, "mode"), tile_n, grid,
+                                          num_sms, summary, buf, 10 * max(1, nrec.value),
+                                          ctypes.byref(nrec)), "sk_grouped_plan_describe")
+    keys = ("mode", "tile_n", "tile_k", "grid", "tiles", "sk_tiles", "workspace_bytes",
+            "max_segments")
+    info = dict(zip(keys, list(summary)))
+    info["mode_name"] = MODE_NAMES.get(info["mode"], "?")
+    vals = list(buf)
+    return info, [tuple(vals[10 * i:10 * i + 10]) for i in range(nrec.value)]

@@ -53,8 +53,10 @@ def test_fast_division_matches_integer_division(tmp_path):
     src = tmp_path / "fastdiv.cpp"
     src.write_text(PROGRAM)
     exe = tmp_path / "fastdiv"
-    subprocess.run([cxx, "-O2", "-std=c++17", "-I", os.path.dirname(HEADER), str(src), "-o",
-                    str(exe)], check=True)
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", os.path.dirname(HEADER), "-I", cuda_inc,
+                    str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     checked, bad = map(int, out.stdout.split())
     assert out.returncode == 0 and bad == 0 and checked > 5_000_000

@@ -256,3 +256,15 @@ def test_extreme_shapes_full_size_sampled(m, n, k, mode):
                                          (4096, 4096, 4096, {"cluster_m": 2, "raster_group": 4})])
 def test_large_pairs_full_size_sampled(m, n, k, attrs):
     _sampled_check(m, n, k, 1.0, 0.5, "hybrid", seed=11, attrs=attrs)
+
+
+@pytest.mark.parametrize("m,n,k,tile_n", [(129, 255, 80, 128), (300, 40, 2000, 128),
+                                          (64, 520, 136, 256), (1000, 777, 520, 256)])
+@pytest.mark.parametrize("c_type", ["bf16", "f32"])
+@pytest.mark.parametrize("mode", ["dp", "sk"])
+def test_coalesced_store_path(m, n, k, tile_n, c_type, mode):
+    """SK_ATTR_STORE = 2: the epilogue writes C with coalesced stores from its
+    staging buffer (clipped at the ragged edges) instead of TMA stores."""
+    prob = Problem(m, n, k, "bf16", c_type, "normal", seed=m + 3 * k, beta=0.5)
+    (C,), info, _ = prob.run(1.0, 0.5, mode, plan_attrs={"tile_n": tile_n, "store": 2})
+    prob.check(C, 1.0, 0.5, f"store=2 {m}x{n}x{k} bn={tile_n} {mode}")
