@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--variants", default="auto,dp,sk")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-grouped", action="store_true")
     return ap.parse_args()
 
 
@@ -604,7 +605,82 @@ def ours_arm(args):
                                  "geomean": geomean(sp)}
         line["vs_dp_geomean"] = results[headline]["geomean_tflops"] / \
             results["dp"]["geomean_tflops"]
+    if not args.no_grouped:
+        line["grouped"] = run_grouped(max(3, min(args.steps, 10)), args.warmup)
     print(json.dumps(line), flush=True)
+
+
+def run_grouped(steps, warmup):
+    """The grouped workload (256 problems, see inputs.grouped_shapes) as one
+    Stream-K launch across all problems, against the same 256 GEMMs as
+    separate launches of the single-GEMM path replayed from one CUDA graph.
+    Inputs are device-resident; each problem has its own A, B and C."""
+    import torch
+    from paper_2301_03598_gb300 import inputs
+    from paper_2301_03598_gb300 import streamk as sk
+    shapes = inputs.grouped_shapes()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    As, Bs, Cs = [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        As.append(inputs.device_pool(m * k, "bf16", "normal", inputs.GROUPED_SEED + 3 * i, dev).view(m, k))
+        Bs.append(inputs.device_pool(n * k, "bf16", "normal", inputs.GROUPED_SEED + 3 * i + 1, dev).view(n, k))
+        Cs.append(torch.empty(m, n, dtype=torch.bfloat16, device=dev))
+    flops = float(sum(2.0 * m * n * k for m, n, k in shapes))
+    stream = torch.cuda.Stream()
+    gplan = sk.sk_grouped_plan(shapes, "bf16", "bf16", "auto")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, warmup)):
+            sk.sk_grouped_gemm(gplan, As, Bs, Cs, stream=stream)
+        ev[0].record(stream)
+        for _ in range(steps):
+            sk.sk_grouped_gemm(gplan, As, Bs, Cs, stream=stream)
+        ev[1].record(stream)
+    torch.cuda.synchronize()
+    st, dstat = sk.sk_grouped_last_error(gplan)
+    if st != sk.SK_OK:
+        raise RuntimeError(f"grouped launch status {st}/{dstat}")
+    g_ms = ev[0].elapsed_time(ev[1]) / steps
+    ginfo = gplan.info()
+    # the same problems as separate plans, one graph of 256 launches per step
+    plans = make_plans(shapes, "auto", {})
+    ws_keep = [p._workspace for p in plans]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        for p, A, B, C in zip(plans, As, Bs, Cs):
+            sk.sk_gemm(p, A, B, C, stream=stream)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            for p, A, B, C in zip(plans, As, Bs, Cs):
+                sk.sk_gemm(p, A, B, C)
+        for _ in range(max(1, warmup)):
+            graph.replay()
+        ev[0].record(stream)
+        for _ in range(steps):
+            graph.replay()
+        ev[1].record(stream)
+    torch.cuda.synchronize()
+    for p in plans:
+        st, dstat = sk.sk_last_error(p)
+        if st != sk.SK_OK:
+            raise RuntimeError(f"separate launch status {st}/{dstat}")
+    s_ms = ev[0].elapsed_time(ev[1]) / steps
+    del ws_keep
+    for p in plans:
+        p.destroy()
+    gplan.destroy()
+    return {
+        "workload": "grouped GEMM: 256 problems, m log-uniform in [16, 4096] (multiples of 16), "
+                    "n, k uniform from {1024, 2048, 4096, 8192}, BF16 in (a stand-in for the "
+                    "FP8-e4m3 inputs of the grouped configuration), FP32 accumulate, BF16 out",
+        "problems": len(shapes), "gflop": flops / 1e9,
+        "grouped": {"ms": g_ms, "tflops": flops / (g_ms * 1e-3) / 1e12, "launches_per_step": 1,
+                    "plan": {k: ginfo[k] for k in ("mode", "tile_n", "grid", "tiles", "sk_tiles")}},
+        "separate": {"ms": s_ms, "tflops": flops / (s_ms * 1e-3) / 1e12,
+                     "launches_per_step": len(shapes),
+                     "timing": "the 256 single-GEMM launches replayed from one CUDA graph"},
+        "speedup": s_ms / g_ms,
+    }
 
 
 def main():

@@ -387,6 +387,37 @@ bool build_group(const std::vector<GroupShape>& ps, int64_t g, int64_t sk_tiles,
   return true;
 }
 
+// HBM bandwidth the model assumes for operand traffic, bytes per microsecond
+// (the measured copy bandwidth of this GB300, rounded down).
+constexpr double kHbmBytesPerUs = 6.5e6;
+
+// Operand bytes a grouped schedule moves from HBM.  Data-parallel waves run p
+// neighbouring tiles of a problem's raster at once, which share A row blocks
+// and B column blocks in L2: each problem's operands come from HBM about
+// once.  A Stream-K region of more tiles than CTAs gives every CTA its own
+// contiguous run of tiles, far from its neighbours' and at different k
+// offsets, so nothing is shared: every iteration's A and B tiles come from
+// HBM.
+double group_dram_bytes(const std::vector<GroupShape>& ps, const std::vector<int64_t>& m,
+                        const std::vector<int64_t>& n, const std::vector<int64_t>& k,
+                        const GroupPlan& gp, int tile_n) {
+  const double stage = static_cast<double>(kTileM + tile_n) * tile_k_for(tile_n) * 2.0;
+  double bytes = 0.0;
+  int64_t tile0 = 0;
+  for (size_t i = 0; i < ps.size(); ++i) {
+    const int64_t t0 = tile0, t1 = tile0 + ps[i].tiles;
+    tile0 = t1;
+    const int64_t sk = std::max<int64_t>(0, std::min(t1, gp.sk_tiles) - t0);
+    const double once = 2.0 * static_cast<double>(m[i] * k[i] + n[i] * k[i]);
+    const double frac_dp = static_cast<double>(ps[i].tiles - sk) / static_cast<double>(ps[i].tiles);
+    if (gp.sk_tiles > gp.grid)
+      bytes += static_cast<double>(sk) * static_cast<double>(ps[i].ipt) * stage + once * frac_dp;
+    else
+      bytes += once;
+  }
+  return bytes;
+}
+
 // Modelled time of a grouped schedule: the busiest CTA's iterations and
 // segments under the Appendix A.1 terms plus the per-segment term.
 double predict_group(const GroupPlan& gp, const double c[5]) {
@@ -463,10 +494,13 @@ int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_
       const int64_t skt = rem == 0 ? 0 : (w == 0 ? t : rem + p);
       cands.push_back({SK_MODE_HYBRID, skt, skt == t ? g_all : (grid ? grid : p)});
     }
+    const std::vector<int64_t> mv(m, m + count), nv(n, n + count), kv(k, k + count);
     for (const Cand& cd : cands) {
       GroupPlan gp;
       if (!build_group(ps, std::max<int64_t>(cd.g, 1), cd.sk_tiles, &gp)) return SK_ERR_INVALID;
-      const double us = predict_group(gp, c);
+      gp.grid = static_cast<int32_t>(std::max<int64_t>(cd.g, 1));
+      const double us = std::max(predict_group(gp, c),
+                                 c[0] + group_dram_bytes(ps, mv, nv, kv, gp, bn) / kHbmBytesPerUs);
       if (status != SK_OK || us < best_us) {
         gp.mode = cd.mode;
         gp.tile_n = bn;

@@ -96,3 +96,20 @@ def sweep_shapes(count: int = SWEEP_COUNT, seed: int = SWEEP_SEED):
 # Extreme-quantisation shapes (m, n, k): square, deep-K skinny, tall-skinny,
 # and a tile count near the SM count.
 EXTREME_SHAPES = [(8192, 8192, 8192), (256, 256, 65536), (8192, 128, 4096), (1536, 1536, 1536)]
+
+
+# The grouped workload: 256 problems in one launch, m log-uniform in [16, 4096]
+# (rounded to a multiple of 16), n and k drawn uniformly from {1024, 2048,
+# 4096, 8192}.
+GROUPED_SEED = 2301_03598 + 4
+GROUPED_COUNT = 256
+
+
+def grouped_shapes(count: int = GROUPED_COUNT, seed: int = GROUPED_SEED):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ms = np.maximum(16, np.rint(np.exp(rng.uniform(math.log(16), math.log(4096), size=count))
+                                / 16).astype(np.int64) * 16)
+    choices = np.array([1024, 2048, 4096, 8192])
+    ns = rng.choice(choices, size=count)
+    ks = rng.choice(choices, size=count)
+    return [(int(m), int(n), int(k)) for m, n, k in zip(ms, ns, ks)]
