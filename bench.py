@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-grouped", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -607,6 +608,8 @@ def ours_arm(args):
             results["dp"]["geomean_tflops"]
     if not args.no_grouped:
         line["grouped"] = run_grouped(max(3, min(args.steps, 10)), args.warmup)
+    if not args.no_serving:
+        line["serving"] = run_serving()
     print(json.dumps(line), flush=True)
 
 
@@ -681,6 +684,73 @@ def run_grouped(steps, warmup):
                      "timing": "the 256 single-GEMM launches replayed from one CUDA graph"},
         "speedup": s_ms / g_ms,
     }
+
+
+def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
+    """The serving workload: requests arrive as a Poisson process at each rate
+    for `seconds`, each a GEMM drawn from 64 shapes (48 from the shape sweep's
+    distribution, 16 from the grouped workload's), BF16 in / FP32 accumulate /
+    BF16 out.  The continuous-batching server (batches of up to 64 requests,
+    2 concurrent launch slots, 64 GB admission budget) against per-request
+    plain launches (batches of one on one slot), both through the library's
+    server.  Latency: submission to observed completion."""
+    import torch
+    from paper_2301_03598_gb300 import inputs
+    from paper_2301_03598_gb300 import streamk as sk
+    rng = np.random.default_rng(seed)
+    sw, gr = inputs.sweep_shapes(), inputs.grouped_shapes()
+    shapes = [sw[i] for i in rng.choice(len(sw), 48, replace=False)] + \
+             [gr[i] for i in rng.choice(len(gr), 16, replace=False)]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ops = []
+    for i, (m, n, k) in enumerate(shapes):
+        ops.append((inputs.device_pool(m * k, "bf16", "normal", seed + 3 * i, dev).view(m, k),
+                    inputs.device_pool(n * k, "bf16", "normal", seed + 3 * i + 1, dev).view(n, k),
+                    torch.empty(m, n, dtype=torch.bfloat16, device=dev)))
+    flops = np.array([2.0 * m * n * k for m, n, k in shapes])
+    out = {"workload": "Poisson arrivals of single GEMMs, shapes drawn from 48 shapes of the "
+                       "sweep distribution and 16 of the grouped workload's, BF16 in, FP32 "
+                       "accumulate, BF16 out", "seconds_per_rate": seconds, "rates": {}}
+    for rate in rates:
+        n_req = int(rate * seconds)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+        pick = rng.integers(0, len(shapes), size=n_req)
+        res = {}
+        for name, mb, slots in (("server", 64, 2), ("per_request", 1, 1)):
+            srv = sk.sk_server_create("bf16", "bf16", max_batch=mb, slots=slots,
+                                      hbm_budget_bytes=64 << 30)
+            try:
+                for j in range(8):   # warm the launch path
+                    A, B, C = ops[j]
+                    srv.wait(srv.submit(A, B, C))
+                torch.cuda.synchronize()
+                tickets = []
+                t0 = time.perf_counter()
+                for a_t, j in zip(arrivals, pick):
+                    while time.perf_counter() - t0 < a_t:
+                        pass
+                    A, B, C = ops[j]
+                    tickets.append(srv.submit(A, B, C))
+                lats = []
+                for t in tickets:
+                    st, lat = srv.wait(t)
+                    if st != sk.SK_OK:
+                        raise RuntimeError(f"served request status {st}")
+                    lats.append(lat)
+                wall = time.perf_counter() - t0
+                stats = srv.stats()
+            finally:
+                srv.destroy()
+            lats = np.array(lats)
+            res[name] = {"p50_us": float(np.percentile(lats, 50)),
+                         "p99_us": float(np.percentile(lats, 99)),
+                         "mean_us": float(lats.mean()),
+                         "requests_per_s": n_req / wall,
+                         "tflops": float(flops[pick].sum() / wall / 1e12),
+                         "batches": stats["batches"] - 8, "largest_batch": stats["max_batch"]}
+        res["p99_speedup"] = res["per_request"]["p99_us"] / res["server"]["p99_us"]
+        out["rates"][str(rate)] = res
+    return out
 
 
 def main():

@@ -111,6 +111,7 @@ typedef enum {
 
 typedef struct sk_plan_s* sk_plan_t;
 typedef struct sk_grouped_s* sk_grouped_t;
+typedef struct sk_server_s* sk_server_t;
 
 /* Host-only description of a schedule (sk_plan_describe).  The schedule's
  * unit is a cluster of cluster_m CTAs computing a tile_m x tile_n tile
@@ -324,6 +325,55 @@ int sk_grouped_destroy(sk_grouped_t plan);
 int sk_grouped_plan_describe(int count, const int64_t* m, const int64_t* n, const int64_t* k,
                              int mode, int tile_n, int grid, int num_sms, int64_t* summary,
                              int32_t* records, int64_t capacity, int64_t* nrec);
+
+/* ---------------------------------------------------------------- autotuning
+ * Measured choice among the configurations the planner would otherwise pick
+ * by its model: every tile width (128, 256 when n > 128) x cluster size (1,
+ * 2 when m > 128; grouped plans: 1) x schedule (data-parallel, two-tile
+ * hybrid, basic Stream-K with the model's grid size) is planned, launched
+ * once untimed and `reps` times timed with CUDA events on `stream`, and the
+ * fastest is kept as the plan's fixed configuration (later sk_plan_get shows
+ * it).  C is overwritten with A*B (alpha 1, beta 0) by the timing launches;
+ * *best_us (when non-NULL) receives the kept configuration's mean time per
+ * launch.  Synchronous.  Candidates that cannot be planned (an attached
+ * workspace too small for them) are skipped.  Returns SK_ERR_CUDA when no
+ * candidate ran. */
+int sk_plan_autotune(sk_plan_t plan, const void* A, const void* B, void* C, int reps, void* stream,
+                     double* best_us);
+int sk_grouped_autotune(sk_grouped_t plan, const void* const* A, const void* const* B,
+                        void* const* C, int reps, void* stream, double* best_us);
+
+/* ---------------------------------------------------------------- serving loop
+ * Continuous batching over the grouped launch.  Requests (independent GEMMs,
+ * layouts and rules as for grouped problems, device pointers owned by the
+ * caller and left untouched until the request completes) are queued on
+ * submission.  A worker thread admits queued requests, oldest first, into a
+ * free launch slot: at most max_batch requests per batch, and while the
+ * operand bytes (2(mk + kn) + mn * sizeof(C)) of all admitted, unfinished
+ * requests stay within hbm_budget_bytes (a lone request is always admitted).
+ * Each batch is planned as one grouped Stream-K launch (SK_MODE_AUTO) and
+ * launched on its slot's stream; slots run concurrently, so a batch admitted
+ * while others are in flight overlaps them.  The server keeps its schedules,
+ * problem tables and fixup workspaces on the device, preallocated per slot.
+ *
+ * sk_server_create: slots 1..8 concurrent batches, max_batch 1..4096.
+ * sk_server_submit: queue one request; *ticket identifies it.  k must be a
+ *   multiple of 8; pointers 16-byte aligned.
+ * sk_server_poll: *state 0 queued, 1 running, 2 done (then *latency_us is
+ *   submission-to-completion and the ticket is retired; the return value is
+ *   the request's status).
+ * sk_server_wait: block until the request is done; returns its status.
+ * sk_server_stats: 6 int64: submitted, completed, batches launched, largest
+ *   batch, problems launched, queued now.
+ * sk_server_destroy: drain the queue, wait for every batch, free. */
+int sk_server_create(sk_server_t* out, sk_dtype ab_type, sk_dtype c_type, int max_batch, int slots,
+                     int64_t hbm_budget_bytes);
+int sk_server_submit(sk_server_t server, int64_t m, int64_t n, int64_t k, const void* A,
+                     const void* B, void* C, float alpha, float beta, uint64_t* ticket);
+int sk_server_poll(sk_server_t server, uint64_t ticket, int* state, double* latency_us);
+int sk_server_wait(sk_server_t server, uint64_t ticket, double* latency_us);
+int sk_server_stats(sk_server_t server, int64_t* stats);
+int sk_server_destroy(sk_server_t server);
 
 #ifdef __cplusplus
 }

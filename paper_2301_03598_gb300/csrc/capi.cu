@@ -19,35 +19,13 @@
 #include "../../include/streamk.h"
 #include "launch.h"
 #include "planner.h"
+#include "host_util.h"
 #include "sk_args.h"
+
+using namespace sk::host;
 
 namespace {
 
-constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;  // 2 s per device-side wait
-
-// Launch epochs are unique per process, so flags left in a workspace by any
-// earlier launch (of any plan sharing it) never match a later launch.
-std::atomic<uint32_t> g_epoch{0};
-
-uint32_t next_epoch() {
-  uint32_t e = g_epoch.fetch_add(1, std::memory_order_relaxed) + 1;
-  while (e == 0) e = g_epoch.fetch_add(1, std::memory_order_relaxed) + 1;
-  return e;
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
 
 // C = beta * C for k == 0 (no MAC-loop iterations).
 template <typename TC>
@@ -74,8 +52,6 @@ __global__ void scale_kernel(TC* C, int64_t m, int64_t n, int64_t ldc, float bet
       *p = __float2half_rn(v);
   }
 }
-
-size_t dtype_size(int t) { return t == SK_F32 ? 4 : 2; }
 
 }  // namespace
 
@@ -117,12 +93,6 @@ struct sk_plan_s {
 
 namespace {
 
-int cuda_status(cudaError_t e) {
-  if (e == cudaSuccess) return SK_OK;
-  if (e == cudaErrorMemoryAllocation) return SK_ERR_NOMEM;
-  return SK_ERR_CUDA;
-}
-
 // Run the planner for the plan's (possibly swapped) shape and make sure the
 // workspace is large enough.
 int replan(sk_plan_s* p) {
@@ -153,66 +123,6 @@ int replan(sk_plan_s* p) {
   return SK_OK;
 }
 
-int encode_operand(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows, int64_t kdim,
-                   int64_t ld, int box_rows) {
-  auto fn = encode_fn();
-  if (fn == nullptr) return SK_ERR_CUDA;
-  cuuint64_t dims[2] = {static_cast<cuuint64_t>(kdim), static_cast<cuuint64_t>(rows)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(sk::kBlkK), static_cast<cuuint32_t>(box_rows)};
-  cuuint32_t estr[2] = {1, 1};
-  CUtensorMapDataType dt =
-      dtype == SK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  CUresult r = fn(tm, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? SK_OK : SK_ERR_INVALID;
-}
-
-// The same operand viewed as {64, rows, k/64} with strides {ld, 128 B}: one
-// box {64, box_rows, 2} holds two consecutive 64-wide k-blocks.  Only the
-// k-blocks that lie entirely inside k are addressed through this view (the
-// innermost extent is 64 regardless of k); the kernel loads a tail k-block
-// through the 2-D map, which fills columns beyond k with zeros.
-int encode_operand_3d(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows, int64_t kdim,
-                      int64_t ld, int box_rows) {
-  auto fn = encode_fn();
-  if (fn == nullptr) return SK_ERR_CUDA;
-  const int64_t kfull = kdim / sk::kBlkK;
-  if (kfull < 2) return SK_ERR_INVALID;
-  cuuint64_t dims[3] = {static_cast<cuuint64_t>(sk::kBlkK), static_cast<cuuint64_t>(rows),
-                        static_cast<cuuint64_t>(kfull)};
-  cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 2, static_cast<cuuint64_t>(sk::kBlkK) * 2};
-  cuuint32_t box[3] = {static_cast<cuuint32_t>(sk::kBlkK), static_cast<cuuint32_t>(box_rows), 2};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUtensorMapDataType dt =
-      dtype == SK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  CUresult r = fn(tm, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? SK_OK : SK_ERR_INVALID;
-}
-
-// Tensor map of the output for TMA stores: rows x cols (cols contiguous),
-// boxes of 32 rows x 128 bytes, 128-byte swizzle (the epilogue's staging
-// layout).  Returns false when the layout cannot be stored by TMA.
-bool encode_output(CUtensorMap* tm, void* ptr, int c_type, int64_t rows, int64_t cols, int64_t ld) {
-  auto fn = encode_fn();
-  const int64_t esz = static_cast<int64_t>(dtype_size(c_type));
-  if (fn == nullptr || (reinterpret_cast<uintptr_t>(ptr) & 15u) || (ld * esz) % 16 != 0) return false;
-  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * esz)};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), 32};
-  cuuint32_t estr[2] = {1, 1};
-  CUtensorMapDataType dt = c_type == SK_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                           : c_type == SK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  CUresult r = fn(tm, dt, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 // The walk's precomputed divisors (see FastDiv in sk_args.h).
 void set_divisors(sk::SkArgs& a, const sk_schedule_info& s) {
   const int32_t group = std::max(1, s.raster_group);
@@ -225,23 +135,6 @@ void set_divisors(sk::SkArgs& a, const sk_schedule_info& s) {
   a.div_rows = sk::make_fastdiv(static_cast<uint32_t>(group));
   a.div_rows_last = sk::make_fastdiv(static_cast<uint32_t>(rows_last));
   a.fast_iters = s.sk_iters < (int64_t(1) << 31) ? 1 : 0;
-}
-
-// The epilogue's store path for an aligned C (SkArgs::c_tma): the requested
-// one, else the default.
-int store_path(int req) { return req == 1 ? 1 : req == 2 ? 2 : 1; }
-
-// tcgen05 kind::f16 instruction descriptor: FP32 accumulator, A/B format,
-// both operands K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-uint32_t make_idesc(int in_dtype, int tile_n, int cluster_m) {
-  const uint32_t fmt = in_dtype == SK_BF16 ? 1u : 0u;
-  uint32_t d = 0;
-  d |= 1u << 4;                                         // D: F32
-  d |= fmt << 7;                                        // A: F16 / BF16
-  d |= fmt << 10;                                       // B: F16 / BF16
-  d |= static_cast<uint32_t>(tile_n >> 3) << 17;        // N
-  d |= static_cast<uint32_t>((sk::kBlkM * cluster_m) >> 4) << 24;  // M (256 for a CTA pair)
-  return d;
 }
 
 int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, float beta,
@@ -1156,6 +1049,112 @@ int sk_grouped_schedule(sk_grouped_t g, int32_t* records, int64_t capacity, int6
     }
   }
   return SK_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ autotuning
+namespace {
+
+// Mean device time of `reps` launches of `launch` on `stream` (after one
+// untimed launch), in microseconds; negative on a launch or device error.
+template <typename F>
+double time_launches(F&& launch, int reps, cudaStream_t stream) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.0;
+  double us = -1.0;
+  if (launch() == SK_OK && cudaEventRecord(e0, stream) == cudaSuccess) {
+    bool ok = true;
+    for (int r = 0; r < reps && ok; ++r) ok = launch() == SK_OK;
+    float ms = 0.0f;
+    if (ok && cudaEventRecord(e1, stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+      us = 1e3 * ms / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return us;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sk_plan_autotune(sk_plan_t p, const void* A, const void* B, void* C, int reps, void* stream_v,
+                     double* best_us) {
+  if (p == nullptr || reps < 1) return SK_ERR_INVALID;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+  const int saved[4] = {p->tile_n_req, p->cluster_req, p->mode_req, p->grid_req};
+  const int64_t km = p->swap ? p->n : p->m, kn = p->swap ? p->m : p->n;
+  const int tns[2] = {128, 256}, cms[2] = {1, 2}, modes[3] = {SK_MODE_DP, SK_MODE_HYBRID, SK_MODE_SK};
+  double best = -1.0;
+  int bt = saved[0], bc = saved[1], bm = saved[2];
+  for (int tn : tns) {
+    if (tn == 256 && kn <= 128) continue;
+    for (int cm : cms) {
+      if (cm == 2 && km <= sk::kTileM) continue;
+      for (int md : modes) {
+        p->tile_n_req = tn;
+        p->cluster_req = cm;
+        p->mode_req = md;
+        p->grid_req = 0;
+        if (replan(p) != SK_OK) continue;  // e.g. an attached workspace too small for it
+        const double us = time_launches(
+            [&] { return gemm_impl(p, A, B, C, 1.0f, 0.0f, nullptr, 0, stream); }, reps, stream);
+        int dev_status = 0;
+        if (us < 0.0 || sk_last_error(p, &dev_status) != SK_OK) continue;
+        if (best < 0.0 || us < best) {
+          best = us;
+          bt = tn;
+          bc = cm;
+          bm = md;
+        }
+      }
+    }
+  }
+  p->tile_n_req = best < 0.0 ? saved[0] : bt;
+  p->cluster_req = best < 0.0 ? saved[1] : bc;
+  p->mode_req = best < 0.0 ? saved[2] : bm;
+  p->grid_req = best < 0.0 ? saved[3] : 0;
+  const int st = replan(p);
+  if (st != SK_OK) return st;
+  if (best_us) *best_us = best;
+  return best < 0.0 ? SK_ERR_CUDA : SK_OK;
+}
+
+int sk_grouped_autotune(sk_grouped_t g, const void* const* A, const void* const* B, void* const* C,
+                        int reps, void* stream_v, double* best_us) {
+  if (g == nullptr || reps < 1) return SK_ERR_INVALID;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+  const int saved[3] = {g->tile_n_req, g->mode_req, g->grid_req};
+  const int tns[2] = {128, 256}, modes[3] = {SK_MODE_DP, SK_MODE_HYBRID, SK_MODE_SK};
+  double best = -1.0;
+  int bt = saved[0], bm = saved[1];
+  for (int tn : tns) {
+    for (int md : modes) {
+      g->tile_n_req = tn;
+      g->mode_req = md;
+      g->grid_req = 0;
+      if (grouped_replan(g) != SK_OK) continue;
+      const double us = time_launches(
+          [&] { return grouped_impl(g, A, B, C, nullptr, nullptr, nullptr, 0, stream); }, reps,
+          stream);
+      int dev_status = 0;
+      if (us < 0.0 || sk_grouped_last_error(g, &dev_status) != SK_OK) continue;
+      if (best < 0.0 || us < best) {
+        best = us;
+        bt = tn;
+        bm = md;
+      }
+    }
+  }
+  g->tile_n_req = best < 0.0 ? saved[0] : bt;
+  g->mode_req = best < 0.0 ? saved[1] : bm;
+  g->grid_req = best < 0.0 ? saved[2] : 0;
+  const int st = grouped_replan(g);
+  if (st != SK_OK) return st;
+  if (best_us) *best_us = best;
+  return best < 0.0 ? SK_ERR_CUDA : SK_OK;
 }
 
 }  // extern "C"

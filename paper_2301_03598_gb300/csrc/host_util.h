@@ -1,0 +1,36 @@
+// Host helpers shared by the C ABI's translation units (host_util.cu).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace sk {
+namespace host {
+
+constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;  // 2 s per device-side wait
+
+// A launch epoch unique in this process (never 0).
+uint32_t next_epoch();
+// cuTensorMapEncodeTiled from the driver, or nullptr.
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
+size_t dtype_size(int t);
+int cuda_status(cudaError_t e);
+// 2-D map of a K-contiguous operand (rows x kdim, pitch ld elements), boxes of
+// one 64-wide k-block x box_rows rows, 128-byte swizzle.
+int encode_operand(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows, int64_t kdim,
+                   int64_t ld, int box_rows);
+// 3-D view {64, rows, k/64} of the same operand: boxes of two k-blocks.
+int encode_operand_3d(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows, int64_t kdim,
+                      int64_t ld, int box_rows);
+// Output map for TMA stores; false when C cannot be stored by TMA.
+bool encode_output(CUtensorMap* tm, void* ptr, int c_type, int64_t rows, int64_t cols, int64_t ld);
+// The epilogue store path for an aligned C (SkArgs::c_tma) for a request.
+int store_path(int req);
+// tcgen05 kind::f16 instruction descriptor.
+uint32_t make_idesc(int in_dtype, int tile_n, int cluster_m);
+
+}  // namespace host
+}  // namespace sk

@@ -1,0 +1,415 @@
+// A serving loop over the grouped Stream-K launch: requests (independent
+// GEMMs of any shape) are queued as they arrive; a worker thread admits them
+// into batches, bounded by a problem count and by the HBM their operands
+// pin, plans each batch as one Stream-K iteration space (the grouped
+// schedule), and launches it on one of a few streams, so that a batch admitted
+// while others run overlaps them on the device.  Completion is observed with
+// events; each request's latency runs from submission to that observation.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/streamk.h"
+#include "host_util.h"
+#include "launch.h"
+#include "planner.h"
+#include "sk_args.h"
+
+using namespace sk::host;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+struct Request {
+  uint64_t id;
+  int64_t m, n, k;
+  const void* A;
+  const void* B;
+  void* C;
+  float alpha, beta;
+  int64_t bytes;
+  Clock::time_point submitted;
+};
+
+// One batch in flight: its stream, buffers and requests.
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  sk::GroupSeg* d_segs = nullptr;
+  int32_t* d_start = nullptr;
+  sk::GroupProblem* d_probs = nullptr;
+  int32_t* d_err = nullptr;
+  char* ws = nullptr;
+  sk::GroupSeg* h_segs = nullptr;   // pinned staging of the uploads
+  int32_t* h_start = nullptr;
+  sk::GroupProblem* h_probs = nullptr;
+  int32_t* h_err = nullptr;
+  std::vector<Request> reqs;
+  int64_t bytes = 0;
+  bool busy = false;
+};
+
+}  // namespace
+
+struct sk_server_s {
+  int ab_type = 0, c_type = 0, max_batch = 1, num_sms = 0;
+  int64_t budget = 0, segs_cap = 0;
+  std::vector<Slot> slots;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request> pending;
+  // id -> (state, latency_us, status): state 0 queued, 1 running, 2 done
+  struct Entry {
+    int state = 0;
+    int status = SK_OK;
+    double latency_us = 0.0;
+  };
+  std::unordered_map<uint64_t, Entry> entries;
+  std::condition_variable done_cv;
+  int64_t inflight_bytes = 0;
+  uint64_t next_id = 1;
+  int64_t submitted = 0, completed = 0, batches = 0, max_batch_seen = 0, problems_launched = 0;
+  bool stop = false;
+  int device = 0;
+  std::thread worker;
+};
+
+namespace {
+
+constexpr int64_t kSegsPerProblem = 1024;  // record capacity per admitted problem (grown on demand)
+
+void free_slot(Slot& s) {
+  if (s.d_segs) cudaFree(s.d_segs);
+  if (s.d_start) cudaFree(s.d_start);
+  if (s.d_probs) cudaFree(s.d_probs);
+  if (s.d_err) cudaFree(s.d_err);
+  if (s.ws) cudaFree(s.ws);
+  if (s.h_segs) cudaFreeHost(s.h_segs);
+  if (s.h_start) cudaFreeHost(s.h_start);
+  if (s.h_probs) cudaFreeHost(s.h_probs);
+  if (s.h_err) cudaFreeHost(s.h_err);
+  if (s.done) cudaEventDestroy(s.done);
+  if (s.stream) cudaStreamDestroy(s.stream);
+  s = Slot();
+}
+
+cudaError_t alloc_slot(Slot& s, int max_batch, int64_t segs_cap, int num_sms) {
+  cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+  const size_t ws = static_cast<size_t>(sk::kFlagBytes) + static_cast<size_t>(num_sms) * sk::kBlkM * 256 * 4;
+  if (e == cudaSuccess) e = cudaMalloc(&s.d_segs, static_cast<size_t>(segs_cap) * sizeof(sk::GroupSeg));
+  if (e == cudaSuccess) e = cudaMalloc(&s.d_start, static_cast<size_t>(num_sms + 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s.d_probs, static_cast<size_t>(max_batch) * sizeof(sk::GroupProblem));
+  if (e == cudaSuccess) e = cudaMalloc(&s.d_err, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(s.d_err, 0, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s.ws, ws);
+  if (e == cudaSuccess) e = cudaMemset(s.ws, 0, ws);
+  if (e == cudaSuccess) e = cudaMallocHost(&s.h_segs, static_cast<size_t>(segs_cap) * sizeof(sk::GroupSeg));
+  if (e == cudaSuccess) e = cudaMallocHost(&s.h_start, static_cast<size_t>(num_sms + 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&s.h_probs, static_cast<size_t>(max_batch) * sizeof(sk::GroupProblem));
+  if (e == cudaSuccess) e = cudaMallocHost(&s.h_err, 4 * sizeof(int32_t));
+  return e;
+}
+
+// Plan and launch the requests of a slot as one grouped launch.  Returns an
+// sk_status; on failure nothing is in flight on the slot.
+int launch_slot(sk_server_s* sv, Slot& s) {
+  const int count = static_cast<int>(s.reqs.size());
+  std::vector<int64_t> m(count), n(count), k(count);
+  for (int i = 0; i < count; ++i) {
+    m[i] = s.reqs[i].m;
+    n[i] = s.reqs[i].n;
+    k[i] = s.reqs[i].k;
+  }
+  sk::GroupPlan gp;
+  int st = sk::describe_grouped(count, m.data(), n.data(), k.data(), SK_MODE_AUTO, 0, 0,
+                                sv->num_sms, &gp);
+  if (st != SK_OK) return st;
+  if (static_cast<int64_t>(gp.segs.size()) > sv->segs_cap) return SK_ERR_NOMEM;
+  for (int i = 0; i < count; ++i) {
+    const Request& r = s.reqs[i];
+    sk::GroupProblem& pr = s.h_probs[i];
+    std::memset(static_cast<void*>(&pr), 0, sizeof(pr));
+    st = encode_operand(&pr.tmA, r.A, sv->ab_type, r.m, r.k, r.k, sk::kBlkM);
+    if (st == SK_OK) st = encode_operand(&pr.tmB, r.B, sv->ab_type, r.n, r.k, r.k, gp.tile_n);
+    const bool use3d = gp.tile_k == 2 * sk::kBlkK && r.k / sk::kBlkK >= 2;
+    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmA3, r.A, sv->ab_type, r.m, r.k, r.k, sk::kBlkM);
+    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmB3, r.B, sv->ab_type, r.n, r.k, r.k, gp.tile_n);
+    if (st != SK_OK) return st;
+    if (!use3d) {
+      pr.tmA3 = pr.tmA;
+      pr.tmB3 = pr.tmB;
+    }
+    const bool c_tma = encode_output(&pr.tmC, r.C, sv->c_type, r.m, r.n, r.n);
+    if (!c_tma) pr.tmC = pr.tmA;
+    pr.C = r.C;
+    pr.ldc = r.n;
+    pr.m = static_cast<int32_t>(r.m);
+    pr.n = static_cast<int32_t>(r.n);
+    pr.c_tma = c_tma ? store_path(0) : 0;
+    pr.c_vec = (r.n * static_cast<int64_t>(dtype_size(sv->c_type))) % 16 == 0 ? 1 : 0;
+    pr.alpha = r.alpha;
+    pr.beta = r.beta;
+  }
+  std::memcpy(s.h_segs, gp.segs.data(), gp.segs.size() * sizeof(sk::GroupSeg));
+  std::memcpy(s.h_start, gp.start.data(), gp.start.size() * sizeof(int32_t));
+  cudaError_t e = cudaMemcpyAsync(s.d_segs, s.h_segs, gp.segs.size() * sizeof(sk::GroupSeg),
+                                  cudaMemcpyHostToDevice, s.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s.d_start, s.h_start, gp.start.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice, s.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s.d_probs, s.h_probs, static_cast<size_t>(count) * sizeof(sk::GroupProblem),
+                        cudaMemcpyHostToDevice, s.stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  sk::SkArgs a{};
+  a.grid = gp.grid;
+  a.idesc = make_idesc(sv->ab_type, gp.tile_n, 1);
+  const bool split = gp.workspace_bytes > 0;
+  a.flags = split ? reinterpret_cast<uint32_t*>(s.ws) : nullptr;
+  a.partials = split ? reinterpret_cast<float*>(s.ws + sk::kFlagBytes) : nullptr;
+  a.epoch = next_epoch();
+  a.err = s.d_err;
+  a.trace_cap = gp.max_segments;
+  a.debug_skip_signal = -1;
+  a.timeout_ns = kDefaultTimeoutNs;
+  a.pdl = 0;
+  a.gsegs = s.d_segs;
+  a.gseg_start = s.d_start;
+  a.gprobs = s.d_probs;
+  e = gp.tile_n == 256 ? sk::launch_grouped_bn256(sv->c_type, s.h_probs[0].tmA, a, split, s.stream)
+                       : sk::launch_grouped_bn128(sv->c_type, s.h_probs[0].tmA, a, split, s.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_err, s.d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  ++sv->batches;
+  sv->problems_launched += count;
+  sv->max_batch_seen = std::max<int64_t>(sv->max_batch_seen, count);
+  return SK_OK;
+}
+
+void finish(sk_server_s* sv, Slot& s, int status) {
+  const auto now = Clock::now();
+  for (const Request& r : s.reqs) {
+    auto& e = sv->entries[r.id];
+    e.state = 2;
+    e.status = status;
+    e.latency_us = std::chrono::duration<double, std::micro>(now - r.submitted).count();
+    ++sv->completed;
+  }
+  sv->inflight_bytes -= s.bytes;
+  s.reqs.clear();
+  s.bytes = 0;
+  s.busy = false;
+}
+
+void worker_loop(sk_server_s* sv) {
+  cudaSetDevice(sv->device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  while (true) {
+    // retire finished batches
+    bool any_busy = false;
+    for (Slot& s : sv->slots) {
+      if (!s.busy) continue;
+      const cudaError_t q = cudaEventQuery(s.done);
+      if (q == cudaErrorNotReady) {
+        any_busy = true;
+        continue;
+      }
+      int status = q == cudaSuccess ? SK_OK : SK_ERR_CUDA;
+      if (status == SK_OK && s.h_err[0] != 0) {
+        status = SK_ERR_TIMEOUT;
+        cudaMemset(s.d_err, 0, 4 * sizeof(int32_t));
+        cudaMemset(s.ws, 0, static_cast<size_t>(sk::kFlagBytes));
+      }
+      finish(sv, s, status);
+      sv->done_cv.notify_all();
+    }
+    if (sv->stop && sv->pending.empty() && !any_busy) break;
+    // admit a batch into a free slot
+    Slot* free_slot_p = nullptr;
+    for (Slot& s : sv->slots)
+      if (!s.busy) {
+        free_slot_p = &s;
+        break;
+      }
+    if (free_slot_p != nullptr && !sv->pending.empty()) {
+      Slot& s = *free_slot_p;
+      while (!sv->pending.empty() && static_cast<int>(s.reqs.size()) < sv->max_batch) {
+        const Request& r = sv->pending.front();
+        const bool nothing_else = s.reqs.empty() && sv->inflight_bytes == 0;
+        if (!nothing_else && sv->inflight_bytes + s.bytes + r.bytes > sv->budget) break;
+        s.bytes += r.bytes;
+        s.reqs.push_back(r);
+        sv->entries[r.id].state = 1;
+        sv->pending.pop_front();
+      }
+      if (!s.reqs.empty()) {
+        sv->inflight_bytes += s.bytes;
+        s.busy = true;
+        const int st = launch_slot(sv, s);
+        if (st != SK_OK) {
+          finish(sv, s, st);
+          sv->done_cv.notify_all();
+        }
+        continue;
+      }
+    }
+    // nothing to launch now: poll in-flight batches, or sleep until a submission
+    if (any_busy) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(2));
+      lk.lock();
+    } else {
+      sv->cv.wait_for(lk, std::chrono::milliseconds(5),
+                      [&] { return sv->stop || !sv->pending.empty(); });
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sk_server_create(sk_server_t* out, sk_dtype ab_type, sk_dtype c_type, int max_batch, int slots,
+                     int64_t hbm_budget_bytes) {
+  if (out == nullptr) return SK_ERR_INVALID;
+  *out = nullptr;
+  if (max_batch < 1 || max_batch > 4096 || slots < 1 || slots > 8 || hbm_budget_bytes <= 0)
+    return SK_ERR_INVALID;
+  if (!(ab_type == SK_F16 || ab_type == SK_BF16)) return SK_ERR_UNSUPPORTED;
+  if (!(c_type == SK_F32 || c_type == SK_BF16 || c_type == SK_F16)) return SK_ERR_UNSUPPORTED;
+  int dev = 0, major = 0, minor = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SK_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SK_ERR_CUDA;
+  if (major != 10 || minor != 3) return SK_ERR_DEVICE;
+  size_t s1 = 0, s2 = 0;
+  cudaError_t e = sk::prepare_bn128(&s1);
+  if (e == cudaSuccess) e = sk::prepare_bn256(&s2);
+  if (e != cudaSuccess) return cuda_status(e);
+  sk_server_s* sv = new (std::nothrow) sk_server_s();
+  if (sv == nullptr) return SK_ERR_NOMEM;
+  sv->ab_type = ab_type;
+  sv->c_type = c_type;
+  sv->max_batch = max_batch;
+  sv->num_sms = sms;
+  sv->budget = hbm_budget_bytes;
+  sv->device = dev;
+  sv->segs_cap = std::max<int64_t>(static_cast<int64_t>(max_batch) * kSegsPerProblem, 65536);
+  sv->slots.resize(static_cast<size_t>(slots));
+  for (Slot& s : sv->slots) {
+    e = alloc_slot(s, max_batch, sv->segs_cap, sms);
+    if (e != cudaSuccess) {
+      for (Slot& t : sv->slots) free_slot(t);
+      delete sv;
+      return cuda_status(e);
+    }
+  }
+  sv->worker = std::thread(worker_loop, sv);
+  *out = sv;
+  return SK_OK;
+}
+
+int sk_server_submit(sk_server_t sv, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                     void* C, float alpha, float beta, uint64_t* ticket) {
+  if (sv == nullptr || ticket == nullptr || m < 1 || n < 1 || k < 1 || k % 8 != 0 ||
+      m > INT32_MAX || n > INT32_MAX || k > INT32_MAX || A == nullptr || B == nullptr ||
+      C == nullptr || (reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u) ||
+      (reinterpret_cast<uintptr_t>(C) & 15u))
+    return SK_ERR_INVALID;
+  Request r{};
+  r.m = m;
+  r.n = n;
+  r.k = k;
+  r.A = A;
+  r.B = B;
+  r.C = C;
+  r.alpha = alpha;
+  r.beta = beta;
+  r.bytes = 2 * (m * k + n * k) + m * n * static_cast<int64_t>(dtype_size(sv->c_type));
+  r.submitted = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) return SK_ERR_INVALID;
+    r.id = sv->next_id++;
+    sv->entries[r.id] = sk_server_s::Entry{};
+    sv->pending.push_back(r);
+    ++sv->submitted;
+  }
+  sv->cv.notify_one();
+  *ticket = r.id;
+  return SK_OK;
+}
+
+int sk_server_poll(sk_server_t sv, uint64_t ticket, int* state, double* latency_us) {
+  if (sv == nullptr || state == nullptr) return SK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->entries.find(ticket);
+  if (it == sv->entries.end()) return SK_ERR_INVALID;
+  *state = it->second.state;
+  if (latency_us) *latency_us = it->second.latency_us;
+  if (it->second.state == 2) {
+    const int st = it->second.status;
+    sv->entries.erase(it);
+    return st;
+  }
+  return SK_OK;
+}
+
+int sk_server_wait(sk_server_t sv, uint64_t ticket, double* latency_us) {
+  if (sv == nullptr) return SK_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->entries.find(ticket);
+  if (it == sv->entries.end()) return SK_ERR_INVALID;
+  sv->done_cv.wait(lk, [&] {
+    auto e = sv->entries.find(ticket);
+    return e == sv->entries.end() || e->second.state == 2;
+  });
+  it = sv->entries.find(ticket);
+  if (it == sv->entries.end()) return SK_ERR_INVALID;  // retired by a concurrent poll
+  const int st = it->second.status;
+  if (latency_us) *latency_us = it->second.latency_us;
+  sv->entries.erase(it);
+  return st;
+}
+
+int sk_server_stats(sk_server_t sv, int64_t* stats) {
+  if (sv == nullptr || stats == nullptr) return SK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  const int64_t v[6] = {sv->submitted, sv->completed, sv->batches, sv->max_batch_seen,
+                        sv->problems_launched, static_cast<int64_t>(sv->pending.size())};
+  for (int i = 0; i < 6; ++i) stats[i] = v[i];
+  return SK_OK;
+}
+
+int sk_server_destroy(sk_server_t sv) {
+  if (sv == nullptr) return SK_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  for (Slot& s : sv->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    free_slot(s);
+  }
+  delete sv;
+  return SK_OK;
+}
+
+}  // extern "C"

@@ -95,6 +95,16 @@ def lib() -> ctypes.CDLL:
     L.sk_grouped_get.argtypes = [vp, i32, i64p]
     L.sk_grouped_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), i64, i64p]
     L.sk_grouped_destroy.argtypes = [vp]
+    dblp = ctypes.POINTER(ctypes.c_double)
+    L.sk_server_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i64]
+    L.sk_server_submit.argtypes = [vp, i64, i64, i64, vp, vp, vp, f32, f32,
+                                   ctypes.POINTER(ctypes.c_uint64)]
+    L.sk_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32), dblp]
+    L.sk_server_wait.argtypes = [vp, ctypes.c_uint64, dblp]
+    L.sk_server_stats.argtypes = [vp, i64p]
+    L.sk_server_destroy.argtypes = [vp]
+    L.sk_plan_autotune.argtypes = [vp, vp, vp, vp, i32, vp, dblp]
+    L.sk_grouped_autotune.argtypes = [vp, vpp, vpp, vpp, i32, vp, dblp]
     L.sk_grouped_plan_describe.argtypes = [i32, i64p, i64p, i64p, i32, i32, i32, i32, i64p,
                                            ctypes.POINTER(ctypes.c_int32), i64, i64p]
     L.sk_status_string.argtypes = [i32]
@@ -104,7 +114,9 @@ def lib() -> ctypes.CDLL:
                  "sk_grid_model", "sk_gemm_noalloc", "sk_grouped_plan", "sk_grouped_gemm",
                  "sk_grouped_gemm_traced", "sk_grouped_last_error", "sk_grouped_set",
                  "sk_grouped_get", "sk_grouped_schedule", "sk_grouped_destroy",
-                 "sk_grouped_plan_describe"):
+                 "sk_grouped_plan_describe", "sk_plan_autotune", "sk_grouped_autotune",
+                 "sk_server_create", "sk_server_submit", "sk_server_poll", "sk_server_wait",
+                 "sk_server_stats", "sk_server_destroy"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -438,3 +450,77 @@ def sk_grouped_plan_describe(shapes, mode="auto", tile_n: int = 0, grid: int = 0
     info["mode_name"] = MODE_NAMES.get(info["mode"], "?")
     vals = list(buf)
     return info, [tuple(vals[10 * i:10 * i + 10]) for i in range(nrec.value)]
+
+
+def sk_plan_autotune(plan: Plan, A, B, C, reps: int = 5, stream=None) -> float:
+    """Time every configuration on these operands and keep the fastest (C is
+    overwritten).  Returns the kept configuration's mean microseconds."""
+    best = ctypes.c_double(0.0)
+    _check(lib().sk_plan_autotune(plan.handle, _ptr(A), _ptr(B), _ptr(C), int(reps),
+                                  _stream(stream), ctypes.byref(best)), "sk_plan_autotune")
+    return best.value
+
+
+def sk_grouped_autotune(plan: GroupedPlan, As, Bs, Cs, reps: int = 3, stream=None) -> float:
+    best = ctypes.c_double(0.0)
+    _check(lib().sk_grouped_autotune(plan.handle, _ptr_array(As), _ptr_array(Bs), _ptr_array(Cs),
+                                     int(reps), _stream(stream), ctypes.byref(best)),
+           "sk_grouped_autotune")
+    return best.value
+
+
+# ---------------------------------------------------------------- serving loop
+class Server:
+    """Owner of an sk_server_t (continuous batching over grouped launches)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def submit(self, A, B, C, alpha: float = 1.0, beta: float = 0.0) -> int:
+        """Queue C = alpha*A@B + beta*C (A m x k, B an n x k tensor, C m x n);
+        returns the ticket.  The tensors must stay alive until it completes."""
+        m, k = A.shape
+        n = B.shape[0]
+        t = ctypes.c_uint64(0)
+        _check(lib().sk_server_submit(self.handle, m, n, k, _ptr(A), _ptr(B), _ptr(C), alpha, beta,
+                                      ctypes.byref(t)), "sk_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """(done, status, latency_us)."""
+        st = ctypes.c_int(0)
+        lat = ctypes.c_double(0.0)
+        rc = lib().sk_server_poll(self.handle, ticket, ctypes.byref(st), ctypes.byref(lat))
+        return st.value == 2, rc, lat.value
+
+    def wait(self, ticket: int):
+        """Block until the request is done: (status, latency_us)."""
+        lat = ctypes.c_double(0.0)
+        rc = lib().sk_server_wait(self.handle, ticket, ctypes.byref(lat))
+        return rc, lat.value
+
+    def stats(self):
+        v = (ctypes.c_int64 * 6)()
+        _check(lib().sk_server_stats(self.handle, v), "sk_server_stats")
+        return dict(zip(("submitted", "completed", "batches", "max_batch", "problems", "queued"),
+                        list(v)))
+
+    def destroy(self):
+        if self.handle:
+            lib().sk_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
+def sk_server_create(ab_type="bf16", c_type="bf16", max_batch: int = 64, slots: int = 2,
+                     hbm_budget_bytes: int = 64 << 30) -> Server:
+    h = ctypes.c_void_p()
+    _check(lib().sk_server_create(ctypes.byref(h), _code(DTYPES, _dtype_name(ab_type), "dtype"),
+                                  _code(DTYPES, _dtype_name(c_type), "dtype"), max_batch, slots,
+                                  int(hbm_budget_bytes)), "sk_server_create")
+    return Server(h.value)

@@ -141,3 +141,24 @@ def test_grouped_single_problem_equals_gemm_bitwise():
     finally:
         plan.destroy()
         gplan.destroy()
+
+
+def test_grouped_autotune_keeps_a_correct_configuration():
+    shapes = GROUP
+    probs = [Problem(m, n, k, "bf16", "bf16", "normal", seed=50 + i) for i, (m, n, k) in enumerate(shapes)]
+    plan = sk.sk_grouped_plan(shapes, "bf16", "bf16", "auto")
+    try:
+        As = [p.A.cuda() for p in probs]
+        Bs = [p.B.cuda() for p in probs]
+        Cs = [torch.zeros(p.m, p.n, dtype=torch.bfloat16, device="cuda") for p in probs]
+        us = sk.sk_grouped_autotune(plan, As, Bs, Cs, reps=2)
+        info = plan.info()
+        assert us > 0 and info["tile_n"] in (128, 256)
+        for C in Cs:
+            C.zero_()
+        sk.sk_grouped_gemm(plan, As, Bs, Cs)
+        assert sk.sk_grouped_last_error(plan)[0] == sk.SK_OK
+        for p, C in zip(probs, Cs):
+            p.check(C.cpu(), 1.0, 0.0, "grouped autotuned")
+    finally:
+        plan.destroy()

@@ -12,6 +12,7 @@ import torch
 
 from gemm_check import Problem, hybrid_shape, num_sms
 from oracle import schedule as S
+from paper_2301_03598_gb300 import streamk as sk
 
 pytestmark = pytest.mark.gpu
 
@@ -268,3 +269,24 @@ def test_coalesced_store_path(m, n, k, tile_n, c_type, mode):
     prob = Problem(m, n, k, "bf16", c_type, "normal", seed=m + 3 * k, beta=0.5)
     (C,), info, _ = prob.run(1.0, 0.5, mode, plan_attrs={"tile_n": tile_n, "store": 2})
     prob.check(C, 1.0, 0.5, f"store=2 {m}x{n}x{k} bn={tile_n} {mode}")
+
+
+@pytest.mark.parametrize("m,n,k", [(1000, 3000, 712), (384, 384, 4096), (4096, 128, 1024)])
+def test_autotune_keeps_a_correct_configuration(m, n, k):
+    """sk_plan_autotune times every configuration and keeps one; the plan then
+    computes the right result with it."""
+    prob = Problem(m, n, k, "bf16", "bf16", "normal", seed=m + k)
+    plan = sk.sk_plan(m, n, k, "bf16", "bf16", "bf16")
+    try:
+        A, B = prob.A.cuda(), prob.B.cuda()
+        C = torch.zeros(m, n, dtype=torch.bfloat16, device="cuda")
+        us = sk.sk_plan_autotune(plan, A, B, C, reps=3)
+        info = plan.info()
+        assert us > 0 and info["tile_n"] in (128, 256) and info["cluster_m"] in (1, 2)
+        assert info["mode"] in (sk.MODES["dp"], sk.MODES["hybrid"], sk.MODES["sk"])
+        C.zero_()
+        sk.sk_gemm(plan, A, B, C, 1.0, 0.0)
+        assert sk.sk_last_error(plan)[0] == sk.SK_OK
+        prob.check(C.cpu(), 1.0, 0.0, f"autotuned {m}x{n}x{k} {info['tile_n']}/{info['cluster_m']}")
+    finally:
+        plan.destroy()
