@@ -686,14 +686,53 @@ def run_grouped(steps, warmup):
     }
 
 
+def _plain_launches(sk, plans, ops, arrivals, pick):
+    """One launch per request at its arrival time on one stream; returns the
+    arrival-to-completion latencies (us) and the wall time of the run."""
+    import collections
+    import torch
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for j in range(8):   # warm the launch path
+            A, B, C = ops[j]
+            sk.sk_gemm(plans[j], A, B, C, stream=s)
+    torch.cuda.synchronize()
+    pend, lats = collections.deque(), []
+    t0 = time.perf_counter()
+    for a_t, j in zip(arrivals, pick):
+        while True:
+            now = time.perf_counter() - t0
+            while pend and pend[0][0].query():
+                lats.append((now - pend.popleft()[1]) * 1e6)
+            if now >= a_t:
+                break
+        A, B, C = ops[j]
+        sk.sk_gemm(plans[j], A, B, C, stream=s)
+        ev = torch.cuda.Event()
+        ev.record(s)
+        pend.append((ev, a_t))
+    while pend:
+        now = time.perf_counter() - t0
+        while pend and pend[0][0].query():
+            lats.append((now - pend.popleft()[1]) * 1e6)
+    wall = time.perf_counter() - t0
+    for p in plans:
+        st, dev_st = sk.sk_last_error(p)
+        if st != sk.SK_OK or dev_st != 0:
+            raise RuntimeError(f"plain launch status {st}, device status {dev_st}")
+    return np.array(lats), wall
+
+
 def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
     """The serving workload: requests arrive as a Poisson process at each rate
     for `seconds`, each a GEMM drawn from 64 shapes (48 from the shape sweep's
     distribution, 16 from the grouped workload's), BF16 in / FP32 accumulate /
     BF16 out.  The continuous-batching server (batches of up to 64 requests,
-    2 concurrent launch slots, 64 GB admission budget) against per-request
-    plain launches (batches of one on one slot), both through the library's
-    server.  Latency: submission to observed completion."""
+    2 concurrent launch slots, 64 GB admission budget) against two baselines:
+    the same server with batches of one on one slot, and plain launches, one
+    `sk_gemm` per request on arrival from a plan made per shape beforehand,
+    on one stream, completion seen by polling an event recorded after each
+    launch.  Latency: arrival to observed completion."""
     import torch
     from paper_2301_03598_gb300 import inputs
     from paper_2301_03598_gb300 import streamk as sk
@@ -708,6 +747,7 @@ def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
                     inputs.device_pool(n * k, "bf16", "normal", seed + 3 * i + 1, dev).view(n, k),
                     torch.empty(m, n, dtype=torch.bfloat16, device=dev)))
     flops = np.array([2.0 * m * n * k for m, n, k in shapes])
+    plans = [sk.sk_plan(m, n, k, "bf16", "bf16", "bf16") for m, n, k in shapes]
     out = {"workload": "Poisson arrivals of single GEMMs, shapes drawn from 48 shapes of the "
                        "sweep distribution and 16 of the grouped workload's, BF16 in, FP32 "
                        "accumulate, BF16 out", "seconds_per_rate": seconds, "rates": {}}
@@ -748,8 +788,17 @@ def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
                          "requests_per_s": n_req / wall,
                          "tflops": float(flops[pick].sum() / wall / 1e12),
                          "batches": stats["batches"] - 8, "largest_batch": stats["max_batch"]}
+        lats, wall = _plain_launches(sk, plans, ops, arrivals, pick)
+        res["plain_launch"] = {"p50_us": float(np.percentile(lats, 50)),
+                               "p99_us": float(np.percentile(lats, 99)),
+                               "mean_us": float(lats.mean()),
+                               "requests_per_s": n_req / wall,
+                               "tflops": float(flops[pick].sum() / wall / 1e12)}
         res["p99_speedup"] = res["per_request"]["p99_us"] / res["server"]["p99_us"]
+        res["p99_speedup_vs_plain"] = res["plain_launch"]["p99_us"] / res["server"]["p99_us"]
         out["rates"][str(rate)] = res
+    for p in plans:
+        p.destroy()
     return out
 
 

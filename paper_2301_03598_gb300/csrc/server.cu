@@ -46,14 +46,20 @@ struct Request {
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  sk::GroupSeg* d_segs = nullptr;
-  int32_t* d_start = nullptr;
+  // One device block and its pinned staging copy, uploaded with one copy per
+  // batch: the problem table, then the per-CTA segment starts, then the
+  // segment records.
+  char* d_block = nullptr;
+  char* h_block = nullptr;
+  size_t off_start = 0, off_segs = 0;
   sk::GroupProblem* d_probs = nullptr;
+  int32_t* d_start = nullptr;
+  sk::GroupSeg* d_segs = nullptr;
+  sk::GroupProblem* h_probs = nullptr;
+  int32_t* h_start = nullptr;
+  sk::GroupSeg* h_segs = nullptr;
   int32_t* d_err = nullptr;
   char* ws = nullptr;
-  sk::GroupSeg* h_segs = nullptr;   // pinned staging of the uploads
-  int32_t* h_start = nullptr;
-  sk::GroupProblem* h_probs = nullptr;
   int32_t* h_err = nullptr;
   std::vector<Request> reqs;
   int64_t bytes = 0;
@@ -90,14 +96,10 @@ namespace {
 constexpr int64_t kSegsPerProblem = 1024;  // record capacity per admitted problem (grown on demand)
 
 void free_slot(Slot& s) {
-  if (s.d_segs) cudaFree(s.d_segs);
-  if (s.d_start) cudaFree(s.d_start);
-  if (s.d_probs) cudaFree(s.d_probs);
+  if (s.d_block) cudaFree(s.d_block);
   if (s.d_err) cudaFree(s.d_err);
   if (s.ws) cudaFree(s.ws);
-  if (s.h_segs) cudaFreeHost(s.h_segs);
-  if (s.h_start) cudaFreeHost(s.h_start);
-  if (s.h_probs) cudaFreeHost(s.h_probs);
+  if (s.h_block) cudaFreeHost(s.h_block);
   if (s.h_err) cudaFreeHost(s.h_err);
   if (s.done) cudaEventDestroy(s.done);
   if (s.stream) cudaStreamDestroy(s.stream);
@@ -108,22 +110,32 @@ cudaError_t alloc_slot(Slot& s, int max_batch, int64_t segs_cap, int num_sms) {
   cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
   const size_t ws = static_cast<size_t>(sk::kFlagBytes) + static_cast<size_t>(num_sms) * sk::kBlkM * 256 * 4;
-  if (e == cudaSuccess) e = cudaMalloc(&s.d_segs, static_cast<size_t>(segs_cap) * sizeof(sk::GroupSeg));
-  if (e == cudaSuccess) e = cudaMalloc(&s.d_start, static_cast<size_t>(num_sms + 1) * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&s.d_probs, static_cast<size_t>(max_batch) * sizeof(sk::GroupProblem));
+  auto up = [](size_t v) { return (v + 127) / 128 * 128; };
+  s.off_start = up(static_cast<size_t>(max_batch) * sizeof(sk::GroupProblem));
+  s.off_segs = s.off_start + up(static_cast<size_t>(num_sms + 1) * sizeof(int32_t));
+  const size_t block = s.off_segs + static_cast<size_t>(segs_cap) * sizeof(sk::GroupSeg);
+  if (e == cudaSuccess) e = cudaMalloc(&s.d_block, block);
+  if (e == cudaSuccess) e = cudaMallocHost(&s.h_block, block);
+  if (e == cudaSuccess) {
+    s.d_probs = reinterpret_cast<sk::GroupProblem*>(s.d_block);
+    s.d_start = reinterpret_cast<int32_t*>(s.d_block + s.off_start);
+    s.d_segs = reinterpret_cast<sk::GroupSeg*>(s.d_block + s.off_segs);
+    s.h_probs = reinterpret_cast<sk::GroupProblem*>(s.h_block);
+    s.h_start = reinterpret_cast<int32_t*>(s.h_block + s.off_start);
+    s.h_segs = reinterpret_cast<sk::GroupSeg*>(s.h_block + s.off_segs);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&s.d_err, 4 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(s.d_err, 0, 4 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.ws, ws);
   if (e == cudaSuccess) e = cudaMemset(s.ws, 0, ws);
-  if (e == cudaSuccess) e = cudaMallocHost(&s.h_segs, static_cast<size_t>(segs_cap) * sizeof(sk::GroupSeg));
-  if (e == cudaSuccess) e = cudaMallocHost(&s.h_start, static_cast<size_t>(num_sms + 1) * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMallocHost(&s.h_probs, static_cast<size_t>(max_batch) * sizeof(sk::GroupProblem));
   if (e == cudaSuccess) e = cudaMallocHost(&s.h_err, 4 * sizeof(int32_t));
   return e;
 }
 
 // Plan and launch the requests of a slot as one grouped launch.  Returns an
-// sk_status; on failure nothing is in flight on the slot.
+// sk_status; on failure nothing is in flight on the slot.  Runs without the
+// server lock: it reads only the slot (owned by the worker while busy) and
+// the server's immutable settings.
 int launch_slot(sk_server_s* sv, Slot& s) {
   const int count = static_cast<int>(s.reqs.size());
   std::vector<int64_t> m(count), n(count), k(count);
@@ -164,14 +176,9 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   }
   std::memcpy(s.h_segs, gp.segs.data(), gp.segs.size() * sizeof(sk::GroupSeg));
   std::memcpy(s.h_start, gp.start.data(), gp.start.size() * sizeof(int32_t));
-  cudaError_t e = cudaMemcpyAsync(s.d_segs, s.h_segs, gp.segs.size() * sizeof(sk::GroupSeg),
+  cudaError_t e = cudaMemcpyAsync(s.d_block, s.h_block,
+                                  s.off_segs + gp.segs.size() * sizeof(sk::GroupSeg),
                                   cudaMemcpyHostToDevice, s.stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s.d_start, s.h_start, gp.start.size() * sizeof(int32_t),
-                        cudaMemcpyHostToDevice, s.stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s.d_probs, s.h_probs, static_cast<size_t>(count) * sizeof(sk::GroupProblem),
-                        cudaMemcpyHostToDevice, s.stream);
   if (e != cudaSuccess) return cuda_status(e);
   sk::SkArgs a{};
   a.grid = gp.grid;
@@ -193,9 +200,6 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_err, s.d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s.stream);
   if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
   if (e != cudaSuccess) return cuda_status(e);
-  ++sv->batches;
-  sv->problems_launched += count;
-  sv->max_batch_seen = std::max<int64_t>(sv->max_batch_seen, count);
   return SK_OK;
 }
 
@@ -258,10 +262,17 @@ void worker_loop(sk_server_s* sv) {
       if (!s.reqs.empty()) {
         sv->inflight_bytes += s.bytes;
         s.busy = true;
+        lk.unlock();  // planning and encoding do not block submitters
         const int st = launch_slot(sv, s);
+        lk.lock();
         if (st != SK_OK) {
           finish(sv, s, st);
           sv->done_cv.notify_all();
+        } else {
+          const int64_t count = static_cast<int64_t>(s.reqs.size());
+          ++sv->batches;
+          sv->problems_launched += count;
+          sv->max_batch_seen = std::max<int64_t>(sv->max_batch_seen, count);
         }
         continue;
       }
