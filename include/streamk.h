@@ -49,7 +49,11 @@ typedef enum {
   SK_ERR_DEVICE = 6       /* the current device is not sm_103 (GB300) */
 } sk_status;
 
-typedef enum { SK_F16 = 0, SK_BF16 = 1, SK_F32 = 2 } sk_dtype;
+/* SK_E4M3: 8-bit floating point (OCP FP8 E4M3: 1 sign, 4 exponent bits with
+ * bias 7, 3 mantissa bits, no infinities, 0x7F / 0xFF NaN, largest finite
+ * 448), used as A and B with one FP32 scale per 128 x 128 block of each
+ * operand (sk_gemm_scaled). */
+typedef enum { SK_F16 = 0, SK_BF16 = 1, SK_F32 = 2, SK_E4M3 = 3 } sk_dtype;
 
 /* Storage order of a matrix.  For A (m x k): ROW_MAJOR = k contiguous;
  * for B (k x n): COL_MAJOR = k contiguous; for C (m x n): ROW_MAJOR = n
@@ -137,8 +141,10 @@ typedef struct {
 /*
  * Create a plan for one GEMM shape on the current CUDA device.
  *   m, n, k   >= 0 (m*n == 0: sk_gemm is a no-op; k == 0: C = beta*C).
- *   a_type == b_type in {SK_F16, SK_BF16}; c_type in {SK_F32, SK_BF16, SK_F16};
- *   compute_type must be SK_F32 (FP32 accumulation, Section 6).
+ *   a_type == b_type in {SK_F16, SK_BF16, SK_E4M3}; c_type in {SK_F32, SK_BF16,
+ *   SK_F16}; compute_type must be SK_F32 (FP32 accumulation, Section 6).
+ *   E4M3 plans run 128 x 128 x 128 tiles on single CTAs (SK_ATTR_TILE_N 128,
+ *   SK_ATTR_CLUSTER_M 1) and are launched with sk_gemm_scaled.
  *   a_layout SK_ROW_MAJOR, b_layout SK_COL_MAJOR, c_layout either.
  *   mode: an sk_mode.
  * Allocates the plan's device workspace (fixup partials and flags, Algorithm 5
@@ -163,6 +169,27 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
  */
 int sk_gemm(sk_plan_t plan, const void* A, const void* B, void* C, float alpha, float beta,
             void* stream);
+
+/*
+ * Block-scaled E4M3 GEMM on an SK_E4M3 plan:
+ *   C = alpha * sum_kb Sa[i/128][kb] * Sb[j/128][kb] * (A_kb * B_kb)[i][j] + beta * C
+ * where kb runs over the k-blocks of 128 (the last one ragged), A_kb is
+ * columns [128 kb, 128 kb + 128) of A (E4M3 bytes, row-major m x k) and B_kb
+ * rows of B (E4M3, column-major k x n, i.e. an n x k row-major array).
+ * Every product of a k-block is accumulated in FP32 by the tensor cores, then
+ * scaled and summed in FP32 in k order; Stream-K partials and the fixup stay
+ * FP32 (the paper's Section 4 schedule is unchanged: one MAC-loop iteration
+ * is one k-block of 128).
+ *   scale_a: device FP32 array [ceil(m/128)][ceil(k/128)], row-major;
+ *   scale_b: device FP32 array [ceil(n/128)][ceil(k/128)], row-major; both
+ *   read-only, 4-byte aligned, not copied (they must stay valid until the
+ *   launch completes).  A, B, C as for sk_gemm (k a multiple of 16 so that
+ *   the dense rows are 16-byte multiples).
+ * Returns SK_ERR_INVALID for a null scale pointer or a plan whose inputs are
+ * not E4M3; sk_gemm on an E4M3 plan also returns SK_ERR_INVALID.
+ */
+int sk_gemm_scaled(sk_plan_t plan, const void* A, const void* B, const float* scale_a,
+                   const float* scale_b, void* C, float alpha, float beta, void* stream);
 
 /*
  * sk_gemm that also records the schedule each CTA executed, with device
@@ -310,6 +337,15 @@ int sk_grouped_plan(sk_grouped_t* out, int count, const int64_t* m, const int64_
                     const int64_t* k, sk_dtype ab_type, sk_dtype c_type, int mode);
 int sk_grouped_gemm(sk_grouped_t plan, const void* const* A, const void* const* B,
                     void* const* C, const float* alpha, const float* beta, void* stream);
+/* sk_grouped_gemm for an SK_E4M3 group (ab_type SK_E4M3: 128 x 128 x 128
+ * tiles, k_i a multiple of 16): SA / SB are host arrays of count device
+ * pointers to each problem's block scales, laid out as for sk_gemm_scaled
+ * ([ceil(m_i/128)][ceil(k_i/128)] and [ceil(n_i/128)][ceil(k_i/128)] FP32,
+ * row-major).  sk_grouped_gemm on an E4M3 group, or this call on a 16-bit
+ * group, returns SK_ERR_INVALID. */
+int sk_grouped_gemm_scaled(sk_grouped_t plan, const void* const* A, const void* const* B,
+                           const float* const* SA, const float* const* SB, void* const* C,
+                           const float* alpha, const float* beta, void* stream);
 int sk_grouped_gemm_traced(sk_grouped_t plan, const void* const* A, const void* const* B,
                            void* const* C, const float* alpha, const float* beta, int32_t* trace,
                            int64_t trace_ints, void* stream);
@@ -342,6 +378,13 @@ int sk_plan_autotune(sk_plan_t plan, const void* A, const void* B, void* C, int 
                      double* best_us);
 int sk_grouped_autotune(sk_grouped_t plan, const void* const* A, const void* const* B,
                         void* const* C, int reps, void* stream, double* best_us);
+/* The same for E4M3 plans (one tile shape, so only the schedule is chosen),
+ * with the block scales of sk_gemm_scaled / sk_grouped_gemm_scaled. */
+int sk_plan_autotune_scaled(sk_plan_t plan, const void* A, const void* B, const float* scale_a,
+                            const float* scale_b, void* C, int reps, void* stream, double* best_us);
+int sk_grouped_autotune_scaled(sk_grouped_t plan, const void* const* A, const void* const* B,
+                               const float* const* SA, const float* const* SB, void* const* C,
+                               int reps, void* stream, double* best_us);
 
 /* ---------------------------------------------------------------- serving loop
  * Continuous batching over the grouped launch.  Requests (independent GEMMs,

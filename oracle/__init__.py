@@ -11,6 +11,8 @@ Contents:
 * ``schedule`` -- the decompositions of Algorithms 2, 4, 5, the hybrids of
   Section 5.2 and the grid-size model of Appendix A.1, in Python.
 * ``rounding`` -- round-to-nearest-even onto FP32 / FP16 / BF16 and their ulp.
+* ``e4m3`` -- the E4M3 code values and the block-scaled E4M3 GEMM (operands
+  dequantized exactly, then the FP64 GEMM above).
 
 The C library is compiled with gcc on first use (or by ``build()``), next to
 its source.
@@ -24,7 +26,7 @@ import threading
 
 import numpy as np
 
-from . import rounding, schedule  # noqa: F401
+from . import e4m3, rounding, schedule  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle_gemm.c")

@@ -137,9 +137,15 @@ void set_divisors(sk::SkArgs& a, const sk_schedule_info& s) {
   a.fast_iters = s.sk_iters < (int64_t(1) << 31) ? 1 : 0;
 }
 
-int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, float beta,
-              int32_t* trace, int64_t trace_ints, void* stream_v) {
+int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
+              const float* scale_b, void* C, float alpha, float beta, int32_t* trace,
+              int64_t trace_ints, void* stream_v) {
   if (p == nullptr) return SK_ERR_INVALID;
+  // E4M3 plans take their block scales; 16-bit plans take none
+  const bool f8 = p->a_type == SK_E4M3;
+  if (f8 != (scale_a != nullptr) || f8 != (scale_b != nullptr)) return SK_ERR_INVALID;
+  if (f8 && ((reinterpret_cast<uintptr_t>(scale_a) & 3u) || (reinterpret_cast<uintptr_t>(scale_b) & 3u)))
+    return SK_ERR_INVALID;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
   if (p->m == 0 || p->n == 0) return SK_OK;
   if (C == nullptr || (reinterpret_cast<uintptr_t>(C) & 15u)) return SK_ERR_INVALID;
@@ -181,7 +187,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   const int64_t kn = p->swap ? p->m : p->n;
   const int64_t klda = p->swap ? p->ldb : p->lda;
   const int64_t kldb = p->swap ? p->lda : p->ldb;
-  const bool use3d = s.tile_k == 2 * sk::kBlkK && p->k / sk::kBlkK >= 2;
+  const bool use3d = !f8 && s.tile_k == 2 * sk::kBlkK && p->k / sk::kBlkK >= 2;
   if (ka != p->cached_a) {
     int st = encode_operand(&p->tm_a, ka, p->a_type, km, p->k, klda, sk::kBlkM);
     if (st == SK_OK && use3d)
@@ -234,6 +240,11 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   a.debug_skip_signal = p->debug_skip_signal;
   a.timeout_ns = p->timeout_ns;
   a.pdl = p->pdl ? 1 : 0;
+  if (f8) {
+    a.scale_a = p->swap ? scale_b : scale_a;
+    a.scale_b = p->swap ? scale_a : scale_b;
+    a.ld_scale = static_cast<int32_t>((p->k + 127) / 128);
+  }
 
   // Split schedules need every CTA resident at once.  Single CTAs ask the
   // launch to guarantee it (cooperative attribute).  Clustered launches go
@@ -243,6 +254,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, void* C, float alpha, f
   // all CTAs become resident; the bounded waits turn anything else into an
   // error status.
   const bool cooperative = split && s.cluster_m == 1;
+  if (f8) return cuda_status(sk::launch_f8(p->c_type, p->tm_a, p->tm_b, p->tm_c, a, cooperative, stream));
   const CUtensorMap& ta3 = use3d ? p->tm_a3 : p->tm_a;
   const CUtensorMap& tb3 = use3d ? p->tm_b3 : p->tm_b;
   cudaError_t e = s.tile_n == 256
@@ -277,7 +289,8 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
   *out = nullptr;
   if (m < 0 || n < 0 || k < 0) return SK_ERR_INVALID;
   if (mode < SK_MODE_AUTO || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
-  if (!((a_type == SK_F16 || a_type == SK_BF16) && b_type == a_type)) return SK_ERR_UNSUPPORTED;
+  if (!((a_type == SK_F16 || a_type == SK_BF16 || a_type == SK_E4M3) && b_type == a_type))
+    return SK_ERR_UNSUPPORTED;
   if (!(c_type == SK_F32 || c_type == SK_BF16 || c_type == SK_F16)) return SK_ERR_UNSUPPORTED;
   if (compute_type != SK_F32) return SK_ERR_UNSUPPORTED;
   if (a_layout != SK_ROW_MAJOR || b_layout != SK_COL_MAJOR) return SK_ERR_UNSUPPORTED;
@@ -309,9 +322,14 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
   p->swap = c_layout == SK_COL_MAJOR;
   p->device = dev;
   p->num_sms = sms;
-  size_t s1 = 0, s2 = 0;
+  if (a_type == SK_E4M3) {  // 128 x 128 x 128 single-CTA tiles
+    p->tile_n_req = 128;
+    p->cluster_req = 1;
+  }
+  size_t s1 = 0, s2 = 0, s3 = 0;
   cudaError_t e = sk::prepare_bn128(&s1);
   if (e == cudaSuccess) e = sk::prepare_bn256(&s2);
+  if (e == cudaSuccess) e = sk::prepare_f8(&s3);
   if (e != cudaSuccess) {
     delete p;
     return cuda_status(e);
@@ -344,13 +362,19 @@ int sk_plan_destroy(sk_plan_t p) {
 
 int sk_gemm(sk_plan_t p, const void* A, const void* B, void* C, float alpha, float beta,
             void* stream) {
-  return gemm_impl(p, A, B, C, alpha, beta, nullptr, 0, stream);
+  return gemm_impl(p, A, B, nullptr, nullptr, C, alpha, beta, nullptr, 0, stream);
+}
+
+int sk_gemm_scaled(sk_plan_t p, const void* A, const void* B, const float* scale_a,
+                   const float* scale_b, void* C, float alpha, float beta, void* stream) {
+  if (scale_a == nullptr || scale_b == nullptr) return SK_ERR_INVALID;
+  return gemm_impl(p, A, B, scale_a, scale_b, C, alpha, beta, nullptr, 0, stream);
 }
 
 int sk_gemm_traced(sk_plan_t p, const void* A, const void* B, void* C, float alpha, float beta,
                    int32_t* trace, int64_t trace_ints, void* stream) {
   if (trace == nullptr) return SK_ERR_INVALID;
-  return gemm_impl(p, A, B, C, alpha, beta, trace, trace_ints, stream);
+  return gemm_impl(p, A, B, nullptr, nullptr, C, alpha, beta, trace, trace_ints, stream);
 }
 
 int sk_last_error(sk_plan_t p, int* device_status) {
@@ -380,6 +404,7 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
   switch (attr) {
     case SK_ATTR_TILE_N: {
       if (v != 0 && v != 128 && v != 256) return SK_ERR_UNSUPPORTED;
+      if (p->a_type == SK_E4M3) return v == 0 || v == 128 ? SK_OK : SK_ERR_UNSUPPORTED;
       const int old = p->tile_n_req;
       p->tile_n_req = static_cast<int>(v);
       int st = replan(p);
@@ -438,6 +463,7 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
       return SK_OK;
     case SK_ATTR_CLUSTER_M: {
       if (v != 0 && v != 1 && v != 2) return SK_ERR_UNSUPPORTED;
+      if (p->a_type == SK_E4M3) return v == 0 || v == 1 ? SK_OK : SK_ERR_UNSUPPORTED;
       const int old = p->cluster_req;
       p->cluster_req = static_cast<int>(v);
       int st = replan(p);
@@ -693,6 +719,7 @@ struct sk_grouped_s {
   bool copy_pending = false;
   bool table_valid = false;
   std::vector<const void*> enc_a, enc_b;
+  std::vector<const float*> enc_sa, enc_sb;
   std::vector<void*> enc_c;
   std::vector<float> enc_alpha, enc_beta;
   // knobs
@@ -759,10 +786,14 @@ int grouped_replan(sk_grouped_s* g) {
   return SK_OK;
 }
 
-int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B, void* const* C,
+int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
+                 const float* const* SA, const float* const* SB, void* const* C,
                  const float* alpha, const float* beta, int32_t* trace, int64_t trace_ints,
                  void* stream_v) {
   if (g == nullptr || A == nullptr || B == nullptr || C == nullptr) return SK_ERR_INVALID;
+  // E4M3 groups take every problem's block scales; 16-bit groups take none
+  const bool f8 = g->ab_type == SK_E4M3;
+  if (f8 != (SA != nullptr) || f8 != (SB != nullptr)) return SK_ERR_INVALID;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
   const sk::GroupPlan& gp = g->plan;
   if (trace != nullptr) {
@@ -781,9 +812,14 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B, vo
         (reinterpret_cast<uintptr_t>(A[i]) & 15u) || (reinterpret_cast<uintptr_t>(B[i]) & 15u) ||
         (reinterpret_cast<uintptr_t>(C[i]) & 15u))
       return SK_ERR_INVALID;
+    const float* sa = f8 ? SA[i] : nullptr;
+    const float* sb = f8 ? SB[i] : nullptr;
+    if (f8 && (sa == nullptr || sb == nullptr || (reinterpret_cast<uintptr_t>(sa) & 3u) ||
+               (reinterpret_cast<uintptr_t>(sb) & 3u)))
+      return SK_ERR_INVALID;
     changed[static_cast<size_t>(i)] =
         !g->table_valid || A[i] != g->enc_a[i] || B[i] != g->enc_b[i] || C[i] != g->enc_c[i] ||
-        al != g->enc_alpha[i] || be != g->enc_beta[i];
+        al != g->enc_alpha[i] || be != g->enc_beta[i] || sa != g->enc_sa[i] || sb != g->enc_sb[i];
     dirty = dirty || changed[static_cast<size_t>(i)];
   }
   if (dirty && g->copy_pending) {
@@ -798,7 +834,7 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B, vo
     const int64_t m = g->m[i], n = g->n[i], k = g->k[i];
     int st = encode_operand(&pr.tmA, A[i], g->ab_type, m, k, k, sk::kBlkM);
     if (st == SK_OK) st = encode_operand(&pr.tmB, B[i], g->ab_type, n, k, k, gp.tile_n);
-    const bool use3d = gp.tile_k == 2 * sk::kBlkK && k / sk::kBlkK >= 2;
+    const bool use3d = !f8 && gp.tile_k == 2 * sk::kBlkK && k / sk::kBlkK >= 2;
     if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmA3, A[i], g->ab_type, m, k, k, sk::kBlkM);
     if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmB3, B[i], g->ab_type, n, k, k, gp.tile_n);
     if (st != SK_OK) {
@@ -819,6 +855,11 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B, vo
     pr.c_vec = (n * static_cast<int64_t>(dtype_size(g->c_type))) % 16 == 0 ? 1 : 0;
     pr.alpha = al;
     pr.beta = be;
+    pr.scale_a = f8 ? SA[i] : nullptr;
+    pr.scale_b = f8 ? SB[i] : nullptr;
+    pr.ld_scale = static_cast<int32_t>((k + 127) / 128);
+    g->enc_sa[i] = pr.scale_a;
+    g->enc_sb[i] = pr.scale_b;
     g->enc_a[i] = A[i];
     g->enc_b[i] = B[i];
     g->enc_c[i] = C[i];
@@ -852,8 +893,9 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B, vo
   a.gseg_start = g->d_start;
   a.gprobs = g->d_probs;
   const CUtensorMap& any = g->h_probs[0].tmA;
-  cudaError_t e = gp.tile_n == 256 ? sk::launch_grouped_bn256(g->c_type, any, a, split, stream)
-                                   : sk::launch_grouped_bn128(g->c_type, any, a, split, stream);
+  cudaError_t e = f8                ? sk::launch_grouped_f8(g->c_type, any, a, split, stream)
+                  : gp.tile_n == 256 ? sk::launch_grouped_bn256(g->c_type, any, a, split, stream)
+                                     : sk::launch_grouped_bn128(g->c_type, any, a, split, stream);
   if (e != cudaSuccess) return cuda_status(e);
   g->last_stream = stream;
   g->launched = true;
@@ -870,12 +912,13 @@ int sk_grouped_plan(sk_grouped_t* out, int count, const int64_t* m, const int64_
   *out = nullptr;
   if (count < 1 || count > (1 << 20) || m == nullptr || n == nullptr || k == nullptr)
     return SK_ERR_INVALID;
-  if (!(ab_type == SK_F16 || ab_type == SK_BF16)) return SK_ERR_UNSUPPORTED;
+  if (!(ab_type == SK_F16 || ab_type == SK_BF16 || ab_type == SK_E4M3)) return SK_ERR_UNSUPPORTED;
   if (!(c_type == SK_F32 || c_type == SK_BF16 || c_type == SK_F16)) return SK_ERR_UNSUPPORTED;
   if (mode != SK_MODE_AUTO && mode != SK_MODE_DP && mode != SK_MODE_SK && mode != SK_MODE_HYBRID)
     return SK_ERR_UNSUPPORTED;
+  const int64_t k_align = ab_type == SK_E4M3 ? 16 : 8;
   for (int i = 0; i < count; ++i)  // dense rows of A and B must be 16-byte multiples (TMA)
-    if (k[i] < 1 || k[i] % 8 != 0) return SK_ERR_INVALID;
+    if (k[i] < 1 || k[i] % k_align != 0) return SK_ERR_INVALID;
   int dev = 0, major = 0, minor = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SK_ERR_CUDA;
   if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
@@ -899,9 +942,13 @@ int sk_grouped_plan(sk_grouped_t* out, int count, const int64_t* m, const int64_
   g->enc_c.assign(count, nullptr);
   g->enc_alpha.assign(count, 0.0f);
   g->enc_beta.assign(count, 0.0f);
-  size_t s1 = 0, s2 = 0;
+  g->enc_sa.assign(count, nullptr);
+  g->enc_sb.assign(count, nullptr);
+  if (ab_type == SK_E4M3) g->tile_n_req = 128;  // 128 x 128 x 128 tiles
+  size_t s1 = 0, s2 = 0, s3 = 0;
   cudaError_t e = sk::prepare_bn128(&s1);
   if (e == cudaSuccess) e = sk::prepare_bn256(&s2);
+  if (e == cudaSuccess) e = sk::prepare_f8(&s3);
   void *errw = nullptr, *probs = nullptr, *hprobs = nullptr;
   const size_t table = static_cast<size_t>(count) * sizeof(sk::GroupProblem);
   if (e == cudaSuccess) e = cudaMalloc(&errw, 4 * sizeof(int32_t));
@@ -941,14 +988,21 @@ int sk_grouped_destroy(sk_grouped_t g) {
 
 int sk_grouped_gemm(sk_grouped_t g, const void* const* A, const void* const* B, void* const* C,
                     const float* alpha, const float* beta, void* stream) {
-  return grouped_impl(g, A, B, C, alpha, beta, nullptr, 0, stream);
+  return grouped_impl(g, A, B, nullptr, nullptr, C, alpha, beta, nullptr, 0, stream);
+}
+
+int sk_grouped_gemm_scaled(sk_grouped_t g, const void* const* A, const void* const* B,
+                           const float* const* SA, const float* const* SB, void* const* C,
+                           const float* alpha, const float* beta, void* stream) {
+  if (SA == nullptr || SB == nullptr) return SK_ERR_INVALID;
+  return grouped_impl(g, A, B, SA, SB, C, alpha, beta, nullptr, 0, stream);
 }
 
 int sk_grouped_gemm_traced(sk_grouped_t g, const void* const* A, const void* const* B,
                            void* const* C, const float* alpha, const float* beta, int32_t* trace,
                            int64_t trace_ints, void* stream) {
   if (trace == nullptr) return SK_ERR_INVALID;
-  return grouped_impl(g, A, B, C, alpha, beta, trace, trace_ints, stream);
+  return grouped_impl(g, A, B, nullptr, nullptr, C, alpha, beta, trace, trace_ints, stream);
 }
 
 int sk_grouped_last_error(sk_grouped_t g, int* device_status) {
@@ -974,6 +1028,8 @@ int sk_grouped_set(sk_grouped_t g, int attr, int64_t v) {
     case SK_ATTR_TILE_N:
     case SK_ATTR_GRID:
     case SK_ATTR_MODE: {
+      if (attr == SK_ATTR_TILE_N && g->ab_type == SK_E4M3)
+        return v == 0 || v == 128 ? SK_OK : SK_ERR_UNSUPPORTED;
       const int t = g->tile_n_req, gr = g->grid_req, md = g->mode_req;
       if (attr == SK_ATTR_TILE_N) g->tile_n_req = static_cast<int>(v);
       if (attr == SK_ATTR_GRID) g->grid_req = static_cast<int>(v);
@@ -1076,23 +1132,20 @@ double time_launches(F&& launch, int reps, cudaStream_t stream) {
   return us;
 }
 
-}  // namespace
-
-extern "C" {
-
-int sk_plan_autotune(sk_plan_t p, const void* A, const void* B, void* C, int reps, void* stream_v,
-                     double* best_us) {
+int plan_autotune(sk_plan_t p, const void* A, const void* B, const float* scale_a,
+                  const float* scale_b, void* C, int reps, void* stream_v, double* best_us) {
   if (p == nullptr || reps < 1) return SK_ERR_INVALID;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
   const int saved[4] = {p->tile_n_req, p->cluster_req, p->mode_req, p->grid_req};
   const int64_t km = p->swap ? p->n : p->m, kn = p->swap ? p->m : p->n;
+  const bool f8 = p->a_type == SK_E4M3;  // one tile shape: 128 x 128 single CTAs
   const int tns[2] = {128, 256}, cms[2] = {1, 2}, modes[3] = {SK_MODE_DP, SK_MODE_HYBRID, SK_MODE_SK};
   double best = -1.0;
   int bt = saved[0], bc = saved[1], bm = saved[2];
   for (int tn : tns) {
-    if (tn == 256 && kn <= 128) continue;
+    if (tn == 256 && (kn <= 128 || f8)) continue;
     for (int cm : cms) {
-      if (cm == 2 && km <= sk::kTileM) continue;
+      if (cm == 2 && (km <= sk::kTileM || f8)) continue;
       for (int md : modes) {
         p->tile_n_req = tn;
         p->cluster_req = cm;
@@ -1100,7 +1153,8 @@ int sk_plan_autotune(sk_plan_t p, const void* A, const void* B, void* C, int rep
         p->grid_req = 0;
         if (replan(p) != SK_OK) continue;  // e.g. an attached workspace too small for it
         const double us = time_launches(
-            [&] { return gemm_impl(p, A, B, C, 1.0f, 0.0f, nullptr, 0, stream); }, reps, stream);
+            [&] { return gemm_impl(p, A, B, scale_a, scale_b, C, 1.0f, 0.0f, nullptr, 0, stream); },
+            reps, stream);
         int dev_status = 0;
         if (us < 0.0 || sk_last_error(p, &dev_status) != SK_OK) continue;
         if (best < 0.0 || us < best) {
@@ -1122,8 +1176,9 @@ int sk_plan_autotune(sk_plan_t p, const void* A, const void* B, void* C, int rep
   return best < 0.0 ? SK_ERR_CUDA : SK_OK;
 }
 
-int sk_grouped_autotune(sk_grouped_t g, const void* const* A, const void* const* B, void* const* C,
-                        int reps, void* stream_v, double* best_us) {
+int grouped_autotune(sk_grouped_t g, const void* const* A, const void* const* B,
+                     const float* const* SA, const float* const* SB, void* const* C, int reps,
+                     void* stream_v, double* best_us) {
   if (g == nullptr || reps < 1) return SK_ERR_INVALID;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
   const int saved[3] = {g->tile_n_req, g->mode_req, g->grid_req};
@@ -1131,14 +1186,15 @@ int sk_grouped_autotune(sk_grouped_t g, const void* const* A, const void* const*
   double best = -1.0;
   int bt = saved[0], bm = saved[1];
   for (int tn : tns) {
+    if (tn == 256 && g->ab_type == SK_E4M3) continue;
     for (int md : modes) {
       g->tile_n_req = tn;
       g->mode_req = md;
       g->grid_req = 0;
       if (grouped_replan(g) != SK_OK) continue;
       const double us = time_launches(
-          [&] { return grouped_impl(g, A, B, C, nullptr, nullptr, nullptr, 0, stream); }, reps,
-          stream);
+          [&] { return grouped_impl(g, A, B, SA, SB, C, nullptr, nullptr, nullptr, 0, stream); },
+          reps, stream);
       int dev_status = 0;
       if (us < 0.0 || sk_grouped_last_error(g, &dev_status) != SK_OK) continue;
       if (best < 0.0 || us < best) {
@@ -1155,6 +1211,33 @@ int sk_grouped_autotune(sk_grouped_t g, const void* const* A, const void* const*
   if (st != SK_OK) return st;
   if (best_us) *best_us = best;
   return best < 0.0 ? SK_ERR_CUDA : SK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sk_plan_autotune(sk_plan_t p, const void* A, const void* B, void* C, int reps, void* stream,
+                     double* best_us) {
+  return plan_autotune(p, A, B, nullptr, nullptr, C, reps, stream, best_us);
+}
+
+int sk_plan_autotune_scaled(sk_plan_t p, const void* A, const void* B, const float* scale_a,
+                            const float* scale_b, void* C, int reps, void* stream, double* best_us) {
+  if (scale_a == nullptr || scale_b == nullptr) return SK_ERR_INVALID;
+  return plan_autotune(p, A, B, scale_a, scale_b, C, reps, stream, best_us);
+}
+
+int sk_grouped_autotune(sk_grouped_t g, const void* const* A, const void* const* B, void* const* C,
+                        int reps, void* stream, double* best_us) {
+  return grouped_autotune(g, A, B, nullptr, nullptr, C, reps, stream, best_us);
+}
+
+int sk_grouped_autotune_scaled(sk_grouped_t g, const void* const* A, const void* const* B,
+                               const float* const* SA, const float* const* SB, void* const* C,
+                               int reps, void* stream, double* best_us) {
+  if (SA == nullptr || SB == nullptr) return SK_ERR_INVALID;
+  return grouped_autotune(g, A, B, SA, SB, C, reps, stream, best_us);
 }
 
 }  // extern "C"

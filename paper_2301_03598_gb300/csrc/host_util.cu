@@ -39,7 +39,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-size_t dtype_size(int t) { return t == SK_F32 ? 4 : 2; }
+size_t dtype_size(int t) { return t == SK_F32 ? 4 : t == SK_E4M3 ? 1 : 2; }
 
 
 int cuda_status(cudaError_t e) {
@@ -52,12 +52,14 @@ int encode_operand(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows, in
                    int64_t ld, int box_rows) {
   auto fn = encode_fn();
   if (fn == nullptr) return SK_ERR_CUDA;
+  const int64_t esz = static_cast<int64_t>(dtype_size(dtype));
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(kdim), static_cast<cuuint64_t>(rows)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(sk::kBlkK), static_cast<cuuint32_t>(box_rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * esz)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / esz), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
-  CUtensorMapDataType dt =
-      dtype == SK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUtensorMapDataType dt = dtype == SK_BF16   ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                           : dtype == SK_E4M3 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   CUresult r = fn(tm, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -113,7 +115,8 @@ bool encode_output(CUtensorMap* tm, void* ptr, int c_type, int64_t rows, int64_t
 // one, else the default.
 int store_path(int req) { return req == 1 ? 1 : req == 2 ? 2 : 1; }
 
-// tcgen05 kind::f16 instruction descriptor: FP32 accumulator, A/B format,
+// tcgen05 kind::f16 / kind::f8f6f4 instruction descriptor: FP32
+// accumulator, A/B format (F16 0 / BF16 1; E4M3 0),
 // both operands K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 uint32_t make_idesc(int in_dtype, int tile_n, int cluster_m) {
   const uint32_t fmt = in_dtype == SK_BF16 ? 1u : 0u;

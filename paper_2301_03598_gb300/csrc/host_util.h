@@ -19,7 +19,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
 size_t dtype_size(int t);
 int cuda_status(cudaError_t e);
 // 2-D map of a K-contiguous operand (rows x kdim, pitch ld elements), boxes of
-// one 64-wide k-block x box_rows rows, 128-byte swizzle.
+// one k-block (128 bytes: 64 16-bit or 128 E4M3 elements) x box_rows rows,
+// 128-byte swizzle.
 int encode_operand(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows, int64_t kdim,
                    int64_t ld, int box_rows);
 // 3-D view {64, rows, k/64} of the same operand: boxes of two k-blocks.
@@ -29,7 +30,7 @@ int encode_operand_3d(CUtensorMap* tm, const void* ptr, int dtype, int64_t rows,
 bool encode_output(CUtensorMap* tm, void* ptr, int c_type, int64_t rows, int64_t cols, int64_t ld);
 // The epilogue store path for an aligned C (SkArgs::c_tma) for a request.
 int store_path(int req);
-// tcgen05 kind::f16 instruction descriptor.
+// tcgen05 instruction descriptor (kind::f16, or kind::f8f6f4 for E4M3).
 uint32_t make_idesc(int in_dtype, int tile_n, int cluster_m);
 
 }  // namespace host

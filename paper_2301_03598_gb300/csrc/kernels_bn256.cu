@@ -38,7 +38,7 @@ static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<256, CM, TC, false>, ta, tb, tc, ta3, tb3, args);
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<256, CM, TC, false, false>, ta, tb, tc, ta3, tb3, args);
 }
 
 template <int CM>
@@ -88,7 +88,7 @@ static cudaError_t launch_grouped_one(const CUtensorMap& tm, const SkArgs& args,
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<256, 1, TC, true>, tm, tm, tm, tm, tm, args);
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<256, 1, TC, true, false>, tm, tm, tm, tm, tm, args);
 }
 
 cudaError_t launch_grouped_bn256(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
@@ -107,11 +107,11 @@ cudaError_t launch_grouped_bn256(int c_dtype, const CUtensorMap& tm, const SkArg
 
 template <int CM, typename TC>
 static cudaError_t set_smem() {
-  cudaError_t e = cudaFuncSetAttribute(sk_gemm_kernel<256, CM, TC, false>,
+  cudaError_t e = cudaFuncSetAttribute(sk_gemm_kernel<256, CM, TC, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg<256, CM>::kSmemBytes);
   if (e != cudaSuccess || CM != 1) return e;
-  return cudaFuncSetAttribute(sk_gemm_kernel<256, 1, TC, true>,
+  return cudaFuncSetAttribute(sk_gemm_kernel<256, 1, TC, true, false>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<256, CM>::kSmemBytes);
 }
 

@@ -25,8 +25,16 @@ cudaError_t launch_grouped_bn128(int c_dtype, const CUtensorMap& tm, const SkArg
                                  bool cooperative, cudaStream_t stream);
 cudaError_t launch_grouped_bn256(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
                                  bool cooperative, cudaStream_t stream);
+// E4M3 operands with per-128 x 128-block scales (args.scale_a / scale_b):
+// 128 x 128 single-CTA tiles, 2-D maps of 128-byte k-blocks.
+cudaError_t launch_f8(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
+                      const CUtensorMap& tc, const SkArgs& args, bool cooperative,
+                      cudaStream_t stream);
+cudaError_t launch_grouped_f8(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
+                              bool cooperative, cudaStream_t stream);
 // Dynamic shared memory of one CTA; also sets the kernels' opt-in limit.
 cudaError_t prepare_bn128(size_t* smem_bytes);
 cudaError_t prepare_bn256(size_t* smem_bytes);
+cudaError_t prepare_f8(size_t* smem_bytes);
 
 }  // namespace sk

@@ -9,13 +9,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <memory>
 #include <new>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -87,13 +90,19 @@ struct sk_server_s {
   uint64_t next_id = 1;
   int64_t submitted = 0, completed = 0, batches = 0, max_batch_seen = 0, problems_launched = 0;
   bool stop = false;
+  std::atomic<int64_t> queued{0};  // submissions not yet admitted (read without the lock)
+  // Schedules of batch compositions seen before, keyed by the batch's
+  // (m, n, k) sequence; used by the worker only.
+  std::unordered_map<std::string, std::shared_ptr<const sk::GroupPlan>> plan_cache;
   int device = 0;
   std::thread worker;
 };
 
 namespace {
 
-constexpr int64_t kSegsPerProblem = 1024;  // record capacity per admitted problem (grown on demand)
+constexpr int64_t kSegsPerProblem = 1024;  // record capacity per admitted problem
+constexpr size_t kPlanCacheEntries = 4096;
+constexpr int kIdleSpinUs = 200;  // idle worker: spin before sleeping
 
 void free_slot(Slot& s) {
   if (s.d_block) cudaFree(s.d_block);
@@ -144,10 +153,30 @@ int launch_slot(sk_server_s* sv, Slot& s) {
     n[i] = s.reqs[i].n;
     k[i] = s.reqs[i].k;
   }
-  sk::GroupPlan gp;
-  int st = sk::describe_grouped(count, m.data(), n.data(), k.data(), SK_MODE_AUTO, 0, 0,
-                                sv->num_sms, &gp);
-  if (st != SK_OK) return st;
+  std::string key(3 * sizeof(int64_t) * static_cast<size_t>(count), '\0');
+  for (int i = 0; i < count; ++i) {
+    const int64_t v[3] = {m[i], n[i], k[i]};
+    std::memcpy(&key[3 * sizeof(int64_t) * static_cast<size_t>(i)], v, sizeof(v));
+  }
+  std::shared_ptr<const sk::GroupPlan> cached;
+  auto hit = sv->plan_cache.find(key);
+  if (hit != sv->plan_cache.end()) {
+    cached = hit->second;
+  } else {
+    // Small batches choose among every schedule; larger ones take
+    // data-parallel waves, which the model picks for them anyway and which
+    // cost the planner one candidate per tile width.
+    auto fresh = std::make_shared<sk::GroupPlan>();
+    const int mode = count <= 4 ? SK_MODE_AUTO : SK_MODE_DP;
+    const int st = sk::describe_grouped(count, m.data(), n.data(), k.data(), mode, 0, 0,
+                                        sv->num_sms, fresh.get());
+    if (st != SK_OK) return st;
+    if (sv->plan_cache.size() >= kPlanCacheEntries) sv->plan_cache.clear();
+    sv->plan_cache.emplace(std::move(key), fresh);
+    cached = std::move(fresh);
+  }
+  const sk::GroupPlan& gp = *cached;
+  int st = SK_OK;
   if (static_cast<int64_t>(gp.segs.size()) > sv->segs_cap) return SK_ERR_NOMEM;
   for (int i = 0; i < count; ++i) {
     const Request& r = s.reqs[i];
@@ -258,6 +287,7 @@ void worker_loop(sk_server_s* sv) {
         s.reqs.push_back(r);
         sv->entries[r.id].state = 1;
         sv->pending.pop_front();
+        sv->queued.fetch_sub(1, std::memory_order_relaxed);
       }
       if (!s.reqs.empty()) {
         sv->inflight_bytes += s.bytes;
@@ -277,15 +307,23 @@ void worker_loop(sk_server_s* sv) {
         continue;
       }
     }
-    // nothing to launch now: poll in-flight batches, or sleep until a submission
+    // Nothing to launch now.  With batches in flight, poll their events
+    // (yielding the core between polls: a timed sleep would round up to the
+    // kernel's timer slack, tens of microseconds).  Idle, spin a while for a
+    // submission before blocking on the condition variable.
+    lk.unlock();
     if (any_busy) {
-      lk.unlock();
-      std::this_thread::sleep_for(std::chrono::microseconds(2));
-      lk.lock();
+      std::this_thread::yield();
     } else {
+      const auto t0 = Clock::now();
+      while (sv->queued.load(std::memory_order_relaxed) == 0 &&
+             Clock::now() - t0 < std::chrono::microseconds(kIdleSpinUs))
+        std::this_thread::yield();
+    }
+    lk.lock();
+    if (!any_busy)
       sv->cv.wait_for(lk, std::chrono::milliseconds(5),
                       [&] { return sv->stop || !sv->pending.empty(); });
-    }
   }
 }
 
@@ -360,6 +398,7 @@ int sk_server_submit(sk_server_t sv, int64_t m, int64_t n, int64_t k, const void
     sv->entries[r.id] = sk_server_s::Entry{};
     sv->pending.push_back(r);
     ++sv->submitted;
+    sv->queued.fetch_add(1, std::memory_order_relaxed);
   }
   sv->cv.notify_one();
   *ticket = r.id;

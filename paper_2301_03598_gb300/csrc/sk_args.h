@@ -82,6 +82,10 @@ struct alignas(128) GroupProblem {
   int32_t m, n;
   int32_t c_tma, c_vec;
   float alpha, beta;
+  // E4M3 problems: FP32 scales per 128 x 128 block, [ceil(rows/128)][ld_scale]
+  const float* scale_a;
+  const float* scale_b;
+  int32_t ld_scale;  // ceil(k / 128)
 };
 
 struct SkArgs {
@@ -126,6 +130,11 @@ struct SkArgs {
   const GroupSeg* gsegs;
   const int32_t* gseg_start;
   const GroupProblem* gprobs;
+  // E4M3 launches: FP32 scale of every 128 x 128 block of A (m x k) and of B
+  // (n x k), row-major [ceil(rows / 128)][ld_scale], ld_scale = ceil(k / 128)
+  const float* scale_a;
+  const float* scale_b;
+  int32_t ld_scale;
 };
 
 }  // namespace sk

@@ -37,30 +37,44 @@ constexpr int kEpiWarp0 = 2;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 
-// Shared-memory stage ring per CTA: 192 KiB of operand stages.  A stage
-// holds KD consecutive 64-wide k-blocks (one MAC-loop iteration of BLK_K =
-// 64 * KD): KD = 2 for BLK_N = 128, whose 2-D stages are too small for the
-// SM's TMA path (a stage costs about as much as its bytes), KD = 1 for 256.
-template <int BN, int CM>
+// Shared-memory stage ring per CTA: 192 KiB of operand stages.  A k-block is
+// one 128-byte row per operand row: 64 16-bit elements, or 128 FP8 elements
+// (F8).  A stage holds KD consecutive k-blocks (one MAC-loop iteration):
+// KD = 2 for 16-bit BLK_N = 128, whose 2-D stages are too small for the SM's
+// TMA path (a stage costs about as much as its bytes), KD = 1 otherwise.
+//
+// F8 (E4M3 operands with one FP32 scale per 128 x 128 block of A and of B):
+// every k-block of 128 is one scale block, so the MMA warp writes each
+// k-block's product into one of kAccBufs rotating TMEM buffers and the
+// epilogue warps add it, times the block's two scales, into a running FP32
+// sum held in registers; the tile segment's sum goes to TMEM columns
+// [kAccBufs * BN, (kAccBufs + 1) * BN) for the common epilogue.
+template <int BN, int CM, bool F8 = false>
 struct Cfg {
-  static constexpr int KD = BN == 128 ? 2 : 1;
-  static constexpr int kSubA = kBlkM * kBlkK * 2;       // one k-block of this CTA's 128 A rows
-  static constexpr int kSubB = (BN / CM) * kBlkK * 2;   // one k-block of its BN/CM B rows
+  static constexpr int KD = (BN == 128 && !F8) ? 2 : 1;
+  static constexpr int kKElems = F8 ? 128 : kBlkK;  // elements of one k-block
+  static constexpr int kSubA = kBlkM * 128;          // one k-block of this CTA's 128 A rows
+  static constexpr int kSubB = (BN / CM) * 128;      // one k-block of its BN/CM B rows
   static constexpr int kABytes = KD * kSubA;
   static constexpr int kBBytes = KD * kSubB;
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kStages = (192 * 1024) / kStageBytes;  // 3, 4 (BN 128); 4, 6 (BN 256)
-  static constexpr int kTmemCols = 2 * BN;  // two FP32 accumulators of BN columns
+  static constexpr int kStages = (192 * 1024) / kStageBytes;  // 3, 4 (BN 128); 4, 6 (BN 256); F8: 6
+  static constexpr int kAccBufs = F8 ? 3 : 2;
+  // F8: three product buffers and the segment sum; else two accumulators
+  static constexpr int kTmemCols = F8 ? 4 * BN : 2 * BN;
+  static constexpr int kSumCol = kAccBufs * BN;  // F8: the segment sum's first column
   // Output staging for TMA stores: per epilogue warp one buffer of 32 rows x
   // 128 B, 128-byte swizzled (1 KiB aligned).
   static constexpr int kStagingOffset = kStages * kStageBytes;
   static constexpr int kStagingBytesPerWarp = 32 * 128;
   static constexpr int kStagingBytes = kEpiWarps * kStagingBytesPerWarp;
   static constexpr int kBarOffset = kStagingOffset + kStagingBytes;
-  static constexpr int kNumBars = 2 * kStages + 5;
+  static constexpr int kNumBars = 2 * kStages + 2 * kAccBufs + 1;
   static constexpr int kSmemBytes = kBarOffset + 256 + 1024;  // + barriers, + 1 KiB alignment
   static_assert(kNumBars * 8 + 8 <= 256, "barrier area");
   static_assert(kSmemBytes <= 232448, "shared memory per CTA");
+  static_assert(!F8 || (BN == 128 && CM == 1), "F8 tiles are 128 x 128 single-CTA tiles");
+  static_assert(kTmemCols <= 512, "TMEM columns");
 };
 
 // Where a bounded wait gave up (err[2]).
@@ -424,14 +438,15 @@ __device__ __forceinline__ void add_beta_c(const OutView& o, int grow, int gcol,
 // per k-block, the even CTA issues the pair MMAs (M = 256), and each CTA's
 // TMEM receives its own 128 rows of the accumulator, which its epilogue
 // spills, fixes up and stores exactly as a single CTA does.
-template <int BN, int CM, typename TC, bool GROUPED>
+template <int BN, int CM, typename TC, bool GROUPED, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmA3,
                    const __grid_constant__ CUtensorMap tmB3, const __grid_constant__ SkArgs a) {
   static_assert(CM == 1 || CM == 2, "cluster size along M");
   static_assert(!GROUPED || CM == 1, "grouped launches use single CTAs");
-  using C_ = Cfg<BN, CM>;
+  using C_ = Cfg<BN, CM, F8>;
+  constexpr int NB = C_::kAccBufs;
   constexpr int S = C_::kStages;
   constexpr int KD = C_::KD;
   extern __shared__ uint8_t smem_raw[];
@@ -447,8 +462,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
   auto accf_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
-  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * S + 4);
+  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * S + NB + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * S + 2 * NB);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -475,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(full_bar(s), 1);   // the issuer's producer arrives with both CTAs' bytes
       mbar_init(empty_bar(s), 1);  // released by the issuer's commit
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NB; ++b) {
       mbar_init(accf_bar(b), 1);
       mbar_init(acce_bar(b), CM * kEpiWarps);  // every epilogue warp of the pair
     }
@@ -574,8 +589,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               ready = tma_load_3d_pair_probe(stage_b(stage), pB3, fb, 0, brow, k0, empty_bar(next),
                                              next_phase ^ 1u);
             } else if constexpr (KD == 1) {
-              tma_load_2d_pair(stage_a(stage), pA, fb, k0 * kBlkK, tm * kBlkM);
-              ready = tma_load_2d_pair_probe(stage_b(stage), pB, fb, k0 * kBlkK, brow,
+              tma_load_2d_pair(stage_a(stage), pA, fb, k0 * C_::kKElems, tm * kBlkM);
+              ready = tma_load_2d_pair_probe(stage_b(stage), pB, fb, k0 * C_::kKElems, brow,
                                              empty_bar(next), next_phase ^ 1u);
             } else {
 #pragma unroll
@@ -593,8 +608,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               ready = tma_load_3d_probe(stage_b(stage), pB3, fb, 0, brow, k0, empty_bar(next),
                                         next_phase ^ 1u);
             } else if constexpr (KD == 1) {
-              tma_load_2d(stage_a(stage), pA, fb, k0 * kBlkK, tm * kBlkM);
-              ready = tma_load_2d_probe(stage_b(stage), pB, fb, k0 * kBlkK, brow, empty_bar(next),
+              tma_load_2d(stage_a(stage), pA, fb, k0 * C_::kKElems, tm * kBlkM);
+              ready = tma_load_2d_probe(stage_b(stage), pB, fb, k0 * C_::kKElems, brow, empty_bar(next),
                                         next_phase ^ 1u);
             } else {
 #pragma unroll
@@ -654,7 +669,47 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ready: the current stage's full barrier is known to have completed
       // (probed while the previous k-block's last MMA was issued).
       bool ready = false;
-      while (ok && cur.next(a, sg)) {
+      if constexpr (F8) {
+        // One product per k-block (one scale block) into the rotating
+        // buffers; the epilogue warps scale and sum them.
+        while (ok && cur.next(a, sg)) {
+          for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
+            if (!wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty) ||
+                (!ready && !wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            int next = stage + 1;
+            uint32_t next_phase = phase;
+            if (next == S) {
+              next = 0;
+              next_phase ^= 1u;
+            }
+            const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+            const uint64_t adesc = smem_desc_sw128(stage_a(stage));
+            const uint64_t bdesc = smem_desc_sw128(stage_b(stage));
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              // 32 E4M3 elements (32 B) along K per MMA
+              if (kk == 3)
+                ready = mma_f8_probe(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
+                                     full_bar(next), next_phase);
+              else
+                mma_f8(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
+            }
+            mma_commit(empty_bar(stage));
+            mma_commit(accf_bar(acc));
+            stage = next;
+            phase = next_phase;
+            if (++acc == NB) {
+              acc = 0;
+              acc_phase ^= 1u;
+            }
+          }
+        }
+      }
+      while (!F8 && ok && cur.next(a, sg)) {
         const int kb0 = sg.kb0, kb1 = sg.kb1;
         if (!wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) break;
         tc_fence_after();
@@ -736,6 +791,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t acc_phase = 0;
     // the single GEMM's output; a grouped segment switches to its problem's
     OutView out{a.C, a.ldc, a.m, a.n, a.c_vec, a.c_tma, a.alpha, a.beta, &tmC};
+    // F8: the block scales (row-major, ld_scale k-blocks per 128-row block)
+    const float* scale_a = a.scale_a;
+    const float* scale_b = a.scale_b;
+    int32_t ld_scale = a.ld_scale;
+    constexpr int kCpu = (sizeof(TC) == 4) ? 1 : 2;  // 32-column chunks per output unit
     float* const my_slot = a.partials + static_cast<size_t>(cta) * (kBlkM * BN);
     const uint32_t staging = base + static_cast<uint32_t>(C_::kStagingOffset +
                                                          (warp - kEpiWarp0) * C_::kStagingBytesPerWarp);
@@ -762,25 +822,105 @@ __global__ void __launch_bounds__(kThreads, 1)
         const GroupProblem* gp = a.gprobs + sg.problem;
         out = OutView{gp->C, gp->ldc, gp->m, gp->n, gp->c_vec, gp->c_tma, gp->alpha, gp->beta, &gp->tmC};
         if (lane == 0 && out.c_tma == 1) tensormap_acquire(out.tmC);
+        if constexpr (F8) {
+          scale_a = gp->scale_a;
+          scale_b = gp->scale_b;
+          ld_scale = gp->ld_scale;
+        }
       }
 
-      bool fail = !wait_bar(accf_bar(acc), acc_phase, abort_flag, a, kAtEpiAccFull);
+      bool fail = false;
+      if constexpr (F8) {
+        // The segment's sum over its k-blocks, in k order, of
+        // scale_a[tm][kb] * scale_b[tn][kb] * (product of k-block kb), for
+        // this warp's output units (the columns it stores below).
+        constexpr int kMine = BN / (32 * kCpu) / 2;
+        float sum[kMine][32 * kCpu];
+#pragma unroll
+        for (int i = 0; i < kMine; ++i)
+#pragma unroll
+          for (int j = 0; j < 32 * kCpu; ++j) sum[i][j] = 0.0f;
+        const float* sa = scale_a + static_cast<size_t>(tm) * ld_scale;
+        const float* sb = scale_b + static_cast<size_t>(tn) * ld_scale;
+        // lane l holds the scale product of k-block first + l; the next 32
+        // are loaded one window ahead
+        auto window = [&](int first) {
+          const int kb = first + lane;
+          return kb < kb1 ? __ldg(sa + kb) * __ldg(sb + kb) : 0.0f;
+        };
+        float s_cur = window(kb0);
+        float s_nxt = kb0 + 32 < kb1 ? window(kb0 + 32) : 0.0f;
+        for (int kb = kb0; kb < kb1; ++kb) {
+          const int i = kb - kb0;
+          if (i > 0 && (i & 31) == 0) {
+            s_cur = s_nxt;
+            if (kb + 32 < kb1) s_nxt = window(kb + 32);
+          }
+          const float sc = __shfl_sync(0xffffffffu, s_cur, i & 31);
+          if (!wait_bar(accf_bar(acc), acc_phase, abort_flag, a, kAtEpiAccFull)) {
+            fail = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t pbase = tmem_base + lane_base + static_cast<uint32_t>(acc * BN);
+          uint32_t r[kMine][32 * kCpu];
+#pragma unroll
+          for (int mi = 0; mi < kMine; ++mi) {
+            const uint32_t col = static_cast<uint32_t>((col_half + 2 * mi) * 32 * kCpu);
+            if constexpr (kCpu == 2)
+              tmem_ld_x64(pbase + col, r[mi]);
+            else
+              tmem_ld_x32(pbase + col, r[mi]);
+          }
+          tmem_wait_ld();
+          // the product buffer is read: the MMA warp may overwrite it
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce_bar(acc));
+#pragma unroll
+          for (int mi = 0; mi < kMine; ++mi)
+#pragma unroll
+            for (int j = 0; j < 32 * kCpu; ++j) sum[mi][j] = fmaf(sc, __uint_as_float(r[mi][j]), sum[mi][j]);
+          if (++acc == NB) {
+            acc = 0;
+            acc_phase ^= 1u;
+          }
+        }
+        if (!fail) {
+          const uint32_t sbase = tmem_base + lane_base + static_cast<uint32_t>(C_::kSumCol);
+#pragma unroll
+          for (int mi = 0; mi < kMine; ++mi) {
+            const uint32_t col = static_cast<uint32_t>((col_half + 2 * mi) * 32 * kCpu);
+            uint32_t w[32 * kCpu];
+#pragma unroll
+            for (int j = 0; j < 32 * kCpu; ++j) w[j] = __float_as_uint(sum[mi][j]);
+            if constexpr (kCpu == 2)
+              tmem_st_x64(sbase + col, w);
+            else
+              tmem_st_x32(sbase + col, w);
+          }
+          // this thread reads back exactly the lanes and columns it wrote
+          tmem_wait_st();
+        }
+      } else {
+        fail = !wait_bar(accf_bar(acc), acc_phase, abort_flag, a, kAtEpiAccFull);
+      }
       if (epi_any(fail)) break;
       tc_fence_after();
       const uint64_t t_acc = tracer ? globaltimer_ns() : 0;
       uint64_t t_fix = t_acc;
 
-      const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(acc * BN);
+      const uint32_t tbase =
+          tmem_base + lane_base + static_cast<uint32_t>(F8 ? C_::kSumCol : acc * BN);
       const int grow = tm * kBlkM + row;
       const int col0 = tn * BN;
       // Column units of 128 output bytes (32 FP32 or 64 16-bit columns); the
       // two warps of a lane quarter take alternate units.  Only units holding
       // columns < n are read, spilled, fixed up and stored.
-      constexpr int kCpu = (sizeof(TC) == 4) ? 1 : 2;  // 32-column chunks per unit
       const int nchunks = (min(BN, out.n - col0) + 31) / 32;
       const int nunits = (nchunks + kCpu - 1) / kCpu;
       const int my_last_unit = (nunits - 1 - col_half) >= 0 ? nunits - 1 - ((nunits - 1 - col_half) & 1) : -1;
-      if (my_last_unit < 0) {
+      if (!F8 && my_last_unit < 0) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) release_acc(acc);
@@ -796,7 +936,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           else
             tmem_ld_x32(tbase + static_cast<uint32_t>(u * 32), r);
           tmem_wait_ld();
-          if (u == my_last_unit) {
+          if (!F8 && u == my_last_unit) {
             // all of this warp's TMEM reads are done: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
@@ -972,8 +1112,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         ++nrec;
         tb[0] = nrec;
       }
-      acc ^= 1;
-      if (acc == 0) acc_phase ^= 1u;
+      if constexpr (!F8) {
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1u;
+      }
     }
     // The staging buffers are read before the CTA's shared memory goes away;
     // the global writes themselves complete with the grid.

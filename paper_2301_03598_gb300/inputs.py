@@ -73,6 +73,44 @@ def device_pool(numel: int, dtype: str, dist: str, seed: int, device) -> torch.T
     return out
 
 
+def e4m3_quantize(x: torch.Tensor):
+    """Block-scaled E4M3 storage of a float32 matrix (any device): one FP32
+    scale per 128 x 128 block, amax / 448 (1 for an all-zero block), and the
+    codes of x / scale rounded by torch's float8_e4m3fn conversion (RN-even;
+    |x / scale| <= 448 by construction).  Returns (codes uint8 rows x cols,
+    scales float32 [ceil(rows/128), ceil(cols/128)])."""
+    rows, cols = x.shape
+    nbr, nbc = -(-rows // 128), -(-cols // 128)
+    pad = torch.zeros(nbr * 128, nbc * 128, dtype=torch.float32, device=x.device)
+    pad[:rows, :cols] = x
+    amax = pad.abs().view(nbr, 128, nbc, 128).amax(dim=(1, 3))
+    scales = torch.where(amax > 0, amax / 448.0, torch.ones_like(amax))
+    full = scales.repeat_interleave(128, 0).repeat_interleave(128, 1)[:rows, :cols]
+    codes = (x / full).to(torch.float8_e4m3fn).view(torch.uint8).contiguous()
+    return codes, scales.contiguous()
+
+
+def host_e4m3_matrix(rows: int, cols: int, dist: str, seed: int):
+    """A rows x cols block-scaled E4M3 operand on the CPU: (codes, scales),
+    values drawn as in ``host_matrix`` before quantisation."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return e4m3_quantize(torch.from_numpy(_draw(rng, (rows, cols), dist)))
+
+
+def device_e4m3_matrix(rows: int, cols: int, seed: int, device, dist: str = "normal"):
+    """The same drawn on the device (Philox), for operands too large to make
+    on the host: (codes, scales) device tensors."""
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    if dist == "normal":
+        x = torch.randn(rows, cols, generator=gen, device=device, dtype=torch.float32)
+    elif dist == "uniform":
+        x = torch.rand(rows, cols, generator=gen, device=device, dtype=torch.float32) * 2 - 1
+    else:
+        raise ValueError(dist)
+    return e4m3_quantize(x)
+
+
 def log_uniform_shapes(count: int, seed: int, lo: int = 128, hi: int = 8192,
                        multiple: int = 16) -> List[Tuple[int, int, int]]:
     """``count`` shapes (m, n, k), each drawn log-uniform in [lo, hi] and rounded

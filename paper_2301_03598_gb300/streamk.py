@@ -17,7 +17,7 @@ from .build import INCLUDE, LIB
 
 SK_OK, SK_ERR_INVALID, SK_ERR_UNSUPPORTED, SK_ERR_CUDA, SK_ERR_TIMEOUT, SK_ERR_NOMEM, \
     SK_ERR_DEVICE = range(7)
-DTYPES = {"f16": 0, "bf16": 1, "f32": 2}
+DTYPES = {"f16": 0, "bf16": 1, "f32": 2, "e4m3": 3}
 LAYOUTS = {"row": 0, "col": 1}
 MODES = {"auto": 0, "dp": 1, "sk": 2, "hybrid": 3, "hybrid1": 4}
 MODE_NAMES = {v: k for k, v in MODES.items()}
@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
                           i32]
     L.sk_gemm.argtypes = [vp, vp, vp, vp, f32, f32, vp]
     L.sk_gemm_traced.argtypes = [vp, vp, vp, vp, f32, f32, vp, i64, vp]
+    L.sk_gemm_scaled.argtypes = [vp, vp, vp, vp, vp, vp, f32, f32, vp]
     L.sk_last_error.argtypes = [vp, ctypes.POINTER(i32)]
     L.sk_plan_destroy.argtypes = [vp]
     L.sk_plan_set.argtypes = [vp, i32, i64]
@@ -90,6 +91,7 @@ def lib() -> ctypes.CDLL:
     L.sk_grouped_plan.argtypes = [ctypes.POINTER(vp), i32, i64p, i64p, i64p, i32, i32, i32]
     L.sk_grouped_gemm.argtypes = [vp, vpp, vpp, vpp, f32p, f32p, vp]
     L.sk_grouped_gemm_traced.argtypes = [vp, vpp, vpp, vpp, f32p, f32p, vp, i64, vp]
+    L.sk_grouped_gemm_scaled.argtypes = [vp, vpp, vpp, vpp, vpp, vpp, f32p, f32p, vp]
     L.sk_grouped_last_error.argtypes = [vp, ctypes.POINTER(i32)]
     L.sk_grouped_set.argtypes = [vp, i32, i64]
     L.sk_grouped_get.argtypes = [vp, i32, i64p]
@@ -105,6 +107,8 @@ def lib() -> ctypes.CDLL:
     L.sk_server_destroy.argtypes = [vp]
     L.sk_plan_autotune.argtypes = [vp, vp, vp, vp, i32, vp, dblp]
     L.sk_grouped_autotune.argtypes = [vp, vpp, vpp, vpp, i32, vp, dblp]
+    L.sk_plan_autotune_scaled.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, dblp]
+    L.sk_grouped_autotune_scaled.argtypes = [vp, vpp, vpp, vpp, vpp, vpp, i32, vp, dblp]
     L.sk_grouped_plan_describe.argtypes = [i32, i64p, i64p, i64p, i32, i32, i32, i32, i64p,
                                            ctypes.POINTER(ctypes.c_int32), i64, i64p]
     L.sk_status_string.argtypes = [i32]
@@ -115,6 +119,8 @@ def lib() -> ctypes.CDLL:
                  "sk_grouped_gemm_traced", "sk_grouped_last_error", "sk_grouped_set",
                  "sk_grouped_get", "sk_grouped_schedule", "sk_grouped_destroy",
                  "sk_grouped_plan_describe", "sk_plan_autotune", "sk_grouped_autotune",
+                 "sk_gemm_scaled", "sk_grouped_gemm_scaled", "sk_plan_autotune_scaled",
+                 "sk_grouped_autotune_scaled",
                  "sk_server_create", "sk_server_submit", "sk_server_poll", "sk_server_wait",
                  "sk_server_stats", "sk_server_destroy"):
         getattr(L, name).restype = i32
@@ -146,7 +152,8 @@ def _code(table, v, what):
 def _dtype_name(x):
     try:
         import torch
-        m = {torch.float16: "f16", torch.bfloat16: "bf16", torch.float32: "f32"}
+        m = {torch.float16: "f16", torch.bfloat16: "bf16", torch.float32: "f32",
+             torch.float8_e4m3fn: "e4m3"}
         if x in m:
             return m[x]
     except ImportError:  # pragma: no cover
@@ -259,6 +266,16 @@ def sk_gemm(plan: Plan, A, B, C, alpha: float = 1.0, beta: float = 0.0, stream=N
     i.e. an n x k row-major tensor).  Asynchronous on ``stream``."""
     _check(lib().sk_gemm(plan.handle, _ptr(A), _ptr(B), _ptr(C), alpha, beta, _stream(stream)),
            "sk_gemm")
+
+
+def sk_gemm_scaled(plan: Plan, A, B, scale_a, scale_b, C, alpha: float = 1.0, beta: float = 0.0,
+                   stream=None) -> None:
+    """Block-scaled E4M3 GEMM: C = alpha * sum over k-blocks of 128 of
+    scale_a[i/128, kb] * scale_b[j/128, kb] * A_kb @ B_kb + beta * C, with
+    scale_a FP32 [ceil(m/128), ceil(k/128)] and scale_b [ceil(n/128),
+    ceil(k/128)] on the device."""
+    _check(lib().sk_gemm_scaled(plan.handle, _ptr(A), _ptr(B), _ptr(scale_a), _ptr(scale_b),
+                                _ptr(C), alpha, beta, _stream(stream)), "sk_gemm_scaled")
 
 
 def sk_gemm_traced(plan: Plan, A, B, C, alpha: float, beta: float, trace, stream=None) -> None:
@@ -400,6 +417,15 @@ def sk_grouped_gemm(plan: GroupedPlan, As, Bs, Cs, alpha=None, beta=None, stream
            "sk_grouped_gemm")
 
 
+def sk_grouped_gemm_scaled(plan: GroupedPlan, As, Bs, SAs, SBs, Cs, alpha=None, beta=None,
+                           stream=None) -> None:
+    """sk_grouped_gemm for an E4M3 group, with every problem's block scales."""
+    _check(lib().sk_grouped_gemm_scaled(plan.handle, _ptr_array(As), _ptr_array(Bs),
+                                        _ptr_array(SAs), _ptr_array(SBs), _ptr_array(Cs),
+                                        _f32_array(alpha), _f32_array(beta), _stream(stream)),
+           "sk_grouped_gemm_scaled")
+
+
 def sk_grouped_gemm_traced(plan: GroupedPlan, As, Bs, Cs, alpha, beta, trace, stream=None) -> None:
     _check(lib().sk_grouped_gemm_traced(plan.handle, _ptr_array(As), _ptr_array(Bs),
                                         _ptr_array(Cs), _f32_array(alpha), _f32_array(beta),
@@ -458,6 +484,25 @@ def sk_plan_autotune(plan: Plan, A, B, C, reps: int = 5, stream=None) -> float:
     best = ctypes.c_double(0.0)
     _check(lib().sk_plan_autotune(plan.handle, _ptr(A), _ptr(B), _ptr(C), int(reps),
                                   _stream(stream), ctypes.byref(best)), "sk_plan_autotune")
+    return best.value
+
+
+def sk_plan_autotune_scaled(plan: Plan, A, B, scale_a, scale_b, C, reps: int = 5,
+                            stream=None) -> float:
+    best = ctypes.c_double(0.0)
+    _check(lib().sk_plan_autotune_scaled(plan.handle, _ptr(A), _ptr(B), _ptr(scale_a),
+                                         _ptr(scale_b), _ptr(C), int(reps), _stream(stream),
+                                         ctypes.byref(best)), "sk_plan_autotune_scaled")
+    return best.value
+
+
+def sk_grouped_autotune_scaled(plan: GroupedPlan, As, Bs, SAs, SBs, Cs, reps: int = 3,
+                               stream=None) -> float:
+    best = ctypes.c_double(0.0)
+    _check(lib().sk_grouped_autotune_scaled(plan.handle, _ptr_array(As), _ptr_array(Bs),
+                                            _ptr_array(SAs), _ptr_array(SBs), _ptr_array(Cs),
+                                            int(reps), _stream(stream), ctypes.byref(best)),
+           "sk_grouped_autotune_scaled")
     return best.value
 
 

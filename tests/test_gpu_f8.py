@@ -1,0 +1,205 @@
+"""Block-scaled E4M3 GEMMs on the GPU through the C ABI (sk_gemm_scaled,
+sk_grouped_gemm_scaled) against the FP64 oracle on the same codes and scales.
+
+Bound per element (gemm_check.bound with |A||B| of the dequantized operands):
+every k-block's products are exact in FP32 and summed by the tensor cores in
+FP32, then scaled (one rounding) and added to the FP32 running sum (one
+rounding per k-block), and Stream-K partials are added in FP32, all within
+k * 2^-22 relative to sum |a||b| for k >= 16."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import e4m3
+from paper_2301_03598_gb300 import inputs
+from paper_2301_03598_gb300 import streamk as sk
+
+from gemm_check import bound, check_bound
+
+pytestmark = pytest.mark.gpu
+
+
+class F8Problem:
+    def __init__(self, m, n, k, c_type="bf16", seed=0, beta=0.0, dist="normal",
+                 scale_spread=False):
+        self.m, self.n, self.k, self.c_type = m, n, k, c_type
+        self.qA, self.sA = inputs.host_e4m3_matrix(m, k, dist, seed * 7 + 1)
+        self.qB, self.sB = inputs.host_e4m3_matrix(n, k, dist, seed * 7 + 2)
+        if scale_spread:
+            # exact powers of two per block, 2^-8 .. 2^8: a scale taken from
+            # the wrong block is off by orders of magnitude
+            g = np.random.Generator(np.random.PCG64(seed + 99))
+            self.sA = self.sA * torch.from_numpy(np.exp2(g.integers(-8, 9, self.sA.shape)).astype(np.float32))
+            self.sB = self.sB * torch.from_numpy(np.exp2(g.integers(-8, 9, self.sB.shape)).astype(np.float32))
+        if beta != 0.0:
+            self.Cin, _ = inputs.host_matrix(m, n, c_type, dist, seed * 7 + 3)
+        else:
+            self.Cin = torch.zeros((m, n), dtype=inputs.DTYPES[c_type])
+
+    def oracle(self, alpha, beta):
+        Cin64 = inputs.widen(self.Cin)
+        return e4m3.gemm(self.qA.numpy(), self.sA.numpy(), self.qB.numpy(), self.sB.numpy(),
+                         alpha, beta, Cin64 if beta != 0.0 else None)
+
+    def run(self, alpha=1.0, beta=0.0, mode="auto", attrs=None, reps=1, c_layout="row"):
+        plan = sk.sk_plan(self.m, self.n, self.k, "e4m3", "e4m3", self.c_type, "f32", "row",
+                          "col", c_layout, mode)
+        try:
+            for key, v in (attrs or {}).items():
+                plan.set(key, v)
+            A, B = self.qA.cuda(), self.qB.cuda()
+            sA, sB = self.sA.cuda(), self.sB.cuda()
+            outs = []
+            for _ in range(reps):
+                C = self.Cin.clone().cuda() if c_layout == "row" else self.Cin.t().contiguous().cuda()
+                sk.sk_gemm_scaled(plan, A, B, sA, sB, C, alpha, beta)
+                st, dev = sk.sk_last_error(plan)
+                assert st == sk.SK_OK, (sk.sk_status_string(st), dev)
+                out = C.cpu()
+                outs.append(out if c_layout == "row" else out.t().contiguous())
+            return outs, plan.info()
+        finally:
+            plan.destroy()
+
+    def check(self, C, alpha, beta, what=""):
+        C64, absAB = self.oracle(alpha, beta)
+        b = bound(self.k, alpha, beta, absAB, C64, inputs.widen(self.Cin), self.c_type)
+        return check_bound(inputs.widen(C), C64, b, what)
+
+
+SHAPES = [(384, 384, 4096), (300, 260, 1008), (129, 1000, 144), (16, 128, 16), (1000, 520, 2048),
+          (1, 1, 16)]
+
+
+@pytest.mark.parametrize("mode", ["auto", "dp", "sk", "hybrid"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_f8_matches_oracle(shape, mode):
+    p = F8Problem(*shape, seed=3)
+    outs, info = p.run(1.0, 0.0, mode)
+    assert info["tile_n"] == 128 and info["tile_k"] == 128 and info["cluster_m"] == 1
+    p.check(outs[0], 1.0, 0.0, f"e4m3 {shape} {mode}")
+
+
+@pytest.mark.parametrize("grid", [7, 40, 151])
+def test_f8_split_tiles_with_spread_scales(grid):
+    # 9 tiles of 32 k-blocks over g CTAs: every tile split, owners fix up
+    p = F8Problem(384, 384, 4096, seed=5, scale_spread=True)
+    outs, info = p.run(1.0, 0.0, "sk", {"grid": grid})
+    assert info["grid"] == grid
+    p.check(outs[0], 1.0, 0.0, f"e4m3 spread scales g={grid}")
+
+
+@pytest.mark.parametrize("c_type", ["f32", "f16", "bf16"])
+def test_f8_alpha_beta_output_types(c_type):
+    p = F8Problem(520, 300, 1024, c_type=c_type, seed=7, beta=0.5)
+    outs, _ = p.run(1.5, 0.5, "hybrid")
+    p.check(outs[0], 1.5, 0.5, f"e4m3 beta {c_type}")
+
+
+def test_f8_column_major_c_and_uniform_values():
+    p = F8Problem(260, 390, 656, seed=8, dist="uniform", scale_spread=True)
+    outs, _ = p.run(1.0, 0.0, "sk", {"grid": 33}, c_layout="col")
+    p.check(outs[0], 1.0, 0.0, "e4m3 column-major C")
+
+
+def test_f8_bitwise_reproducible():
+    p = F8Problem(640, 384, 8192, seed=9)
+    outs, _ = p.run(1.0, 0.0, "sk", {"grid": 100}, reps=3)
+    assert all(torch.equal(outs[0], o) for o in outs[1:])
+    p.check(outs[0], 1.0, 0.0, "e4m3 reproducible")
+
+
+def test_f8_entry_point_contract():
+    plan = sk.sk_plan(256, 256, 256, "e4m3", "e4m3", "bf16")
+    try:
+        A = torch.zeros(256, 256, dtype=torch.uint8, device="cuda")
+        C = torch.zeros(256, 256, dtype=torch.bfloat16, device="cuda")
+        s = torch.ones(2, 2, dtype=torch.float32, device="cuda")
+        with pytest.raises(sk.StreamKError) as e:
+            sk.sk_gemm(plan, A, A, C)                    # scales are required
+        assert e.value.status == sk.SK_ERR_INVALID
+        with pytest.raises(sk.StreamKError) as e:
+            plan.set("tile_n", 256)
+        assert e.value.status == sk.SK_ERR_UNSUPPORTED
+        with pytest.raises(sk.StreamKError) as e:
+            plan.set("cluster_m", 2)
+        assert e.value.status == sk.SK_ERR_UNSUPPORTED
+        sk.sk_gemm_scaled(plan, A, A, s, s, C)
+        assert sk.sk_last_error(plan)[0] == sk.SK_OK
+        assert float(C.float().abs().max()) == 0.0
+    finally:
+        plan.destroy()
+    plan16 = sk.sk_plan(128, 128, 128, "bf16", "bf16", "bf16")
+    try:
+        X = torch.zeros(128, 128, dtype=torch.bfloat16, device="cuda")
+        s = torch.ones(1, 1, dtype=torch.float32, device="cuda")
+        with pytest.raises(sk.StreamKError) as e:
+            sk.sk_gemm_scaled(plan16, X, X, s, s, X)     # 16-bit plans take no scales
+        assert e.value.status == sk.SK_ERR_INVALID
+    finally:
+        plan16.destroy()
+
+
+def test_f8_large_sampled_entries():
+    # 4096 x 4096 x 8192 on device-drawn operands; 4,096 sampled outputs
+    m, n, k = 4096, 4096, 8192
+    qA, sA = inputs.device_e4m3_matrix(m, k, 31, "cuda")
+    qB, sB = inputs.device_e4m3_matrix(n, k, 32, "cuda")
+    C = torch.empty(m, n, dtype=torch.bfloat16, device="cuda")
+    plan = sk.sk_plan(m, n, k, "e4m3", "e4m3", "bf16")
+    try:
+        sk.sk_gemm_scaled(plan, qA, qB, sA, sB, C)
+        assert sk.sk_last_error(plan)[0] == sk.SK_OK
+    finally:
+        plan.destroy()
+    g = np.random.Generator(np.random.PCG64(5))
+    rows, cols = g.integers(0, m, 4096), g.integers(0, n, 4096)
+    want, absAB = e4m3.gemm_entries(rows, cols, qA.cpu().numpy(), sA.cpu().numpy(),
+                                    qB.cpu().numpy(), sB.cpu().numpy())
+    got = C.cpu()[torch.from_numpy(rows), torch.from_numpy(cols)]
+    b = bound(k, 1.0, 0.0, absAB, want, None, "bf16")
+    check_bound(inputs.widen(got), want, b, "e4m3 4096x4096x8192 sampled")
+
+
+GROUP = [(300, 500, 704), (128, 128, 4096), (1000, 200, 128), (64, 520, 1024), (17, 1000, 304),
+         (777, 96, 2000)]
+
+
+def _grouped(shapes, mode, c_type="bf16", beta=0.0, attrs=None, seed=0, autotune=False):
+    probs = [F8Problem(m, n, k, c_type, seed=seed + 13 * i, beta=beta, scale_spread=(i % 2 == 1))
+             for i, (m, n, k) in enumerate(shapes)]
+    plan = sk.sk_grouped_plan(shapes, "e4m3", c_type, mode)
+    try:
+        for key, v in (attrs or {}).items():
+            plan.set(key, v)
+        As = [p.qA.cuda() for p in probs]
+        Bs = [p.qB.cuda() for p in probs]
+        SAs = [p.sA.cuda() for p in probs]
+        SBs = [p.sB.cuda() for p in probs]
+        if autotune:
+            scratch = [torch.empty(p.m, p.n, dtype=inputs.DTYPES[c_type], device="cuda")
+                       for p in probs]
+            sk.sk_grouped_autotune_scaled(plan, As, Bs, SAs, SBs, scratch, reps=2)
+        Cs = [p.Cin.clone().cuda() for p in probs]
+        alphas = [1.0 + 0.25 * (i % 3) for i in range(len(shapes))]
+        sk.sk_grouped_gemm_scaled(plan, As, Bs, SAs, SBs, Cs, alphas, [beta] * len(shapes))
+        st, dev = sk.sk_grouped_last_error(plan)
+        assert st == sk.SK_OK, (sk.sk_status_string(st), dev)
+        return probs, [c.cpu() for c in Cs], alphas, plan.info()
+    finally:
+        plan.destroy()
+
+
+@pytest.mark.parametrize("mode,attrs", [("auto", {}), ("dp", {}), ("sk", {"grid": 29}),
+                                        ("hybrid", {})])
+def test_f8_grouped_matches_oracle(mode, attrs):
+    probs, outs, alphas, info = _grouped(GROUP, mode, attrs=attrs, seed=4)
+    assert info["tile_n"] == 128
+    for p, C, al in zip(probs, outs, alphas):
+        p.check(C, al, 0.0, f"e4m3 grouped {mode} {p.m}x{p.n}x{p.k}")
+
+
+def test_f8_grouped_beta_f32_and_autotune():
+    probs, outs, alphas, info = _grouped(GROUP, "auto", "f32", 0.5, seed=6, autotune=True)
+    for p, C, al in zip(probs, outs, alphas):
+        p.check(C, al, 0.5, f"e4m3 grouped autotuned {p.m}x{p.n}x{p.k}")
