@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-grouped", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-f8", action="store_true")
     return ap.parse_args()
 
 
@@ -608,6 +609,9 @@ def ours_arm(args):
             results["dp"]["geomean_tflops"]
     if not args.no_grouped:
         line["grouped"] = run_grouped(max(3, min(args.steps, 10)), args.warmup)
+    if not args.no_f8:
+        line["grouped_e4m3"] = run_grouped_f8(max(3, min(args.steps, 10)), args.warmup)
+        line["e4m3_shapes"] = run_f8_shapes(peaks)
     if not args.no_serving:
         line["serving"] = run_serving()
     print(json.dumps(line), flush=True)
@@ -684,6 +688,125 @@ def run_grouped(steps, warmup):
                      "timing": "the 256 single-GEMM launches replayed from one CUDA graph"},
         "speedup": s_ms / g_ms,
     }
+
+
+def run_grouped_f8(steps, warmup):
+    """The grouped workload with E4M3 operands (per-128 x 128-block FP32 scales,
+    values N(0,1) before quantisation), BF16 out: one autotuned Stream-K
+    launch across the 256 problems against 256 separate sk_gemm_scaled
+    launches replayed from one CUDA graph."""
+    import torch
+    from paper_2301_03598_gb300 import inputs
+    from paper_2301_03598_gb300 import streamk as sk
+    shapes = inputs.grouped_shapes()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    As, Bs, SAs, SBs, Cs = [], [], [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        qa, sa = inputs.device_e4m3_matrix(m, k, inputs.GROUPED_SEED + 3 * i, dev)
+        qb, sb = inputs.device_e4m3_matrix(n, k, inputs.GROUPED_SEED + 3 * i + 1, dev)
+        As.append(qa)
+        Bs.append(qb)
+        SAs.append(sa)
+        SBs.append(sb)
+        Cs.append(torch.empty(m, n, dtype=torch.bfloat16, device=dev))
+    flops = float(sum(2.0 * m * n * k for m, n, k in shapes))
+    stream = torch.cuda.Stream()
+    gplan = sk.sk_grouped_plan(shapes, "e4m3", "bf16", "auto")
+    tuned_us = sk.sk_grouped_autotune_scaled(gplan, As, Bs, SAs, SBs, Cs, reps=3, stream=stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, warmup)):
+            sk.sk_grouped_gemm_scaled(gplan, As, Bs, SAs, SBs, Cs, stream=stream)
+        ev[0].record(stream)
+        for _ in range(steps):
+            sk.sk_grouped_gemm_scaled(gplan, As, Bs, SAs, SBs, Cs, stream=stream)
+        ev[1].record(stream)
+    torch.cuda.synchronize()
+    st, dstat = sk.sk_grouped_last_error(gplan)
+    if st != sk.SK_OK:
+        raise RuntimeError(f"grouped e4m3 launch status {st}/{dstat}")
+    g_ms = ev[0].elapsed_time(ev[1]) / steps
+    ginfo = gplan.info()
+    plans = [sk.sk_plan(m, n, k, "e4m3", "e4m3", "bf16") for m, n, k in shapes]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        for args in zip(plans, As, Bs, SAs, SBs, Cs):
+            sk.sk_gemm_scaled(*args, stream=stream)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            for args in zip(plans, As, Bs, SAs, SBs, Cs):
+                sk.sk_gemm_scaled(*args)
+        for _ in range(max(1, warmup)):
+            graph.replay()
+        ev[0].record(stream)
+        for _ in range(steps):
+            graph.replay()
+        ev[1].record(stream)
+    torch.cuda.synchronize()
+    for p in plans:
+        st, dstat = sk.sk_last_error(p)
+        if st != sk.SK_OK:
+            raise RuntimeError(f"separate e4m3 launch status {st}/{dstat}")
+    s_ms = ev[0].elapsed_time(ev[1]) / steps
+    for p in plans:
+        p.destroy()
+    gplan.destroy()
+    return {
+        "workload": "grouped GEMM: the 256 problems of the grouped workload, FP8-e4m3 A and B "
+                    "with per-128x128-block FP32 scales (N(0,1) before quantisation), FP32 "
+                    "accumulate, BF16 out",
+        "problems": len(shapes), "gflop": flops / 1e9,
+        "grouped": {"ms": g_ms, "tflops": flops / (g_ms * 1e-3) / 1e12, "launches_per_step": 1,
+                    "autotune_best_us": tuned_us,
+                    "plan": {k: ginfo[k] for k in ("mode", "tile_n", "grid", "tiles", "sk_tiles")}},
+        "separate": {"ms": s_ms, "tflops": flops / (s_ms * 1e-3) / 1e12,
+                     "launches_per_step": len(shapes),
+                     "timing": "the 256 sk_gemm_scaled launches replayed from one CUDA graph"},
+        "speedup": s_ms / g_ms,
+    }
+
+
+F8_SHAPES = [(8192, 8192, 8192), (4096, 4096, 4096), (2048, 2048, 8192), (384, 384, 4096),
+             (256, 256, 65536)]
+
+
+def run_f8_shapes(peaks, reps=20):
+    """Single E4M3 GEMMs (AUTO plans, BF16 out), each timed over `reps`
+    back-to-back launches after warm-up; TFLOP/s against the FP8 peak taken
+    as twice the measured BF16 burst peak (the nominal dense ratio)."""
+    import torch
+    from paper_2301_03598_gb300 import inputs
+    from paper_2301_03598_gb300 import streamk as sk
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"peak_tflops": 2.0 * peaks["bf16_tflops"],
+           "peak_kind": "2 x bf16 burst (" + peaks["source"] + ")", "shapes": []}
+    stream = torch.cuda.Stream()
+    for (m, n, k) in F8_SHAPES:
+        qa, sa = inputs.device_e4m3_matrix(m, k, 77, dev)
+        qb, sb = inputs.device_e4m3_matrix(n, k, 78, dev)
+        C = torch.empty(m, n, dtype=torch.bfloat16, device=dev)
+        plan = sk.sk_plan(m, n, k, "e4m3", "e4m3", "bf16")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                sk.sk_gemm_scaled(plan, qa, qb, sa, sb, C, stream=stream)
+            ev[0].record(stream)
+            for _ in range(reps):
+                sk.sk_gemm_scaled(plan, qa, qb, sa, sb, C, stream=stream)
+            ev[1].record(stream)
+        torch.cuda.synchronize()
+        st, dstat = sk.sk_last_error(plan)
+        if st != sk.SK_OK:
+            raise RuntimeError(f"e4m3 {m}x{n}x{k} status {st}/{dstat}")
+        us = ev[0].elapsed_time(ev[1]) * 1e3 / reps
+        tf = 2.0 * m * n * k / (us * 1e-6) / 1e12
+        info = plan.info()
+        out["shapes"].append({"m": m, "n": n, "k": k, "us": us, "tflops": tf,
+                              "frac_of_peak": tf / out["peak_tflops"],
+                              "plan": {x: info[x] for x in ("mode", "grid", "tiles", "sk_tiles")}})
+        plan.destroy()
+        del qa, qb, sa, sb, C
+    return out
 
 
 def _plain_launches(sk, plans, ops, arrivals, pick):

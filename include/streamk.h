@@ -143,8 +143,9 @@ typedef struct {
  *   m, n, k   >= 0 (m*n == 0: sk_gemm is a no-op; k == 0: C = beta*C).
  *   a_type == b_type in {SK_F16, SK_BF16, SK_E4M3}; c_type in {SK_F32, SK_BF16,
  *   SK_F16}; compute_type must be SK_F32 (FP32 accumulation, Section 6).
- *   E4M3 plans run 128 x 128 x 128 tiles on single CTAs (SK_ATTR_TILE_N 128,
- *   SK_ATTR_CLUSTER_M 1) and are launched with sk_gemm_scaled.
+ *   E4M3 plans run BLK_N = 128, BLK_K = 128 tiles (SK_ATTR_TILE_N 128 only) on
+ *   single CTAs by default (SK_ATTR_CLUSTER_M 2 selects CTA pairs) and are
+ *   launched with sk_gemm_scaled.
  *   a_layout SK_ROW_MAJOR, b_layout SK_COL_MAJOR, c_layout either.
  *   mode: an sk_mode.
  * Allocates the plan's device workspace (fixup partials and flags, Algorithm 5
@@ -391,17 +392,24 @@ int sk_grouped_autotune_scaled(sk_grouped_t plan, const void* const* A, const vo
  * layouts and rules as for grouped problems, device pointers owned by the
  * caller and left untouched until the request completes) are queued on
  * submission.  A worker thread admits queued requests, oldest first, into a
- * free launch slot: at most max_batch requests per batch, and while the
- * operand bytes (2(mk + kn) + mn * sizeof(C)) of all admitted, unfinished
- * requests stay within hbm_budget_bytes (a lone request is always admitted).
- * Each batch is planned as one grouped Stream-K launch (SK_MODE_AUTO) and
- * launched on its slot's stream; slots run concurrently, so a batch admitted
- * while others are in flight overlaps them.  The server keeps its schedules,
- * problem tables and fixup workspaces on the device, preallocated per slot.
+ * free launch slot: at most max_batch requests per batch, all of one input
+ * type (the server's 16-bit type, or E4M3 for sk_server_submit_scaled), and
+ * while the operand bytes (size(A) + size(B) + mn * sizeof(C)) of all
+ * admitted, unfinished requests stay within hbm_budget_bytes (a lone request
+ * is always admitted).  Each batch is one grouped Stream-K launch: up to 4
+ * requests planned by the grouped model (SK_MODE_AUTO, schedules cached by
+ * batch composition), larger batches as data-parallel waves.  The device
+ * derives each CTA's segments from a per-problem walk table, so planning a
+ * batch costs O(batch + SMs) on the host.  A batch is launched on its slot's
+ * stream; slots run concurrently, so a batch admitted while others are in
+ * flight overlaps them.  Problem and walk tables and fixup workspaces live
+ * on the device, preallocated per slot.
  *
  * sk_server_create: slots 1..8 concurrent batches, max_batch 1..4096.
  * sk_server_submit: queue one request; *ticket identifies it.  k must be a
  *   multiple of 8; pointers 16-byte aligned.
+ * sk_server_submit_scaled: queue one E4M3 request with block scales as for
+ *   sk_gemm_scaled (k a multiple of 16, scales 4-byte aligned).
  * sk_server_poll: *state 0 queued, 1 running, 2 done (then *latency_us is
  *   submission-to-completion and the ticket is retired; the return value is
  *   the request's status).
@@ -413,6 +421,9 @@ int sk_server_create(sk_server_t* out, sk_dtype ab_type, sk_dtype c_type, int ma
                      int64_t hbm_budget_bytes);
 int sk_server_submit(sk_server_t server, int64_t m, int64_t n, int64_t k, const void* A,
                      const void* B, void* C, float alpha, float beta, uint64_t* ticket);
+int sk_server_submit_scaled(sk_server_t server, int64_t m, int64_t n, int64_t k, const void* A,
+                            const void* B, const float* scale_a, const float* scale_b, void* C,
+                            float alpha, float beta, uint64_t* ticket);
 int sk_server_poll(sk_server_t server, uint64_t ticket, int* state, double* latency_us);
 int sk_server_wait(sk_server_t server, uint64_t ticket, double* latency_us);
 int sk_server_stats(sk_server_t server, int64_t* stats);

@@ -254,7 +254,9 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   // all CTAs become resident; the bounded waits turn anything else into an
   // error status.
   const bool cooperative = split && s.cluster_m == 1;
-  if (f8) return cuda_status(sk::launch_f8(p->c_type, p->tm_a, p->tm_b, p->tm_c, a, cooperative, stream));
+  if (f8)
+    return cuda_status(
+        sk::launch_f8(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, a, cooperative, stream));
   const CUtensorMap& ta3 = use3d ? p->tm_a3 : p->tm_a;
   const CUtensorMap& tb3 = use3d ? p->tm_b3 : p->tm_b;
   cudaError_t e = s.tile_n == 256
@@ -322,7 +324,10 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
   p->swap = c_layout == SK_COL_MAJOR;
   p->device = dev;
   p->num_sms = sms;
-  if (a_type == SK_E4M3) {  // 128 x 128 x 128 single-CTA tiles
+  if (a_type == SK_E4M3) {
+    // 128 x 128 x 128 tiles on single CTAs: a pair's per-k-block buffer
+    // hand-off crosses SMs and was measured 2.4x slower (SK_ATTR_CLUSTER_M 2
+    // still selects it)
     p->tile_n_req = 128;
     p->cluster_req = 1;
   }
@@ -463,7 +468,6 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
       return SK_OK;
     case SK_ATTR_CLUSTER_M: {
       if (v != 0 && v != 1 && v != 2) return SK_ERR_UNSUPPORTED;
-      if (p->a_type == SK_E4M3) return v == 0 || v == 1 ? SK_OK : SK_ERR_UNSUPPORTED;
       const int old = p->cluster_req;
       p->cluster_req = static_cast<int>(v);
       int st = replan(p);
@@ -706,8 +710,8 @@ struct sk_grouped_s {
   int mode_req = SK_MODE_AUTO, tile_n_req = 0, grid_req = 0;
   int device = 0, num_sms = 0;
   sk::GroupPlan plan;
-  // device
-  sk::GroupSeg* d_segs = nullptr;
+  // device: the walk table and per-CTA start problems
+  sk::GroupWalk* d_walk = nullptr;
   int32_t* d_start = nullptr;
   sk::GroupProblem* d_probs = nullptr;
   char* ws = nullptr;
@@ -733,13 +737,13 @@ struct sk_grouped_s {
 namespace {
 
 void grouped_free_schedule(sk_grouped_s* g) {
-  if (g->d_segs) cudaFree(g->d_segs);
+  if (g->d_walk) cudaFree(g->d_walk);
   if (g->d_start) cudaFree(g->d_start);
-  g->d_segs = nullptr;
+  g->d_walk = nullptr;
   g->d_start = nullptr;
 }
 
-// Plan the group and upload its segment records; grow the workspace if the
+// Plan the group and upload its walk table; grow the workspace if the
 // schedule splits tiles.  Any cached problem table is re-encoded next launch
 // (the tile width sets the tensor-map boxes).
 int grouped_replan(sk_grouped_s* g) {
@@ -766,20 +770,19 @@ int grouped_replan(sk_grouped_s* g) {
     g->ws_bytes = static_cast<size_t>(gp.workspace_bytes);
   }
   grouped_free_schedule(g);
-  void *segs = nullptr, *start = nullptr;
-  const size_t seg_bytes = std::max<size_t>(1, gp.segs.size()) * sizeof(sk::GroupSeg);
-  cudaError_t e = cudaMalloc(&segs, seg_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&start, gp.start.size() * sizeof(int32_t));
-  if (e == cudaSuccess && !gp.segs.empty())
-    e = cudaMemcpy(segs, gp.segs.data(), gp.segs.size() * sizeof(sk::GroupSeg), cudaMemcpyHostToDevice);
+  void *walk = nullptr, *start = nullptr;
+  cudaError_t e = cudaMalloc(&walk, gp.walk.size() * sizeof(sk::GroupWalk));
+  if (e == cudaSuccess) e = cudaMalloc(&start, gp.gstart.size() * sizeof(int32_t));
   if (e == cudaSuccess)
-    e = cudaMemcpy(start, gp.start.data(), gp.start.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(walk, gp.walk.data(), gp.walk.size() * sizeof(sk::GroupWalk), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(start, gp.gstart.data(), gp.gstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
-    if (segs) cudaFree(segs);
+    if (walk) cudaFree(walk);
     if (start) cudaFree(start);
     return cuda_status(e);
   }
-  g->d_segs = static_cast<sk::GroupSeg*>(segs);
+  g->d_walk = static_cast<sk::GroupWalk*>(walk);
   g->d_start = static_cast<int32_t*>(start);
   g->plan = std::move(gp);
   g->table_valid = false;
@@ -876,7 +879,7 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
     g->table_valid = true;
   }
   sk::SkArgs a{};
-  a.grid = gp.grid;
+  sk::set_group_walk_args(a, gp);
   a.idesc = make_idesc(g->ab_type, gp.tile_n, 1);
   a.c_tma = 0;
   const bool split = gp.workspace_bytes > 0;
@@ -889,8 +892,8 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
   a.debug_skip_signal = -1;
   a.timeout_ns = g->timeout_ns;
   a.pdl = g->pdl ? 1 : 0;
-  a.gsegs = g->d_segs;
-  a.gseg_start = g->d_start;
+  a.gwalk = g->d_walk;
+  a.gstart = g->d_start;
   a.gprobs = g->d_probs;
   const CUtensorMap& any = g->h_probs[0].tmA;
   cudaError_t e = f8                ? sk::launch_grouped_f8(g->c_type, any, a, split, stream)
@@ -1138,14 +1141,14 @@ int plan_autotune(sk_plan_t p, const void* A, const void* B, const float* scale_
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
   const int saved[4] = {p->tile_n_req, p->cluster_req, p->mode_req, p->grid_req};
   const int64_t km = p->swap ? p->n : p->m, kn = p->swap ? p->m : p->n;
-  const bool f8 = p->a_type == SK_E4M3;  // one tile shape: 128 x 128 single CTAs
+  const bool f8 = p->a_type == SK_E4M3;  // BLK_N = 128 only
   const int tns[2] = {128, 256}, cms[2] = {1, 2}, modes[3] = {SK_MODE_DP, SK_MODE_HYBRID, SK_MODE_SK};
   double best = -1.0;
   int bt = saved[0], bc = saved[1], bm = saved[2];
   for (int tn : tns) {
     if (tn == 256 && (kn <= 128 || f8)) continue;
     for (int cm : cms) {
-      if (cm == 2 && (km <= sk::kTileM || f8)) continue;
+      if (cm == 2 && km <= sk::kTileM) continue;
       for (int md : modes) {
         p->tile_n_req = tn;
         p->cluster_req = cm;

@@ -9,16 +9,23 @@
 
 namespace sk {
 
-template <typename TC, bool GROUPED>
+template <int CM, typename TC, bool GROUPED>
 static cudaError_t launch_f8_one(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
                                  const SkArgs& args, bool cooperative, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>(args.grid));
+  cfg.gridDim = dim3(static_cast<unsigned>(args.grid * CM));
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = Cfg<128, 1, true>::kSmemBytes;
+  cfg.dynamicSmemBytes = Cfg<128, CM, true>::kSmemBytes;
   cfg.stream = stream;
-  cudaLaunchAttribute attr[2];
+  cudaLaunchAttribute attr[3];
   unsigned na = 0;
+  if (CM > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = CM;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
   if (cooperative) {
     attr[na].id = cudaLaunchAttributeCooperative;
     attr[na].val.cooperative = 1;
@@ -31,45 +38,50 @@ static cudaError_t launch_f8_one(const CUtensorMap& ta, const CUtensorMap& tb, c
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, 1, TC, GROUPED, true>, ta, tb, tc, ta, tb,
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, CM, TC, GROUPED, true>, ta, tb, tc, ta, tb,
                             args);
 }
 
-template <bool GROUPED>
+template <int CM, bool GROUPED>
 static cudaError_t launch_f8_c(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
                                const CUtensorMap& tc, const SkArgs& args, bool cooperative,
                                cudaStream_t stream) {
   switch (c_dtype) {
     case SK_F32:
-      return launch_f8_one<float, GROUPED>(ta, tb, tc, args, cooperative, stream);
+      return launch_f8_one<CM, float, GROUPED>(ta, tb, tc, args, cooperative, stream);
     case SK_BF16:
-      return launch_f8_one<__nv_bfloat16, GROUPED>(ta, tb, tc, args, cooperative, stream);
+      return launch_f8_one<CM, __nv_bfloat16, GROUPED>(ta, tb, tc, args, cooperative, stream);
     case SK_F16:
-      return launch_f8_one<__half, GROUPED>(ta, tb, tc, args, cooperative, stream);
+      return launch_f8_one<CM, __half, GROUPED>(ta, tb, tc, args, cooperative, stream);
     default:
       return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_f8(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
+cudaError_t launch_f8(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
                       const CUtensorMap& tc, const SkArgs& args, bool cooperative,
                       cudaStream_t stream) {
-  return launch_f8_c<false>(c_dtype, ta, tb, tc, args, cooperative, stream);
+  return cluster_m == 2 ? launch_f8_c<2, false>(c_dtype, ta, tb, tc, args, cooperative, stream)
+                        : launch_f8_c<1, false>(c_dtype, ta, tb, tc, args, cooperative, stream);
 }
 
 cudaError_t launch_grouped_f8(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
                               bool cooperative, cudaStream_t stream) {
-  return launch_f8_c<true>(c_dtype, tm, tm, tm, args, cooperative, stream);
+  return launch_f8_c<1, true>(c_dtype, tm, tm, tm, args, cooperative, stream);
 }
 
 template <typename TC>
 static cudaError_t set_smem_f8() {
-  constexpr int bytes = Cfg<128, 1, true>::kSmemBytes;
   cudaError_t e = cudaFuncSetAttribute(sk_gemm_kernel<128, 1, TC, false, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg<128, 1, true>::kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sk_gemm_kernel<128, 2, TC, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128, 2, true>::kSmemBytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sk_gemm_kernel<128, 1, TC, true, true>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Cfg<128, 1, true>::kSmemBytes);
 }
 
 cudaError_t prepare_f8(size_t* smem_bytes) {

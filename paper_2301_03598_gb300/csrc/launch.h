@@ -19,15 +19,16 @@ cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, cons
 cudaError_t launch_bn256(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
                          const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
                          const SkArgs& args, bool cooperative, cudaStream_t stream);
-// A grouped launch (args.grid single CTAs walking args.gsegs); tm is any valid
+// A grouped launch (args.grid single CTAs walking args.gwalk); tm is any valid
 // tensor map (the kernel's tensor-map parameters are unused there).
 cudaError_t launch_grouped_bn128(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
                                  bool cooperative, cudaStream_t stream);
 cudaError_t launch_grouped_bn256(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
                                  bool cooperative, cudaStream_t stream);
 // E4M3 operands with per-128 x 128-block scales (args.scale_a / scale_b):
-// 128 x 128 single-CTA tiles, 2-D maps of 128-byte k-blocks.
-cudaError_t launch_f8(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
+// BLK_N = 128, single CTAs or CTA pairs (cluster_m 2, 256 x 128 tiles), 2-D
+// maps of 128-byte k-blocks.
+cudaError_t launch_f8(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
                       const CUtensorMap& tc, const SkArgs& args, bool cooperative,
                       cudaStream_t stream);
 cudaError_t launch_grouped_f8(int c_dtype, const CUtensorMap& tm, const SkArgs& args,

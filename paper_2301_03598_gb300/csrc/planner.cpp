@@ -387,6 +387,54 @@ bool build_group(const std::vector<GroupShape>& ps, int64_t g, int64_t sk_tiles,
   return true;
 }
 
+// The device walk table of a schedule (Stream-K over the first sk_tiles
+// global tiles, data-parallel round-robin after them, over g CTAs): one
+// entry per problem plus a sentinel with the totals, and per CTA the
+// problems holding its first Stream-K iteration and first data-parallel tile.
+void build_walk(const std::vector<GroupShape>& ps, int64_t g, int64_t sk_tiles, GroupPlan* out) {
+  const size_t P = ps.size();
+  out->walk.assign(P + 1, GroupWalk{});
+  int64_t t = 0, it = 0;
+  for (size_t i = 0; i <= P; ++i) {
+    GroupWalk& w = out->walk[i];
+    w.tile_off = static_cast<int32_t>(t);
+    w.iter_off = static_cast<int32_t>(it);
+    if (i == P) break;
+    const GroupShape& p = ps[i];
+    const int64_t rows_last = p.tiles_m - (cdiv(p.tiles_m, p.group_m) - 1) * p.group_m;
+    w.tiles_m = static_cast<int32_t>(p.tiles_m);
+    w.tiles_n = static_cast<int32_t>(p.tiles_n);
+    w.ipt = static_cast<int32_t>(p.ipt);
+    w.group_m = static_cast<int32_t>(p.group_m);
+    w.kfull64 = static_cast<int32_t>(p.kfull64);
+    w.div_ipt = make_fastdiv(static_cast<uint32_t>(p.ipt));
+    w.div_band = make_fastdiv(static_cast<uint32_t>(p.group_m * p.tiles_n));
+    w.div_rows = make_fastdiv(static_cast<uint32_t>(p.group_m));
+    w.div_rows_last = make_fastdiv(static_cast<uint32_t>(std::max<int64_t>(1, rows_last)));
+    t += p.tiles;
+    it += p.tiles * p.ipt;
+  }
+  // global iteration at which global tile sk_tiles starts
+  size_t pi = 0;
+  while (pi < P && out->walk[pi + 1].tile_off <= sk_tiles) ++pi;
+  const int64_t sk_iters =
+      pi < P ? out->walk[pi].iter_off + (sk_tiles - out->walk[pi].tile_off) * ps[pi].ipt : it;
+  out->gstart.assign(static_cast<size_t>(2 * g), 0);
+  const int64_t q = sk_iters / g, r = sk_iters % g;
+  size_t a = 0, b = 0;
+  for (int64_t x = 0; x < g; ++x) {
+    const int64_t first = x * q + std::min(x, r);
+    while (a + 1 < P && out->walk[a + 1].iter_off <= first) ++a;
+    const int64_t j = sk_tiles + x;
+    while (b + 1 < P && out->walk[b + 1].tile_off <= j) ++b;
+    out->gstart[static_cast<size_t>(2 * x)] = static_cast<int32_t>(a);
+    out->gstart[static_cast<size_t>(2 * x + 1)] = static_cast<int32_t>(b);
+  }
+  out->tiles = t;
+  out->sk_tiles = sk_tiles;
+  out->sk_iters = sk_iters;
+}
+
 // HBM bandwidth the model assumes for operand traffic, bytes per microsecond
 // (the measured copy bandwidth of this GB300, rounded down).
 constexpr double kHbmBytesPerUs = 6.5e6;
@@ -438,6 +486,59 @@ double predict_group(const GroupPlan& gp, const double c[5]) {
 }
 
 }  // namespace
+
+void set_group_walk_args(SkArgs& a, const GroupPlan& gp) {
+  a.grid = gp.grid;
+  a.tiles = static_cast<int32_t>(gp.tiles);
+  a.sk_tiles = static_cast<int32_t>(gp.sk_tiles);
+  a.sk_q = static_cast<int32_t>(gp.sk_iters / gp.grid);
+  a.sk_r = static_cast<int32_t>(gp.sk_iters % gp.grid);
+  a.div_q1 = make_fastdiv(static_cast<uint32_t>(a.sk_q + 1));
+  a.div_q = make_fastdiv(static_cast<uint32_t>(std::max(1, a.sk_q)));
+  a.fast_iters = 1;  // the planner keeps the concatenated space below 2^31
+}
+
+int describe_grouped_dp(int count, const int64_t* m, const int64_t* n, const int64_t* k,
+                        int tile_n, int num_sms, GroupPlan* out) {
+  if (out == nullptr || count < 1 || m == nullptr || n == nullptr || k == nullptr || num_sms < 1 ||
+      num_sms > kMaxGrid)
+    return SK_ERR_INVALID;
+  if (tile_n != 0 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  int64_t max_n = 0;
+  for (int i = 0; i < count; ++i) {
+    if (m[i] < 1 || n[i] < 1 || k[i] < 1 || m[i] > INT32_MAX || n[i] > INT32_MAX || k[i] > INT32_MAX)
+      return SK_ERR_INVALID;
+    max_n = std::max(max_n, n[i]);
+  }
+  const int bn = tile_n ? tile_n : (max_n > 128 ? 256 : 128);
+  const int bk = tile_k_for(bn);
+  std::vector<GroupShape> ps(static_cast<size_t>(count));
+  int64_t t = 0, total_iters = 0;
+  for (int j = 0; j < count; ++j) {
+    GroupShape& p = ps[static_cast<size_t>(j)];
+    p.tiles_m = cdiv(m[j], kTileM);
+    p.tiles_n = cdiv(n[j], bn);
+    p.tiles = p.tiles_m * p.tiles_n;
+    p.ipt = cdiv(k[j], bk);
+    p.group_m = std::min<int64_t>(p.tiles_m, 16);
+    p.kfull64 = bk == 128 && k[j] / 64 >= 2 ? k[j] / 64 : 0;
+    t += p.tiles;
+    total_iters += p.tiles * p.ipt;
+  }
+  if (t > INT32_MAX || total_iters > INT32_MAX) return SK_ERR_INVALID;
+  const int64_t g = std::min<int64_t>(num_sms, t);
+  out->segs.clear();
+  out->start.clear();
+  build_walk(ps, g, 0, out);
+  out->mode = SK_MODE_DP;
+  out->tile_n = bn;
+  out->tile_k = bk;
+  out->grid = static_cast<int32_t>(g);
+  out->split = false;
+  out->workspace_bytes = 0;
+  out->max_segments = static_cast<int>(cdiv(t, g));
+  return SK_OK;
+}
 
 int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_t* k, int mode,
                      int tile_n, int grid, int num_sms, GroupPlan* out) {
@@ -498,6 +599,7 @@ int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_
     for (const Cand& cd : cands) {
       GroupPlan gp;
       if (!build_group(ps, std::max<int64_t>(cd.g, 1), cd.sk_tiles, &gp)) return SK_ERR_INVALID;
+      build_walk(ps, std::max<int64_t>(cd.g, 1), cd.sk_tiles, &gp);
       gp.grid = static_cast<int32_t>(std::max<int64_t>(cd.g, 1));
       const double us = std::max(predict_group(gp, c),
                                  c[0] + group_dram_bytes(ps, mv, nv, kv, gp, bn) / kHbmBytesPerUs);

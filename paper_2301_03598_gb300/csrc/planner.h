@@ -34,8 +34,19 @@ struct GroupPlan {
   bool split = false;
   std::vector<GroupSeg> segs;
   std::vector<int32_t> start;
+  // what the device walks: count + 1 table entries, 2 * grid start problems
+  std::vector<GroupWalk> walk;
+  std::vector<int32_t> gstart;
 };
 int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_t* k, int mode,
                      int tile_n, int grid, int num_sms, GroupPlan* out);
+// The launch-wide walk fields of SkArgs for a grouped schedule: grid, tile
+// count, Stream-K region and its within-one split, and their divisors.
+void set_group_walk_args(SkArgs& a, const GroupPlan& gp);
+// Data-parallel waves over the group (one CTA per tile, at most num_sms CTAs)
+// without the segment records: the walk table only, in O(count + grid).
+// tile_n 0 picks 256 when some n > 128.
+int describe_grouped_dp(int count, const int64_t* m, const int64_t* n, const int64_t* k,
+                        int tile_n, int num_sms, GroupPlan* out);
 
 }  // namespace sk

@@ -379,6 +379,63 @@ __device__ __forceinline__ bool mma_f8_probe(uint32_t d_tmem, uint64_t a_desc, u
   return ready != 0;
 }
 
+// The last kind::f8f6f4 MMA of a k-block plus probes of two barriers (the
+// next stage's full barrier and the next product buffer's empty barrier):
+// bit 0 / bit 1 of the result say whether each probed phase had completed.
+__device__ __forceinline__ uint32_t mma_f8_probe2(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                                  uint32_t idesc, uint32_t accumulate, uint32_t bar0,
+                                                  uint32_t parity0, uint32_t bar1, uint32_t parity1) {
+  uint32_t ready;
+  asm volatile(
+      "{\n\t.reg .pred p, q0, q1;\n\t.reg .u32 r0, r1;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q0, [%5], %6;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q1, [%7], %8;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%1], %2, %3, %9, p;\n\t"
+      "selp.u32 r0, 1, 0, q0;\n\t"
+      "selp.u32 r1, 2, 0, q1;\n\t"
+      "or.b32 %0, r0, r1;\n\t}"
+      : "=r"(ready)
+      : "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(accumulate), "r"(bar0), "r"(parity0),
+        "r"(bar1), "r"(parity1), "r"(idesc)
+      : "memory");
+  return ready;
+}
+
+// kind::f8f6f4 (E4M3) over a CTA pair, as mma_f16_pair.
+__device__ __forceinline__ void mma_f8_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// mma_f8_probe2 for a pair MMA.
+__device__ __forceinline__ uint32_t mma_f8_pair_probe2(uint32_t d_tmem, uint64_t a_desc,
+                                                       uint64_t b_desc, uint32_t idesc,
+                                                       uint32_t accumulate, uint32_t bar0,
+                                                       uint32_t parity0, uint32_t bar1,
+                                                       uint32_t parity1) {
+  uint32_t ready;
+  asm volatile(
+      "{\n\t.reg .pred p, q0, q1;\n\t.reg .u32 r0, r1;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q0, [%5], %6;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 q1, [%7], %8;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%1], %2, %3, %9, p;\n\t"
+      "selp.u32 r0, 1, 0, q0;\n\t"
+      "selp.u32 r1, 2, 0, q1;\n\t"
+      "or.b32 %0, r0, r1;\n\t}"
+      : "=r"(ready)
+      : "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(accumulate), "r"(bar0), "r"(parity0),
+        "r"(bar1), "r"(parity1), "r"(idesc)
+      : "memory");
+  return ready;
+}
+
 // The same for a pair MMA (cta_group::2).
 __device__ __forceinline__ bool mma_f16_pair_probe(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                                    uint32_t idesc, uint32_t accumulate, uint32_t bar,

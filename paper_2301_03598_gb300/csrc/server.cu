@@ -40,8 +40,11 @@ struct Request {
   const void* A;
   const void* B;
   void* C;
+  const float* scale_a;  // E4M3 requests: block scales; else null
+  const float* scale_b;
   float alpha, beta;
   int64_t bytes;
+  bool f8;
   Clock::time_point submitted;
 };
 
@@ -50,17 +53,16 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   // One device block and its pinned staging copy, uploaded with one copy per
-  // batch: the problem table, then the per-CTA segment starts, then the
-  // segment records.
+  // batch: the problem table, the walk table, the per-CTA start problems.
   char* d_block = nullptr;
   char* h_block = nullptr;
-  size_t off_start = 0, off_segs = 0;
+  size_t off_walk = 0, off_start = 0;
   sk::GroupProblem* d_probs = nullptr;
+  sk::GroupWalk* d_walk = nullptr;
   int32_t* d_start = nullptr;
-  sk::GroupSeg* d_segs = nullptr;
   sk::GroupProblem* h_probs = nullptr;
+  sk::GroupWalk* h_walk = nullptr;
   int32_t* h_start = nullptr;
-  sk::GroupSeg* h_segs = nullptr;
   int32_t* d_err = nullptr;
   char* ws = nullptr;
   int32_t* h_err = nullptr;
@@ -73,11 +75,14 @@ struct Slot {
 
 struct sk_server_s {
   int ab_type = 0, c_type = 0, max_batch = 1, num_sms = 0;
-  int64_t budget = 0, segs_cap = 0;
+  int64_t budget = 0;
   std::vector<Slot> slots;
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<Request> pending;
+  // queued requests by input type (0: the server's 16-bit type, 1: E4M3);
+  // a batch takes one type, the one whose oldest request is older
+  std::deque<Request> pending[2];
+  bool none_pending() const { return pending[0].empty() && pending[1].empty(); }
   // id -> (state, latency_us, status): state 0 queued, 1 running, 2 done
   struct Entry {
     int state = 0;
@@ -100,8 +105,8 @@ struct sk_server_s {
 
 namespace {
 
-constexpr int64_t kSegsPerProblem = 1024;  // record capacity per admitted problem
 constexpr size_t kPlanCacheEntries = 4096;
+constexpr int kModelledBatch = 4;  // batches up to this size get the full model
 constexpr int kIdleSpinUs = 200;  // idle worker: spin before sleeping
 
 void free_slot(Slot& s) {
@@ -115,23 +120,23 @@ void free_slot(Slot& s) {
   s = Slot();
 }
 
-cudaError_t alloc_slot(Slot& s, int max_batch, int64_t segs_cap, int num_sms) {
+cudaError_t alloc_slot(Slot& s, int max_batch, int num_sms) {
   cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
   const size_t ws = static_cast<size_t>(sk::kFlagBytes) + static_cast<size_t>(num_sms) * sk::kBlkM * 256 * 4;
   auto up = [](size_t v) { return (v + 127) / 128 * 128; };
-  s.off_start = up(static_cast<size_t>(max_batch) * sizeof(sk::GroupProblem));
-  s.off_segs = s.off_start + up(static_cast<size_t>(num_sms + 1) * sizeof(int32_t));
-  const size_t block = s.off_segs + static_cast<size_t>(segs_cap) * sizeof(sk::GroupSeg);
+  s.off_walk = up(static_cast<size_t>(max_batch) * sizeof(sk::GroupProblem));
+  s.off_start = s.off_walk + up(static_cast<size_t>(max_batch + 1) * sizeof(sk::GroupWalk));
+  const size_t block = s.off_start + static_cast<size_t>(2 * num_sms) * sizeof(int32_t);
   if (e == cudaSuccess) e = cudaMalloc(&s.d_block, block);
   if (e == cudaSuccess) e = cudaMallocHost(&s.h_block, block);
   if (e == cudaSuccess) {
     s.d_probs = reinterpret_cast<sk::GroupProblem*>(s.d_block);
+    s.d_walk = reinterpret_cast<sk::GroupWalk*>(s.d_block + s.off_walk);
     s.d_start = reinterpret_cast<int32_t*>(s.d_block + s.off_start);
-    s.d_segs = reinterpret_cast<sk::GroupSeg*>(s.d_block + s.off_segs);
     s.h_probs = reinterpret_cast<sk::GroupProblem*>(s.h_block);
+    s.h_walk = reinterpret_cast<sk::GroupWalk*>(s.h_block + s.off_walk);
     s.h_start = reinterpret_cast<int32_t*>(s.h_block + s.off_start);
-    s.h_segs = reinterpret_cast<sk::GroupSeg*>(s.h_block + s.off_segs);
   }
   if (e == cudaSuccess) e = cudaMalloc(&s.d_err, 4 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(s.d_err, 0, 4 * sizeof(int32_t));
@@ -147,46 +152,57 @@ cudaError_t alloc_slot(Slot& s, int max_batch, int64_t segs_cap, int num_sms) {
 // the server's immutable settings.
 int launch_slot(sk_server_s* sv, Slot& s) {
   const int count = static_cast<int>(s.reqs.size());
+  const bool f8 = s.reqs[0].f8;  // a batch holds one input type
+  const int ab_type = f8 ? SK_E4M3 : sv->ab_type;
   std::vector<int64_t> m(count), n(count), k(count);
   for (int i = 0; i < count; ++i) {
     m[i] = s.reqs[i].m;
     n[i] = s.reqs[i].n;
     k[i] = s.reqs[i].k;
   }
-  std::string key(3 * sizeof(int64_t) * static_cast<size_t>(count), '\0');
-  for (int i = 0; i < count; ++i) {
-    const int64_t v[3] = {m[i], n[i], k[i]};
-    std::memcpy(&key[3 * sizeof(int64_t) * static_cast<size_t>(i)], v, sizeof(v));
-  }
-  std::shared_ptr<const sk::GroupPlan> cached;
-  auto hit = sv->plan_cache.find(key);
-  if (hit != sv->plan_cache.end()) {
-    cached = hit->second;
+  // Small batches choose among every schedule (cached by composition); larger
+  // ones take data-parallel waves, planned in O(count + grid) with no records.
+  std::shared_ptr<const sk::GroupPlan> plan;
+  const int tile_n = f8 ? 128 : 0;
+  if (count <= kModelledBatch) {
+    std::string key(3 * sizeof(int64_t) * static_cast<size_t>(count) + 1, '\0');
+    key[0] = f8 ? 1 : 0;
+    for (int i = 0; i < count; ++i) {
+      const int64_t v[3] = {m[i], n[i], k[i]};
+      std::memcpy(&key[1 + 3 * sizeof(int64_t) * static_cast<size_t>(i)], v, sizeof(v));
+    }
+    auto hit = sv->plan_cache.find(key);
+    if (hit != sv->plan_cache.end()) {
+      plan = hit->second;
+    } else {
+      auto fresh = std::make_shared<sk::GroupPlan>();
+      const int st = sk::describe_grouped(count, m.data(), n.data(), k.data(), SK_MODE_AUTO,
+                                          tile_n, 0, sv->num_sms, fresh.get());
+      if (st != SK_OK) return st;
+      fresh->segs.clear();  // the device walks the table; records are not kept
+      fresh->start.clear();
+      if (sv->plan_cache.size() >= kPlanCacheEntries) sv->plan_cache.clear();
+      sv->plan_cache.emplace(std::move(key), fresh);
+      plan = std::move(fresh);
+    }
   } else {
-    // Small batches choose among every schedule; larger ones take
-    // data-parallel waves, which the model picks for them anyway and which
-    // cost the planner one candidate per tile width.
     auto fresh = std::make_shared<sk::GroupPlan>();
-    const int mode = count <= 4 ? SK_MODE_AUTO : SK_MODE_DP;
-    const int st = sk::describe_grouped(count, m.data(), n.data(), k.data(), mode, 0, 0,
-                                        sv->num_sms, fresh.get());
+    const int st = sk::describe_grouped_dp(count, m.data(), n.data(), k.data(), tile_n,
+                                           sv->num_sms, fresh.get());
     if (st != SK_OK) return st;
-    if (sv->plan_cache.size() >= kPlanCacheEntries) sv->plan_cache.clear();
-    sv->plan_cache.emplace(std::move(key), fresh);
-    cached = std::move(fresh);
+    plan = std::move(fresh);
   }
-  const sk::GroupPlan& gp = *cached;
+  const sk::GroupPlan& gp = *plan;
   int st = SK_OK;
-  if (static_cast<int64_t>(gp.segs.size()) > sv->segs_cap) return SK_ERR_NOMEM;
   for (int i = 0; i < count; ++i) {
     const Request& r = s.reqs[i];
     sk::GroupProblem& pr = s.h_probs[i];
     std::memset(static_cast<void*>(&pr), 0, sizeof(pr));
-    st = encode_operand(&pr.tmA, r.A, sv->ab_type, r.m, r.k, r.k, sk::kBlkM);
-    if (st == SK_OK) st = encode_operand(&pr.tmB, r.B, sv->ab_type, r.n, r.k, r.k, gp.tile_n);
-    const bool use3d = gp.tile_k == 2 * sk::kBlkK && r.k / sk::kBlkK >= 2;
-    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmA3, r.A, sv->ab_type, r.m, r.k, r.k, sk::kBlkM);
-    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmB3, r.B, sv->ab_type, r.n, r.k, r.k, gp.tile_n);
+    st = encode_operand(&pr.tmA, r.A, ab_type, r.m, r.k, r.k, sk::kBlkM);
+    if (st == SK_OK) st = encode_operand(&pr.tmB, r.B, ab_type, r.n, r.k, r.k, gp.tile_n);
+    const bool use3d = !f8 && gp.tile_k == 2 * sk::kBlkK && r.k / sk::kBlkK >= 2;
+    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmA3, r.A, ab_type, r.m, r.k, r.k, sk::kBlkM);
+    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmB3, r.B, ab_type, r.n, r.k, r.k, gp.tile_n);
     if (st != SK_OK) return st;
     if (!use3d) {
       pr.tmA3 = pr.tmA;
@@ -202,16 +218,19 @@ int launch_slot(sk_server_s* sv, Slot& s) {
     pr.c_vec = (r.n * static_cast<int64_t>(dtype_size(sv->c_type))) % 16 == 0 ? 1 : 0;
     pr.alpha = r.alpha;
     pr.beta = r.beta;
+    pr.scale_a = r.scale_a;
+    pr.scale_b = r.scale_b;
+    pr.ld_scale = static_cast<int32_t>((r.k + 127) / 128);
   }
-  std::memcpy(s.h_segs, gp.segs.data(), gp.segs.size() * sizeof(sk::GroupSeg));
-  std::memcpy(s.h_start, gp.start.data(), gp.start.size() * sizeof(int32_t));
+  std::memcpy(s.h_walk, gp.walk.data(), gp.walk.size() * sizeof(sk::GroupWalk));
+  std::memcpy(s.h_start, gp.gstart.data(), gp.gstart.size() * sizeof(int32_t));
   cudaError_t e = cudaMemcpyAsync(s.d_block, s.h_block,
-                                  s.off_segs + gp.segs.size() * sizeof(sk::GroupSeg),
+                                  s.off_start + gp.gstart.size() * sizeof(int32_t),
                                   cudaMemcpyHostToDevice, s.stream);
   if (e != cudaSuccess) return cuda_status(e);
   sk::SkArgs a{};
-  a.grid = gp.grid;
-  a.idesc = make_idesc(sv->ab_type, gp.tile_n, 1);
+  sk::set_group_walk_args(a, gp);
+  a.idesc = make_idesc(ab_type, gp.tile_n, 1);
   const bool split = gp.workspace_bytes > 0;
   a.flags = split ? reinterpret_cast<uint32_t*>(s.ws) : nullptr;
   a.partials = split ? reinterpret_cast<float*>(s.ws + sk::kFlagBytes) : nullptr;
@@ -221,11 +240,13 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   a.debug_skip_signal = -1;
   a.timeout_ns = kDefaultTimeoutNs;
   a.pdl = 0;
-  a.gsegs = s.d_segs;
-  a.gseg_start = s.d_start;
+  a.gwalk = s.d_walk;
+  a.gstart = s.d_start;
   a.gprobs = s.d_probs;
-  e = gp.tile_n == 256 ? sk::launch_grouped_bn256(sv->c_type, s.h_probs[0].tmA, a, split, s.stream)
-                       : sk::launch_grouped_bn128(sv->c_type, s.h_probs[0].tmA, a, split, s.stream);
+  const CUtensorMap& any = s.h_probs[0].tmA;
+  e = f8                ? sk::launch_grouped_f8(sv->c_type, any, a, split, s.stream)
+      : gp.tile_n == 256 ? sk::launch_grouped_bn256(sv->c_type, any, a, split, s.stream)
+                         : sk::launch_grouped_bn128(sv->c_type, any, a, split, s.stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_err, s.d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s.stream);
   if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
   if (e != cudaSuccess) return cuda_status(e);
@@ -269,7 +290,7 @@ void worker_loop(sk_server_s* sv) {
       finish(sv, s, status);
       sv->done_cv.notify_all();
     }
-    if (sv->stop && sv->pending.empty() && !any_busy) break;
+    if (sv->stop && sv->none_pending() && !any_busy) break;
     // admit a batch into a free slot
     Slot* free_slot_p = nullptr;
     for (Slot& s : sv->slots)
@@ -277,16 +298,20 @@ void worker_loop(sk_server_s* sv) {
         free_slot_p = &s;
         break;
       }
-    if (free_slot_p != nullptr && !sv->pending.empty()) {
+    if (free_slot_p != nullptr && !sv->none_pending()) {
       Slot& s = *free_slot_p;
-      while (!sv->pending.empty() && static_cast<int>(s.reqs.size()) < sv->max_batch) {
-        const Request& r = sv->pending.front();
+      const int t = sv->pending[0].empty()   ? 1
+                    : sv->pending[1].empty() ? 0
+                    : (sv->pending[1].front().id < sv->pending[0].front().id ? 1 : 0);
+      std::deque<Request>& q = sv->pending[t];
+      while (!q.empty() && static_cast<int>(s.reqs.size()) < sv->max_batch) {
+        const Request& r = q.front();
         const bool nothing_else = s.reqs.empty() && sv->inflight_bytes == 0;
         if (!nothing_else && sv->inflight_bytes + s.bytes + r.bytes > sv->budget) break;
         s.bytes += r.bytes;
         s.reqs.push_back(r);
         sv->entries[r.id].state = 1;
-        sv->pending.pop_front();
+        q.pop_front();
         sv->queued.fetch_sub(1, std::memory_order_relaxed);
       }
       if (!s.reqs.empty()) {
@@ -323,7 +348,7 @@ void worker_loop(sk_server_s* sv) {
     lk.lock();
     if (!any_busy)
       sv->cv.wait_for(lk, std::chrono::milliseconds(5),
-                      [&] { return sv->stop || !sv->pending.empty(); });
+                      [&] { return sv->stop || !sv->none_pending(); });
   }
 }
 
@@ -346,9 +371,10 @@ int sk_server_create(sk_server_t* out, sk_dtype ab_type, sk_dtype c_type, int ma
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return SK_ERR_CUDA;
   if (major != 10 || minor != 3) return SK_ERR_DEVICE;
-  size_t s1 = 0, s2 = 0;
+  size_t s1 = 0, s2 = 0, s3 = 0;
   cudaError_t e = sk::prepare_bn128(&s1);
   if (e == cudaSuccess) e = sk::prepare_bn256(&s2);
+  if (e == cudaSuccess) e = sk::prepare_f8(&s3);
   if (e != cudaSuccess) return cuda_status(e);
   sk_server_s* sv = new (std::nothrow) sk_server_s();
   if (sv == nullptr) return SK_ERR_NOMEM;
@@ -358,10 +384,9 @@ int sk_server_create(sk_server_t* out, sk_dtype ab_type, sk_dtype c_type, int ma
   sv->num_sms = sms;
   sv->budget = hbm_budget_bytes;
   sv->device = dev;
-  sv->segs_cap = std::max<int64_t>(static_cast<int64_t>(max_batch) * kSegsPerProblem, 65536);
   sv->slots.resize(static_cast<size_t>(slots));
   for (Slot& s : sv->slots) {
-    e = alloc_slot(s, max_batch, sv->segs_cap, sms);
+    e = alloc_slot(s, max_batch, sms);
     if (e != cudaSuccess) {
       for (Slot& t : sv->slots) free_slot(t);
       delete sv;
@@ -373,12 +398,21 @@ int sk_server_create(sk_server_t* out, sk_dtype ab_type, sk_dtype c_type, int ma
   return SK_OK;
 }
 
-int sk_server_submit(sk_server_t sv, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
-                     void* C, float alpha, float beta, uint64_t* ticket) {
-  if (sv == nullptr || ticket == nullptr || m < 1 || n < 1 || k < 1 || k % 8 != 0 ||
+}  // extern "C"
+
+namespace {
+
+int submit(sk_server_t sv, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+           const float* scale_a, const float* scale_b, void* C, float alpha, float beta,
+           uint64_t* ticket) {
+  const bool f8 = scale_a != nullptr;
+  if (sv == nullptr || ticket == nullptr || m < 1 || n < 1 || k < 1 || k % (f8 ? 16 : 8) != 0 ||
       m > INT32_MAX || n > INT32_MAX || k > INT32_MAX || A == nullptr || B == nullptr ||
       C == nullptr || (reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u) ||
       (reinterpret_cast<uintptr_t>(C) & 15u))
+    return SK_ERR_INVALID;
+  if (f8 && (scale_b == nullptr || (reinterpret_cast<uintptr_t>(scale_a) & 3u) ||
+             (reinterpret_cast<uintptr_t>(scale_b) & 3u)))
     return SK_ERR_INVALID;
   Request r{};
   r.m = m;
@@ -387,22 +421,42 @@ int sk_server_submit(sk_server_t sv, int64_t m, int64_t n, int64_t k, const void
   r.A = A;
   r.B = B;
   r.C = C;
+  r.scale_a = scale_a;
+  r.scale_b = scale_b;
+  r.f8 = f8;
   r.alpha = alpha;
   r.beta = beta;
-  r.bytes = 2 * (m * k + n * k) + m * n * static_cast<int64_t>(dtype_size(sv->c_type));
+  const int64_t in_bytes = f8 ? 1 : 2;
+  r.bytes = in_bytes * (m * k + n * k) + m * n * static_cast<int64_t>(dtype_size(sv->c_type));
   r.submitted = Clock::now();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stop) return SK_ERR_INVALID;
     r.id = sv->next_id++;
     sv->entries[r.id] = sk_server_s::Entry{};
-    sv->pending.push_back(r);
+    sv->pending[f8 ? 1 : 0].push_back(r);
     ++sv->submitted;
     sv->queued.fetch_add(1, std::memory_order_relaxed);
   }
   sv->cv.notify_one();
   *ticket = r.id;
   return SK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sk_server_submit(sk_server_t sv, int64_t m, int64_t n, int64_t k, const void* A, const void* B,
+                     void* C, float alpha, float beta, uint64_t* ticket) {
+  return submit(sv, m, n, k, A, B, nullptr, nullptr, C, alpha, beta, ticket);
+}
+
+int sk_server_submit_scaled(sk_server_t sv, int64_t m, int64_t n, int64_t k, const void* A,
+                            const void* B, const float* scale_a, const float* scale_b, void* C,
+                            float alpha, float beta, uint64_t* ticket) {
+  if (scale_a == nullptr || scale_b == nullptr) return SK_ERR_INVALID;
+  return submit(sv, m, n, k, A, B, scale_a, scale_b, C, alpha, beta, ticket);
 }
 
 int sk_server_poll(sk_server_t sv, uint64_t ticket, int* state, double* latency_us) {
@@ -441,7 +495,8 @@ int sk_server_stats(sk_server_t sv, int64_t* stats) {
   if (sv == nullptr || stats == nullptr) return SK_ERR_INVALID;
   std::lock_guard<std::mutex> lk(sv->mu);
   const int64_t v[6] = {sv->submitted, sv->completed, sv->batches, sv->max_batch_seen,
-                        sv->problems_launched, static_cast<int64_t>(sv->pending.size())};
+                        sv->problems_launched,
+                        static_cast<int64_t>(sv->pending[0].size() + sv->pending[1].size())};
   for (int i = 0; i < 6; ++i) stats[i] = v[i];
   return SK_OK;
 }

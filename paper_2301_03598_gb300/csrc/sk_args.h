@@ -73,6 +73,24 @@ struct alignas(16) GroupSeg {
 };
 static_assert(sizeof(GroupSeg) == 32, "segment record size");
 
+// The walk of a grouped launch over problem i (device table of count + 1
+// entries, the last a sentinel holding the totals): its first tile and first
+// MAC-loop iteration in the concatenated space, its tile grid and raster,
+// and the divisors the walk needs.  Each CTA derives its segments from this
+// table exactly as the single-GEMM walk does (Stream-K share, then
+// data-parallel tiles), advancing a problem cursor as it goes.
+struct alignas(16) GroupWalk {
+  int32_t tile_off;  // first global tile of the problem
+  int32_t iter_off;  // first global iteration
+  int32_t tiles_m, tiles_n;
+  int32_t ipt;       // iterations per tile
+  int32_t group_m;   // raster band height in tiles
+  int32_t kfull64;   // k-blocks of 64 entirely inside k
+  int32_t pad;
+  FastDiv div_ipt, div_band, div_rows, div_rows_last;
+};
+static_assert(sizeof(GroupWalk) == 64, "walk entry size");
+
 // Per-problem operands of a grouped launch (device memory, 128-byte aligned
 // for the tensor maps, which TMA reads in place).
 struct alignas(128) GroupProblem {
@@ -126,9 +144,12 @@ struct SkArgs {
   int32_t debug_skip_signal;  // CTA index that withholds its Signal (tests), -1 off
   uint64_t timeout_ns;
   int32_t pdl;  // launched with programmatic stream serialization (host side only)
-  // grouped launches: CTA x walks gsegs[gseg_start[x] .. gseg_start[x+1])
-  const GroupSeg* gsegs;
-  const int32_t* gseg_start;
+  // grouped launches: the walk table and, per CTA x, the problems holding
+  // its first Stream-K iteration (gstart[2x]) and first data-parallel tile
+  // (gstart[2x + 1]); tiles / sk_tiles / sk_q / sk_r / grid describe the
+  // concatenated space
+  const GroupWalk* gwalk;
+  const int32_t* gstart;
   const GroupProblem* gprobs;
   // E4M3 launches: FP32 scale of every 128 x 128 block of A (m x k) and of B
   // (n x k), row-major [ceil(rows / 128)][ld_scale], ld_scale = ceil(k / 128)

@@ -73,7 +73,7 @@ struct Cfg {
   static constexpr int kSmemBytes = kBarOffset + 256 + 1024;  // + barriers, + 1 KiB alignment
   static_assert(kNumBars * 8 + 8 <= 256, "barrier area");
   static_assert(kSmemBytes <= 232448, "shared memory per CTA");
-  static_assert(!F8 || (BN == 128 && CM == 1), "F8 tiles are 128 x 128 single-CTA tiles");
+  static_assert(!F8 || BN == 128, "F8 tiles are 128 (or 256 for a pair) x 128");
   static_assert(kTmemCols <= 512, "TMEM columns");
 };
 
@@ -216,37 +216,77 @@ struct Seg {
   int problem, tile, tm, tn, kb0, kb1, role, peer_first, peer_last, kfull64;
 };
 
-// A CTA's segments: derived from its Stream-K share and data-parallel tiles
-// (single GEMM), or read from the records the host laid out (grouped).
+// Tile raster of one problem of a grouped launch (as tile_coords).
+__device__ __forceinline__ void group_tile_coords(const GroupWalk& w, int tile, int& tm, int& tn) {
+  const int band_tiles = w.group_m * w.tiles_n;
+  const int band = static_cast<int>(fast_div(static_cast<uint32_t>(tile), w.div_band));
+  const int first_m = band * w.group_m;
+  const int rows = min(w.group_m, w.tiles_m - first_m);
+  const int local = tile - band * band_tiles;
+  tn = static_cast<int>(
+      fast_div(static_cast<uint32_t>(local), rows == w.group_m ? w.div_rows : w.div_rows_last));
+  tm = first_m + local - tn * rows;
+}
+
+// A CTA's segments, derived from its Stream-K share and data-parallel tiles:
+// of one GEMM, or (grouped) of the problems' concatenated iteration space,
+// where a problem cursor follows the CTA through the walk table.
 template <bool GROUPED>
 struct SegCursor {
   Walker w;
-  int idx, end, x;
+  int x, pi_sk, pi_dp;
 
   __device__ __forceinline__ void init(const SkArgs& a, int unit) {
     x = unit;
+    w.init(a, unit);
     if constexpr (GROUPED) {
-      idx = a.gseg_start[unit];
-      end = a.gseg_start[unit + 1];
-    } else {
-      w.init(a, unit);
+      pi_sk = a.gstart[2 * unit];
+      pi_dp = a.gstart[2 * unit + 1];
     }
   }
 
   __device__ __forceinline__ bool next(const SkArgs& a, Seg& s) {
     if constexpr (GROUPED) {
-      if (idx >= end) return false;
-      const GroupSeg r = a.gsegs[idx++];
-      s.problem = r.problem;
-      s.tile = r.tile;
-      s.tm = r.tm;
-      s.tn = r.tn;
-      s.kb0 = r.kb0;
-      s.kb1 = r.kb1;
-      s.role = r.role;
-      s.peer_first = r.peer_first;
-      s.peer_last = r.peer_last;
-      s.kfull64 = r.kfull64;
+      const GroupWalk* gw = a.gwalk;
+      int lt;
+      if (w.it < w.it_end) {
+        // Algorithm 5 over the concatenated iterations
+        const int32_t it = static_cast<int32_t>(w.it);
+        while (gw[pi_sk + 1].iter_off <= it) ++pi_sk;
+        const GroupWalk p = gw[pi_sk];
+        const int32_t local = it - p.iter_off;
+        lt = static_cast<int>(fast_div(static_cast<uint32_t>(local), p.div_ipt));
+        const int32_t start = p.iter_off + lt * p.ipt;
+        const int32_t end = start + p.ipt;
+        s.problem = pi_sk;
+        s.kb0 = it - start;
+        s.kb1 = static_cast<int>(min(w.it_end, static_cast<int64_t>(end)) - start);
+        s.role = s.kb0 != 0 ? kRolePartial : (s.kb1 != p.ipt ? kRoleOwner : kRoleWhole);
+        s.peer_first = s.peer_last = -1;
+        if (s.role == kRoleOwner) {
+          s.peer_first = x + 1;
+          s.peer_last = cta_of_iter(a, end - 1);
+        }
+        s.kfull64 = p.kfull64;
+        group_tile_coords(p, lt, s.tm, s.tn);
+        w.it = end;
+      } else if (w.dp_tile < a.tiles) {
+        const int32_t j = w.dp_tile;
+        while (gw[pi_dp + 1].tile_off <= j) ++pi_dp;
+        const GroupWalk p = gw[pi_dp];
+        lt = j - p.tile_off;
+        s.problem = pi_dp;
+        s.kb0 = 0;
+        s.kb1 = p.ipt;
+        s.role = kRoleWhole;
+        s.peer_first = s.peer_last = -1;
+        s.kfull64 = p.kfull64;
+        group_tile_coords(p, lt, s.tm, s.tn);
+        w.dp_tile += a.grid;
+      } else {
+        return false;
+      }
+      s.tile = lt;
       return true;
     } else {
       int tile, kb0, kb1;
@@ -672,9 +712,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       if constexpr (F8) {
         // One product per k-block (one scale block) into the rotating
         // buffers; the epilogue warps scale and sum them.
+        // ready_acc: the current product buffer is known to be free (probed
+        // with the previous k-block's last MMA, like `ready` for the stage)
+        bool ready_acc = false;
         while (ok && cur.next(a, sg)) {
           for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
-            if (!wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty) ||
+            if ((!ready_acc && !wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) ||
                 (!ready && !wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull))) {
               ok = false;
               break;
@@ -686,26 +729,46 @@ __global__ void __launch_bounds__(kThreads, 1)
               next = 0;
               next_phase ^= 1u;
             }
+            int nacc = acc + 1;
+            uint32_t nacc_phase = acc_phase;
+            if (nacc == NB) {
+              nacc = 0;
+              nacc_phase ^= 1u;
+            }
             const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
             const uint64_t adesc = smem_desc_sw128(stage_a(stage));
             const uint64_t bdesc = smem_desc_sw128(stage_b(stage));
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               // 32 E4M3 elements (32 B) along K per MMA
-              if (kk == 3)
-                ready = mma_f8_probe(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
-                                     full_bar(next), next_phase);
-              else
+              if (kk == 3) {
+                uint32_t r;
+                if constexpr (kPair)
+                  r = mma_f8_pair_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
+                                         full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
+                else
+                  r = mma_f8_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
+                                    full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
+                ready = (r & 1u) != 0;
+                ready_acc = (r & 2u) != 0;
+              } else if constexpr (kPair) {
+                mma_f8_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
+              } else {
                 mma_f8(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
+              }
             }
-            mma_commit(empty_bar(stage));
-            mma_commit(accf_bar(acc));
+            // frees the stage and publishes the product (in both CTAs of a pair)
+            if constexpr (kPair) {
+              mma_commit_pair_multicast(empty_bar(stage), kPairMask);
+              mma_commit_pair_multicast(accf_bar(acc), kPairMask);
+            } else {
+              mma_commit(empty_bar(stage));
+              mma_commit(accf_bar(acc));
+            }
             stage = next;
             phase = next_phase;
-            if (++acc == NB) {
-              acc = 0;
-              acc_phase ^= 1u;
-            }
+            acc = nacc;
+            acc_phase = nacc_phase;
           }
         }
       }
@@ -876,7 +939,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // the product buffer is read: the MMA warp may overwrite it
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(acce_bar(acc));
+          if (lane == 0) release_acc(acc);
 #pragma unroll
           for (int mi = 0; mi < kMine; ++mi)
 #pragma unroll

@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
     L.sk_server_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i64]
     L.sk_server_submit.argtypes = [vp, i64, i64, i64, vp, vp, vp, f32, f32,
                                    ctypes.POINTER(ctypes.c_uint64)]
+    L.sk_server_submit_scaled.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp, f32, f32,
+                                          ctypes.POINTER(ctypes.c_uint64)]
     L.sk_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32), dblp]
     L.sk_server_wait.argtypes = [vp, ctypes.c_uint64, dblp]
     L.sk_server_stats.argtypes = [vp, i64p]
@@ -120,7 +122,7 @@ def lib() -> ctypes.CDLL:
                  "sk_grouped_get", "sk_grouped_schedule", "sk_grouped_destroy",
                  "sk_grouped_plan_describe", "sk_plan_autotune", "sk_grouped_autotune",
                  "sk_gemm_scaled", "sk_grouped_gemm_scaled", "sk_plan_autotune_scaled",
-                 "sk_grouped_autotune_scaled",
+                 "sk_grouped_autotune_scaled", "sk_server_submit_scaled",
                  "sk_server_create", "sk_server_submit", "sk_server_poll", "sk_server_wait",
                  "sk_server_stats", "sk_server_destroy"):
         getattr(L, name).restype = i32
@@ -529,6 +531,17 @@ class Server:
         t = ctypes.c_uint64(0)
         _check(lib().sk_server_submit(self.handle, m, n, k, _ptr(A), _ptr(B), _ptr(C), alpha, beta,
                                       ctypes.byref(t)), "sk_server_submit")
+        return t.value
+
+    def submit_scaled(self, A, B, scale_a, scale_b, C, alpha: float = 1.0,
+                      beta: float = 0.0) -> int:
+        """Queue a block-scaled E4M3 request (as sk_gemm_scaled)."""
+        m, k = A.shape
+        n = B.shape[0]
+        t = ctypes.c_uint64(0)
+        _check(lib().sk_server_submit_scaled(self.handle, m, n, k, _ptr(A), _ptr(B),
+                                             _ptr(scale_a), _ptr(scale_b), _ptr(C), alpha, beta,
+                                             ctypes.byref(t)), "sk_server_submit_scaled")
         return t.value
 
     def poll(self, ticket: int):

@@ -75,16 +75,29 @@ SHAPES = [(384, 384, 4096), (300, 260, 1008), (129, 1000, 144), (16, 128, 16), (
 @pytest.mark.parametrize("shape", SHAPES)
 def test_f8_matches_oracle(shape, mode):
     p = F8Problem(*shape, seed=3)
-    outs, info = p.run(1.0, 0.0, mode)
+    outs, info = p.run(1.0, 0.0, mode, {"cluster_m": 1})
     assert info["tile_n"] == 128 and info["tile_k"] == 128 and info["cluster_m"] == 1
     p.check(outs[0], 1.0, 0.0, f"e4m3 {shape} {mode}")
+
+
+@pytest.mark.parametrize("mode,grid", [("dp", 0), ("sk", 0), ("sk", 37), ("hybrid", 0)])
+@pytest.mark.parametrize("shape", [(1000, 520, 2048), (384, 384, 4096), (129, 1000, 144)])
+def test_f8_cta_pairs(shape, mode, grid):
+    # 256 x 128 tiles on CTA pairs (two-SM E4M3 MMAs), ragged rows and k
+    p = F8Problem(*shape, seed=12, scale_spread=True)
+    attrs = {"cluster_m": 2}
+    if grid:
+        attrs["grid"] = grid
+    outs, info = p.run(1.0, 0.0, mode, attrs)
+    assert info["cluster_m"] == 2
+    p.check(outs[0], 1.0, 0.0, f"e4m3 pair {shape} {mode} g={grid}")
 
 
 @pytest.mark.parametrize("grid", [7, 40, 151])
 def test_f8_split_tiles_with_spread_scales(grid):
     # 9 tiles of 32 k-blocks over g CTAs: every tile split, owners fix up
     p = F8Problem(384, 384, 4096, seed=5, scale_spread=True)
-    outs, info = p.run(1.0, 0.0, "sk", {"grid": grid})
+    outs, info = p.run(1.0, 0.0, "sk", {"cluster_m": 1, "grid": grid})
     assert info["grid"] == grid
     p.check(outs[0], 1.0, 0.0, f"e4m3 spread scales g={grid}")
 
@@ -104,7 +117,7 @@ def test_f8_column_major_c_and_uniform_values():
 
 def test_f8_bitwise_reproducible():
     p = F8Problem(640, 384, 8192, seed=9)
-    outs, _ = p.run(1.0, 0.0, "sk", {"grid": 100}, reps=3)
+    outs, _ = p.run(1.0, 0.0, "sk", {"cluster_m": 1, "grid": 100}, reps=3)
     assert all(torch.equal(outs[0], o) for o in outs[1:])
     p.check(outs[0], 1.0, 0.0, "e4m3 reproducible")
 
@@ -120,9 +133,6 @@ def test_f8_entry_point_contract():
         assert e.value.status == sk.SK_ERR_INVALID
         with pytest.raises(sk.StreamKError) as e:
             plan.set("tile_n", 256)
-        assert e.value.status == sk.SK_ERR_UNSUPPORTED
-        with pytest.raises(sk.StreamKError) as e:
-            plan.set("cluster_m", 2)
         assert e.value.status == sk.SK_ERR_UNSUPPORTED
         sk.sk_gemm_scaled(plan, A, A, s, s, C)
         assert sk.sk_last_error(plan)[0] == sk.SK_OK

@@ -72,3 +72,32 @@ def test_server_budget_limits_batches():
         assert st["max_batch"] == 1 and st["batches"] == len(SHAPES)
     for p, C in zip(probs, outs):
         p.check(C, 1.0, 0.0, "budget-limited")
+
+
+def test_server_mixed_bf16_and_e4m3_requests():
+    """BF16 and block-scaled E4M3 requests interleaved: batches take one input
+    type each, and every result matches its oracle."""
+    from test_gpu_f8 import F8Problem
+    probs, dev = _requests(seed=4)
+    f8 = [F8Problem(m, n, k, "bf16", seed=40 + i, scale_spread=(i % 2 == 0))
+          for i, (m, n, k) in enumerate(SHAPES) if k % 16 == 0]
+    f8dev = [(p.qA.cuda(), p.qB.cuda(), p.sA.cuda(), p.sB.cuda()) for p in f8]
+    Cs = [p.Cin.clone().cuda() for p in probs]
+    C8 = [p.Cin.clone().cuda() for p in f8]
+    with sk.sk_server_create("bf16", "bf16", max_batch=8, slots=2) as server:
+        tickets = []
+        for i in range(max(len(probs), len(f8))):
+            if i < len(probs):
+                tickets.append(server.submit(dev[i][0], dev[i][1], Cs[i]))
+            if i < len(f8):
+                A, B, sA, sB = f8dev[i]
+                tickets.append(server.submit_scaled(A, B, sA, sB, C8[i]))
+        for t in tickets:
+            st, _ = server.wait(t)
+            assert st == sk.SK_OK
+        assert server.stats()["completed"] == len(tickets)
+    torch.cuda.synchronize()
+    for p, C in zip(probs, Cs):
+        p.check(C.cpu(), 1.0, 0.0, f"served bf16 {p.m}x{p.n}x{p.k}")
+    for p, C in zip(f8, C8):
+        p.check(C.cpu(), 1.0, 0.0, f"served e4m3 {p.m}x{p.n}x{p.k}")
