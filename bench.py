@@ -809,28 +809,25 @@ def run_f8_shapes(peaks, reps=20):
     return out
 
 
-def _plain_launches(sk, plans, ops, arrivals, pick):
+def _plain_launches(sk, launch, plans, arrivals, pick):
     """One launch per request at its arrival time on one stream; returns the
     arrival-to-completion latencies (us) and the wall time of the run."""
     import collections
     import torch
     s = torch.cuda.Stream()
-    with torch.cuda.stream(s):
-        for j in range(8):   # warm the launch path
-            A, B, C = ops[j]
-            sk.sk_gemm(plans[j], A, B, C, stream=s)
+    for j in range(8):   # warm the launch path
+        launch(j % len(plans), j % 2, s)
     torch.cuda.synchronize()
     pend, lats = collections.deque(), []
     t0 = time.perf_counter()
-    for a_t, j in zip(arrivals, pick):
+    for a_t, (j, d) in zip(arrivals, pick):
         while True:
             now = time.perf_counter() - t0
             while pend and pend[0][0].query():
                 lats.append((now - pend.popleft()[1]) * 1e6)
             if now >= a_t:
                 break
-        A, B, C = ops[j]
-        sk.sk_gemm(plans[j], A, B, C, stream=s)
+        launch(j, d, s)
         ev = torch.cuda.Event()
         ev.record(s)
         pend.append((ev, a_t))
@@ -839,23 +836,26 @@ def _plain_launches(sk, plans, ops, arrivals, pick):
         while pend and pend[0][0].query():
             lats.append((now - pend.popleft()[1]) * 1e6)
     wall = time.perf_counter() - t0
-    for p in plans:
-        st, dev_st = sk.sk_last_error(p)
-        if st != sk.SK_OK or dev_st != 0:
-            raise RuntimeError(f"plain launch status {st}, device status {dev_st}")
+    for pair in plans:
+        for p in pair:
+            st, dev_st = sk.sk_last_error(p)
+            if st != sk.SK_OK or dev_st != 0:
+                raise RuntimeError(f"plain launch status {st}, device status {dev_st}")
     return np.array(lats), wall
 
 
 def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
     """The serving workload: requests arrive as a Poisson process at each rate
     for `seconds`, each a GEMM drawn from 64 shapes (48 from the shape sweep's
-    distribution, 16 from the grouped workload's), BF16 in / FP32 accumulate /
-    BF16 out.  The continuous-batching server (batches of up to 64 requests,
-    2 concurrent launch slots, 64 GB admission budget) against two baselines:
-    the same server with batches of one on one slot, and plain launches, one
-    `sk_gemm` per request on arrival from a plan made per shape beforehand,
-    on one stream, completion seen by polling an event recorded after each
-    launch.  Latency: arrival to observed completion."""
+    distribution, 16 from the grouped workload's), half of them BF16 and half
+    block-scaled E4M3 (chosen per request), FP32 accumulate, BF16 out.  The
+    continuous-batching server (batches of up to 64 requests of one input
+    type, 2 concurrent launch slots, 64 GB admission budget) against two
+    baselines: the same server with batches of one on one slot, and plain
+    launches, one `sk_gemm` / `sk_gemm_scaled` per request on arrival from
+    plans made per shape beforehand, on one stream, completion seen by
+    polling an event recorded after each launch.  Latency: arrival to
+    observed completion."""
     import torch
     from paper_2301_03598_gb300 import inputs
     from paper_2301_03598_gb300 import streamk as sk
@@ -866,34 +866,50 @@ def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
     dev = torch.device("cuda", torch.cuda.current_device())
     ops = []
     for i, (m, n, k) in enumerate(shapes):
+        qa, sa = inputs.device_e4m3_matrix(m, k, seed + 3 * i + 2, dev)
+        qb, sb = inputs.device_e4m3_matrix(n, k, seed + 3 * i + 3, dev)
         ops.append((inputs.device_pool(m * k, "bf16", "normal", seed + 3 * i, dev).view(m, k),
                     inputs.device_pool(n * k, "bf16", "normal", seed + 3 * i + 1, dev).view(n, k),
-                    torch.empty(m, n, dtype=torch.bfloat16, device=dev)))
+                    qa, qb, sa, sb, torch.empty(m, n, dtype=torch.bfloat16, device=dev)))
     flops = np.array([2.0 * m * n * k for m, n, k in shapes])
-    plans = [sk.sk_plan(m, n, k, "bf16", "bf16", "bf16") for m, n, k in shapes]
+    plans = [(sk.sk_plan(m, n, k, "bf16", "bf16", "bf16"), sk.sk_plan(m, n, k, "e4m3", "e4m3", "bf16"))
+             for m, n, k in shapes]
+
+    def submit(srv, j, d):
+        A, B, qa, qb, sa, sb, C = ops[j]
+        return srv.submit(A, B, C) if d == 0 else srv.submit_scaled(qa, qb, sa, sb, C)
+
+    def launch(j, d, stream):
+        A, B, qa, qb, sa, sb, C = ops[j]
+        if d == 0:
+            sk.sk_gemm(plans[j][0], A, B, C, stream=stream)
+        else:
+            sk.sk_gemm_scaled(plans[j][1], qa, qb, sa, sb, C, stream=stream)
+
     out = {"workload": "Poisson arrivals of single GEMMs, shapes drawn from 48 shapes of the "
-                       "sweep distribution and 16 of the grouped workload's, BF16 in, FP32 "
-                       "accumulate, BF16 out", "seconds_per_rate": seconds, "rates": {}}
+                       "sweep distribution and 16 of the grouped workload's, half BF16 and half "
+                       "FP8-e4m3 with per-128x128-block FP32 scales, FP32 accumulate, BF16 out",
+           "seconds_per_rate": seconds, "rates": {}}
     for rate in rates:
         n_req = int(rate * seconds)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
-        pick = rng.integers(0, len(shapes), size=n_req)
+        pick = list(zip(rng.integers(0, len(shapes), size=n_req).tolist(),
+                        rng.integers(0, 2, size=n_req).tolist()))
+        req_flops = float(sum(flops[j] for j, _ in pick))
         res = {}
         for name, mb, slots in (("server", 64, 2), ("per_request", 1, 1)):
             srv = sk.sk_server_create("bf16", "bf16", max_batch=mb, slots=slots,
                                       hbm_budget_bytes=64 << 30)
             try:
                 for j in range(8):   # warm the launch path
-                    A, B, C = ops[j]
-                    srv.wait(srv.submit(A, B, C))
+                    srv.wait(submit(srv, j, j % 2))
                 torch.cuda.synchronize()
                 tickets = []
                 t0 = time.perf_counter()
-                for a_t, j in zip(arrivals, pick):
+                for a_t, (j, d) in zip(arrivals, pick):
                     while time.perf_counter() - t0 < a_t:
                         pass
-                    A, B, C = ops[j]
-                    tickets.append(srv.submit(A, B, C))
+                    tickets.append(submit(srv, j, d))
                 lats = []
                 for t in tickets:
                     st, lat = srv.wait(t)
@@ -909,19 +925,20 @@ def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
                          "p99_us": float(np.percentile(lats, 99)),
                          "mean_us": float(lats.mean()),
                          "requests_per_s": n_req / wall,
-                         "tflops": float(flops[pick].sum() / wall / 1e12),
+                         "tflops": req_flops / wall / 1e12,
                          "batches": stats["batches"] - 8, "largest_batch": stats["max_batch"]}
-        lats, wall = _plain_launches(sk, plans, ops, arrivals, pick)
+        lats, wall = _plain_launches(sk, launch, plans, arrivals, pick)
         res["plain_launch"] = {"p50_us": float(np.percentile(lats, 50)),
                                "p99_us": float(np.percentile(lats, 99)),
                                "mean_us": float(lats.mean()),
                                "requests_per_s": n_req / wall,
-                               "tflops": float(flops[pick].sum() / wall / 1e12)}
+                               "tflops": req_flops / wall / 1e12}
         res["p99_speedup"] = res["per_request"]["p99_us"] / res["server"]["p99_us"]
         res["p99_speedup_vs_plain"] = res["plain_launch"]["p99_us"] / res["server"]["p99_us"]
         out["rates"][str(rate)] = res
-    for p in plans:
-        p.destroy()
+    for pair in plans:
+        for p in pair:
+            p.destroy()
     return out
 
 

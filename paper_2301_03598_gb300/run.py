@@ -9,7 +9,9 @@ after ``--warmup`` untimed runs).  The second runs the first N shapes of the
 2,000-shape log-uniform BF16 sweep once each, every shape on operands of its
 own, and prints the total time.  Both end by reading the plan's status and
 exit non-zero on any error, so they serve as the command under a profiler.
-Operands are seeded Philox normals on the device.
+Operands are seeded Philox normals on the device; with ``--dtype e4m3`` they
+are quantised to E4M3 with one FP32 scale per 128 x 128 block and run through
+``sk_gemm_scaled``.
 """
 from __future__ import annotations
 
@@ -24,10 +26,21 @@ from . import streamk as sk
 
 
 def _operands(m, n, k, ab, c, seed, device):
+    C = torch.zeros(m, n, dtype=inputs.DTYPES[c], device=device)
+    if ab == "e4m3":
+        A, sA = inputs.device_e4m3_matrix(m, k, seed, device)
+        B, sB = inputs.device_e4m3_matrix(n, k, seed + 1, device)
+        return A, B, C, (sA, sB)
     A = inputs.device_pool(m * k, ab, "normal", seed, device).view(m, k)
     B = inputs.device_pool(n * k, ab, "normal", seed + 1, device).view(n, k)
-    C = torch.zeros(m, n, dtype=inputs.DTYPES[c], device=device)
-    return A, B, C
+    return A, B, C, None
+
+
+def _gemm(plan, A, B, C, scales, args):
+    if scales is None:
+        sk.sk_gemm(plan, A, B, C, args.alpha, args.beta)
+    else:
+        sk.sk_gemm_scaled(plan, A, B, scales[0], scales[1], C, args.alpha, args.beta)
 
 
 def _plan(m, n, k, args):
@@ -47,16 +60,16 @@ def _check(plan):
 
 def run_one(args, device):
     m, n, k = args.shape
-    A, B, C = _operands(m, n, k, args.dtype, args.out, args.seed, device)
+    A, B, C, sc = _operands(m, n, k, args.dtype, args.out, args.seed, device)
     plan = _plan(m, n, k, args)
     for _ in range(args.warmup):
-        sk.sk_gemm(plan, A, B, C, args.alpha, args.beta)
+        _gemm(plan, A, B, C, sc, args)
     s = torch.cuda.current_stream(device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(device)
     e0.record(s)
     for _ in range(args.reps):
-        sk.sk_gemm(plan, A, B, C, args.alpha, args.beta)
+        _gemm(plan, A, B, C, sc, args)
     e1.record(s)
     torch.cuda.synchronize(device)
     _check(plan)
@@ -76,14 +89,14 @@ def run_sweep(args, device):
         plans.append(_plan(m, n, k, args))
         ops.append(_operands(m, n, k, args.dtype, args.out, args.seed + 2 * i, device))
     for _ in range(args.warmup):
-        for p, (A, B, C) in zip(plans, ops):
-            sk.sk_gemm(p, A, B, C, args.alpha, args.beta)
+        for p, (A, B, C, sc) in zip(plans, ops):
+            _gemm(p, A, B, C, sc, args)
     s = torch.cuda.current_stream(device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(device)
     e0.record(s)
-    for p, (A, B, C) in zip(plans, ops):
-        sk.sk_gemm(p, A, B, C, args.alpha, args.beta)
+    for p, (A, B, C, sc) in zip(plans, ops):
+        _gemm(p, A, B, C, sc, args)
     e1.record(s)
     torch.cuda.synchronize(device)
     for p in plans:
@@ -99,7 +112,7 @@ def main(argv=None):
     ap.add_argument("shape", nargs="*", type=int, help="M N K")
     ap.add_argument("--sweep", type=int, default=0, help="run the first N sweep shapes")
     ap.add_argument("--mode", default="auto", choices=sorted(sk.MODES))
-    ap.add_argument("--dtype", default="bf16", choices=["bf16", "f16"])
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "f16", "e4m3"])
     ap.add_argument("--out", default="bf16", choices=["bf16", "f16", "f32"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
