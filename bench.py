@@ -901,8 +901,11 @@ def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
             srv = sk.sk_server_create("bf16", "bf16", max_batch=mb, slots=slots,
                                       hbm_budget_bytes=64 << 30)
             try:
-                for j in range(8):   # warm the launch path
-                    srv.wait(submit(srv, j, j % 2))
+                # warm the launch path: every shape and input type once, alone
+                # (the plain arm below plans every shape before timing too)
+                for j in range(len(shapes)):
+                    for d in (0, 1):
+                        srv.wait(submit(srv, j, d))
                 torch.cuda.synchronize()
                 tickets = []
                 t0 = time.perf_counter()
@@ -926,7 +929,8 @@ def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
                          "mean_us": float(lats.mean()),
                          "requests_per_s": n_req / wall,
                          "tflops": req_flops / wall / 1e12,
-                         "batches": stats["batches"] - 8, "largest_batch": stats["max_batch"]}
+                         "batches": stats["batches"] - 2 * len(shapes),
+                         "largest_batch": stats["max_batch"]}
         lats, wall = _plain_launches(sk, launch, plans, arrivals, pick)
         res["plain_launch"] = {"p50_us": float(np.percentile(lats, 50)),
                                "p99_us": float(np.percentile(lats, 99)),

@@ -163,7 +163,14 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
  *   16 bytes).  C: device pointer, 16-byte aligned; read only if beta != 0.
  *   C may not alias A or B.
  * The launch is persistent (g <= SM count CTAs, co-resident by cooperative
- * launch whenever CTAs wait on one another).  Results are bitwise reproducible
+ * launch whenever single CTAs wait on one another).  Two launch forms rely on
+ * SMs freeing up instead, which holds within one stream but not while other
+ * streams' kernels occupy SMs at the same time: a CTA-pair plan that splits
+ * tiles (clustered, without the cooperative guarantee) and a launch with
+ * programmatic dependent launch (its CTAs take SMs before the stream's
+ * previous kernel has finished).  Under concurrent streams a fixup wait may
+ * then run out (SK_ERR_TIMEOUT); plans for concurrent use should set
+ * SK_ATTR_CLUSTER_M 1 and SK_ATTR_PDL 0.  Results are bitwise reproducible
  * run to run for a given plan: the fixup adds the contributing CTAs' partials
  * in increasing CTA order.  Returns SK_ERR_INVALID for bad pointers,
  * SK_ERR_CUDA if the launch fails.

@@ -139,7 +139,7 @@ void set_divisors(sk::SkArgs& a, const sk_schedule_info& s) {
 
 int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
               const float* scale_b, void* C, float alpha, float beta, int32_t* trace,
-              int64_t trace_ints, void* stream_v) {
+              int64_t trace_ints, void* stream_v, int32_t* err_host = nullptr) {
   if (p == nullptr) return SK_ERR_INVALID;
   // E4M3 plans take their block scales; 16-bit plans take none
   const bool f8 = p->a_type == SK_E4M3;
@@ -235,6 +235,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   a.partials = split ? reinterpret_cast<float*>(p->ws + sk::kFlagBytes) : nullptr;
   a.epoch = next_epoch();
   a.err = p->err;
+  a.err_host = err_host;
   a.trace = trace;
   a.trace_cap = s.max_segments;
   a.debug_skip_signal = p->debug_skip_signal;
@@ -268,6 +269,14 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
 }
 
 }  // namespace
+
+namespace sk {
+int gemm_reporting(sk_plan_t p, const void* A, const void* B, const float* scale_a,
+                   const float* scale_b, void* C, float alpha, float beta, void* stream,
+                   int32_t* err_host) {
+  return gemm_impl(p, A, B, scale_a, scale_b, C, alpha, beta, nullptr, 0, stream, err_host);
+}
+}  // namespace sk
 
 extern "C" {
 

@@ -7,6 +7,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "../../include/streamk.h"
+
 namespace sk {
 namespace host {
 
@@ -34,4 +36,11 @@ int store_path(int req);
 uint32_t make_idesc(int in_dtype, int tile_n, int cluster_m);
 
 }  // namespace host
+
+// sk_gemm / sk_gemm_scaled (scales null for 16-bit plans) whose launch also
+// stores a device failure status into err_host (a device pointer to mapped
+// pinned host memory, or nullptr).
+int gemm_reporting(sk_plan_t p, const void* A, const void* B, const float* scale_a,
+                   const float* scale_b, void* C, float alpha, float beta, void* stream,
+                   int32_t* err_host);
 }  // namespace sk

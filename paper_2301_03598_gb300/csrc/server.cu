@@ -65,7 +65,10 @@ struct Slot {
   int32_t* h_start = nullptr;
   int32_t* d_err = nullptr;
   char* ws = nullptr;
-  int32_t* h_err = nullptr;
+  // mapped pinned word a failing launch writes its status into (host view,
+  // device view); cleared before each launch
+  int32_t* h_status = nullptr;
+  int32_t* d_status = nullptr;
   std::vector<Request> reqs;
   int64_t bytes = 0;
   bool busy = false;
@@ -99,6 +102,50 @@ struct sk_server_s {
   // Schedules of batch compositions seen before, keyed by the batch's
   // (m, n, k) sequence; used by the worker only.
   std::unordered_map<std::string, std::shared_ptr<const sk::GroupPlan>> plan_cache;
+  // Tensor maps encoded before, keyed by (kind, pointer, dtype, rows, cols,
+  // box rows); used by the worker only.
+  struct MapKey {
+    const void* ptr;
+    int64_t rows, cols;
+    int32_t kind, dtype, box;
+    bool operator==(const MapKey& o) const {
+      return ptr == o.ptr && rows == o.rows && cols == o.cols && kind == o.kind &&
+             dtype == o.dtype && box == o.box;
+    }
+  };
+  struct MapHash {
+    size_t operator()(const MapKey& k) const {
+      uint64_t h = reinterpret_cast<uintptr_t>(k.ptr) * 0x9E3779B97F4A7C15ull;
+      h ^= static_cast<uint64_t>(k.rows) * 0xC2B2AE3D27D4EB4Full + (h << 6) + (h >> 2);
+      h ^= static_cast<uint64_t>(k.cols) * 0x165667B19E3779F9ull + (h << 6) + (h >> 2);
+      h ^= static_cast<uint64_t>(k.kind * 1024 + k.dtype * 512 + k.box) + (h << 6) + (h >> 2);
+      return static_cast<size_t>(h);
+    }
+  };
+  struct MapEntry {
+    CUtensorMap map;
+    int status;  // SK_OK, or the encode failure (kind 2: 1 = TMA store possible)
+  };
+  std::unordered_map<MapKey, MapEntry, MapHash> map_cache;
+  // single-GEMM plans for lone requests, per (m, n, k, input type, slot):
+  // a plan owns its fixup workspace, so concurrent slots never share one;
+  // used by the worker only, destroyed with the server
+  struct PlanKey {
+    int64_t m, n, k;
+    int32_t ab, slot;
+    bool operator==(const PlanKey& o) const {
+      return m == o.m && n == o.n && k == o.k && ab == o.ab && slot == o.slot;
+    }
+  };
+  struct PlanHash {
+    size_t operator()(const PlanKey& k) const {
+      uint64_t h = static_cast<uint64_t>(k.m) * 0x9E3779B97F4A7C15ull;
+      h ^= static_cast<uint64_t>(k.n) * 0xC2B2AE3D27D4EB4Full + (h << 6) + (h >> 2);
+      h ^= static_cast<uint64_t>(k.k) * 0x165667B19E3779F9ull + (h << 6) + (h >> 2);
+      return static_cast<size_t>(h ^ static_cast<uint64_t>(k.ab * 64 + k.slot));
+    }
+  };
+  std::unordered_map<PlanKey, sk_plan_t, PlanHash> single_plans;
   int device = 0;
   std::thread worker;
 };
@@ -106,6 +153,7 @@ struct sk_server_s {
 namespace {
 
 constexpr size_t kPlanCacheEntries = 4096;
+constexpr size_t kMapCacheEntries = 16384;
 constexpr int kModelledBatch = 4;  // batches up to this size get the full model
 constexpr int kIdleSpinUs = 200;  // idle worker: spin before sleeping
 
@@ -114,7 +162,7 @@ void free_slot(Slot& s) {
   if (s.d_err) cudaFree(s.d_err);
   if (s.ws) cudaFree(s.ws);
   if (s.h_block) cudaFreeHost(s.h_block);
-  if (s.h_err) cudaFreeHost(s.h_err);
+  if (s.h_status) cudaFreeHost(s.h_status);
   if (s.done) cudaEventDestroy(s.done);
   if (s.stream) cudaStreamDestroy(s.stream);
   s = Slot();
@@ -142,7 +190,10 @@ cudaError_t alloc_slot(Slot& s, int max_batch, int num_sms) {
   if (e == cudaSuccess) e = cudaMemset(s.d_err, 0, 4 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s.ws, ws);
   if (e == cudaSuccess) e = cudaMemset(s.ws, 0, ws);
-  if (e == cudaSuccess) e = cudaMallocHost(&s.h_err, 4 * sizeof(int32_t));
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(reinterpret_cast<void**>(&s.h_status), 4 * sizeof(int32_t), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s.d_status), s.h_status, 0);
+  if (e == cudaSuccess) s.h_status[0] = 0;
   return e;
 }
 
@@ -150,8 +201,64 @@ cudaError_t alloc_slot(Slot& s, int max_batch, int num_sms) {
 // sk_status; on failure nothing is in flight on the slot.  Runs without the
 // server lock: it reads only the slot (owned by the worker while busy) and
 // the server's immutable settings.
+// Tensor map through the server's cache: kind 0 = 2-D operand, 1 = 3-D
+// operand view, 2 = output (status 1 when C can be stored by TMA, else 0).
+int cached_map(sk_server_s* sv, CUtensorMap* out, int kind, const void* ptr, int dtype,
+               int64_t rows, int64_t cols, int box) {
+  const sk_server_s::MapKey key{ptr, rows, cols, kind, dtype, box};
+  auto it = sv->map_cache.find(key);
+  if (it == sv->map_cache.end()) {
+    sk_server_s::MapEntry e{};
+    if (kind == 0)
+      e.status = encode_operand(&e.map, ptr, dtype, rows, cols, cols, box);
+    else if (kind == 1)
+      e.status = encode_operand_3d(&e.map, ptr, dtype, rows, cols, cols, box);
+    else
+      e.status = encode_output(&e.map, const_cast<void*>(ptr), dtype, rows, cols, cols) ? 1 : 0;
+    if (sv->map_cache.size() >= kMapCacheEntries) sv->map_cache.clear();
+    it = sv->map_cache.emplace(key, e).first;
+  }
+  *out = it->second.map;
+  return it->second.status;
+}
+
+// A lone request runs as a single GEMM from a plan cached per shape and input
+// type: its arguments travel by value with the launch, so nothing is uploaded
+// first.
+int launch_single(sk_server_s* sv, Slot& s) {
+  const Request& r = s.reqs[0];
+  const int ab_type = r.f8 ? SK_E4M3 : sv->ab_type;
+  const sk_server_s::PlanKey key{r.m, r.n, r.k, ab_type, static_cast<int32_t>(&s - sv->slots.data())};
+  auto it = sv->single_plans.find(key);
+  if (it == sv->single_plans.end()) {
+    sk_plan_t p = nullptr;
+    int st = sk_plan(&p, r.m, r.n, r.k, static_cast<sk_dtype>(ab_type),
+                           static_cast<sk_dtype>(ab_type), static_cast<sk_dtype>(sv->c_type), SK_F32,
+                           SK_ROW_MAJOR, SK_COL_MAJOR, SK_ROW_MAJOR, SK_MODE_AUTO);
+    // Launched as the grouped batches are: single CTAs, so that a split
+    // schedule launches cooperatively, and no programmatic dependent launch.
+    // Other slots' kernels share the GPU, and CTAs that wait on their
+    // grid's peers must not depend on SMs those kernels hold: a clustered
+    // split launch has no co-residency guarantee, and a PDL launch puts CTAs
+    // on SMs before its stream's previous kernel has finished.
+    if (st == SK_OK) st = sk_plan_set(p, SK_ATTR_CLUSTER_M, 1);
+    if (st == SK_OK) st = sk_plan_set(p, SK_ATTR_PDL, 0);
+    if (st != SK_OK) {
+      sk_plan_destroy(p);
+      return st;
+    }
+    it = sv->single_plans.emplace(key, p).first;
+  }
+  s.h_status[0] = 0;
+  int st = sk::gemm_reporting(it->second, r.A, r.B, r.scale_a, r.scale_b, r.C, r.alpha, r.beta,
+                              s.stream, s.d_status);
+  if (st != SK_OK) return st;
+  return cuda_status(cudaEventRecord(s.done, s.stream));
+}
+
 int launch_slot(sk_server_s* sv, Slot& s) {
   const int count = static_cast<int>(s.reqs.size());
+  if (count == 1) return launch_single(sv, s);
   const bool f8 = s.reqs[0].f8;  // a batch holds one input type
   const int ab_type = f8 ? SK_E4M3 : sv->ab_type;
   std::vector<int64_t> m(count), n(count), k(count);
@@ -198,17 +305,17 @@ int launch_slot(sk_server_s* sv, Slot& s) {
     const Request& r = s.reqs[i];
     sk::GroupProblem& pr = s.h_probs[i];
     std::memset(static_cast<void*>(&pr), 0, sizeof(pr));
-    st = encode_operand(&pr.tmA, r.A, ab_type, r.m, r.k, r.k, sk::kBlkM);
-    if (st == SK_OK) st = encode_operand(&pr.tmB, r.B, ab_type, r.n, r.k, r.k, gp.tile_n);
+    st = cached_map(sv, &pr.tmA, 0, r.A, ab_type, r.m, r.k, sk::kBlkM);
+    if (st == SK_OK) st = cached_map(sv, &pr.tmB, 0, r.B, ab_type, r.n, r.k, gp.tile_n);
     const bool use3d = !f8 && gp.tile_k == 2 * sk::kBlkK && r.k / sk::kBlkK >= 2;
-    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmA3, r.A, ab_type, r.m, r.k, r.k, sk::kBlkM);
-    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmB3, r.B, ab_type, r.n, r.k, r.k, gp.tile_n);
+    if (st == SK_OK && use3d) st = cached_map(sv, &pr.tmA3, 1, r.A, ab_type, r.m, r.k, sk::kBlkM);
+    if (st == SK_OK && use3d) st = cached_map(sv, &pr.tmB3, 1, r.B, ab_type, r.n, r.k, gp.tile_n);
     if (st != SK_OK) return st;
     if (!use3d) {
       pr.tmA3 = pr.tmA;
       pr.tmB3 = pr.tmB;
     }
-    const bool c_tma = encode_output(&pr.tmC, r.C, sv->c_type, r.m, r.n, r.n);
+    const bool c_tma = cached_map(sv, &pr.tmC, 2, r.C, sv->c_type, r.m, r.n, 0) == 1;
     if (!c_tma) pr.tmC = pr.tmA;
     pr.C = r.C;
     pr.ldc = r.n;
@@ -236,6 +343,7 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   a.partials = split ? reinterpret_cast<float*>(s.ws + sk::kFlagBytes) : nullptr;
   a.epoch = next_epoch();
   a.err = s.d_err;
+  a.err_host = s.d_status;
   a.trace_cap = gp.max_segments;
   a.debug_skip_signal = -1;
   a.timeout_ns = kDefaultTimeoutNs;
@@ -244,10 +352,10 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   a.gstart = s.d_start;
   a.gprobs = s.d_probs;
   const CUtensorMap& any = s.h_probs[0].tmA;
+  s.h_status[0] = 0;
   e = f8                ? sk::launch_grouped_f8(sv->c_type, any, a, split, s.stream)
       : gp.tile_n == 256 ? sk::launch_grouped_bn256(sv->c_type, any, a, split, s.stream)
                          : sk::launch_grouped_bn128(sv->c_type, any, a, split, s.stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_err, s.d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s.stream);
   if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
   if (e != cudaSuccess) return cuda_status(e);
   return SK_OK;
@@ -282,7 +390,7 @@ void worker_loop(sk_server_s* sv) {
         continue;
       }
       int status = q == cudaSuccess ? SK_OK : SK_ERR_CUDA;
-      if (status == SK_OK && s.h_err[0] != 0) {
+      if (status == SK_OK && *reinterpret_cast<volatile int32_t*>(s.h_status) != 0) {
         status = SK_ERR_TIMEOUT;
         cudaMemset(s.d_err, 0, 4 * sizeof(int32_t));
         cudaMemset(s.ws, 0, static_cast<size_t>(sk::kFlagBytes));
@@ -513,6 +621,7 @@ int sk_server_destroy(sk_server_t sv) {
     if (s.stream) cudaStreamSynchronize(s.stream);
     free_slot(s);
   }
+  for (auto& kv : sv->single_plans) sk_plan_destroy(kv.second);
   delete sv;
   return SK_OK;
 }

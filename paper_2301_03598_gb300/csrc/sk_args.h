@@ -139,6 +139,8 @@ struct SkArgs {
   uint32_t epoch;
   // status, tracing, bounded waits
   int32_t* err;         // err[0]: first device status, err[1]: CTA, err[2]: where
+  int32_t* err_host;    // nullptr, or mapped pinned host memory: a failing CTA also stores
+                        // its status here, so the host sees it without a copy
   int32_t* trace;       // nullptr: off; else grid x (header + trace_cap records)
   int32_t trace_cap;    // records per CTA
   int32_t debug_skip_signal;  // CTA index that withholds its Signal (tests), -1 off

@@ -87,6 +87,10 @@ __device__ __forceinline__ void report(const SkArgs& a, int code, int where) {
   }
   atomicExch(reinterpret_cast<unsigned*>(&a.err[3]), a.epoch);
   __threadfence();
+  if (a.err_host != nullptr) {
+    *reinterpret_cast<volatile int32_t*>(a.err_host) = code;
+    __threadfence_system();
+  }
 }
 
 // Bounded mbarrier wait.  Returns false if this CTA is aborting or the time
@@ -926,24 +930,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t pbase = tmem_base + lane_base + static_cast<uint32_t>(acc * BN);
-          uint32_t r[kMine][32 * kCpu];
+          // 32 columns at a time, so that the product needs 32 registers
+          // next to the sum's 64
 #pragma unroll
-          for (int mi = 0; mi < kMine; ++mi) {
-            const uint32_t col = static_cast<uint32_t>((col_half + 2 * mi) * 32 * kCpu);
-            if constexpr (kCpu == 2)
-              tmem_ld_x64(pbase + col, r[mi]);
-            else
-              tmem_ld_x32(pbase + col, r[mi]);
+          for (int c = 0; c < 2; ++c) {
+            const int mi = kCpu == 2 ? 0 : c;
+            const int j0 = kCpu == 2 ? 32 * c : 0;
+            const uint32_t col = static_cast<uint32_t>((col_half + 2 * mi) * 32 * kCpu + j0);
+            uint32_t r[32];
+            tmem_ld_x32(pbase + col, r);
+            tmem_wait_ld();
+            if (c == 1) {
+              // the product buffer is read: the MMA warp may overwrite it
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) release_acc(acc);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) sum[mi][j0 + j] = fmaf(sc, __uint_as_float(r[j]), sum[mi][j0 + j]);
           }
-          tmem_wait_ld();
-          // the product buffer is read: the MMA warp may overwrite it
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) release_acc(acc);
-#pragma unroll
-          for (int mi = 0; mi < kMine; ++mi)
-#pragma unroll
-            for (int j = 0; j < 32 * kCpu; ++j) sum[mi][j] = fmaf(sc, __uint_as_float(r[mi][j]), sum[mi][j]);
           if (++acc == NB) {
             acc = 0;
             acc_phase ^= 1u;

@@ -101,3 +101,24 @@ def test_server_mixed_bf16_and_e4m3_requests():
         p.check(C.cpu(), 1.0, 0.0, f"served bf16 {p.m}x{p.n}x{p.k}")
     for p, C in zip(f8, C8):
         p.check(C.cpu(), 1.0, 0.0, f"served e4m3 {p.m}x{p.n}x{p.k}")
+
+
+def test_server_same_shape_on_concurrent_slots():
+    """Lone requests of one Stream-K-split shape on two slots at once: each slot
+    runs its own plan and fixup workspace, so every result stays exact."""
+    p = Problem(384, 384, 4096, "bf16", "f32", "normal", seed=6)
+    A, B = p.A.cuda(), p.B.cuda()
+    Cs = [torch.zeros(384, 384, dtype=torch.float32, device="cuda") for _ in range(40)]
+    with sk.sk_server_create("bf16", "f32", max_batch=1, slots=2) as server:
+        tickets = [server.submit(A, B, C) for C in Cs]
+        for t in tickets:
+            st, _ = server.wait(t)
+            assert st == sk.SK_OK
+        assert server.stats()["batches"] == len(Cs)
+    torch.cuda.synchronize()
+    C64, absAB = p.oracle(1.0, 0.0)
+    bd = bound(p.k, 1.0, 0.0, absAB, C64, inputs.widen(p.Cin), "f32")
+    first = Cs[0].cpu()
+    for C in Cs:
+        check_bound(inputs.widen(C.cpu()), C64, bd, "concurrent slots")
+        assert torch.equal(C.cpu(), first)   # one plan per slot: the same schedule
