@@ -362,23 +362,6 @@ __device__ __forceinline__ bool mma_f16_probe(uint32_t d_tmem, uint64_t a_desc, 
   return ready != 0;
 }
 
-// The last kind::f8f6f4 MMA of a k-block plus a probe of `bar` for `parity`.
-__device__ __forceinline__ bool mma_f8_probe(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                             uint32_t idesc, uint32_t accumulate, uint32_t bar,
-                                             uint32_t parity) {
-  uint32_t ready;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 q, [%5], %6;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%1], %2, %3, %7, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(ready)
-      : "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(accumulate), "r"(bar), "r"(parity), "r"(idesc)
-      : "memory");
-  return ready != 0;
-}
-
 // The last kind::f8f6f4 MMA of a k-block plus probes of two barriers (the
 // next stage's full barrier and the next product buffer's empty barrier):
 // bit 0 / bit 1 of the result say whether each probed phase had completed.
