@@ -249,6 +249,21 @@ __device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_
       : "memory");
 }
 
+// Two FP32 fused multiply-adds in one packed instruction: (d0, d1) =
+// (s * a0 + c0, s * a1 + c1), each rounded once to nearest even, as fmaf.
+// Operands and results are FP32 bit patterns.
+__device__ __forceinline__ void fma2(uint32_t s, uint32_t a0, uint32_t a1, uint32_t& c0,
+                                     uint32_t& c1) {
+  asm("{\n\t.reg .b64 ss, aa, cc, dd;\n\t"
+      "mov.b64 ss, {%2, %2};\n\t"
+      "mov.b64 aa, {%3, %4};\n\t"
+      "mov.b64 cc, {%0, %1};\n\t"
+      "fma.rn.f32x2 dd, ss, aa, cc;\n\t"
+      "mov.b64 {%0, %1}, dd;\n\t}"
+      : "+r"(c0), "+r"(c1)
+      : "r"(s), "r"(a0), "r"(a1));
+}
+
 // Arrive (once) on `bar` when every tcgen05 operation this thread issued so far
 // has completed.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {

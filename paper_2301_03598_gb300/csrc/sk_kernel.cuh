@@ -902,11 +902,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // scale_a[tm][kb] * scale_b[tn][kb] * (product of k-block kb), for
         // this warp's output units (the columns it stores below).
         constexpr int kMine = BN / (32 * kCpu) / 2;
-        float sum[kMine][32 * kCpu];
+        uint32_t sum[kMine][32 * kCpu];  // FP32 bit patterns
 #pragma unroll
         for (int i = 0; i < kMine; ++i)
 #pragma unroll
-          for (int j = 0; j < 32 * kCpu; ++j) sum[i][j] = 0.0f;
+          for (int j = 0; j < 32 * kCpu; ++j) sum[i][j] = 0u;
         const float* sa = scale_a + static_cast<size_t>(tm) * ld_scale;
         const float* sb = scale_b + static_cast<size_t>(tn) * ld_scale;
         // lane l holds the scale product of k-block first + l; the next 32
@@ -946,8 +946,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               __syncwarp();
               if (lane == 0) release_acc(acc);
             }
+            // sum += sc * product, two columns per packed FMA
+            const uint32_t scb = __float_as_uint(sc);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) sum[mi][j0 + j] = fmaf(sc, __uint_as_float(r[j]), sum[mi][j0 + j]);
+            for (int j = 0; j < 32; j += 2) fma2(scb, r[j], r[j + 1], sum[mi][j0 + j], sum[mi][j0 + j + 1]);
           }
           if (++acc == NB) {
             acc = 0;
@@ -959,13 +961,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int mi = 0; mi < kMine; ++mi) {
             const uint32_t col = static_cast<uint32_t>((col_half + 2 * mi) * 32 * kCpu);
-            uint32_t w[32 * kCpu];
-#pragma unroll
-            for (int j = 0; j < 32 * kCpu; ++j) w[j] = __float_as_uint(sum[mi][j]);
             if constexpr (kCpu == 2)
-              tmem_st_x64(sbase + col, w);
+              tmem_st_x64(sbase + col, sum[mi]);
             else
-              tmem_st_x32(sbase + col, w);
+              tmem_st_x32(sbase + col, sum[mi]);
           }
           // this thread reads back exactly the lanes and columns it wrote
           tmem_wait_st();
