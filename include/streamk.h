@@ -187,7 +187,7 @@ int sk_gemm(sk_plan_t plan, const void* A, const void* B, void* C, float alpha, 
  * Every product of a k-block is accumulated in FP32 by the tensor cores, then
  * scaled and summed in FP32 in k order; Stream-K partials and the fixup stay
  * FP32 (the paper's Section 4 schedule is unchanged: one MAC-loop iteration
- * is one k-block of 128).
+ * is two k-blocks of 128, BLK_K = 256).
  *   scale_a: device FP32 array [ceil(m/128)][ceil(k/128)], row-major;
  *   scale_b: device FP32 array [ceil(n/128)][ceil(k/128)], row-major; both
  *   read-only, 4-byte aligned, not copied (they must stay valid until the

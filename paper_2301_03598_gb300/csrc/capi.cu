@@ -99,7 +99,10 @@ int replan(sk_plan_s* p) {
   const int64_t m = p->swap ? p->n : p->m;
   const int64_t n = p->swap ? p->m : p->n;
   sk_schedule_info s;
-  int st = sk::describe(m, n, p->k, p->mode_req, p->tile_n_req, p->grid_req, p->group_req,
+  // An E4M3 row of k elements is, byte for byte, a 16-bit row of k/2: the
+  // schedule and the TMA boxes are the 16-bit path's for k/2.
+  const bool f8 = p->a_type == SK_E4M3;
+  int st = sk::describe(m, n, f8 ? p->k / 2 : p->k, p->mode_req, p->tile_n_req, p->grid_req, p->group_req,
                         p->cluster_req, p->num_sms, &s);
   if (st != SK_OK) return st;
   if (s.workspace_bytes > 0 && static_cast<size_t>(s.workspace_bytes) > p->ws_bytes) {
@@ -118,6 +121,7 @@ int replan(sk_plan_s* p) {
     p->ws = static_cast<char*>(w);
     p->ws_bytes = static_cast<size_t>(s.workspace_bytes);
   }
+  if (f8) s.tile_k *= 2;  // in E4M3 elements
   p->info = s;
   p->cached_a = p->cached_b = p->cached_c = nullptr;
   return SK_OK;
@@ -187,18 +191,22 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   const int64_t kn = p->swap ? p->m : p->n;
   const int64_t klda = p->swap ? p->ldb : p->lda;
   const int64_t kldb = p->swap ? p->lda : p->ldb;
-  const bool use3d = !f8 && s.tile_k == 2 * sk::kBlkK && p->k / sk::kBlkK >= 2;
+  // E4M3 operands go to TMA as 16-bit rows of k/2 elements (the same bytes)
+  const int tma_type = f8 ? SK_BF16 : p->a_type;
+  const int64_t tk = f8 ? p->k / 2 : p->k;
+  const int64_t tlda = f8 ? klda / 2 : klda, tldb = f8 ? kldb / 2 : kldb;
+  const bool use3d = s.tile_n == 128 && tk / sk::kBlkK >= 2;
   if (ka != p->cached_a) {
-    int st = encode_operand(&p->tm_a, ka, p->a_type, km, p->k, klda, sk::kBlkM);
+    int st = encode_operand(&p->tm_a, ka, tma_type, km, tk, tlda, sk::kBlkM);
     if (st == SK_OK && use3d)
-      st = encode_operand_3d(&p->tm_a3, ka, p->a_type, km, p->k, klda, sk::kBlkM);
+      st = encode_operand_3d(&p->tm_a3, ka, tma_type, km, tk, tlda, sk::kBlkM);
     if (st != SK_OK) return st;
     p->cached_a = ka;
   }
   if (kb != p->cached_b) {
-    int st = encode_operand(&p->tm_b, kb, p->b_type, kn, p->k, kldb, s.tile_n / s.cluster_m);
+    int st = encode_operand(&p->tm_b, kb, tma_type, kn, tk, tldb, s.tile_n / s.cluster_m);
     if (st == SK_OK && use3d)
-      st = encode_operand_3d(&p->tm_b3, kb, p->b_type, kn, p->k, kldb, s.tile_n / s.cluster_m);
+      st = encode_operand_3d(&p->tm_b3, kb, tma_type, kn, tk, tldb, s.tile_n / s.cluster_m);
     if (st != SK_OK) return st;
     p->cached_b = kb;
   }
@@ -222,7 +230,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   a.sk_q = static_cast<int32_t>(s.sk_iters / s.grid);
   a.sk_r = static_cast<int32_t>(s.sk_iters % s.grid);
   set_divisors(a, s);
-  a.kfull64 = use3d ? static_cast<int32_t>(p->k / sk::kBlkK) : 0;
+  a.kfull64 = use3d ? static_cast<int32_t>(tk / sk::kBlkK) : 0;
   a.idesc = make_idesc(p->a_type, s.tile_n, s.cluster_m);
   a.C = C;
   a.ldc = p->ldc;
@@ -255,11 +263,11 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   // all CTAs become resident; the bounded waits turn anything else into an
   // error status.
   const bool cooperative = split && s.cluster_m == 1;
-  if (f8)
-    return cuda_status(
-        sk::launch_f8(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, a, cooperative, stream));
   const CUtensorMap& ta3 = use3d ? p->tm_a3 : p->tm_a;
   const CUtensorMap& tb3 = use3d ? p->tm_b3 : p->tm_b;
+  if (f8)
+    return cuda_status(sk::launch_f8(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3,
+                                     a, cooperative, stream));
   cudaError_t e = s.tile_n == 256
                       ? sk::launch_bn256(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3,
                                          a, cooperative, stream)
@@ -302,6 +310,7 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
   if (mode < SK_MODE_AUTO || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
   if (!((a_type == SK_F16 || a_type == SK_BF16 || a_type == SK_E4M3) && b_type == a_type))
     return SK_ERR_UNSUPPORTED;
+  if (a_type == SK_E4M3 && k % 16 != 0) return SK_ERR_INVALID;  // 16-byte rows
   if (!(c_type == SK_F32 || c_type == SK_BF16 || c_type == SK_F16)) return SK_ERR_UNSUPPORTED;
   if (compute_type != SK_F32) return SK_ERR_UNSUPPORTED;
   if (a_layout != SK_ROW_MAJOR || b_layout != SK_COL_MAJOR) return SK_ERR_UNSUPPORTED;
@@ -757,9 +766,15 @@ void grouped_free_schedule(sk_grouped_s* g) {
 // (the tile width sets the tensor-map boxes).
 int grouped_replan(sk_grouped_s* g) {
   sk::GroupPlan gp;
-  int st = sk::describe_grouped(g->count, g->m.data(), g->n.data(), g->k.data(), g->mode_req,
+  // E4M3 problems are planned as 16-bit problems of k/2 (the same bytes per row)
+  const bool f8 = g->ab_type == SK_E4M3;
+  std::vector<int64_t> kk(g->k);
+  if (f8)
+    for (int64_t& v : kk) v /= 2;
+  int st = sk::describe_grouped(g->count, g->m.data(), g->n.data(), kk.data(), g->mode_req,
                                 g->tile_n_req, g->grid_req, g->num_sms, &gp);
   if (st != SK_OK) return st;
+  if (f8) gp.tile_k *= 2;  // in E4M3 elements
   if (g->launched) {
     cudaError_t e = cudaStreamSynchronize(g->last_stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -844,11 +859,14 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
     const float al = alpha ? alpha[i] : 1.0f, be = beta ? beta[i] : 0.0f;
     sk::GroupProblem& pr = g->h_probs[i];
     const int64_t m = g->m[i], n = g->n[i], k = g->k[i];
-    int st = encode_operand(&pr.tmA, A[i], g->ab_type, m, k, k, sk::kBlkM);
-    if (st == SK_OK) st = encode_operand(&pr.tmB, B[i], g->ab_type, n, k, k, gp.tile_n);
-    const bool use3d = !f8 && gp.tile_k == 2 * sk::kBlkK && k / sk::kBlkK >= 2;
-    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmA3, A[i], g->ab_type, m, k, k, sk::kBlkM);
-    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmB3, B[i], g->ab_type, n, k, k, gp.tile_n);
+    // E4M3 rows go to TMA as 16-bit rows of k/2 elements
+    const int tt = f8 ? SK_BF16 : g->ab_type;
+    const int64_t tk = f8 ? k / 2 : k;
+    int st = encode_operand(&pr.tmA, A[i], tt, m, tk, tk, sk::kBlkM);
+    if (st == SK_OK) st = encode_operand(&pr.tmB, B[i], tt, n, tk, tk, gp.tile_n);
+    const bool use3d = gp.tile_n == 128 && tk / sk::kBlkK >= 2;
+    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmA3, A[i], tt, m, tk, tk, sk::kBlkM);
+    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmB3, B[i], tt, n, tk, tk, gp.tile_n);
     if (st != SK_OK) {
       g->table_valid = false;
       return st;

@@ -1,5 +1,5 @@
 // Instantiations of the persistent Stream-K kernel for E4M3 operands with
-// per-128 x 128-block FP32 scales: 128 x 128 tiles, single CTAs.
+// per-128 x 128-block FP32 scales: BLK_N = 128 on single CTAs or CTA pairs.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -11,7 +11,8 @@ namespace sk {
 
 template <int CM, typename TC, bool GROUPED>
 static cudaError_t launch_f8_one(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
-                                 const SkArgs& args, bool cooperative, cudaStream_t stream) {
+                                 const CUtensorMap& ta3, const CUtensorMap& tb3, const SkArgs& args,
+                                 bool cooperative, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(args.grid * CM));
   cfg.blockDim = dim3(kThreads);
@@ -38,36 +39,37 @@ static cudaError_t launch_f8_one(const CUtensorMap& ta, const CUtensorMap& tb, c
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, CM, TC, GROUPED, true>, ta, tb, tc, ta, tb,
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, CM, TC, GROUPED, true>, ta, tb, tc, ta3, tb3,
                             args);
 }
 
 template <int CM, bool GROUPED>
 static cudaError_t launch_f8_c(int c_dtype, const CUtensorMap& ta, const CUtensorMap& tb,
-                               const CUtensorMap& tc, const SkArgs& args, bool cooperative,
-                               cudaStream_t stream) {
+                               const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
+                               const SkArgs& args, bool cooperative, cudaStream_t stream) {
   switch (c_dtype) {
     case SK_F32:
-      return launch_f8_one<CM, float, GROUPED>(ta, tb, tc, args, cooperative, stream);
+      return launch_f8_one<CM, float, GROUPED>(ta, tb, tc, ta3, tb3, args, cooperative, stream);
     case SK_BF16:
-      return launch_f8_one<CM, __nv_bfloat16, GROUPED>(ta, tb, tc, args, cooperative, stream);
+      return launch_f8_one<CM, __nv_bfloat16, GROUPED>(ta, tb, tc, ta3, tb3, args, cooperative, stream);
     case SK_F16:
-      return launch_f8_one<CM, __half, GROUPED>(ta, tb, tc, args, cooperative, stream);
+      return launch_f8_one<CM, __half, GROUPED>(ta, tb, tc, ta3, tb3, args, cooperative, stream);
     default:
       return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_f8(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
-                      const CUtensorMap& tc, const SkArgs& args, bool cooperative,
-                      cudaStream_t stream) {
-  return cluster_m == 2 ? launch_f8_c<2, false>(c_dtype, ta, tb, tc, args, cooperative, stream)
-                        : launch_f8_c<1, false>(c_dtype, ta, tb, tc, args, cooperative, stream);
+                      const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
+                      const SkArgs& args, bool cooperative, cudaStream_t stream) {
+  return cluster_m == 2
+             ? launch_f8_c<2, false>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream)
+             : launch_f8_c<1, false>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream);
 }
 
 cudaError_t launch_grouped_f8(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
                               bool cooperative, cudaStream_t stream) {
-  return launch_f8_c<1, true>(c_dtype, tm, tm, tm, args, cooperative, stream);
+  return launch_f8_c<1, true>(c_dtype, tm, tm, tm, tm, tm, args, cooperative, stream);
 }
 
 template <typename TC>

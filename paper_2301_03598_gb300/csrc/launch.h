@@ -26,11 +26,12 @@ cudaError_t launch_grouped_bn128(int c_dtype, const CUtensorMap& tm, const SkArg
 cudaError_t launch_grouped_bn256(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
                                  bool cooperative, cudaStream_t stream);
 // E4M3 operands with per-128 x 128-block scales (args.scale_a / scale_b):
-// BLK_N = 128, single CTAs or CTA pairs (cluster_m 2, 256 x 128 tiles), 2-D
-// maps of 128-byte k-blocks.
+// BLK_N = 128, single CTAs or CTA pairs (cluster_m 2, 256 x 128 tiles).  The
+// operand maps view the rows as 16-bit elements (k/2 per row), 2-D and 3-D as
+// for the 16-bit BLK_N = 128 kernels.
 cudaError_t launch_f8(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
-                      const CUtensorMap& tc, const SkArgs& args, bool cooperative,
-                      cudaStream_t stream);
+                      const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
+                      const SkArgs& args, bool cooperative, cudaStream_t stream);
 cudaError_t launch_grouped_f8(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
                               bool cooperative, cudaStream_t stream);
 // Dynamic shared memory of one CTA; also sets the kernels' opt-in limit.

@@ -261,11 +261,12 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   if (count == 1) return launch_single(sv, s);
   const bool f8 = s.reqs[0].f8;  // a batch holds one input type
   const int ab_type = f8 ? SK_E4M3 : sv->ab_type;
+  // E4M3 problems are planned as 16-bit problems of k/2 (the same bytes per row)
   std::vector<int64_t> m(count), n(count), k(count);
   for (int i = 0; i < count; ++i) {
     m[i] = s.reqs[i].m;
     n[i] = s.reqs[i].n;
-    k[i] = s.reqs[i].k;
+    k[i] = f8 ? s.reqs[i].k / 2 : s.reqs[i].k;
   }
   // Small batches choose among every schedule (cached by composition); larger
   // ones take data-parallel waves, planned in O(count + grid) with no records.
@@ -305,11 +306,14 @@ int launch_slot(sk_server_s* sv, Slot& s) {
     const Request& r = s.reqs[i];
     sk::GroupProblem& pr = s.h_probs[i];
     std::memset(static_cast<void*>(&pr), 0, sizeof(pr));
-    st = cached_map(sv, &pr.tmA, 0, r.A, ab_type, r.m, r.k, sk::kBlkM);
-    if (st == SK_OK) st = cached_map(sv, &pr.tmB, 0, r.B, ab_type, r.n, r.k, gp.tile_n);
-    const bool use3d = !f8 && gp.tile_k == 2 * sk::kBlkK && r.k / sk::kBlkK >= 2;
-    if (st == SK_OK && use3d) st = cached_map(sv, &pr.tmA3, 1, r.A, ab_type, r.m, r.k, sk::kBlkM);
-    if (st == SK_OK && use3d) st = cached_map(sv, &pr.tmB3, 1, r.B, ab_type, r.n, r.k, gp.tile_n);
+    // E4M3 rows go to TMA as 16-bit rows of k/2 elements
+    const int tt = f8 ? SK_BF16 : ab_type;
+    const int64_t tk = f8 ? r.k / 2 : r.k;
+    st = cached_map(sv, &pr.tmA, 0, r.A, tt, r.m, tk, sk::kBlkM);
+    if (st == SK_OK) st = cached_map(sv, &pr.tmB, 0, r.B, tt, r.n, tk, gp.tile_n);
+    const bool use3d = gp.tile_n == 128 && tk / sk::kBlkK >= 2;
+    if (st == SK_OK && use3d) st = cached_map(sv, &pr.tmA3, 1, r.A, tt, r.m, tk, sk::kBlkM);
+    if (st == SK_OK && use3d) st = cached_map(sv, &pr.tmB3, 1, r.B, tt, r.n, tk, gp.tile_n);
     if (st != SK_OK) return st;
     if (!use3d) {
       pr.tmA3 = pr.tmA;

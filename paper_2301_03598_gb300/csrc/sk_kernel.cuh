@@ -38,21 +38,23 @@ constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 
 // Shared-memory stage ring per CTA: 192 KiB of operand stages.  A k-block is
-// one 128-byte row per operand row: 64 16-bit elements, or 128 FP8 elements
+// one 128-byte row per operand row: 64 16-bit elements, or 128 E4M3 elements
 // (F8).  A stage holds KD consecutive k-blocks (one MAC-loop iteration):
-// KD = 2 for 16-bit BLK_N = 128, whose 2-D stages are too small for the SM's
-// TMA path (a stage costs about as much as its bytes), KD = 1 otherwise.
+// KD = 2 for BLK_N = 128, whose 2-D stages are too small for the SM's TMA
+// path (a stage costs about as much as its bytes), KD = 1 for 256.
 //
 // F8 (E4M3 operands with one FP32 scale per 128 x 128 block of A and of B):
-// every k-block of 128 is one scale block, so the MMA warp writes each
-// k-block's product into one of kAccBufs rotating TMEM buffers and the
-// epilogue warps add it, times the block's two scales, into a running FP32
-// sum held in registers; the tile segment's sum goes to TMEM columns
-// [kAccBufs * BN, (kAccBufs + 1) * BN) for the common epilogue.
+// the host describes the operands to TMA as 16-bit rows of k/2 elements (the
+// same bytes), so loads and stages are the 16-bit path's.  Every k-block is
+// one scale block: the MMA warp writes each k-block's product into one of
+// kAccBufs rotating TMEM buffers and the epilogue warps add it, times the
+// block's two scales, into a running FP32 sum held in registers; the tile
+// segment's sum goes to TMEM columns [kAccBufs * BN, (kAccBufs + 1) * BN) for
+// the common epilogue.  A stage's second k-block beyond k (an odd count of
+// k-blocks) is zero-filled by TMA and carries scale 0.
 template <int BN, int CM, bool F8 = false>
 struct Cfg {
-  static constexpr int KD = (BN == 128 && !F8) ? 2 : 1;
-  static constexpr int kKElems = F8 ? 128 : kBlkK;  // elements of one k-block
+  static constexpr int KD = BN == 128 ? 2 : 1;
   static constexpr int kSubA = kBlkM * 128;          // one k-block of this CTA's 128 A rows
   static constexpr int kSubB = (BN / CM) * 128;      // one k-block of its BN/CM B rows
   static constexpr int kABytes = KD * kSubA;
@@ -633,8 +635,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               ready = tma_load_3d_pair_probe(stage_b(stage), pB3, fb, 0, brow, k0, empty_bar(next),
                                              next_phase ^ 1u);
             } else if constexpr (KD == 1) {
-              tma_load_2d_pair(stage_a(stage), pA, fb, k0 * C_::kKElems, tm * kBlkM);
-              ready = tma_load_2d_pair_probe(stage_b(stage), pB, fb, k0 * C_::kKElems, brow,
+              tma_load_2d_pair(stage_a(stage), pA, fb, k0 * kBlkK, tm * kBlkM);
+              ready = tma_load_2d_pair_probe(stage_b(stage), pB, fb, k0 * kBlkK, brow,
                                              empty_bar(next), next_phase ^ 1u);
             } else {
 #pragma unroll
@@ -652,8 +654,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               ready = tma_load_3d_probe(stage_b(stage), pB3, fb, 0, brow, k0, empty_bar(next),
                                         next_phase ^ 1u);
             } else if constexpr (KD == 1) {
-              tma_load_2d(stage_a(stage), pA, fb, k0 * C_::kKElems, tm * kBlkM);
-              ready = tma_load_2d_probe(stage_b(stage), pB, fb, k0 * C_::kKElems, brow, empty_bar(next),
+              tma_load_2d(stage_a(stage), pA, fb, k0 * kBlkK, tm * kBlkM);
+              ready = tma_load_2d_probe(stage_b(stage), pB, fb, k0 * kBlkK, brow, empty_bar(next),
                                         next_phase ^ 1u);
             } else {
 #pragma unroll
@@ -720,59 +722,71 @@ __global__ void __launch_bounds__(kThreads, 1)
         // with the previous k-block's last MMA, like `ready` for the stage)
         bool ready_acc = false;
         while (ok && cur.next(a, sg)) {
-          for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
-            if ((!ready_acc && !wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) ||
-                (!ready && !wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull))) {
+          for (int kb = sg.kb0; kb < sg.kb1 && ok; ++kb) {
+            if (!ready && !wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull)) {
               ok = false;
               break;
             }
-            tc_fence_after();
             int next = stage + 1;
             uint32_t next_phase = phase;
             if (next == S) {
               next = 0;
               next_phase ^= 1u;
             }
-            int nacc = acc + 1;
-            uint32_t nacc_phase = acc_phase;
-            if (nacc == NB) {
-              nacc = 0;
-              nacc_phase ^= 1u;
-            }
-            const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
-            const uint64_t adesc = smem_desc_sw128(stage_a(stage));
-            const uint64_t bdesc = smem_desc_sw128(stage_b(stage));
+            // the stage's KD k-blocks, each into its own product buffer
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              // 32 E4M3 elements (32 B) along K per MMA
-              if (kk == 3) {
-                uint32_t r;
-                if constexpr (kPair)
-                  r = mma_f8_pair_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
-                                         full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
-                else
-                  r = mma_f8_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
-                                    full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
-                ready = (r & 1u) != 0;
-                ready_acc = (r & 2u) != 0;
-              } else if constexpr (kPair) {
-                mma_f8_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
-              } else {
-                mma_f8(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
+            for (int j = 0; j < KD; ++j) {
+              if (!ready_acc && !wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) {
+                ok = false;
+                break;
               }
+              tc_fence_after();
+              int nacc = acc + 1;
+              uint32_t nacc_phase = acc_phase;
+              if (nacc == NB) {
+                nacc = 0;
+                nacc_phase ^= 1u;
+              }
+              const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+              const uint64_t adesc = smem_desc_sw128(stage_a(stage) + j * C_::kSubA);
+              const uint64_t bdesc = smem_desc_sw128(stage_b(stage) + j * C_::kSubB);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                // 32 E4M3 elements (32 B) along K per MMA
+                if (kk == 3) {
+                  // with the k-block's last MMA: probe the next product buffer
+                  // and (after the stage's last k-block) the next stage
+                  uint32_t r;
+                  if constexpr (kPair)
+                    r = mma_f8_pair_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
+                                           full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
+                  else
+                    r = mma_f8_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
+                                      full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
+                  if (j == KD - 1) ready = (r & 1u) != 0;
+                  ready_acc = (r & 2u) != 0;
+                } else if constexpr (kPair) {
+                  mma_f8_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
+                } else {
+                  mma_f8(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
+                }
+              }
+              // publishes the product (in both CTAs of a pair)
+              if constexpr (kPair)
+                mma_commit_pair_multicast(accf_bar(acc), kPairMask);
+              else
+                mma_commit(accf_bar(acc));
+              acc = nacc;
+              acc_phase = nacc_phase;
             }
-            // frees the stage and publishes the product (in both CTAs of a pair)
-            if constexpr (kPair) {
+            if (!ok) break;
+            // frees the stage once its MMAs finish
+            if constexpr (kPair)
               mma_commit_pair_multicast(empty_bar(stage), kPairMask);
-              mma_commit_pair_multicast(accf_bar(acc), kPairMask);
-            } else {
+            else
               mma_commit(empty_bar(stage));
-              mma_commit(accf_bar(acc));
-            }
             stage = next;
             phase = next_phase;
-            acc = nacc;
-            acc_phase = nacc_phase;
           }
         }
       }
@@ -909,19 +923,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int j = 0; j < 32 * kCpu; ++j) sum[i][j] = 0u;
         const float* sa = scale_a + static_cast<size_t>(tm) * ld_scale;
         const float* sb = scale_b + static_cast<size_t>(tn) * ld_scale;
+        // The segment's k-blocks: KD per MAC-loop iteration.  Those inside k
+        // (ld_scale of them per row of scales) carry scales; a stage's second
+        // k-block beyond k is all zeros and gets scale 0.
+        const int kq0 = kb0 * KD, kq1 = kb1 * KD;
+        const int kreal = min(kq1, ld_scale);
         // lane l holds the scale product of k-block first + l; the next 32
         // are loaded one window ahead
         auto window = [&](int first) {
-          const int kb = first + lane;
-          return kb < kb1 ? __ldg(sa + kb) * __ldg(sb + kb) : 0.0f;
+          const int kq = first + lane;
+          return kq < kreal ? __ldg(sa + kq) * __ldg(sb + kq) : 0.0f;
         };
-        float s_cur = window(kb0);
-        float s_nxt = kb0 + 32 < kb1 ? window(kb0 + 32) : 0.0f;
-        for (int kb = kb0; kb < kb1; ++kb) {
-          const int i = kb - kb0;
+        float s_cur = window(kq0);
+        float s_nxt = kq0 + 32 < kq1 ? window(kq0 + 32) : 0.0f;
+        for (int kq = kq0; kq < kq1; ++kq) {
+          const int i = kq - kq0;
           if (i > 0 && (i & 31) == 0) {
             s_cur = s_nxt;
-            if (kb + 32 < kb1) s_nxt = window(kb + 32);
+            if (kq + 32 < kq1) s_nxt = window(kq + 32);
           }
           const float sc = __shfl_sync(0xffffffffu, s_cur, i & 31);
           if (!wait_bar(accf_bar(acc), acc_phase, abort_flag, a, kAtEpiAccFull)) {
