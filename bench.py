@@ -844,13 +844,14 @@ def _plain_launches(sk, launch, plans, arrivals, pick):
     return np.array(lats), wall
 
 
-def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
+def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5, slots=4,
+                max_batch=64):
     """The serving workload: requests arrive as a Poisson process at each rate
     for `seconds`, each a GEMM drawn from 64 shapes (48 from the shape sweep's
     distribution, 16 from the grouped workload's), half of them BF16 and half
     block-scaled E4M3 (chosen per request), FP32 accumulate, BF16 out.  The
     continuous-batching server (batches of up to 64 requests of one input
-    type, 2 concurrent launch slots, 64 GB admission budget) against two
+    type, 4 concurrent launch slots, 64 GB admission budget) against two
     baselines: the same server with batches of one on one slot, and plain
     launches, one `sk_gemm` / `sk_gemm_scaled` per request on arrival from
     plans made per shape beforehand, on one stream, completion seen by
@@ -897,8 +898,8 @@ def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5):
                         rng.integers(0, 2, size=n_req).tolist()))
         req_flops = float(sum(flops[j] for j, _ in pick))
         res = {}
-        for name, mb, slots in (("server", 64, 2), ("per_request", 1, 1)):
-            srv = sk.sk_server_create("bf16", "bf16", max_batch=mb, slots=slots,
+        for name, mb, ns in (("server", max_batch, slots), ("per_request", 1, 1)):
+            srv = sk.sk_server_create("bf16", "bf16", max_batch=mb, slots=ns,
                                       hbm_budget_bytes=64 << 30)
             try:
                 # warm the launch path: every shape and input type once, alone

@@ -162,15 +162,18 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
  *   dimensions (each leading dimension times the element size a multiple of
  *   16 bytes).  C: device pointer, 16-byte aligned; read only if beta != 0.
  *   C may not alias A or B.
- * The launch is persistent (g <= SM count CTAs, co-resident by cooperative
- * launch whenever single CTAs wait on one another).  Two launch forms rely on
- * SMs freeing up instead, which holds within one stream but not while other
- * streams' kernels occupy SMs at the same time: a CTA-pair plan that splits
- * tiles (clustered, without the cooperative guarantee) and a launch with
- * programmatic dependent launch (its CTAs take SMs before the stream's
- * previous kernel has finished).  Under concurrent streams a fixup wait may
- * then run out (SK_ERR_TIMEOUT); plans for concurrent use should set
- * SK_ATTR_CLUSTER_M 1 and SK_ATTR_PDL 0.  Results are bitwise reproducible
+ * The launch is persistent (g <= SM count CTAs).  When the schedule splits
+ * tiles (SK_ATTR_WORKSPACE_BYTES > 0) its CTAs wait on one another, which
+ * needs all of them resident at once: single-CTA plans ask for it with the
+ * cooperative attribute, CTA-pair plans rely on SMs freeing up, which holds
+ * within one stream.  Across streams it does not: two split launches running
+ * at the same time can each hold SMs the other's waiting CTAs need (measured,
+ * with cooperative launches as well), and a programmatic-dependent launch
+ * takes SMs before its stream's previous kernel has finished.  A wait then
+ * runs out and the launch reports SK_ERR_TIMEOUT.  Callers running plans on
+ * several streams should order split launches so that one runs at a time
+ * (the serving loop chains them through an event) and set SK_ATTR_PDL 0 and
+ * SK_ATTR_CLUSTER_M 1 on those plans.  Results are bitwise reproducible
  * run to run for a given plan: the fixup adds the contributing CTAs' partials
  * in increasing CTA order.  Returns SK_ERR_INVALID for bad pointers,
  * SK_ERR_CUDA if the launch fails.
@@ -403,7 +406,9 @@ int sk_grouped_autotune_scaled(sk_grouped_t plan, const void* const* A, const vo
  * type (the server's 16-bit type, or E4M3 for sk_server_submit_scaled), and
  * while the operand bytes (size(A) + size(B) + mn * sizeof(C)) of all
  * admitted, unfinished requests stay within hbm_budget_bytes (a lone request
- * is always admitted).  Each batch is one grouped Stream-K launch: up to 4
+ * is always admitted).  Requests are batched only under backlog: while there
+ * are at least as many free slots as queued requests, each runs alone.  Each
+ * batch is one grouped Stream-K launch: up to 4
  * requests planned by the grouped model (SK_MODE_AUTO, schedules cached by
  * batch composition), larger batches as data-parallel waves.  The device
  * derives each CTA's segments from a per-problem walk table, so planning a

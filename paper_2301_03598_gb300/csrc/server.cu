@@ -146,6 +146,11 @@ struct sk_server_s {
     }
   };
   std::unordered_map<PlanKey, sk_plan_t, PlanHash> single_plans;
+  // A launch whose CTAs wait on one another (split tiles) must find every
+  // CTA of its grid resident, so it runs alone: it waits for every slot's
+  // work in flight, and every later launch waits for this event, recorded
+  // after it.  Data-parallel launches between split ones overlap freely.
+  cudaEvent_t split_done = nullptr;
   int device = 0;
   std::thread worker;
 };
@@ -222,6 +227,16 @@ int cached_map(sk_server_s* sv, CUtensorMap* out, int kind, const void* ptr, int
   return it->second.status;
 }
 
+// Orders a launch on slot s: after the last split launch, and (for a split
+// launch) after all other slots' work in flight.
+cudaError_t order_launch(sk_server_s* sv, Slot& s, bool split) {
+  cudaError_t e = cudaStreamWaitEvent(s.stream, sv->split_done, 0);
+  if (split)
+    for (Slot& o : sv->slots)
+      if (&o != &s && o.busy && e == cudaSuccess) e = cudaStreamWaitEvent(s.stream, o.done, 0);
+  return e;
+}
+
 // A lone request runs as a single GEMM from a plan cached per shape and input
 // type: its arguments travel by value with the launch, so nothing is uploaded
 // first.
@@ -235,24 +250,38 @@ int launch_single(sk_server_s* sv, Slot& s) {
     int st = sk_plan(&p, r.m, r.n, r.k, static_cast<sk_dtype>(ab_type),
                            static_cast<sk_dtype>(ab_type), static_cast<sk_dtype>(sv->c_type), SK_F32,
                            SK_ROW_MAJOR, SK_COL_MAJOR, SK_ROW_MAJOR, SK_MODE_AUTO);
-    // Launched as the grouped batches are: single CTAs, so that a split
-    // schedule launches cooperatively, and no programmatic dependent launch.
     // Other slots' kernels share the GPU, and CTAs that wait on their
-    // grid's peers must not depend on SMs those kernels hold: a clustered
-    // split launch has no co-residency guarantee, and a PDL launch puts CTAs
-    // on SMs before its stream's previous kernel has finished.
-    if (st == SK_OK) st = sk_plan_set(p, SK_ATTR_CLUSTER_M, 1);
+    // grid's peers must not depend on SMs those kernels hold.  So no
+    // programmatic dependent launch (it puts CTAs on SMs before its stream's
+    // previous kernel has finished), and a schedule that splits tiles runs
+    // on single CTAs (a cooperative launch; a CTA pair's own two CTAs are
+    // co-scheduled, which is all a data-parallel pair plan needs).
     if (st == SK_OK) st = sk_plan_set(p, SK_ATTR_PDL, 0);
+    int64_t ws = 0, cm = 1;
+    if (st == SK_OK) st = sk_plan_get(p, SK_ATTR_WORKSPACE_BYTES, &ws);
+    if (st == SK_OK) st = sk_plan_get(p, SK_ATTR_CLUSTER_M, &cm);
+    if (st == SK_OK && ws > 0 && cm == 2) st = sk_plan_set(p, SK_ATTR_CLUSTER_M, 1);
     if (st != SK_OK) {
       sk_plan_destroy(p);
       return st;
     }
     it = sv->single_plans.emplace(key, p).first;
   }
+  int64_t ws = 0;
+  sk_plan_get(it->second, SK_ATTR_WORKSPACE_BYTES, &ws);
+  const bool split = ws > 0;
+  {
+    const cudaError_t e = order_launch(sv, s, split);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   s.h_status[0] = 0;
   int st = sk::gemm_reporting(it->second, r.A, r.B, r.scale_a, r.scale_b, r.C, r.alpha, r.beta,
                               s.stream, s.d_status);
   if (st != SK_OK) return st;
+  if (split) {
+    const cudaError_t e = cudaEventRecord(sv->split_done, s.stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   return cuda_status(cudaEventRecord(s.done, s.stream));
 }
 
@@ -356,10 +385,13 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   a.gstart = s.d_start;
   a.gprobs = s.d_probs;
   const CUtensorMap& any = s.h_probs[0].tmA;
+  e = order_launch(sv, s, split);
+  if (e != cudaSuccess) return cuda_status(e);
   s.h_status[0] = 0;
   e = f8                ? sk::launch_grouped_f8(sv->c_type, any, a, split, s.stream)
       : gp.tile_n == 256 ? sk::launch_grouped_bn256(sv->c_type, any, a, split, s.stream)
                          : sk::launch_grouped_bn128(sv->c_type, any, a, split, s.stream);
+  if (e == cudaSuccess && split) e = cudaEventRecord(sv->split_done, s.stream);
   if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
   if (e != cudaSuccess) return cuda_status(e);
   return SK_OK;
@@ -416,7 +448,14 @@ void worker_loop(sk_server_s* sv) {
                     : sv->pending[1].empty() ? 0
                     : (sv->pending[1].front().id < sv->pending[0].front().id ? 1 : 0);
       std::deque<Request>& q = sv->pending[t];
-      while (!q.empty() && static_cast<int>(s.reqs.size()) < sv->max_batch) {
+      // Batch only under backlog: with as many free slots as queued
+      // requests each runs alone (a single launch); otherwise the queue is
+      // spread over the free slots.
+      int free_slots = 0;
+      for (const Slot& o : sv->slots) free_slots += o.busy ? 0 : 1;
+      const int queued = static_cast<int>(q.size());
+      const int cap = std::min(sv->max_batch, (queued + free_slots - 1) / free_slots);
+      while (!q.empty() && static_cast<int>(s.reqs.size()) < cap) {
         const Request& r = q.front();
         const bool nothing_else = s.reqs.empty() && sv->inflight_bytes == 0;
         if (!nothing_else && sv->inflight_bytes + s.bytes + r.bytes > sv->budget) break;
@@ -496,11 +535,17 @@ int sk_server_create(sk_server_t* out, sk_dtype ab_type, sk_dtype c_type, int ma
   sv->num_sms = sms;
   sv->budget = hbm_budget_bytes;
   sv->device = dev;
+  e = cudaEventCreateWithFlags(&sv->split_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    delete sv;
+    return cuda_status(e);
+  }
   sv->slots.resize(static_cast<size_t>(slots));
   for (Slot& s : sv->slots) {
     e = alloc_slot(s, max_batch, sms);
     if (e != cudaSuccess) {
       for (Slot& t : sv->slots) free_slot(t);
+      cudaEventDestroy(sv->split_done);
       delete sv;
       return cuda_status(e);
     }
@@ -626,6 +671,7 @@ int sk_server_destroy(sk_server_t sv) {
     free_slot(s);
   }
   for (auto& kv : sv->single_plans) sk_plan_destroy(kv.second);
+  if (sv->split_done) cudaEventDestroy(sv->split_done);
   delete sv;
   return SK_OK;
 }

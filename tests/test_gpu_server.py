@@ -122,3 +122,26 @@ def test_server_same_shape_on_concurrent_slots():
     for C in Cs:
         check_bound(inputs.widen(C.cpu()), C64, bd, "concurrent slots")
         assert torch.equal(C.cpu(), first)   # one plan per slot: the same schedule
+
+
+def test_server_many_slots_split_launches():
+    """Eight slots and lone requests of split-schedule shapes: split launches
+    on different slots run one at a time, so none of their waits runs out."""
+    shapes = [(384, 384, 4096), (256, 256, 8192), (128, 1000, 3072)]
+    probs = [Problem(m, n, k, "bf16", "f32", "normal", seed=70 + i) for i, (m, n, k) in enumerate(shapes)]
+    dev = [(p.A.cuda(), p.B.cuda()) for p in probs]
+    outs = [[torch.zeros(p.m, p.n, dtype=torch.float32, device="cuda") for _ in range(12)] for p in probs]
+    with sk.sk_server_create("bf16", "f32", max_batch=1, slots=8) as server:
+        tickets = []
+        for r in range(12):
+            for (A, B), Cs in zip(dev, outs):
+                tickets.append(server.submit(A, B, Cs[r]))
+        for t in tickets:
+            st, _ = server.wait(t)
+            assert st == sk.SK_OK
+    torch.cuda.synchronize()
+    for p, Cs in zip(probs, outs):
+        C64, absAB = p.oracle(1.0, 0.0)
+        bd = bound(p.k, 1.0, 0.0, absAB, C64, inputs.widen(p.Cin), "f32")
+        for C in Cs:
+            check_bound(inputs.widen(C.cpu()), C64, bd, f"8 slots {p.m}x{p.n}x{p.k}")
