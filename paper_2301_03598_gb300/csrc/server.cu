@@ -127,22 +127,20 @@ struct sk_server_s {
     int status;  // SK_OK, or the encode failure (kind 2: 1 = TMA store possible)
   };
   std::unordered_map<MapKey, MapEntry, MapHash> map_cache;
-  // single-GEMM plans for lone requests, per (m, n, k, input type, slot):
-  // a plan owns its fixup workspace, so concurrent slots never share one;
+  // single-GEMM plans for lone requests, per (m, n, k, input type); they all
+  // run on the fifo stream, so their workspaces are never used concurrently;
   // used by the worker only, destroyed with the server
   struct PlanKey {
     int64_t m, n, k;
-    int32_t ab, slot;
-    bool operator==(const PlanKey& o) const {
-      return m == o.m && n == o.n && k == o.k && ab == o.ab && slot == o.slot;
-    }
+    int32_t ab;
+    bool operator==(const PlanKey& o) const { return m == o.m && n == o.n && k == o.k && ab == o.ab; }
   };
   struct PlanHash {
     size_t operator()(const PlanKey& k) const {
       uint64_t h = static_cast<uint64_t>(k.m) * 0x9E3779B97F4A7C15ull;
       h ^= static_cast<uint64_t>(k.n) * 0xC2B2AE3D27D4EB4Full + (h << 6) + (h >> 2);
       h ^= static_cast<uint64_t>(k.k) * 0x165667B19E3779F9ull + (h << 6) + (h >> 2);
-      return static_cast<size_t>(h ^ static_cast<uint64_t>(k.ab * 64 + k.slot));
+      return static_cast<size_t>(h ^ static_cast<uint64_t>(k.ab));
     }
   };
   std::unordered_map<PlanKey, sk_plan_t, PlanHash> single_plans;
@@ -151,6 +149,10 @@ struct sk_server_s {
   // work in flight, and every later launch waits for this event, recorded
   // after it.  Data-parallel launches between split ones overlap freely.
   cudaEvent_t split_done = nullptr;
+  // Lone requests run on one stream in arrival order, as plain launches do
+  // (with their plans' own launch form: programmatic dependent launch, CTA
+  // pairs); batches run on their slots' streams.
+  cudaStream_t fifo = nullptr;
   int device = 0;
   std::thread worker;
 };
@@ -227,40 +229,33 @@ int cached_map(sk_server_s* sv, CUtensorMap* out, int kind, const void* ptr, int
   return it->second.status;
 }
 
-// Orders a launch on slot s: after the last split launch, and (for a split
-// launch) after all other slots' work in flight.
-cudaError_t order_launch(sk_server_s* sv, Slot& s, bool split) {
-  cudaError_t e = cudaStreamWaitEvent(s.stream, sv->split_done, 0);
+// Orders a launch of slot s on `stream`: after the last split launch, and
+// (for a split launch) after all other slots' work in flight.
+cudaError_t order_launch(sk_server_s* sv, Slot& s, cudaStream_t stream, bool split) {
+  cudaError_t e = cudaStreamWaitEvent(stream, sv->split_done, 0);
   if (split)
     for (Slot& o : sv->slots)
-      if (&o != &s && o.busy && e == cudaSuccess) e = cudaStreamWaitEvent(s.stream, o.done, 0);
+      if (&o != &s && o.busy && e == cudaSuccess) e = cudaStreamWaitEvent(stream, o.done, 0);
   return e;
 }
 
 // A lone request runs as a single GEMM from a plan cached per shape and input
-// type: its arguments travel by value with the launch, so nothing is uploaded
-// first.
+// type, on the fifo stream: its arguments travel by value with the launch, so
+// nothing is uploaded first.
 int launch_single(sk_server_s* sv, Slot& s) {
   const Request& r = s.reqs[0];
   const int ab_type = r.f8 ? SK_E4M3 : sv->ab_type;
-  const sk_server_s::PlanKey key{r.m, r.n, r.k, ab_type, static_cast<int32_t>(&s - sv->slots.data())};
+  const sk_server_s::PlanKey key{r.m, r.n, r.k, ab_type};
   auto it = sv->single_plans.find(key);
   if (it == sv->single_plans.end()) {
     sk_plan_t p = nullptr;
+    // The plan's own launch form (CTA pairs, programmatic dependent launch)
+    // is safe here: within one stream a kernel's CTAs only wait for SMs that
+    // earlier kernels of the stream free on their own, and a split launch
+    // runs alone with respect to the slots' streams (order_launch).
     int st = sk_plan(&p, r.m, r.n, r.k, static_cast<sk_dtype>(ab_type),
-                           static_cast<sk_dtype>(ab_type), static_cast<sk_dtype>(sv->c_type), SK_F32,
-                           SK_ROW_MAJOR, SK_COL_MAJOR, SK_ROW_MAJOR, SK_MODE_AUTO);
-    // Other slots' kernels share the GPU, and CTAs that wait on their
-    // grid's peers must not depend on SMs those kernels hold.  So no
-    // programmatic dependent launch (it puts CTAs on SMs before its stream's
-    // previous kernel has finished), and a schedule that splits tiles runs
-    // on single CTAs (a cooperative launch; a CTA pair's own two CTAs are
-    // co-scheduled, which is all a data-parallel pair plan needs).
-    if (st == SK_OK) st = sk_plan_set(p, SK_ATTR_PDL, 0);
-    int64_t ws = 0, cm = 1;
-    if (st == SK_OK) st = sk_plan_get(p, SK_ATTR_WORKSPACE_BYTES, &ws);
-    if (st == SK_OK) st = sk_plan_get(p, SK_ATTR_CLUSTER_M, &cm);
-    if (st == SK_OK && ws > 0 && cm == 2) st = sk_plan_set(p, SK_ATTR_CLUSTER_M, 1);
+                     static_cast<sk_dtype>(ab_type), static_cast<sk_dtype>(sv->c_type), SK_F32,
+                     SK_ROW_MAJOR, SK_COL_MAJOR, SK_ROW_MAJOR, SK_MODE_AUTO);
     if (st != SK_OK) {
       sk_plan_destroy(p);
       return st;
@@ -271,18 +266,18 @@ int launch_single(sk_server_s* sv, Slot& s) {
   sk_plan_get(it->second, SK_ATTR_WORKSPACE_BYTES, &ws);
   const bool split = ws > 0;
   {
-    const cudaError_t e = order_launch(sv, s, split);
+    const cudaError_t e = order_launch(sv, s, sv->fifo, split);
     if (e != cudaSuccess) return cuda_status(e);
   }
   s.h_status[0] = 0;
   int st = sk::gemm_reporting(it->second, r.A, r.B, r.scale_a, r.scale_b, r.C, r.alpha, r.beta,
-                              s.stream, s.d_status);
+                              sv->fifo, s.d_status);
   if (st != SK_OK) return st;
   if (split) {
-    const cudaError_t e = cudaEventRecord(sv->split_done, s.stream);
+    const cudaError_t e = cudaEventRecord(sv->split_done, sv->fifo);
     if (e != cudaSuccess) return cuda_status(e);
   }
-  return cuda_status(cudaEventRecord(s.done, s.stream));
+  return cuda_status(cudaEventRecord(s.done, sv->fifo));
 }
 
 int launch_slot(sk_server_s* sv, Slot& s) {
@@ -385,7 +380,7 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   a.gstart = s.d_start;
   a.gprobs = s.d_probs;
   const CUtensorMap& any = s.h_probs[0].tmA;
-  e = order_launch(sv, s, split);
+  e = order_launch(sv, s, s.stream, split);
   if (e != cudaSuccess) return cuda_status(e);
   s.h_status[0] = 0;
   e = f8                ? sk::launch_grouped_f8(sv->c_type, any, a, split, s.stream)
@@ -536,7 +531,9 @@ int sk_server_create(sk_server_t* out, sk_dtype ab_type, sk_dtype c_type, int ma
   sv->budget = hbm_budget_bytes;
   sv->device = dev;
   e = cudaEventCreateWithFlags(&sv->split_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->fifo, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
+    if (sv->split_done) cudaEventDestroy(sv->split_done);
     delete sv;
     return cuda_status(e);
   }
@@ -546,6 +543,7 @@ int sk_server_create(sk_server_t* out, sk_dtype ab_type, sk_dtype c_type, int ma
     if (e != cudaSuccess) {
       for (Slot& t : sv->slots) free_slot(t);
       cudaEventDestroy(sv->split_done);
+      cudaStreamDestroy(sv->fifo);
       delete sv;
       return cuda_status(e);
     }
@@ -666,10 +664,12 @@ int sk_server_destroy(sk_server_t sv) {
   }
   sv->cv.notify_all();
   if (sv->worker.joinable()) sv->worker.join();
+  if (sv->fifo) cudaStreamSynchronize(sv->fifo);
   for (Slot& s : sv->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
     free_slot(s);
   }
+  if (sv->fifo) cudaStreamDestroy(sv->fifo);
   for (auto& kv : sv->single_plans) sk_plan_destroy(kv.second);
   if (sv->split_done) cudaEventDestroy(sv->split_done);
   delete sv;
