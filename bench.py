@@ -436,6 +436,20 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate_replicas(med, total_ms, flops, world, all_reduce_max=None):
+    """Whole-job figures of `world` independent replicas (weak scaling): each
+    shape's time and the step total are the maxima over ranks (the slowest
+    replica sets the pace), and the value is the geo-mean TFLOP/s of those
+    times times `world`.  all_reduce_max maps a float64 array to its
+    elementwise maximum over ranks.  Returns (med, total_ms, value)."""
+    med = np.asarray(med, np.float64)
+    if world > 1:
+        arr = np.asarray(all_reduce_max(np.append(med, total_ms)), np.float64)
+        med, total_ms = arr[:-1], float(arr[-1])
+    tflops = np.asarray(flops, np.float64) / (med * 1e-3) / 1e12
+    return med, total_ms, geomean(tflops) * world
+
+
 def reference_arm(args):
     """The oracle as the reference: FP64 CPU GEMM on a bounded sample per step."""
     rank, world, local = dist_env()
@@ -531,16 +545,15 @@ def ours_arm(args):
     peak = peaks["bf16_tflops_sustained"]
 
     # whole-job aggregation over replicas: per-shape max time over ranks
-    med = H["_med"]
-    total_ms = H["ms_per_step"] * args.steps
-    if world > 1:
+    def all_reduce_max(arr):
         import torch.distributed as dist
-        t = torch.tensor(np.append(med, total_ms), dtype=torch.float64, device="cuda")
+        t = torch.tensor(arr, dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        arr = t.cpu().numpy()
-        med, total_ms = arr[:-1], float(arr[-1])
+        return t.cpu().numpy()
+
+    med, total_ms, value = aggregate_replicas(H["_med"], H["ms_per_step"] * args.steps, flops,
+                                              world, all_reduce_max)
     tflops = flops / (med * 1e-3) / 1e12
-    value = geomean(tflops) * world
 
     e2e = None
     if not args.no_e2e:
