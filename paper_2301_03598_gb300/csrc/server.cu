@@ -161,6 +161,7 @@ namespace {
 
 constexpr size_t kPlanCacheEntries = 4096;
 constexpr size_t kMapCacheEntries = 16384;
+constexpr size_t kSinglePlanCap = 256;  // cached single-GEMM plans (each owns a workspace)
 constexpr int kModelledBatch = 4;  // batches up to this size get the full model
 constexpr int kIdleSpinUs = 200;  // idle worker: spin before sleeping
 
@@ -248,6 +249,14 @@ int launch_single(sk_server_s* sv, Slot& s) {
   const sk_server_s::PlanKey key{r.m, r.n, r.k, ab_type};
   auto it = sv->single_plans.find(key);
   if (it == sv->single_plans.end()) {
+    if (sv->single_plans.size() >= kSinglePlanCap) {
+      // every plan's launches are on the fifo stream: once it has drained,
+      // none is in use
+      const cudaError_t e = cudaStreamSynchronize(sv->fifo);
+      if (e != cudaSuccess) return cuda_status(e);
+      for (auto& kv : sv->single_plans) sk_plan_destroy(kv.second);
+      sv->single_plans.clear();
+    }
     sk_plan_t p = nullptr;
     // The plan's own launch form (CTA pairs, programmatic dependent launch)
     // is safe here: within one stream a kernel's CTAs only wait for SMs that
