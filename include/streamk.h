@@ -407,15 +407,19 @@ int sk_grouped_autotune_scaled(sk_grouped_t plan, const void* const* A, const vo
  * while the operand bytes (size(A) + size(B) + mn * sizeof(C)) of all
  * admitted, unfinished requests stay within hbm_budget_bytes (a lone request
  * is always admitted).  Requests are batched only under backlog: while there
- * are at least as many free slots as queued requests, each runs alone.  Each
- * batch is one grouped Stream-K launch: up to 4
- * requests planned by the grouped model (SK_MODE_AUTO, schedules cached by
- * batch composition), larger batches as data-parallel waves.  The device
- * derives each CTA's segments from a per-problem walk table, so planning a
- * batch costs O(batch + SMs) on the host.  A batch is launched on its slot's
- * stream; slots run concurrently, so a batch admitted while others are in
- * flight overlaps them.  Problem and walk tables and fixup workspaces live
- * on the device, preallocated per slot.
+ * are at least as many free slots as queued requests, each runs alone.  A
+ * lone request is one single-GEMM launch from a plan cached per shape and
+ * input type (at most 256 plans), on one stream shared by all lone requests,
+ * in arrival order.  A batch is one grouped Stream-K launch on its slot's own
+ * stream: up to 4 requests planned by the grouped model (SK_MODE_AUTO,
+ * schedules cached by batch composition), larger batches as data-parallel
+ * waves; the device derives each CTA's segments from a per-problem walk
+ * table, so planning a batch costs O(batch + SMs) on the host.  Launches of
+ * different slots overlap on the device, except that a launch whose schedule
+ * splits tiles runs alone (it waits for all work in flight and later
+ * launches wait for it).  A failing launch reports through a mapped pinned
+ * word, so completion needs no copy back.  Problem and walk tables and fixup
+ * workspaces live on the device, preallocated per slot.
  *
  * sk_server_create: slots 1..8 concurrent batches, max_batch 1..4096.
  * sk_server_submit: queue one request; *ticket identifies it.  k must be a
