@@ -857,7 +857,7 @@ def _plain_launches(sk, launch, plans, arrivals, pick):
     return np.array(lats), wall
 
 
-def run_serving(rates=(5000, 20000, 40000), seconds=0.5, seed=2301_03598 + 5, slots=4,
+def run_serving(rates=(2000, 5000, 20000, 40000, 50000), seconds=0.5, seed=2301_03598 + 5, slots=4,
                 max_batch=64):
     """The serving workload: requests arrive as a Poisson process at each rate
     for `seconds`, each a GEMM drawn from 64 shapes (48 from the shape sweep's
