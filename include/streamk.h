@@ -110,7 +110,7 @@ typedef enum {
   SK_ATTR_TRACE_INTS = 31,   /* get: int32 entries sk_gemm_traced needs */
   SK_ATTR_TRACE_CAP = 32,    /* get: trace records per CTA */
   SK_ATTR_CTAS = 33,         /* get: CTAs launched (grid * cluster_m) */
-  SK_ATTR_SEGMENTS = 34      /* get (grouped plans): segment records of the schedule */
+  SK_ATTR_SEGMENTS = 34      /* get (grouped plans): segments of the schedule */
 } sk_attr;
 
 typedef struct sk_plan_s* sk_plan_t;
@@ -318,10 +318,11 @@ const char* sk_status_string(int status);
  *
  * sk_grouped_plan: count >= 1 problems, m/n/k host arrays of count entries
  *   (each >= 1, k a multiple of 8 so that dense 16-bit rows are 16-byte
- *   multiples as TMA requires); mode SK_MODE_AUTO (the model picks data-parallel, the
- *   two-tile hybrid or basic Stream-K, and the tile width), SK_MODE_DP,
- *   SK_MODE_SK or SK_MODE_HYBRID.  The plan owns its device schedule (one
- *   32-byte record per segment), problem table, workspace and status words.
+ *   multiples as TMA requires; 16 for E4M3); mode SK_MODE_AUTO (the model picks
+ *   data-parallel, the two-tile hybrid or basic Stream-K, and the tile width),
+ *   SK_MODE_DP, SK_MODE_SK or SK_MODE_HYBRID.  The plan owns its device walk
+ *   table (64 bytes per problem and 8 per CTA, from which each CTA derives its
+ *   segments), problem table, workspace and status words.
  *   Returns SK_ERR_INVALID / SK_ERR_UNSUPPORTED for bad arguments,
  *   SK_ERR_DEVICE off sm_103a, SK_ERR_CUDA / SK_ERR_NOMEM on allocation.
  * sk_grouped_gemm: A, B, C are host arrays of count device pointers (16-byte

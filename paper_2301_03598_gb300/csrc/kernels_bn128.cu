@@ -64,7 +64,7 @@ cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, cons
                         : launch_cm<1>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream);
 }
 
-// Grouped launches: single CTAs, segment records and problem table in args
+// Grouped launches: single CTAs, the walk table and problem table in args
 // (the tensor-map parameters are not read).
 template <typename TC>
 static cudaError_t launch_grouped_one(const CUtensorMap& tm, const SkArgs& args, bool cooperative,

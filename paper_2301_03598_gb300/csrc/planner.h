@@ -25,9 +25,10 @@ int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]);
 void model_coefficients(int tile_n, int cluster_m, double out[5]);
 int64_t workspace_bytes_for(int grid, int tile_n);
 
-// A grouped launch's schedule: per-CTA segment records (CTA x owns
-// segs[start[x] .. start[x+1])) over the problems' concatenated iteration
-// space, single CTAs, one tile width for all problems.
+// A grouped launch's schedule over the problems' concatenated iteration space
+// (single CTAs, one tile width for all problems): per-CTA segment records
+// (CTA x owns segs[start[x] .. start[x+1])) for the model and the schedule
+// query, and the walk table the device derives the same segments from.
 struct GroupPlan {
   int mode = 0, tile_n = 0, tile_k = 0, grid = 0, max_segments = 1;
   int64_t tiles = 0, sk_tiles = 0, sk_iters = 0, workspace_bytes = 0;

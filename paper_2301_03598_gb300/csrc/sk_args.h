@@ -58,8 +58,9 @@ __device__ __forceinline__ uint32_t fast_div(uint32_t n, FastDiv f) {
 #endif
 
 // Grouped GEMM: one launch runs several problems as one Stream-K iteration
-// space.  The host planner lays the schedule out as per-CTA lists of segment
-// records; the kernel walks its list instead of deriving segments.
+// space.  The host planner evaluates candidate schedules as per-CTA lists of
+// segment records (also what the schedule query returns); the kernel derives
+// the same segments from the walk table below.
 struct alignas(16) GroupSeg {
   int32_t problem;
   int32_t tile;        // the problem's tile index (its raster order)
