@@ -10,13 +10,21 @@
 //   warp 0      TMA producer: streams the A and B fragments of every MAC-loop
 //               iteration (Algorithm 3's LoadFragment) into an S-stage ring of
 //               128-byte-swizzled shared-memory tiles.
-//   warp 1      TMEM allocator and MMA issuer: one thread issues BLK_K/16
-//               tcgen05.mma per iteration into one of two TMEM accumulators.
-//   warps 2..9  epilogue: per tile segment, either spill the FP32 partial sums
-//               to this CTA's workspace slot and Signal (segment does not start
-//               the tile), or Wait for the contributing CTAs in increasing order
-//               and add their partials (tile started here, not finished here),
-//               then compute alpha*acc + beta*C and store the tile.
+//   warp 1      TMEM allocator and MMA issuer: one thread issues four
+//               tcgen05.mma per 128-byte k-block into one of two TMEM
+//               accumulators (E4M3: one product per k-block into one of three
+//               rotating buffers).
+//   warps 2..9  epilogue: (E4M3: first sums the k-block products times their
+//               block scales in FP32) per tile segment, either spill the FP32
+//               partial sums to this CTA's workspace slot and Signal (segment
+//               does not start the tile), or Wait for the contributing CTAs in
+//               increasing order and add their partials (tile started here, not
+//               finished here), then compute alpha*acc + beta*C and store the
+//               tile.
+//
+// A grouped launch walks the problems' concatenated iteration space with the
+// same roles, reading each problem's operands, output and scales from device
+// tables.
 //
 // Every wait is bounded by SkArgs::timeout_ns; on expiry the kernel records a
 // status in SkArgs::err and all roles unwind, drain their in-flight TMA loads
