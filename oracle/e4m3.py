@@ -37,17 +37,28 @@ def decode(codes) -> np.ndarray:
     return np.where((e == 15) & (f == 7), np.nan, out)
 
 
+def dequantize_rows(codes, row_scales) -> np.ndarray:
+    """Exact float64 values of r rows taken from an E4M3 operand: ``codes`` is
+    r x cols, and row i of ``row_scales`` [r, ceil(cols/128)] is the scale row
+    of the 128-row block that row i came from."""
+    q = decode(codes)
+    s = np.asarray(row_scales, dtype=np.float64)
+    rows, cols = q.shape
+    if s.shape != (rows, -(-cols // BLOCK)):
+        raise ValueError(f"row scales shape {s.shape}, expected {(rows, -(-cols // BLOCK))}")
+    return q * np.repeat(s, BLOCK, axis=1)[:, :cols]
+
+
 def dequantize(codes, scales) -> np.ndarray:
     """Exact float64 values of a rows x cols E4M3 operand whose 128 x 128
     blocks carry the FP32 scales ``scales`` [ceil(rows/128), ceil(cols/128)]."""
-    q = decode(codes)
-    s = np.asarray(scales, dtype=np.float64)
-    rows, cols = q.shape
+    codes = np.asarray(codes, dtype=np.uint8)
+    s = np.asarray(scales)
+    rows, cols = codes.shape
     nbr, nbc = -(-rows // BLOCK), -(-cols // BLOCK)
     if s.shape != (nbr, nbc):
         raise ValueError(f"scales shape {s.shape}, expected {(nbr, nbc)}")
-    full = np.repeat(np.repeat(s, BLOCK, axis=0), BLOCK, axis=1)[:rows, :cols]
-    return q * full
+    return dequantize_rows(codes, s[np.arange(rows) // BLOCK])
 
 
 def gemm(qA, sA, qB, sB, alpha: float = 1.0, beta: float = 0.0, C_in=None, nthreads: int = 0):
@@ -61,8 +72,23 @@ def gemm(qA, sA, qB, sB, alpha: float = 1.0, beta: float = 0.0, C_in=None, nthre
 
 def gemm_entries(rows, cols, qA, sA, qB, sB, alpha: float = 1.0, beta: float = 0.0, C_in=None,
                  nthreads: int = 0):
-    """Entries (rows[e], cols[e]) of the block-scaled GEMM and of |Adq| @ |Bdq|^T."""
+    """Entries (rows[e], cols[e]) of the block-scaled GEMM and of |Adq| @ |Bdq|^T.
+    For operands too large to bring to the host, pass only the referenced rows
+    of qA and qB with ``dequantize_rows``' per-row scales through
+    ``gemm_entries_rows``."""
     from . import gemm_entries as entries64
     A = dequantize(qA, sA)
     B = dequantize(qB, sB)
     return entries64(rows, cols, A, B.T, alpha, beta, C_in, nthreads)
+
+
+def gemm_entries_rows(ri, ci, qA_rows, sA_rows, qB_rows, sB_rows, alpha: float = 1.0,
+                      beta: float = 0.0, C_in=None, nthreads: int = 0):
+    """Entries (ri[e], ci[e]) of the block-scaled GEMM of row subsets: qA_rows
+    (r_a x k) and qB_rows (r_b x k) are rows taken from A and B, sA_rows and
+    sB_rows their per-row scale rows (see ``dequantize_rows``); ri and ci index
+    into the taken rows."""
+    from . import gemm_entries as entries64
+    A = dequantize_rows(qA_rows, sA_rows)
+    B = dequantize_rows(qB_rows, sB_rows)
+    return entries64(ri, ci, A, B.T, alpha, beta, C_in, nthreads)

@@ -151,25 +151,35 @@ def test_f8_entry_point_contract():
         plan16.destroy()
 
 
-def test_f8_large_sampled_entries():
-    # 4096 x 4096 x 8192 on device-drawn operands; 4,096 sampled outputs
+@pytest.mark.parametrize("mode,attrs", [("auto", {}), ("sk", {"grid": 151})])
+def test_f8_large_sampled_entries(mode, attrs):
+    # 4096 x 4096 x 8192 on device-drawn operands: 4,096 sampled outputs plus
+    # entries along tile edges (Stream-K seams, ragged-free but split tiles)
     m, n, k = 4096, 4096, 8192
     qA, sA = inputs.device_e4m3_matrix(m, k, 31, "cuda")
     qB, sB = inputs.device_e4m3_matrix(n, k, 32, "cuda")
-    C = torch.empty(m, n, dtype=torch.bfloat16, device="cuda")
-    plan = sk.sk_plan(m, n, k, "e4m3", "e4m3", "bf16")
+    C = torch.full((m, n), float("nan"), dtype=torch.bfloat16, device="cuda")
+    plan = sk.sk_plan(m, n, k, "e4m3", "e4m3", "bf16", mode=mode)
     try:
+        for key, v in attrs.items():
+            plan.set(key, v)
         sk.sk_gemm_scaled(plan, qA, qB, sA, sB, C)
         assert sk.sk_last_error(plan)[0] == sk.SK_OK
+        info = plan.info()
     finally:
         plan.destroy()
     g = np.random.Generator(np.random.PCG64(5))
-    rows, cols = g.integers(0, m, 4096), g.integers(0, n, 4096)
+    rows, cols = list(g.integers(0, m, 4096)), list(g.integers(0, n, 4096))
+    for e in (0, 127, 128, 2047, 2048, m - 1):
+        rows += [e] * 64 + list(g.integers(0, m, 64))
+        cols += list(g.integers(0, n, 64)) + [e] * 64
+    rows, cols = np.array(rows, np.int64), np.array(cols, np.int64)
     want, absAB = e4m3.gemm_entries(rows, cols, qA.cpu().numpy(), sA.cpu().numpy(),
                                     qB.cpu().numpy(), sB.cpu().numpy())
     got = C.cpu()[torch.from_numpy(rows), torch.from_numpy(cols)]
     b = bound(k, 1.0, 0.0, absAB, want, None, "bf16")
-    check_bound(inputs.widen(got), want, b, "e4m3 4096x4096x8192 sampled")
+    check_bound(inputs.widen(got), want, b,
+                f"e4m3 4096x4096x8192 sampled ({info['mode']}, g {info['grid']})")
 
 
 GROUP = [(300, 500, 704), (128, 128, 4096), (1000, 200, 128), (64, 520, 1024), (17, 1000, 304),

@@ -127,3 +127,26 @@ def test_quantizer_scales_and_range():
     assert rel.max() <= 2.0 ** -4 + 1e-12
     q0, s0 = inputs.e4m3_quantize(torch.zeros(130, 10))
     assert (s0.numpy() == 1.0).all() and (q0.numpy() == 0).all()
+
+
+def test_row_subset_entries_equal_full_gemm_entries():
+    # rows taken across 128-row blocks (with their blocks' scale rows) give the
+    # same entries as the whole operands, and each taken value is
+    # scale * decode(code) element by element
+    m, n, k = 300, 260, 400
+    qA, sA = inputs.host_e4m3_matrix(m, k, "normal", 31)
+    qB, sB = inputs.host_e4m3_matrix(n, k, "normal", 32)
+    qA, sA, qB, sB = qA.numpy(), sA.numpy(), qB.numpy(), sB.numpy()
+    ra = np.array([0, 127, 128, 255, 256, 299])
+    rb = np.array([3, 128, 259])
+    vals = e4m3.decode(np.arange(256, dtype=np.uint8))
+    sub = e4m3.dequantize_rows(qA[ra], sA[ra // 128])
+    for i, r in enumerate(ra):
+        for l in (0, 127, 128, 399):
+            assert sub[i, l] == float(sA[r // 128, l // 128]) * vals[qA[r, l]]
+    ri = np.array([0, 1, 2, 3, 4, 5, 5])
+    ci = np.array([0, 1, 2, 0, 1, 2, 0])
+    got, gabs = e4m3.gemm_entries_rows(ri, ci, qA[ra], sA[ra // 128], qB[rb], sB[rb // 128],
+                                       alpha=0.5)
+    want, wabs = e4m3.gemm_entries(ra[ri], rb[ci], qA, sA, qB, sB, alpha=0.5)
+    assert np.array_equal(got, want) and np.array_equal(gabs, wabs)
