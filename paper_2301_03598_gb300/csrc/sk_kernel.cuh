@@ -1067,8 +1067,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (role == kRoleOwner) {
           // Wait(flags[y][quarter][u]) for every peer y: the unit this warp
           // adds next, so the fixup overlaps the peers' remaining spills.
-          for (int y = peer_first; y <= peer_last && !fail; y += CM)
+          // The lanes poll the peers' flags at once (lane l takes peers l,
+          // l + 32, ...), one acquire round trip instead of one per peer; the
+          // warp barrier then orders every lane's acquire before all lanes'
+          // reads of the partials, as the peer's barrier orders its lanes'
+          // stores before its release.
+          for (int y = peer_first + lane * CM; y <= peer_last && !fail; y += 32 * CM)
             fail = !wait_flag(&a.flags[y * kFlagsPerCtaDev + quarter * 8 + u], abort_flag, a);
+          __syncwarp();
           if (__any_sync(0xffffffffu, fail)) {
             fail = true;
             break;
