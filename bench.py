@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--no-grouped", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-f8", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     return ap.parse_args()
 
 
@@ -622,6 +623,8 @@ def ours_arm(args):
             results["dp"]["geomean_tflops"]
     if not args.no_grouped:
         line["grouped"] = run_grouped(max(3, min(args.steps, 10)), args.warmup)
+    if not args.no_configs:
+        line["config_shapes"] = run_config_shapes(peaks)
     if not args.no_f8:
         line["grouped_e4m3"] = run_grouped_f8(max(3, min(args.steps, 10)), args.warmup)
         line["e4m3_shapes"] = run_f8_shapes(peaks)
@@ -819,6 +822,73 @@ def run_f8_shapes(peaks, reps=20):
                               "plan": {x: info[x] for x in ("mode", "grid", "tiles", "sk_tiles")}})
         plan.destroy()
         del qa, qb, sa, sb, C
+    return out
+
+
+CONFIG_SHAPES = [("single GEMM, FP16 in U[-1,1], FP32 out, beta = 0", "f16", "f32", 0.0,
+                  [(384, 384, 4096)]),
+                 ("extreme shapes, BF16 in N(0,1), BF16 out, beta = 0.5 with random C", "bf16",
+                  "bf16", 0.5, [(8192, 8192, 8192), (256, 256, 65536), (8192, 128, 4096),
+                                (1536, 1536, 1536)])]
+
+
+def run_config_shapes(peaks, reps=20):
+    """The single-GEMM and extreme-shape workloads under each schedule (DP
+    tiling, basic Stream-K at the modelled grid, the two-tile hybrid, AUTO),
+    each timed over `reps` back-to-back launches after warm-up on the same
+    operands (only 8192^3's exceed the L2).  TFLOP/s against the measured BF16
+    burst peak and against the shape's attainable roofline
+    min(peak, AI x HBM bandwidth), AI = flops / (A + B read, C read if beta != 0,
+    C written)."""
+    import torch
+    from paper_2301_03598_gb300 import inputs
+    from paper_2301_03598_gb300 import streamk as sk
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peak, bw = peaks["bf16_tflops"], peaks["hbm_gbs"]
+    out = {"peak_tflops": peak, "peak_kind": "bf16 burst (" + peaks["source"] + ")",
+           "hbm_gbs": bw, "l2": "operands reused across the timed launches; only 8192^3 "
+                               "exceeds the L2", "configs": []}
+    stream = torch.cuda.Stream()
+    for what, ab, c_type, beta, shapes in CONFIG_SHAPES:
+        dist = "uniform" if ab == "f16" else "normal"
+        rows = []
+        for (m, n, k) in shapes:
+            A = inputs.device_pool(m * k, ab, dist, 91, dev).view(m, k)
+            B = inputs.device_pool(n * k, ab, dist, 92, dev).view(n, k)
+            C = (inputs.device_pool(m * n, c_type, "normal", 93, dev).view(m, n) if beta
+                 else torch.zeros(m, n, dtype=inputs.DTYPES[c_type], device=dev))
+            flops = 2.0 * m * n * k
+            cb = C.element_size() * m * n
+            nbytes = A.element_size() * (m * k + n * k) + cb * (2 if beta else 1)
+            attainable = min(peak, flops / nbytes * bw / 1e3)
+            row = {"m": m, "n": n, "k": k, "gflop": flops / 1e9, "mbytes": nbytes / 1e6,
+                   "attainable_tflops": attainable, "modes": {}}
+            for mode in ("dp", "sk", "hybrid", "auto"):
+                plan = sk.sk_plan(m, n, k, ab, ab, c_type, mode=mode)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                with torch.cuda.stream(stream):
+                    for _ in range(3):
+                        sk.sk_gemm(plan, A, B, C, 1.0, beta, stream=stream)
+                    ev[0].record(stream)
+                    for _ in range(reps):
+                        sk.sk_gemm(plan, A, B, C, 1.0, beta, stream=stream)
+                    ev[1].record(stream)
+                torch.cuda.synchronize()
+                st, dstat = sk.sk_last_error(plan)
+                if st != sk.SK_OK:
+                    raise RuntimeError(f"{m}x{n}x{k} {mode} status {st}/{dstat}")
+                us = ev[0].elapsed_time(ev[1]) * 1e3 / reps
+                tf = flops / (us * 1e-6) / 1e12
+                info = plan.info()
+                row["modes"][mode] = {"us": us, "tflops": tf, "frac_of_peak": tf / peak,
+                                      "frac_of_attainable": tf / attainable,
+                                      "plan": {x: info[x] for x in (
+                                          "mode", "tile_n", "cluster_m", "grid", "tiles",
+                                          "sk_tiles")}}
+                plan.destroy()
+            rows.append(row)
+            del A, B, C
+        out["configs"].append({"workload": what, "shapes": rows})
     return out
 
 
