@@ -11,8 +11,8 @@
  * the aggregate MAC-loop iterations (output tiles x k-blocks) are split evenly,
  * within one, over a persistent grid of CTAs (Algorithm 5); CTAs that finish a
  * tile they did not start spill FP32 partial sums to a workspace and signal a
- * flag; the CTA that ran the tile's k = 0 iteration waits for them in
- * increasing CTA order, adds their partials and stores the tile.  The two
+ * flag; the CTA that ran the tile's k = 0 iteration waits for their flags,
+ * adds their partials in increasing CTA order and stores the tile.  The two
  * hybrids of Section 5.2 ("DP + one-tile SK" and "two-tile SK + DP") and the
  * data-parallel decomposition (Algorithm 2) are the same kernel with a
  * different schedule.  The grid size of basic Stream-K is chosen by the

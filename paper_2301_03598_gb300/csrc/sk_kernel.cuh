@@ -17,10 +17,10 @@
 //   warps 2..9  epilogue: (E4M3: first sums the k-block products times their
 //               block scales in FP32) per tile segment, either spill the FP32
 //               partial sums to this CTA's workspace slot and Signal (segment
-//               does not start the tile), or Wait for the contributing CTAs in
-//               increasing order and add their partials (tile started here, not
-//               finished here), then compute alpha*acc + beta*C and store the
-//               tile.
+//               does not start the tile), or Wait for the contributing CTAs
+//               (all their flags polled at once) and add their partials in
+//               increasing CTA order (tile started here, not finished here),
+//               then compute alpha*acc + beta*C and store the tile.
 //
 // A grouped launch walks the problems' concatenated iteration space with the
 // same roles, reading each problem's operands, output and scales from device
