@@ -220,3 +220,96 @@ def test_cta_of_iter_agrees_with_ranges():
             x = S.cta_of_iter(i, total, g)
             b, e = S.cta_iter_range(x, total, g)
             assert b <= i < e
+
+
+# ---------------------------------------------------------------------------
+# cluster_trace: the CTA-pair trace, pinned by traces worked out by hand.
+#
+# A schedule unit x of a pair launch is CTAs 2x (rank 0) and 2x + 1 (rank 1).
+# Both run unit x's segments (same tile, k-range and role); rank r computes
+# 128-row block tm * 2 + r of the unit's 256-row tile and takes its partials
+# from, and signals them to, the peers' CTAs of the same rank, 2y + r.
+# Records: (cta, tile, tm, tn, kb0, kb1, role, peer_first, peer_last).
+# ---------------------------------------------------------------------------
+W, P, O = S.ROLE_WHOLE, S.ROLE_PARTIAL, S.ROLE_OWNER
+
+
+def test_cluster_trace_hand_worked_split_schedule():
+    # 512 x 256 x 640 in 256 x 128 pair tiles, BLK_K = 64: tiles_m = tiles_n = 2,
+    # t = 4, 10 iterations per tile, 40 in all.  Algorithm 5 within one over
+    # g = 3 units: q = 13, r = 1, so unit 0 takes [0, 14), unit 1 [14, 27),
+    # unit 2 [27, 40).  Raster with one band (group_m = 2): tile 0 -> (0, 0),
+    # tile 1 -> (1, 0), tile 2 -> (0, 1), tile 3 -> (1, 1).
+    #   unit 0: tile 0 [0, 10) whole; tile 1 [0, 4) owner, peers 1..1
+    #   unit 1: tile 1 [4, 10) partial; tile 2 [0, 7) owner, peers 2..2
+    #   unit 2: tile 2 [7, 10) partial; tile 3 [0, 10) whole
+    prob = S.Problem(512, 256, 640, 256, 128, 64)
+    sched = S.persistent_schedule(prob, 3, prob.tiles, group_m=2)
+    want = [
+        (0, 0, 0, 0, 0, 10, W, -1, -1),
+        (0, 1, 2, 0, 0, 4, O, 2, 2),
+        (1, 0, 1, 0, 0, 10, W, -1, -1),
+        (1, 1, 3, 0, 0, 4, O, 3, 3),
+        (2, 1, 2, 0, 4, 10, P, -1, -1),
+        (2, 2, 0, 1, 0, 7, O, 4, 4),
+        (3, 1, 3, 0, 4, 10, P, -1, -1),
+        (3, 2, 1, 1, 0, 7, O, 5, 5),
+        (4, 2, 0, 1, 7, 10, P, -1, -1),
+        (4, 3, 2, 1, 0, 10, W, -1, -1),
+        (5, 2, 1, 1, 7, 10, P, -1, -1),
+        (5, 3, 3, 1, 0, 10, W, -1, -1),
+    ]
+    assert S.cluster_trace(sched, 2) == want
+
+
+def test_cluster_trace_hand_worked_multi_peer_tile():
+    # One 256 x 128 pair tile, k = 640 (10 iterations) over g = 3 units:
+    # q = 3, r = 1 -> unit 0 [0, 4) owns the tile with peers 1..2, unit 1
+    # [4, 7) and unit 2 [7, 10) spill partials.  Rank r's peers are CTAs
+    # 2 + r .. 4 + r.
+    prob = S.Problem(256, 128, 640, 256, 128, 64)
+    sched = S.persistent_schedule(prob, 3, 1, group_m=1)
+    want = [
+        (0, 0, 0, 0, 0, 4, O, 2, 4),
+        (1, 0, 1, 0, 0, 4, O, 3, 5),
+        (2, 0, 0, 0, 4, 7, P, -1, -1),
+        (3, 0, 1, 0, 4, 7, P, -1, -1),
+        (4, 0, 0, 0, 7, 10, P, -1, -1),
+        (5, 0, 1, 0, 7, 10, P, -1, -1),
+    ]
+    assert S.cluster_trace(sched, 2) == want
+
+
+def test_cluster_trace_hand_worked_hybrid_with_dp_tiles():
+    # 768 x 256 x 384 in pair tiles: tiles_m = 3, tiles_n = 2, t = 6, six
+    # iterations per tile; g = 4 units, Stream-K over the first 2 tiles (12
+    # iterations, q = 3, r = 0), then data-parallel tiles 2 + x + 4j.  Raster
+    # bands of 2 tile rows: tiles 0..3 -> (0,0) (1,0) (0,1) (1,1), then the
+    # last row: tile 4 -> (2, 0), tile 5 -> (2, 1).
+    #   unit 0: tile 0 [0, 3) owner, peers 1..1; dp tile 2
+    #   unit 1: tile 0 [3, 6) partial;           dp tile 3
+    #   unit 2: tile 1 [0, 3) owner, peers 3..3; dp tile 4
+    #   unit 3: tile 1 [3, 6) partial;           dp tile 5
+    prob = S.Problem(768, 256, 384, 256, 128, 64)
+    sched = S.persistent_schedule(prob, 4, 2, group_m=2)
+    want = [
+        (0, 0, 0, 0, 0, 3, O, 2, 2),
+        (0, 2, 0, 1, 0, 6, W, -1, -1),
+        (1, 0, 1, 0, 0, 3, O, 3, 3),
+        (1, 2, 1, 1, 0, 6, W, -1, -1),
+        (2, 0, 0, 0, 3, 6, P, -1, -1),
+        (2, 3, 2, 1, 0, 6, W, -1, -1),
+        (3, 0, 1, 0, 3, 6, P, -1, -1),
+        (3, 3, 3, 1, 0, 6, W, -1, -1),
+        (4, 1, 2, 0, 0, 3, O, 6, 6),
+        (4, 4, 4, 0, 0, 6, W, -1, -1),
+        (5, 1, 3, 0, 0, 3, O, 7, 7),
+        (5, 4, 5, 0, 0, 6, W, -1, -1),
+        (6, 1, 2, 0, 3, 6, P, -1, -1),
+        (6, 5, 4, 1, 0, 6, W, -1, -1),
+        (7, 1, 3, 0, 3, 6, P, -1, -1),
+        (7, 5, 5, 1, 0, 6, W, -1, -1),
+    ]
+    assert S.cluster_trace(sched, 2) == want
+    # cluster_m = 1 is the plain trace of the schedule
+    assert S.cluster_trace(sched, 1) == sched.trace()
