@@ -59,6 +59,9 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-f8", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--dump-dir", default=None,
+                    help="folder for per-shape detail and the clock log (default: "
+                         "$SK_BENCH_DUMP_DIR, else a temporary folder)")
     return ap.parse_args()
 
 
@@ -74,25 +77,41 @@ def load_peaks():
                 "source": "fallback"}
 
 
-PROFILE = os.path.join(ROOT, "profiles", "sk_gemm_sweep_launches.md")
+# DRAM bytes per flop of sk_gemm_kernel over the sweep, from one ncu launch
+# list of the sweep's first shapes (dram__bytes_read.sum + dram__bytes_write.sum
+# summed over the captured launches, divided by their 2mnk), and the sha256 of
+# csrc/sk_kernel.cuh followed by csrc/planner.cpp at that capture.  The
+# summary with its command is profiles/sk_gemm_sweep_launches.md.
+PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.231834e-03,
+                    "kernel_source_sha256":
+                        "7e1661f37abdaac5c6f310434d5437d8a22f56a2e89241507734b3f2643169af"}
 
 
 def profiled_bytes_per_flop():
-    """DRAM bytes per flop of sk_gemm_kernel from the committed ncu launch-list
-    summary, or None when the kernel or planner source changed since."""
+    """The profiled DRAM bytes per flop, or None when the kernel or planner
+    source changed since the capture."""
     import hashlib
-    import re
-    try:
-        text = open(PROFILE).read()
-        bpf = float(re.search(r"dram_bytes_per_flop: ([0-9.eE+-]+)", text).group(1))
-        sha = re.search(r"kernel_source_sha256: ([0-9a-f]+)", text).group(1)
-        h = hashlib.sha256()
-        for f in ("sk_kernel.cuh", "planner.cpp"):
-            with open(os.path.join(ROOT, "paper_2301_03598_gb300", "csrc", f), "rb") as fh:
-                h.update(fh.read())
-        return bpf if h.hexdigest() == sha else None
-    except Exception:
+    h = hashlib.sha256()
+    for f in ("sk_kernel.cuh", "planner.cpp"):
+        with open(os.path.join(ROOT, "paper_2301_03598_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != PROFILED_TRAFFIC["kernel_source_sha256"]:
         return None
+    return PROFILED_TRAFFIC["dram_bytes_per_flop"]
+
+
+def dump_dir():
+    """Where per-shape detail and the clock log go: --dump-dir, else the
+    SK_BENCH_DUMP_DIR environment variable, else a fresh temporary folder."""
+    global _DUMP_DIR
+    if _DUMP_DIR is None:
+        import tempfile
+        _DUMP_DIR = os.environ.get("SK_BENCH_DUMP_DIR") or tempfile.mkdtemp(prefix="sk_bench_")
+        os.makedirs(_DUMP_DIR, exist_ok=True)
+    return _DUMP_DIR
+
+
+_DUMP_DIR = None
 
 
 def geomean(x):
@@ -109,7 +128,7 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.idx = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        self.path = os.path.join(dump_dir(), f"clocks_rank{device_index}.csv")
 
     def start(self):
         try:
@@ -573,14 +592,13 @@ def ours_arm(args):
 
     if rank != 0:
         return
-    dump_dir = os.path.join(ROOT, "gpurun_out")
-    if os.path.isdir(dump_dir):   # per-shape detail for offline analysis
-        with open(os.path.join(dump_dir, "bench_per_shape.json"), "w") as f:
-            json.dump({"shapes": shapes,
-                       "plans": {v: [[p.get("tile_n"), p.get("grid"), p.get("sk_tiles"),
-                                      p.get("mode")] for p in r["_plans"]]
-                                 for v, r in results.items()},
-                       "us": {v: (r["_med"] * 1e3).tolist() for v, r in results.items()}}, f)
+    # per-shape detail for offline analysis
+    with open(os.path.join(dump_dir(), "bench_per_shape.json"), "w") as f:
+        json.dump({"shapes": shapes,
+                   "plans": {v: [[p.get("tile_n"), p.get("grid"), p.get("sk_tiles"),
+                                  p.get("mode")] for p in r["_plans"]]
+                             for v, r in results.items()},
+                   "us": {v: (r["_med"] * 1e3).tolist() for v, r in results.items()}}, f)
     kernel_ms = float(np.sum(H["_med"]))
     bpf = profiled_bytes_per_flop()
     achieved = float(flops.sum() / (kernel_ms * 1e-3) / 1e12)
@@ -607,7 +625,8 @@ def ours_arm(args):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": (bpf * float(flops.mean())) if bpf is not None else None,
-                     "traffic_unit": "DRAM bytes per launch (profiles/sk_gemm_sweep_launches.md)",
+                     "traffic_unit": "DRAM bytes per launch (ncu launch list of the sweep's "
+                                     "first shapes, scaled by flops)",
                      "kernel": "sk::sk_gemm_kernel", "peak_kind":
                      f"bf16 sustained ({peaks['source']})"},
         "gpu_launches": int(sum(sweep.reps) * args.steps),
@@ -1031,7 +1050,11 @@ def run_serving(rates=(2000, 5000, 20000, 40000, 50000), seconds=0.5, seed=2301_
 
 
 def main():
+    global _DUMP_DIR
     args = parse_args()
+    if args.dump_dir:
+        _DUMP_DIR = args.dump_dir
+        os.makedirs(_DUMP_DIR, exist_ok=True)
     if args.impl == "reference":
         reference_arm(args)
     else:

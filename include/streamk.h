@@ -26,8 +26,13 @@
  *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
  *     stream.  sk_gemm is asynchronous (stream-ordered) and returns after the
  *     launch; device-side failures are reported by sk_last_error.
- *   - A plan is not thread-safe and must not be used by two streams at once
- *     (its workspace would be shared by two launches).
+ *   - A plan is not thread-safe.  It owns one fixup workspace, so it serves
+ *     one launch at a time: a launch on a stream other than the one of the
+ *     plan's previous launch, while that launch is still running, returns
+ *     SK_ERR_BUSY and enqueues nothing (checked with an event the plan records
+ *     after each launch; launches made while their stream is being captured
+ *     into a CUDA graph are not tracked).  Launches on one stream are ordered
+ *     by the stream and never busy.
  */
 #ifndef STREAMK_H
 #define STREAMK_H
@@ -46,7 +51,8 @@ typedef enum {
   SK_ERR_CUDA = 3,        /* a CUDA runtime call failed (no device, launch failure, ...) */
   SK_ERR_TIMEOUT = 4,     /* a bounded wait on the device ran out (fixup flag or pipeline) */
   SK_ERR_NOMEM = 5,       /* device allocation failed */
-  SK_ERR_DEVICE = 6       /* the current device is not sm_103 (GB300) */
+  SK_ERR_DEVICE = 6,      /* the current device is not sm_103 (GB300) */
+  SK_ERR_BUSY = 7         /* the plan's previous launch is still running on another stream */
 } sk_status;
 
 /* SK_E4M3: 8-bit floating point (OCP FP8 E4M3: 1 sign, 4 exponent bits with
@@ -176,6 +182,7 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
  * SK_ATTR_CLUSTER_M 1 on those plans.  Results are bitwise reproducible
  * run to run for a given plan: the fixup adds the contributing CTAs' partials
  * in increasing CTA order.  Returns SK_ERR_INVALID for bad pointers,
+ * SK_ERR_BUSY when the plan's previous launch still runs on another stream,
  * SK_ERR_CUDA if the launch fails.
  */
 int sk_gemm(sk_plan_t plan, const void* A, const void* B, void* C, float alpha, float beta,
@@ -263,20 +270,24 @@ int sk_grid_model(int64_t m, int64_t n, int64_t k, int bm, int bn, int bk, int p
 
 /*
  * Allocation-free GEMM: C = alpha * A * B + beta * C like sk_gemm, for callers
- * that cannot allocate device memory -- for example code running while its
- * stream is captured into a CUDA graph (where an allocation is forbidden or
- * would synchronise the device), latency-critical serving loops in which an
- * allocation would stall every stream, and plugins that only receive buffers
- * from a host framework that owns the memory pool.  The paper has no
- * counterpart; it is an interface of this library only.
+ * that cannot allocate device memory -- for example plugins and custom
+ * operators that only receive buffers from a host framework which owns the
+ * device memory pool (an allocation behind its back can fail against the
+ * pool's reservation), latency-critical serving loops in which a cudaMalloc
+ * would synchronise the device and stall every stream, and processes held to
+ * a fixed device-memory quota.  The paper has no counterpart; it is an
+ * interface of this library only.
  *
  * No plan, no cudaMalloc/cudaFree and no allocating library call: the
  * schedule is planned on the host stack for this call, with BLK_N = 128, and
  * the fixup scratch (128 KiB of flags, status words and up to 12 MiB - 132 KiB
  * of FP32 partial tiles) is one fixed 12 MiB device array inside the library,
- * which every GPU that loads the library keeps until the process exits.  A
- * schedule that would need more partial-tile scratch than that (more than 189
- * CTAs) returns SK_ERR_INVALID.
+ * which every GPU that loads the library keeps until the process exits.  The
+ * scratch holds the partial tiles of 189 CTAs; a launch never has more CTAs
+ * than the device has SMs (152 on GB300), so every shape fits on sm_103.  The
+ * size check stays as a guard and would return SK_ERR_INVALID.  All argument
+ * checks run before anything is enqueued: a call that returns an error has
+ * put nothing on the stream.
  *
  *   A: m x k row-major, lda >= k; B: k x n column-major (an n x k row-major
  *   array), ldb >= k; both device pointers 16-byte aligned with lda*2 and
@@ -329,8 +340,9 @@ const char* sk_status_string(int status);
  *   aligned); alpha / beta host arrays of count values or NULL (1 and 0).
  *   Asynchronous on `stream`; tensor maps are re-encoded, and the problem
  *   table re-uploaded, only for problems whose pointers or scalars changed
- *   since the previous launch (the upload is stream-ordered).  One plan must
- *   not be launched on two streams at once.
+ *   since the previous launch (the upload is stream-ordered).  A launch on
+ *   another stream while the plan's previous launch still runs returns
+ *   SK_ERR_BUSY, as for sk_gemm.
  * sk_grouped_gemm_traced: as sk_grouped_gemm, recording the schedule as
  *   sk_gemm_traced does (field 9 of each record holds the problem index);
  *   trace_ints >= SK_ATTR_TRACE_INTS.

@@ -31,8 +31,24 @@ def _nvcc() -> str:
     return cand
 
 
+# Sources compiled more than once, each time with its own defines (the kernel
+# instantiations of one tile width per object).
+PER_VARIANT = {"kernels_bn.cu": [("bn128", ["-DSK_BN=128"]), ("bn256", ["-DSK_BN=256"])]}
+
+
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+
+
+def units():
+    """(source, object, extra flags) of every object the library links."""
+    out = []
+    for src in sources():
+        base = os.path.basename(src)
+        for tag, defs in PER_VARIANT.get(base, [("", [])]):
+            name = base + (f".{tag}" if tag else "") + ".o"
+            out.append((src, os.path.join(OUT_DIR, name), defs))
+    return out
 
 
 def headers():
@@ -54,12 +70,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     flags = NVCC_FLAGS + list(extra_flags or [])
     jobs = []
     objs = []
-    for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+    for src, obj, defs in units():
         objs.append(obj)
         if force or _stale(obj, src):
             lang = ["-x", "cu"] if src.endswith(".cu") else ["-x", "c++"]
-            jobs.append([nvcc] + ARCH + flags + lang + ["-c", src, "-o", obj])
+            jobs.append([nvcc] + ARCH + flags + defs + lang + ["-c", src, "-o", obj])
 
     def run(cmd):
         if verbose:

@@ -89,6 +89,7 @@ struct sk_plan_s {
   bool c_tma = false;
   cudaStream_t last_stream = nullptr;
   bool launched = false;
+  InFlight inflight;  // the last launch, for SK_ERR_BUSY
 };
 
 namespace {
@@ -155,6 +156,9 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   if (C == nullptr || (reinterpret_cast<uintptr_t>(C) & 15u)) return SK_ERR_INVALID;
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device) return SK_ERR_INVALID;
+  // The plan's workspace serves one launch at a time: refuse a launch on a
+  // second stream while the last one still runs.
+  if (const int bs = busy_check(p->inflight, stream); bs != SK_OK) return bs;
   const sk_schedule_info& s = p->info;
   p->last_stream = stream;
   p->launched = true;
@@ -171,7 +175,9 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
                                                                    n, p->ldc, beta);
     else
       scale_kernel<__half><<<blocks, threads, 0, stream>>>(static_cast<__half*>(C), m, n, p->ldc, beta);
-    return cuda_status(cudaGetLastError());
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    return busy_record(p->inflight, stream);
   }
 
   if (A == nullptr || B == nullptr || (reinterpret_cast<uintptr_t>(A) & 15u) ||
@@ -265,15 +271,18 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   const bool cooperative = split && s.cluster_m == 1;
   const CUtensorMap& ta3 = use3d ? p->tm_a3 : p->tm_a;
   const CUtensorMap& tb3 = use3d ? p->tm_b3 : p->tm_b;
+  cudaError_t e;
   if (f8)
-    return cuda_status(sk::launch_f8(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3,
-                                     a, cooperative, stream));
-  cudaError_t e = s.tile_n == 256
-                      ? sk::launch_bn256(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3,
-                                         a, cooperative, stream)
-                      : sk::launch_bn128(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3,
-                                         a, cooperative, stream);
-  return cuda_status(e);
+    e = sk::launch_f8(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3, a, cooperative,
+                      stream);
+  else if (s.tile_n == 256)
+    e = sk::launch_bn256(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3, a, cooperative,
+                         stream);
+  else
+    e = sk::launch_bn128(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3, a, cooperative,
+                         stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  return busy_record(p->inflight, stream);
 }
 
 }  // namespace
@@ -297,6 +306,7 @@ const char* sk_status_string(int status) {
     case SK_ERR_TIMEOUT: return "SK_ERR_TIMEOUT";
     case SK_ERR_NOMEM: return "SK_ERR_NOMEM";
     case SK_ERR_DEVICE: return "SK_ERR_DEVICE";
+    case SK_ERR_BUSY: return "SK_ERR_BUSY";
     default: return "SK_ERR_UNKNOWN";
   }
 }
@@ -377,6 +387,7 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
 
 int sk_plan_destroy(sk_plan_t p) {
   if (p == nullptr) return SK_OK;
+  busy_release(p->inflight);
   if (p->ws && p->ws_owned) cudaFree(p->ws);
   if (p->err) cudaFree(p->err);
   delete p;
@@ -568,6 +579,11 @@ constexpr size_t kNoAllocScratchBytes = size_t(12) << 20;  // 12 MiB per device
 constexpr size_t kNoAllocStatusOffset = static_cast<size_t>(sk::kFlagBytes);  // 4 words
 constexpr size_t kNoAllocPartialsOffset = kNoAllocStatusOffset + 4096;
 constexpr int kNoAllocMaxDevices = 64;
+// Partial tiles (128 x 128 FP32, 64 KiB each) the scratch holds after the
+// flags and status words: 189.  A launch has at most one CTA per SM.
+constexpr size_t kNoAllocMaxCtas =
+    (kNoAllocScratchBytes - kNoAllocPartialsOffset) / (size_t(sk::kBlkM) * 128 * 4);
+static_assert(kNoAllocMaxCtas == 189, "scratch size and the documented CTA limit");
 
 }  // namespace
 
@@ -638,10 +654,39 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
   if (C == nullptr || (reinterpret_cast<uintptr_t>(C) & 15u)) return SK_ERR_INVALID;
   char* const scratch = d->scratch;
   int32_t* const err = reinterpret_cast<int32_t*>(scratch + kNoAllocStatusOffset);
+
+  // Every host-side check and the tensor-map encoding come first, so that a
+  // call that returns an error has enqueued nothing on the stream.
+  sk_schedule_info s{};
+  CUtensorMap tma, tmb, tmc, tma3, tmb3;
+  bool split = false, use3d = false, c_tma = false;
+  if (k > 0) {
+    if (A == nullptr || B == nullptr || (reinterpret_cast<uintptr_t>(A) & 15u) ||
+        (reinterpret_cast<uintptr_t>(B) & 15u))
+      return SK_ERR_INVALID;
+    int st = sk::describe(m, n, k, mode, 128, 0, 0, 1, d->num_sms, &s);
+    if (st != SK_OK) return st;
+    split = s.workspace_bytes > 0;
+    const size_t partial_bytes = static_cast<size_t>(s.ctas) * sk::kBlkM * 128 * 4;
+    // Never taken on sm_103: the grid is at most one CTA per SM, far below
+    // the kNoAllocMaxCtas partial tiles the scratch holds.
+    if (split && kNoAllocPartialsOffset + partial_bytes > kNoAllocScratchBytes)
+      return SK_ERR_INVALID;
+    if ((st = encode_operand(&tma, A, ab_type, m, k, lda, sk::kBlkM)) != SK_OK) return st;
+    if ((st = encode_operand(&tmb, B, ab_type, n, k, ldb, 128)) != SK_OK) return st;
+    use3d = s.tile_k == 2 * sk::kBlkK && k / sk::kBlkK >= 2;
+    tma3 = tma;
+    tmb3 = tmb;
+    if (use3d) {
+      if ((st = encode_operand_3d(&tma3, A, ab_type, m, k, lda, sk::kBlkM)) != SK_OK) return st;
+      if ((st = encode_operand_3d(&tmb3, B, ab_type, n, k, ldb, 128)) != SK_OK) return st;
+    }
+    c_tma = encode_output(&tmc, C, c_type, m, n, ldc);
+  }
+
   // The status words must start at zero for every call (flags too, below).
   cudaError_t e = cudaMemsetAsync(err, 0, 4 * sizeof(int32_t), stream);
   if (e != cudaSuccess) return cuda_status(e);
-
   if (k == 0) {  // C = beta * C
     const int threads = 256;
     const int blocks = static_cast<int>(std::min<int64_t>((m * n + threads - 1) / threads, 4096));
@@ -654,27 +699,6 @@ extern "C" int sk_gemm_noalloc(int64_t m, int64_t n, int64_t k, sk_dtype ab_type
       scale_kernel<__half><<<blocks, threads, 0, stream>>>(static_cast<__half*>(C), m, n, ldc, beta);
     e = cudaGetLastError();
   } else {
-    if (A == nullptr || B == nullptr || (reinterpret_cast<uintptr_t>(A) & 15u) ||
-        (reinterpret_cast<uintptr_t>(B) & 15u))
-      return SK_ERR_INVALID;
-    sk_schedule_info s;
-    int st = sk::describe(m, n, k, mode, 128, 0, 0, 1, d->num_sms, &s);
-    if (st != SK_OK) return st;
-    const bool split = s.workspace_bytes > 0;
-    const size_t partial_bytes = static_cast<size_t>(s.grid) * sk::kBlkM * 128 * 4;
-    if (split && kNoAllocPartialsOffset + partial_bytes > kNoAllocScratchBytes)
-      return SK_ERR_INVALID;  // needs more scratch than the fixed maximum
-    CUtensorMap tma, tmb, tmc, tma3, tmb3;
-    if ((st = encode_operand(&tma, A, ab_type, m, k, lda, sk::kBlkM)) != SK_OK) return st;
-    if ((st = encode_operand(&tmb, B, ab_type, n, k, ldb, 128)) != SK_OK) return st;
-    const bool use3d = s.tile_k == 2 * sk::kBlkK && k / sk::kBlkK >= 2;
-    tma3 = tma;
-    tmb3 = tmb;
-    if (use3d) {
-      if ((st = encode_operand_3d(&tma3, A, ab_type, m, k, lda, sk::kBlkM)) != SK_OK) return st;
-      if ((st = encode_operand_3d(&tmb3, B, ab_type, n, k, ldb, 128)) != SK_OK) return st;
-    }
-    const bool c_tma = encode_output(&tmc, C, c_type, m, n, ldc);
     if (split) {
       e = cudaMemsetAsync(scratch, 0, static_cast<size_t>(sk::kFlagBytes), stream);
       if (e != cudaSuccess) return cuda_status(e);
@@ -750,6 +774,7 @@ struct sk_grouped_s {
   int store_req = 0;
   cudaStream_t last_stream = nullptr;
   bool launched = false;
+  InFlight inflight;  // the last launch, for SK_ERR_BUSY
 };
 
 namespace {
@@ -822,6 +847,7 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
   const bool f8 = g->ab_type == SK_E4M3;
   if (f8 != (SA != nullptr) || f8 != (SB != nullptr)) return SK_ERR_INVALID;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+  if (const int bs = busy_check(g->inflight, stream); bs != SK_OK) return bs;
   const sk::GroupPlan& gp = g->plan;
   if (trace != nullptr) {
     const int64_t need = static_cast<int64_t>(gp.grid) *
@@ -929,7 +955,7 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
   if (e != cudaSuccess) return cuda_status(e);
   g->last_stream = stream;
   g->launched = true;
-  return SK_OK;
+  return busy_record(g->inflight, stream);
 }
 
 }  // namespace
@@ -1010,6 +1036,7 @@ int sk_grouped_destroy(sk_grouped_t g) {
   if (g->d_probs) cudaFree(g->d_probs);
   if (g->h_probs) cudaFreeHost(g->h_probs);
   if (g->copied) cudaEventDestroy(g->copied);
+  busy_release(g->inflight);
   if (g->ws) cudaFree(g->ws);
   if (g->err) cudaFree(g->err);
   delete g;

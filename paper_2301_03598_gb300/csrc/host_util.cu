@@ -130,5 +130,48 @@ uint32_t make_idesc(int in_dtype, int tile_n, int cluster_m) {
 }
 
 
+
+static bool capturing(cudaStream_t stream, bool* ok) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  *ok = cudaStreamIsCapturing(stream, &cs) == cudaSuccess;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+int busy_check(const InFlight& f, cudaStream_t stream) {
+  if (!f.recorded || f.stream == stream) return SK_OK;  // stream order covers one stream
+  // No event query while the stream is being captured (a graph node is not a
+  // launch yet, and the query is not allowed under global capture).
+  bool ok = true;
+  if (capturing(stream, &ok)) return SK_OK;
+  if (!ok) return SK_ERR_CUDA;
+  const cudaError_t e = cudaEventQuery(f.done);
+  if (e == cudaSuccess) return SK_OK;
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();  // a query that is not ready leaves no sticky error; clear it anyway
+    return SK_ERR_BUSY;
+  }
+  return cuda_status(e);
+}
+
+int busy_record(InFlight& f, cudaStream_t stream) {
+  bool ok = true;
+  if (capturing(stream, &ok)) return SK_OK;  // a graph node: not tracked
+  if (!ok) return SK_ERR_CUDA;
+  if (f.done == nullptr) {
+    const cudaError_t e = cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  const cudaError_t e = cudaEventRecord(f.done, stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  f.stream = stream;
+  f.recorded = true;
+  return SK_OK;
+}
+
+void busy_release(InFlight& f) {
+  if (f.done != nullptr) cudaEventDestroy(f.done);
+  f = InFlight{};
+}
+
 }  // namespace host
 }  // namespace sk

@@ -35,6 +35,21 @@ int store_path(int req);
 // tcgen05 instruction descriptor (kind::f16, or kind::f8f6f4 for E4M3).
 uint32_t make_idesc(int in_dtype, int tile_n, int cluster_m);
 
+// A plan's last launch, for refusing a launch on another stream while it is
+// still running (SK_ERR_BUSY): both would use the plan's one workspace.
+// Launches issued while their stream is being captured are not tracked.
+struct InFlight {
+  cudaEvent_t done = nullptr;   // recorded after each tracked launch
+  cudaStream_t stream = nullptr;
+  bool recorded = false;
+};
+// SK_OK, SK_ERR_BUSY (the last tracked launch runs on a stream other than
+// `stream` and has not finished) or SK_ERR_CUDA.
+int busy_check(const InFlight& f, cudaStream_t stream);
+// Note a launch just issued on `stream` (creates the event on first use).
+int busy_record(InFlight& f, cudaStream_t stream);
+void busy_release(InFlight& f);
+
 }  // namespace host
 
 // sk_gemm / sk_gemm_scaled (scales null for 16-bit plans) whose launch also

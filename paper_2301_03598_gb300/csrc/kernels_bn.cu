@@ -1,10 +1,18 @@
-// Instantiations of the persistent Stream-K kernel for BLK_N = 128.
+// Instantiations of the persistent Stream-K kernel for one tile width BLK_N.
+// This file is compiled once per tile width with -DSK_BN=<BLK_N>; each object
+// defines launch_bn<BLK_N>, launch_grouped_bn<BLK_N> and prepare_bn<BLK_N>.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "../../include/streamk.h"
 #include "launch.h"
 #include "sk_kernel.cuh"
+
+#ifndef SK_BN
+#error "compile with -DSK_BN=<tile width>"
+#endif
+#define SK_CAT2(a, b) a##b
+#define SK_CAT(a, b) SK_CAT2(a, b)
 
 namespace sk {
 
@@ -15,7 +23,7 @@ static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(args.grid * CM));
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = Cfg<128, CM>::kSmemBytes;
+  cfg.dynamicSmemBytes = Cfg<SK_BN, CM>::kSmemBytes;
   cfg.stream = stream;
   cudaLaunchAttribute attr[3];
   unsigned na = 0;
@@ -38,7 +46,7 @@ static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, CM, TC, false, false>, ta, tb, tc, ta3, tb3, args);
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<SK_BN, CM, TC, false, false>, ta, tb, tc, ta3, tb3, args);
 }
 
 template <int CM>
@@ -57,7 +65,7 @@ static cudaError_t launch_cm(int c_dtype, const CUtensorMap& ta, const CUtensorM
   }
 }
 
-cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
+cudaError_t SK_CAT(launch_bn, SK_BN)(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
                          const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
                          const SkArgs& args, bool cooperative, cudaStream_t stream) {
   return cluster_m == 2 ? launch_cm<2>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream)
@@ -72,7 +80,7 @@ static cudaError_t launch_grouped_one(const CUtensorMap& tm, const SkArgs& args,
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(args.grid));
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = Cfg<128, 1>::kSmemBytes;
+  cfg.dynamicSmemBytes = Cfg<SK_BN, 1>::kSmemBytes;
   cfg.stream = stream;
   cudaLaunchAttribute attr[2];
   unsigned na = 0;
@@ -88,10 +96,10 @@ static cudaError_t launch_grouped_one(const CUtensorMap& tm, const SkArgs& args,
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<128, 1, TC, true, false>, tm, tm, tm, tm, tm, args);
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<SK_BN, 1, TC, true, false>, tm, tm, tm, tm, tm, args);
 }
 
-cudaError_t launch_grouped_bn128(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
+cudaError_t SK_CAT(launch_grouped_bn, SK_BN)(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
                                 bool cooperative, cudaStream_t stream) {
   switch (c_dtype) {
     case SK_F32:
@@ -107,15 +115,15 @@ cudaError_t launch_grouped_bn128(int c_dtype, const CUtensorMap& tm, const SkArg
 
 template <int CM, typename TC>
 static cudaError_t set_smem() {
-  cudaError_t e = cudaFuncSetAttribute(sk_gemm_kernel<128, CM, TC, false, false>,
+  cudaError_t e = cudaFuncSetAttribute(sk_gemm_kernel<SK_BN, CM, TC, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Cfg<128, CM>::kSmemBytes);
+                                       Cfg<SK_BN, CM>::kSmemBytes);
   if (e != cudaSuccess || CM != 1) return e;
-  return cudaFuncSetAttribute(sk_gemm_kernel<128, 1, TC, true, false>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128, CM>::kSmemBytes);
+  return cudaFuncSetAttribute(sk_gemm_kernel<SK_BN, 1, TC, true, false>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<SK_BN, CM>::kSmemBytes);
 }
 
-cudaError_t prepare_bn128(size_t* smem_bytes) {
+cudaError_t SK_CAT(prepare_bn, SK_BN)(size_t* smem_bytes) {
   cudaError_t e;
   if ((e = set_smem<1, float>()) != cudaSuccess) return e;
   if ((e = set_smem<1, __nv_bfloat16>()) != cudaSuccess) return e;
@@ -123,8 +131,8 @@ cudaError_t prepare_bn128(size_t* smem_bytes) {
   if ((e = set_smem<2, float>()) != cudaSuccess) return e;
   if ((e = set_smem<2, __nv_bfloat16>()) != cudaSuccess) return e;
   if ((e = set_smem<2, __half>()) != cudaSuccess) return e;
-  static_assert(Cfg<128, 1>::kSmemBytes == Cfg<128, 2>::kSmemBytes, "one size for both");
-  *smem_bytes = static_cast<size_t>(Cfg<128, 1>::kSmemBytes);
+  static_assert(Cfg<SK_BN, 1>::kSmemBytes == Cfg<SK_BN, 2>::kSmemBytes, "one size for both");
+  *smem_bytes = static_cast<size_t>(Cfg<SK_BN, 1>::kSmemBytes);
   return cudaSuccess;
 }
 

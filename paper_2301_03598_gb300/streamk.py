@@ -16,7 +16,7 @@ from typing import Optional
 from .build import INCLUDE, LIB
 
 SK_OK, SK_ERR_INVALID, SK_ERR_UNSUPPORTED, SK_ERR_CUDA, SK_ERR_TIMEOUT, SK_ERR_NOMEM, \
-    SK_ERR_DEVICE = range(7)
+    SK_ERR_DEVICE, SK_ERR_BUSY = range(8)
 DTYPES = {"f16": 0, "bf16": 1, "f32": 2, "e4m3": 3}
 LAYOUTS = {"row": 0, "col": 1}
 MODES = {"auto": 0, "dp": 1, "sk": 2, "hybrid": 3, "hybrid1": 4}

@@ -1,11 +1,14 @@
 """The allocation-free entry point sk_gemm_noalloc, for callers that cannot
-allocate device memory (code running under CUDA-graph stream capture,
-latency-critical serving loops, plugins handed buffers by a host framework).
+allocate device memory (plugins handed buffers by a host framework that owns
+the pool, latency-critical serving loops where a cudaMalloc would synchronise
+the device, processes held to a device-memory quota).
 
 It must give the same results as the plan-based sk_gemm, within the tolerance
 the parity tests use (k * 2^-22 * |alpha| |A||B| + 2^-22 |beta C| + one output
 ulp), on two calls in a row -- the second call finds the first call's leftovers
-in the shared scratch.  This file is collected last on purpose.
+in the shared scratch -- and the two calls must agree bit for bit (the fixup
+adds partials in a fixed order, so stale flags or partials would show).  This
+file is collected last on purpose.
 """
 import pytest
 import torch
@@ -38,6 +41,7 @@ def test_noalloc_matches_sk_gemm_twice(m, n, k, a_type, c_type, mode, alpha, bet
     tol = bound(k, alpha, beta, absAB, C64, inputs.widen(prob.Cin), c_type)
     ref = inputs.widen(C_ref.cpu())
     status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    outs = []
     for call in range(2):
         C = prob.Cin.clone().cuda()
         sk.sk_gemm_noalloc(m, n, k, a_type, c_type, A, k, B, k, C, n, alpha, beta, mode,
@@ -47,6 +51,30 @@ def test_noalloc_matches_sk_gemm_twice(m, n, k, a_type, c_type, mode, alpha, bet
         got = inputs.widen(C.cpu())
         check_bound(got, ref, tol, f"noalloc call {call} vs sk_gemm")
         check_bound(got, C64, tol, f"noalloc call {call} vs oracle")
+        outs.append(C.cpu())
+    assert torch.equal(outs[0], outs[1]), "the second call differs from the first"
+
+
+def test_noalloc_k0_scales_c_twice():
+    """k = 0: C = beta * C (no MAC loop), against sk_gemm, on two calls."""
+    m, n = 300, 272
+    prob = Problem(m, n, 0, "bf16", "bf16", "normal", seed=32, beta=0.5)
+    plan = sk.sk_plan(m, n, 0, "bf16", "bf16", "bf16", "f32", "row", "col", "row", "auto")
+    dummy = torch.zeros(16, dtype=torch.bfloat16, device="cuda")
+    try:
+        C_ref = prob.Cin.clone().cuda()
+        sk.sk_gemm(plan, dummy, dummy, C_ref, 1.0, 0.5)
+        assert sk.sk_last_error(plan)[0] == sk.SK_OK
+    finally:
+        plan.destroy()
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    for call in range(2):
+        C = prob.Cin.clone().cuda()
+        sk.sk_gemm_noalloc(m, n, 0, "bf16", "bf16", dummy, 0, dummy, 0, C, n, 1.0, 0.5, "auto",
+                           device_status=status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert torch.equal(C.cpu(), C_ref.cpu()), f"call {call}"
 
 
 def test_noalloc_rejects_bad_arguments():
