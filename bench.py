@@ -52,7 +52,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--count", type=int, default=None, help="shapes in the sweep (default 2000)")
-    ap.add_argument("--variants", default="auto,dp,sk")
+    ap.add_argument("--variants", default="auto,dp,sk,auto+indep",
+                    help="schedules timed on the sweep; the first is the headline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-grouped", action="store_true")
@@ -228,11 +229,21 @@ def _al(x):
     return (x + 127) // 128 * 128  # 256-byte aligned slices
 
 
-def make_plans(shapes, mode, ws_holder):
+def make_plans(shapes, variant, ws_holder):
+    """Plans of one bench variant: a schedule mode (auto, dp, sk, hybrid), with
+    "+indep" the same plans declared to have independent inputs
+    (SK_ATTR_INDEPENDENT_INPUTS: every GEMM of the sweep reads operands that no
+    other GEMM writes, so a launch's MAC loop may overlap its predecessor)."""
     import torch
     from paper_2301_03598_gb300 import streamk as sk
+    mode, _, extra = variant.partition("+")
     plans = [sk.sk_plan(m, n, k, "bf16", "bf16", "bf16", "f32", "row", "col", "row", mode)
              for (m, n, k) in shapes]
+    if extra == "indep":
+        for p in plans:
+            p.set("independent_inputs", 1)
+    elif extra:
+        raise ValueError(f"unknown variant {variant}")
     need = max([p.get("workspace_bytes") for p in plans] + [4096])
     if ws_holder.get("ws") is None or ws_holder["ws"].numel() < need:
         ws_holder["ws"] = torch.empty(need, dtype=torch.uint8, device="cuda")
@@ -640,6 +651,15 @@ def ours_arm(args):
                                  "geomean": geomean(sp)}
         line["vs_dp_geomean"] = results[headline]["geomean_tflops"] / \
             results["dp"]["geomean_tflops"]
+    if "auto+indep" in results and headline == "auto":
+        sp = results["auto+indep"]["_per_shape"] / results["auto"]["_per_shape"]
+        line["independent_inputs"] = {
+            "what": "the headline's plans with SK_ATTR_INDEPENDENT_INPUTS (opt-in, off by "
+                    "default): operand loads and the MAC loop overlap the previous launch, "
+                    "C and workspace accesses keep stream order; not the headline",
+            "geomean_tflops": results["auto+indep"]["geomean_tflops"],
+            "speedup_vs_default": {"geomean": geomean(sp), "min": float(sp.min()),
+                                   "max": float(sp.max())}}
     if not args.no_grouped:
         line["grouped"] = run_grouped(max(3, min(args.steps, 10)), args.warmup)
     if not args.no_configs:
@@ -650,6 +670,38 @@ def ours_arm(args):
     if not args.no_serving:
         line["serving"] = run_serving()
     print(json.dumps(line), flush=True)
+
+
+def grouped_schedules(gplan, launch, steps, warmup, stream, flops):
+    """The same grouped launch under each schedule of the concatenated
+    iteration space, each forced in turn: data-parallel waves, the two-tile
+    hybrid (Stream-K over the first (t mod p) + p tiles) and basic Stream-K
+    (one even split of all iterations).  Restores the plan's mode."""
+    import torch
+    from paper_2301_03598_gb300 import streamk as sk
+    saved = gplan.get("mode")
+    out = {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for name in ("dp", "hybrid", "sk"):
+        gplan.set("mode", sk.MODES[name])
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, warmup)):
+                launch()
+            ev[0].record(stream)
+            for _ in range(steps):
+                launch()
+            ev[1].record(stream)
+        torch.cuda.synchronize()
+        st, dstat = sk.sk_grouped_last_error(gplan)
+        if st != sk.SK_OK:
+            raise RuntimeError(f"grouped {name} status {st}/{dstat}")
+        ms = ev[0].elapsed_time(ev[1]) / steps
+        info = gplan.info()
+        out[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                     "plan": {k: info[k] for k in ("tile_n", "grid", "tiles", "sk_tiles",
+                                                   "workspace_bytes")}}
+    gplan.set("mode", saved)
+    return out
 
 
 def run_grouped(steps, warmup):
@@ -684,6 +736,8 @@ def run_grouped(steps, warmup):
         raise RuntimeError(f"grouped launch status {st}/{dstat}")
     g_ms = ev[0].elapsed_time(ev[1]) / steps
     ginfo = gplan.info()
+    scheds = grouped_schedules(gplan, lambda: sk.sk_grouped_gemm(gplan, As, Bs, Cs, stream=stream),
+                               steps, warmup, stream, flops)
     # the same problems as separate plans, one graph of 256 launches per step
     plans = make_plans(shapes, "auto", {})
     ws_keep = [p._workspace for p in plans]
@@ -718,6 +772,7 @@ def run_grouped(steps, warmup):
         "problems": len(shapes), "gflop": flops / 1e9,
         "grouped": {"ms": g_ms, "tflops": flops / (g_ms * 1e-3) / 1e12, "launches_per_step": 1,
                     "plan": {k: ginfo[k] for k in ("mode", "tile_n", "grid", "tiles", "sk_tiles")}},
+        "schedules": scheds,
         "separate": {"ms": s_ms, "tflops": flops / (s_ms * 1e-3) / 1e12,
                      "launches_per_step": len(shapes),
                      "timing": "the 256 single-GEMM launches replayed from one CUDA graph"},
@@ -762,6 +817,9 @@ def run_grouped_f8(steps, warmup):
         raise RuntimeError(f"grouped e4m3 launch status {st}/{dstat}")
     g_ms = ev[0].elapsed_time(ev[1]) / steps
     ginfo = gplan.info()
+    scheds = grouped_schedules(
+        gplan, lambda: sk.sk_grouped_gemm_scaled(gplan, As, Bs, SAs, SBs, Cs, stream=stream),
+        steps, warmup, stream, flops)
     plans = [sk.sk_plan(m, n, k, "e4m3", "e4m3", "bf16") for m, n, k in shapes]
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.stream(stream):
@@ -793,7 +851,9 @@ def run_grouped_f8(steps, warmup):
         "problems": len(shapes), "gflop": flops / 1e9,
         "grouped": {"ms": g_ms, "tflops": flops / (g_ms * 1e-3) / 1e12, "launches_per_step": 1,
                     "autotune_best_us": tuned_us,
-                    "plan": {k: ginfo[k] for k in ("mode", "tile_n", "grid", "tiles", "sk_tiles")}},
+                    "plan": {k: ginfo[k] for k in ("mode", "tile_n", "grid", "tiles", "sk_tiles",
+                                                   "stages")}},
+        "schedules": scheds,
         "separate": {"ms": s_ms, "tflops": flops / (s_ms * 1e-3) / 1e12,
                      "launches_per_step": len(shapes),
                      "timing": "the 256 sk_gemm_scaled launches replayed from one CUDA graph"},

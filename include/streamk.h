@@ -79,7 +79,9 @@ typedef enum {
 
 /* Plan attributes (sk_plan_set / sk_plan_get).  Settable ones re-plan. */
 typedef enum {
-  SK_ATTR_TILE_N = 1,        /* set/get: BLK_N, 128 or 256; set 0 for automatic */
+  SK_ATTR_TILE_N = 1,        /* set/get: BLK_N, 64, 128 or 256; set 0 for automatic.  64
+                                (128 x 64 tiles, single CTAs only) gives shapes with few
+                                tiles more of them, so fewer CTAs share each tile */
   SK_ATTR_GRID = 2,          /* set: grid size g (in cluster units) for SK_MODE_SK (0 = model);
                                 get: the g in use */
   SK_ATTR_RASTER_GROUP = 3,  /* set/get: tile-raster band height in tiles (0 = automatic) */
@@ -101,10 +103,23 @@ typedef enum {
                                 launch, so the kernel's set-up overlaps the previous kernel
                                 in the stream; it touches global memory only after that
                                 kernel has completed.  0 = plain stream serialisation. */
+  SK_ATTR_INDEPENDENT_INPUTS = 12, /* set/get: 0 (default) or 1.  1 declares that no kernel
+                                earlier in the launch's stream writes A, B (or the scales)
+                                while it may still run, e.g. a stream of independent GEMMs.
+                                With SK_ATTR_PDL 1 the launch then loads A and B and runs its
+                                MAC loop while the previous kernel of the stream finishes; its
+                                reads and writes of C and of the fixup workspace still wait for
+                                that kernel to complete, so C and the workspace keep stream
+                                order.  A wrong declaration (a preceding kernel still writing
+                                A or B) gives wrong results.  No effect with SK_ATTR_PDL 0. */
+  SK_ATTR_STAGES = 13,       /* set/get: pipeline stages of the shared-memory operand ring
+                                the MAC loop cycles through: 0 (set) = all the ring holds
+                                (get returns the count in use), else 2 .. that count;
+                                single and grouped plans; the autotuners choose it */
   SK_ATTR_MODE = 20,         /* get: resolved sk_mode */
   SK_ATTR_TILE_M = 21,       /* get: BLK_M (128) */
   SK_ATTR_TILE_K = 22,       /* get: BLK_K, the depth of one MAC-loop iteration (128 for
-                                BLK_N = 128, 64 for BLK_N = 256) */
+                                BLK_N = 64 and 128, 64 for BLK_N = 256) */
   SK_ATTR_TILES_M = 23,      /* get: ceil(m / BLK_M) */
   SK_ATTR_TILES_N = 24,      /* get: ceil(n / BLK_N) */
   SK_ATTR_TILES = 25,        /* get: t */
@@ -348,10 +363,10 @@ const char* sk_status_string(int status);
  *   trace_ints >= SK_ATTR_TRACE_INTS.
  * sk_grouped_last_error: as sk_last_error.
  * sk_grouped_set: SK_ATTR_TILE_N, SK_ATTR_GRID, SK_ATTR_MODE (replan),
- *   SK_ATTR_TIMEOUT_NS, SK_ATTR_PDL, SK_ATTR_STORE.
+ *   SK_ATTR_TIMEOUT_NS, SK_ATTR_PDL, SK_ATTR_STORE, SK_ATTR_STAGES.
  * sk_grouped_get: SK_ATTR_MODE, TILE_M, TILE_N, TILE_K, GRID, CTAS, TILES,
  *   SK_TILES, DP_TILES, WORKSPACE_BYTES, NUM_SMS, TRACE_CAP, TRACE_INTS,
- *   TIMEOUT_NS, PDL, STORE, SEGMENTS.
+ *   TIMEOUT_NS, PDL, STORE, SEGMENTS, STAGES.
  * sk_grouped_schedule: the host copy of the schedule, 10 int32 per segment
  *   (cta, problem, tile, tm, tn, kb0, kb1, role, peer_first, peer_last), CTA
  *   by CTA in processing order; *count receives the number of segments; with
@@ -388,12 +403,13 @@ int sk_grouped_plan_describe(int count, const int64_t* m, const int64_t* n, cons
 
 /* ---------------------------------------------------------------- autotuning
  * Measured choice among the configurations the planner would otherwise pick
- * by its model: every tile width (128, 256 when n > 128) x cluster size (1,
- * 2 when m > 128; grouped plans: 1) x schedule (data-parallel, two-tile
- * hybrid, basic Stream-K with the model's grid size) is planned, launched
- * once untimed and `reps` times timed with CUDA events on `stream`, and the
- * fastest is kept as the plan's fixed configuration (later sk_plan_get shows
- * it).  C is overwritten with A*B (alpha 1, beta 0) by the timing launches;
+ * by its model: every tile width (64, 128, 256 when n > 128) x cluster size
+ * (1, 2 when m > 128 and the tile is at least 128 wide; grouped plans: 1) x
+ * schedule (data-parallel, two-tile hybrid, basic Stream-K with the model's
+ * grid size) x pipeline depth (the full ring, 3 and 2 stages) is planned,
+ * launched once untimed and `reps` times timed with CUDA events on `stream`,
+ * and the fastest is kept as the plan's fixed configuration (later
+ * sk_plan_get shows it).  C is overwritten with A*B (alpha 1, beta 0) by the timing launches;
  * *best_us (when non-NULL) receives the kept configuration's mean time per
  * launch.  Synchronous.  Candidates that cannot be planned (an attached
  * workspace too small for them) are skipped.  Returns SK_ERR_CUDA when no

@@ -33,7 +33,8 @@ def _nvcc() -> str:
 
 # Sources compiled more than once, each time with its own defines (the kernel
 # instantiations of one tile width per object).
-PER_VARIANT = {"kernels_bn.cu": [("bn128", ["-DSK_BN=128"]), ("bn256", ["-DSK_BN=256"])]}
+PER_VARIANT = {"kernels_bn.cu": [("bn64", ["-DSK_BN=64"]), ("bn128", ["-DSK_BN=128"]),
+                                 ("bn256", ["-DSK_BN=256"])]}
 
 
 def sources():

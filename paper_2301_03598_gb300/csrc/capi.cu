@@ -79,6 +79,8 @@ struct sk_plan_s {
   uint64_t timeout_ns = kDefaultTimeoutNs;
   int debug_skip_signal = -1;
   bool pdl = true;
+  bool early = false;  // SK_ATTR_INDEPENDENT_INPUTS
+  int stages_req = 0;  // SK_ATTR_STAGES (0: all the ring holds)
   int store_req = 0;  // SK_ATTR_STORE
   // TMA descriptor cache
   const void* cached_a = nullptr;
@@ -201,7 +203,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   const int tma_type = f8 ? SK_BF16 : p->a_type;
   const int64_t tk = f8 ? p->k / 2 : p->k;
   const int64_t tlda = f8 ? klda / 2 : klda, tldb = f8 ? kldb / 2 : kldb;
-  const bool use3d = s.tile_n == 128 && tk / sk::kBlkK >= 2;
+  const bool use3d = s.tile_n <= 128 && tk / sk::kBlkK >= 2;
   if (ka != p->cached_a) {
     int st = encode_operand(&p->tm_a, ka, tma_type, km, tk, tlda, sk::kBlkM);
     if (st == SK_OK && use3d)
@@ -255,6 +257,8 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   a.debug_skip_signal = p->debug_skip_signal;
   a.timeout_ns = p->timeout_ns;
   a.pdl = p->pdl ? 1 : 0;
+  a.early = p->pdl && p->early ? 1 : 0;
+  a.stages = p->stages_req;
   if (f8) {
     a.scale_a = p->swap ? scale_b : scale_a;
     a.scale_b = p->swap ? scale_a : scale_b;
@@ -275,6 +279,9 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   if (f8)
     e = sk::launch_f8(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3, a, cooperative,
                       stream);
+  else if (s.tile_n == 64)
+    e = sk::launch_bn64(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3, a, cooperative,
+                        stream);
   else if (s.tile_n == 256)
     e = sk::launch_bn256(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3, a, cooperative,
                          stream);
@@ -359,8 +366,9 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
     p->tile_n_req = 128;
     p->cluster_req = 1;
   }
-  size_t s1 = 0, s2 = 0, s3 = 0;
+  size_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   cudaError_t e = sk::prepare_bn128(&s1);
+  if (e == cudaSuccess) e = sk::prepare_bn64(&s0);
   if (e == cudaSuccess) e = sk::prepare_bn256(&s2);
   if (e == cudaSuccess) e = sk::prepare_f8(&s3);
   if (e != cudaSuccess) {
@@ -437,7 +445,7 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
   const int64_t min_ld_c = p->c_layout == SK_ROW_MAJOR ? p->n : p->m;
   switch (attr) {
     case SK_ATTR_TILE_N: {
-      if (v != 0 && v != 128 && v != 256) return SK_ERR_UNSUPPORTED;
+      if (v != 0 && v != 64 && v != 128 && v != 256) return SK_ERR_UNSUPPORTED;
       if (p->a_type == SK_E4M3) return v == 0 || v == 128 ? SK_OK : SK_ERR_UNSUPPORTED;
       const int old = p->tile_n_req;
       p->tile_n_req = static_cast<int>(v);
@@ -495,6 +503,15 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
       if (v < 0 || v > 2) return SK_ERR_INVALID;
       p->store_req = static_cast<int>(v);
       return SK_OK;
+    case SK_ATTR_INDEPENDENT_INPUTS:
+      if (v != 0 && v != 1) return SK_ERR_INVALID;
+      p->early = v != 0;
+      return SK_OK;
+    case SK_ATTR_STAGES:
+      if (v != 0 && (v < 2 || v > sk::max_stages(p->info.tile_n, p->info.cluster_m)))
+        return SK_ERR_INVALID;
+      p->stages_req = static_cast<int>(v);
+      return SK_OK;
     case SK_ATTR_CLUSTER_M: {
       if (v != 0 && v != 1 && v != 2) return SK_ERR_UNSUPPORTED;
       const int old = p->cluster_req;
@@ -525,6 +542,12 @@ int sk_plan_get(sk_plan_t p, int attr, int64_t* v) {
     case SK_ATTR_DEBUG_SKIP_SIGNAL: *v = p->debug_skip_signal; return SK_OK;
     case SK_ATTR_PDL: *v = p->pdl ? 1 : 0; return SK_OK;
     case SK_ATTR_STORE: *v = p->store_req; return SK_OK;
+    case SK_ATTR_INDEPENDENT_INPUTS: *v = p->early ? 1 : 0; return SK_OK;
+    case SK_ATTR_STAGES: {
+      const int mx = sk::max_stages(s.tile_n, s.cluster_m);
+      *v = p->stages_req >= 2 && p->stages_req < mx ? p->stages_req : mx;
+      return SK_OK;
+    }
     case SK_ATTR_CLUSTER_M: *v = s.cluster_m; return SK_OK;
     case SK_ATTR_CTAS: *v = s.ctas; return SK_OK;
     case SK_ATTR_MODE: *v = s.mode; return SK_OK;
@@ -772,6 +795,7 @@ struct sk_grouped_s {
   uint64_t timeout_ns = kDefaultTimeoutNs;
   bool pdl = true;
   int store_req = 0;
+  int stages_req = 0;  // SK_ATTR_STAGES (0: all the ring holds)
   cudaStream_t last_stream = nullptr;
   bool launched = false;
   InFlight inflight;  // the last launch, for SK_ERR_BUSY
@@ -890,7 +914,7 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
     const int64_t tk = f8 ? k / 2 : k;
     int st = encode_operand(&pr.tmA, A[i], tt, m, tk, tk, sk::kBlkM);
     if (st == SK_OK) st = encode_operand(&pr.tmB, B[i], tt, n, tk, tk, gp.tile_n);
-    const bool use3d = gp.tile_n == 128 && tk / sk::kBlkK >= 2;
+    const bool use3d = gp.tile_n <= 128 && tk / sk::kBlkK >= 2;
     if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmA3, A[i], tt, m, tk, tk, sk::kBlkM);
     if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmB3, B[i], tt, n, tk, tk, gp.tile_n);
     if (st != SK_OK) {
@@ -948,9 +972,11 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
   a.gwalk = g->d_walk;
   a.gstart = g->d_start;
   a.gprobs = g->d_probs;
+  a.stages = g->stages_req;
   const CUtensorMap& any = g->h_probs[0].tmA;
   cudaError_t e = f8                ? sk::launch_grouped_f8(g->c_type, any, a, split, stream)
                   : gp.tile_n == 256 ? sk::launch_grouped_bn256(g->c_type, any, a, split, stream)
+                  : gp.tile_n == 64  ? sk::launch_grouped_bn64(g->c_type, any, a, split, stream)
                                      : sk::launch_grouped_bn128(g->c_type, any, a, split, stream);
   if (e != cudaSuccess) return cuda_status(e);
   g->last_stream = stream;
@@ -1001,8 +1027,9 @@ int sk_grouped_plan(sk_grouped_t* out, int count, const int64_t* m, const int64_
   g->enc_sa.assign(count, nullptr);
   g->enc_sb.assign(count, nullptr);
   if (ab_type == SK_E4M3) g->tile_n_req = 128;  // 128 x 128 x 128 tiles
-  size_t s1 = 0, s2 = 0, s3 = 0;
+  size_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   cudaError_t e = sk::prepare_bn128(&s1);
+  if (e == cudaSuccess) e = sk::prepare_bn64(&s0);
   if (e == cudaSuccess) e = sk::prepare_bn256(&s2);
   if (e == cudaSuccess) e = sk::prepare_f8(&s3);
   void *errw = nullptr, *probs = nullptr, *hprobs = nullptr;
@@ -1113,6 +1140,10 @@ int sk_grouped_set(sk_grouped_t g, int attr, int64_t v) {
       g->store_req = static_cast<int>(v);
       g->table_valid = false;
       return SK_OK;
+    case SK_ATTR_STAGES:
+      if (v != 0 && (v < 2 || v > sk::max_stages(g->plan.tile_n, 1))) return SK_ERR_INVALID;
+      g->stages_req = static_cast<int>(v);
+      return SK_OK;
     default:
       return SK_ERR_INVALID;
   }
@@ -1142,6 +1173,11 @@ int sk_grouped_get(sk_grouped_t g, int attr, int64_t* v) {
     case SK_ATTR_PDL: *v = g->pdl ? 1 : 0; return SK_OK;
     case SK_ATTR_STORE: *v = g->store_req; return SK_OK;
     case SK_ATTR_SEGMENTS: *v = static_cast<int64_t>(gp.segs.size()); return SK_OK;
+    case SK_ATTR_STAGES: {
+      const int mx = sk::max_stages(gp.tile_n, 1);
+      *v = g->stages_req >= 2 && g->stages_req < mx ? g->stages_req : mx;
+      return SK_OK;
+    }
     default: return SK_ERR_INVALID;
   }
 }
@@ -1193,32 +1229,42 @@ int plan_autotune(sk_plan_t p, const void* A, const void* B, const float* scale_
                   const float* scale_b, void* C, int reps, void* stream_v, double* best_us) {
   if (p == nullptr || reps < 1) return SK_ERR_INVALID;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
-  const int saved[4] = {p->tile_n_req, p->cluster_req, p->mode_req, p->grid_req};
+  const int saved[5] = {p->tile_n_req, p->cluster_req, p->mode_req, p->grid_req, p->stages_req};
   const int64_t km = p->swap ? p->n : p->m, kn = p->swap ? p->m : p->n;
   const bool f8 = p->a_type == SK_E4M3;  // BLK_N = 128 only
-  const int tns[2] = {128, 256}, cms[2] = {1, 2}, modes[3] = {SK_MODE_DP, SK_MODE_HYBRID, SK_MODE_SK};
+  const int tns[3] = {64, 128, 256}, cms[2] = {1, 2};
+  const int modes[3] = {SK_MODE_DP, SK_MODE_HYBRID, SK_MODE_SK};
   double best = -1.0;
-  int bt = saved[0], bc = saved[1], bm = saved[2];
+  int bt = saved[0], bc = saved[1], bm = saved[2], bs = saved[4];
   for (int tn : tns) {
     if (tn == 256 && (kn <= 128 || f8)) continue;
+    if (tn == 64 && f8) continue;
     for (int cm : cms) {
-      if (cm == 2 && km <= sk::kTileM) continue;
+      if (cm == 2 && (km <= sk::kTileM || tn == 64)) continue;
+      // pipeline depth: the full ring, and two or three stages
+      const int mx = sk::max_stages(tn, cm);
+      const int stage_opts[3] = {0, 3, 2};
       for (int md : modes) {
-        p->tile_n_req = tn;
-        p->cluster_req = cm;
-        p->mode_req = md;
-        p->grid_req = 0;
-        if (replan(p) != SK_OK) continue;  // e.g. an attached workspace too small for it
-        const double us = time_launches(
-            [&] { return gemm_impl(p, A, B, scale_a, scale_b, C, 1.0f, 0.0f, nullptr, 0, stream); },
-            reps, stream);
-        int dev_status = 0;
-        if (us < 0.0 || sk_last_error(p, &dev_status) != SK_OK) continue;
-        if (best < 0.0 || us < best) {
-          best = us;
-          bt = tn;
-          bc = cm;
-          bm = md;
+        for (int so : stage_opts) {
+          if (so >= mx) continue;
+          p->tile_n_req = tn;
+          p->cluster_req = cm;
+          p->mode_req = md;
+          p->grid_req = 0;
+          p->stages_req = so;
+          if (replan(p) != SK_OK) continue;  // e.g. an attached workspace too small for it
+          const double us = time_launches(
+              [&] { return gemm_impl(p, A, B, scale_a, scale_b, C, 1.0f, 0.0f, nullptr, 0, stream); },
+              reps, stream);
+          int dev_status = 0;
+          if (us < 0.0 || sk_last_error(p, &dev_status) != SK_OK) continue;
+          if (best < 0.0 || us < best) {
+            best = us;
+            bt = tn;
+            bc = cm;
+            bm = md;
+            bs = so;
+          }
         }
       }
     }
@@ -1227,6 +1273,7 @@ int plan_autotune(sk_plan_t p, const void* A, const void* B, const float* scale_
   p->cluster_req = best < 0.0 ? saved[1] : bc;
   p->mode_req = best < 0.0 ? saved[2] : bm;
   p->grid_req = best < 0.0 ? saved[3] : 0;
+  p->stages_req = best < 0.0 ? saved[4] : bs;
   const int st = replan(p);
   if (st != SK_OK) return st;
   if (best_us) *best_us = best;
@@ -1238,32 +1285,39 @@ int grouped_autotune(sk_grouped_t g, const void* const* A, const void* const* B,
                      void* stream_v, double* best_us) {
   if (g == nullptr || reps < 1) return SK_ERR_INVALID;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
-  const int saved[3] = {g->tile_n_req, g->mode_req, g->grid_req};
-  const int tns[2] = {128, 256}, modes[3] = {SK_MODE_DP, SK_MODE_HYBRID, SK_MODE_SK};
+  const int saved[4] = {g->tile_n_req, g->mode_req, g->grid_req, g->stages_req};
+  const int tns[3] = {64, 128, 256}, modes[3] = {SK_MODE_DP, SK_MODE_HYBRID, SK_MODE_SK};
+  const int stage_opts[3] = {0, 3, 2};
   double best = -1.0;
-  int bt = saved[0], bm = saved[1];
+  int bt = saved[0], bm = saved[1], bs = saved[3];
   for (int tn : tns) {
-    if (tn == 256 && g->ab_type == SK_E4M3) continue;
+    if (tn != 128 && g->ab_type == SK_E4M3) continue;
     for (int md : modes) {
-      g->tile_n_req = tn;
-      g->mode_req = md;
-      g->grid_req = 0;
-      if (grouped_replan(g) != SK_OK) continue;
-      const double us = time_launches(
-          [&] { return grouped_impl(g, A, B, SA, SB, C, nullptr, nullptr, nullptr, 0, stream); },
-          reps, stream);
-      int dev_status = 0;
-      if (us < 0.0 || sk_grouped_last_error(g, &dev_status) != SK_OK) continue;
-      if (best < 0.0 || us < best) {
-        best = us;
-        bt = tn;
-        bm = md;
+      for (int so : stage_opts) {
+        if (so >= sk::max_stages(tn, 1)) continue;
+        g->tile_n_req = tn;
+        g->mode_req = md;
+        g->grid_req = 0;
+        g->stages_req = so;
+        if (grouped_replan(g) != SK_OK) continue;
+        const double us = time_launches(
+            [&] { return grouped_impl(g, A, B, SA, SB, C, nullptr, nullptr, nullptr, 0, stream); },
+            reps, stream);
+        int dev_status = 0;
+        if (us < 0.0 || sk_grouped_last_error(g, &dev_status) != SK_OK) continue;
+        if (best < 0.0 || us < best) {
+          best = us;
+          bt = tn;
+          bm = md;
+          bs = so;
+        }
       }
     }
   }
   g->tile_n_req = best < 0.0 ? saved[0] : bt;
   g->mode_req = best < 0.0 ? saved[1] : bm;
   g->grid_req = best < 0.0 ? saved[2] : 0;
+  g->stages_req = best < 0.0 ? saved[3] : bs;
   const int st = grouped_replan(g);
   if (st != SK_OK) return st;
   if (best_us) *best_us = best;

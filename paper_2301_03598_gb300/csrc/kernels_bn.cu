@@ -6,6 +6,7 @@
 
 #include "../../include/streamk.h"
 #include "launch.h"
+#include "planner.h"
 #include "sk_kernel.cuh"
 
 #ifndef SK_BN
@@ -65,11 +66,30 @@ static cudaError_t launch_cm(int c_dtype, const CUtensorMap& ta, const CUtensorM
   }
 }
 
+// BLK_N = 64 tiles (the narrow configuration for shapes with few tiles) run on
+// single CTAs only.
+constexpr bool kPairs = SK_BN != 64;
+static_assert(Cfg<SK_BN, 1>::kStages == max_stages(SK_BN, 1) &&
+                  (!kPairs || Cfg<SK_BN, 2>::kStages == max_stages(SK_BN, 2)),
+              "the host's stage count matches the kernel's ring");
+
+template <bool kWithPairs>
+static cudaError_t launch_any(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
+                              const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
+                              const SkArgs& args, bool cooperative, cudaStream_t stream) {
+  if (cluster_m == 2) {
+    if constexpr (kWithPairs)
+      return launch_cm<2>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream);
+    else
+      return cudaErrorInvalidValue;
+  }
+  return launch_cm<1>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream);
+}
+
 cudaError_t SK_CAT(launch_bn, SK_BN)(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
                          const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
                          const SkArgs& args, bool cooperative, cudaStream_t stream) {
-  return cluster_m == 2 ? launch_cm<2>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream)
-                        : launch_cm<1>(c_dtype, ta, tb, tc, ta3, tb3, args, cooperative, stream);
+  return launch_any<kPairs>(c_dtype, cluster_m, ta, tb, tc, ta3, tb3, args, cooperative, stream);
 }
 
 // Grouped launches: single CTAs, the walk table and problem table in args
@@ -123,15 +143,25 @@ static cudaError_t set_smem() {
                               cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<SK_BN, CM>::kSmemBytes);
 }
 
-cudaError_t SK_CAT(prepare_bn, SK_BN)(size_t* smem_bytes) {
+template <bool kWithPairs>
+static cudaError_t prepare_all() {
   cudaError_t e;
   if ((e = set_smem<1, float>()) != cudaSuccess) return e;
   if ((e = set_smem<1, __nv_bfloat16>()) != cudaSuccess) return e;
   if ((e = set_smem<1, __half>()) != cudaSuccess) return e;
-  if ((e = set_smem<2, float>()) != cudaSuccess) return e;
-  if ((e = set_smem<2, __nv_bfloat16>()) != cudaSuccess) return e;
-  if ((e = set_smem<2, __half>()) != cudaSuccess) return e;
-  static_assert(Cfg<SK_BN, 1>::kSmemBytes == Cfg<SK_BN, 2>::kSmemBytes, "one size for both");
+  if constexpr (kWithPairs) {
+    if ((e = set_smem<2, float>()) != cudaSuccess) return e;
+    if ((e = set_smem<2, __nv_bfloat16>()) != cudaSuccess) return e;
+    if ((e = set_smem<2, __half>()) != cudaSuccess) return e;
+    static_assert(!kWithPairs || Cfg<SK_BN, 1>::kSmemBytes == Cfg<SK_BN, 2>::kSmemBytes,
+                  "one size for both");
+  }
+  return cudaSuccess;
+}
+
+cudaError_t SK_CAT(prepare_bn, SK_BN)(size_t* smem_bytes) {
+  const cudaError_t e = prepare_all<kPairs>();
+  if (e != cudaSuccess) return e;
   *smem_bytes = static_cast<size_t>(Cfg<SK_BN, 1>::kSmemBytes);
   return cudaSuccess;
 }

@@ -1,4 +1,4 @@
-// Kernel launchers, one translation unit per BLK_N.
+// Kernel launchers, one object per BLK_N (64, 128, 256) and one for E4M3.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -10,9 +10,13 @@ namespace sk {
 // c_dtype: SK_F32 / SK_BF16 / SK_F16.  cluster_m: 1, or 2 for CTA pairs along M
 // (the grid is args.grid units of cluster_m CTAs).  ta/tb: 2-D operand maps
 // (boxes of one 64-wide k-block); ta3/tb3: the 3-D views whose boxes hold two
-// k-blocks, used by BLK_N = 128 (pass the 2-D maps when unused).
+// k-blocks, used by BLK_N = 64 and 128 (pass the 2-D maps when unused).
 // cooperative: CTAs wait on one another, so the launch must guarantee
 // co-residency.
+// BLK_N = 64: single CTAs only (cluster_m 2 returns cudaErrorInvalidValue).
+cudaError_t launch_bn64(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
+                        const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
+                        const SkArgs& args, bool cooperative, cudaStream_t stream);
 cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
                          const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
                          const SkArgs& args, bool cooperative, cudaStream_t stream);
@@ -21,6 +25,8 @@ cudaError_t launch_bn256(int c_dtype, int cluster_m, const CUtensorMap& ta, cons
                          const SkArgs& args, bool cooperative, cudaStream_t stream);
 // A grouped launch (args.grid single CTAs walking args.gwalk); tm is any valid
 // tensor map (the kernel's tensor-map parameters are unused there).
+cudaError_t launch_grouped_bn64(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
+                                bool cooperative, cudaStream_t stream);
 cudaError_t launch_grouped_bn128(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
                                  bool cooperative, cudaStream_t stream);
 cudaError_t launch_grouped_bn256(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
@@ -35,6 +41,7 @@ cudaError_t launch_f8(int c_dtype, int cluster_m, const CUtensorMap& ta, const C
 cudaError_t launch_grouped_f8(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
                               bool cooperative, cudaStream_t stream);
 // Dynamic shared memory of one CTA; also sets the kernels' opt-in limit.
+cudaError_t prepare_bn64(size_t* smem_bytes);
 cudaError_t prepare_bn128(size_t* smem_bytes);
 cudaError_t prepare_bn256(size_t* smem_bytes);
 cudaError_t prepare_f8(size_t* smem_bytes);

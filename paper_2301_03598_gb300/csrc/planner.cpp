@@ -38,36 +38,45 @@ int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]) {
 // configuration (BLK_N, CTAs per cluster along M).  The first four are the
 // terms of Appendix A.1: a = fixed per-launch cost, b = a schedule with split
 // tiles (spill, signal, wait), c = one MAC-loop iteration of a unit
-// (BLK_M x BLK_N x BLK_K), d = reading and adding one more peer's partials.  The
-// fifth, e, is the per-segment cost (one accumulator through the epilogue),
-// which the paper's model folds into c.  Fitted by relative least squares to
-// the measured times of the 2,000-shape log-uniform sweep planned with each
-// configuration and each of data-parallel, two-tile hybrid and basic Stream-K
-// forced (12 plans per shape).
-void model_coefficients(int tile_n, int cluster_m, double out[5]) {
-  static const double k128x1[5] = {3.782, 3.548, 0.5514, 0.726, 0.157};
-  static const double k256x1[5] = {4.349, 8.006, 0.3922, 0.839, 0.144};
-  static const double k128x2[5] = {4.501, 4.326, 0.4446, 0.508, 0.309};
-  static const double k256x2[5] = {5.622, 9.815, 0.2957, 0.474, 0.203};
+// (BLK_M x BLK_N x BLK_K), d = reading and adding one more peer's partials.
+// The paper's model folds the epilogue into c; two more terms make it
+// explicit: e = per tile segment (one accumulator handed to the epilogue),
+// and f = the shortest period of consecutive whole tiles of a unit: the next
+// tile's MAC loop overlaps this tile's epilogue, so a tile takes
+// max(c * iterations, f), and f (the epilogue's own time) paces tiles of few
+// iterations.  Fitted by relative least squares to the measured times of the
+// 2,000-shape log-uniform sweep planned with each configuration and each of
+// data-parallel, two-tile hybrid and basic Stream-K forced (15 plans per
+// shape).
+void model_coefficients(int tile_n, int cluster_m, double out[kModelTerms]) {
+  static const double k64x1[kModelTerms] = {3.414, 2.878, 0.4127, 0.468, 0.181, 0.997};
+  static const double k128x1[kModelTerms] = {3.617, 3.848, 0.5570, 0.554, 0.164, 1.388};
+  static const double k256x1[kModelTerms] = {4.294, 8.719, 0.3935, 0.455, 0.145, 1.101};
+  static const double k128x2[kModelTerms] = {4.197, 4.614, 0.4505, 0.441, 0.330, 1.687};
+  static const double k256x2[kModelTerms] = {4.642, 10.448, 0.3041, 0.350, 0.440, 2.371};
   const double* c = cluster_m == 2 ? (tile_n == 256 ? k256x2 : k128x2)
-                                   : (tile_n == 256 ? k256x1 : k128x1);
-  for (int i = 0; i < 5; ++i) out[i] = c[i];
+                                   : (tile_n == 256 ? k256x1 : tile_n == 64 ? k64x1 : k128x1);
+  for (int i = 0; i < kModelTerms; ++i) out[i] = c[i];
 }
 
 // Modelled time of a resolved schedule: the Appendix A.1 terms evaluated on
-// the busiest unit (its Stream-K share plus its data-parallel tiles), plus the
-// per-segment epilogue term.
-static double predict_us(const sk_schedule_info& s, const double c[5]) {
+// the busiest unit (its Stream-K share plus its data-parallel tiles, each of
+// those at least f), plus the per-segment term.
+static double predict_us(const sk_schedule_info& s, const double c[kModelTerms]) {
   const int64_t ipt = s.iters_per_tile, g = std::max<int64_t>(1, s.grid);
   if (s.tiles == 0 || ipt == 0) return c[0];
   const int64_t sk_iters = s.sk_tiles * ipt;
   const int64_t q = sk_iters / g;
-  const int64_t iters_per_unit = cdiv(sk_iters, g) + cdiv(s.dp_tiles, g) * ipt;
+  const int64_t sk_share = cdiv(sk_iters, g);
+  const int64_t dp_per_unit = cdiv(s.dp_tiles, g);
   const double split = s.workspace_bytes > 0 ? 1.0 : 0.0;
   const int64_t peers = s.sk_tiles ? cdiv(ipt, std::max<int64_t>(q, 1)) : 1;
-  const int64_t segs = (s.sk_tiles ? cdiv(q + 1, ipt) + 1 : 0) + cdiv(s.dp_tiles, g);
-  return c[0] + c[1] * split + c[2] * static_cast<double>(iters_per_unit) +
-         c[3] * static_cast<double>(peers - 1) * split + c[4] * static_cast<double>(segs);
+  const int64_t sk_segs = s.sk_tiles ? cdiv(q + 1, ipt) + 1 : 0;
+  const double tile_period = std::max(c[2] * static_cast<double>(ipt), c[5]);
+  return c[0] + c[1] * split + c[2] * static_cast<double>(sk_share) +
+         static_cast<double>(dp_per_unit) * tile_period +
+         c[3] * static_cast<double>(peers - 1) * split +
+         c[4] * static_cast<double>(sk_segs + dp_per_unit);
 }
 
 static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid,
@@ -75,19 +84,26 @@ static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n,
 
 // Planning with choices left open: a tile width or cluster size of 0 tries
 // each candidate configuration, SK_MODE_AUTO tries data-parallel tiling, the
-// two-tile hybrid and basic Stream-K (the latter at every grid size g), and
+// two-tile hybrid and, below one full wave of tiles, basic Stream-K at every
+// grid size g (at a wave or more the hybrid is the paper's Stream-K form; a
+// Stream-K run over many tiles per CTA also loses the raster's L2 reuse), and
 // the schedule with the smallest modelled time is kept (ties: the earliest
 // candidate, i.e. narrower tiles, single CTAs, data-parallel, smaller g).
+// A schedule that splits tiles must beat the best data-parallel one by more
+// than the model's error (kSplitMargin, relative): the model's rms error on
+// the sweep is 5-8%, and a mistaken split costs more than a mistaken wave.
 int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
              int cluster_m, int num_sms, sk_schedule_info* out) {
   if (out == nullptr || num_sms < 1) return SK_ERR_INVALID;
   if (cluster_m != 0 && cluster_m != 1 && cluster_m != 2) return SK_ERR_UNSUPPORTED;
-  if (tile_n != 0 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  if (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  if (tile_n == 64 && cluster_m == 2) return SK_ERR_UNSUPPORTED;
   if (mode < SK_MODE_AUTO || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
-  int tns[2], ntn = 0, cms[2], ncm = 0, modes[3], nmode = 0;
+  int tns[3], ntn = 0, cms[2], ncm = 0, modes[3], nmode = 0;
   if (tile_n) {
     tns[ntn++] = tile_n;
   } else {
+    if (cluster_m != 2) tns[ntn++] = 64;  // narrow tiles: more tiles for few-tile shapes
     tns[ntn++] = 128;
     if (n > 128) tns[ntn++] = 256;  // a 256-wide tile over <= 128 columns only wastes work
   }
@@ -113,9 +129,10 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
       if (status != SK_OK) status = st;
       return;
     }
-    double c[5];
+    double c[kModelTerms];
     model_coefficients(s.tile_n, s.cluster_m, c);
-    const double us = predict_us(s, c);
+    double us = predict_us(s, c);
+    if (mode == SK_MODE_AUTO && s.workspace_bytes > 0) us *= 1.0 + kSplitMargin;
     if (status != SK_OK || us < best_us) {
       *out = s;
       best_us = us;
@@ -124,11 +141,13 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
   };
   for (int i = 0; i < ntn; ++i) {
     for (int j = 0; j < ncm; ++j) {
+      if (tns[i] == 64 && cms[j] == 2) continue;  // BLK_N = 64 runs on single CTAs
       for (int h = 0; h < nmode; ++h) {
         if (mode == SK_MODE_AUTO && modes[h] == SK_MODE_SK && grid == 0) {
           const int64_t units = num_sms / cms[j];
-          const int64_t iters =
-              cdiv(m, int64_t(kTileM) * cms[j]) * cdiv(n, tns[i]) * cdiv(k, tile_k_for(tns[i]));
+          const int64_t tiles = cdiv(m, int64_t(kTileM) * cms[j]) * cdiv(n, tns[i]);
+          if (tiles >= units) continue;  // a wave or more: the hybrids cover it
+          const int64_t iters = tiles * cdiv(k, tile_k_for(tns[i]));
           const int64_t g_max = std::min<int64_t>(units, std::max<int64_t>(iters, 1));
           for (int64_t g = 1; g <= g_max; ++g) consider(SK_MODE_SK, tns[i], cms[j], static_cast<int>(g));
         } else {
@@ -147,7 +166,8 @@ static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n,
   if (cluster_m != 1 && cluster_m != 2) return SK_ERR_UNSUPPORTED;
   if (num_sms > kMaxGrid || grid > num_sms) return SK_ERR_INVALID;
   if (mode < SK_MODE_DP || mode > SK_MODE_HYBRID_ONE_TILE) return SK_ERR_INVALID;
-  if (tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  if (tile_n != 64 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  if (tile_n == 64 && cluster_m != 1) return SK_ERR_UNSUPPORTED;
   // Index arithmetic on the device is 32-bit for tiles and k-blocks.
   if (m > (int64_t(1) << 31) - 1 || n > (int64_t(1) << 31) - 1 || k > (int64_t(1) << 31) - 1)
     return SK_ERR_INVALID;
@@ -177,7 +197,7 @@ static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n,
   const int64_t t = s.tiles;
   const int64_t ipt = s.iters_per_tile;
   const int p = num_sms;
-  double coef[5];
+  double coef[kModelTerms];
   model_coefficients(s.tile_n, s.cluster_m, coef);
 
   if (t == 0 || ipt == 0) {
@@ -468,18 +488,18 @@ double group_dram_bytes(const std::vector<GroupShape>& ps, const std::vector<int
 
 // Modelled time of a grouped schedule: the busiest CTA's iterations and
 // segments under the Appendix A.1 terms plus the per-segment term.
-double predict_group(const GroupPlan& gp, const double c[5]) {
+double predict_group(const GroupPlan& gp, const double c[kModelTerms]) {
   double worst = 0.0;
   int64_t peers_max = 1;
   for (size_t x = 0; x + 1 < gp.start.size(); ++x) {
-    int64_t iters = 0, segs = 0;
+    double t = 0.0;
     for (int32_t i = gp.start[x]; i < gp.start[x + 1]; ++i) {
       const GroupSeg& r = gp.segs[static_cast<size_t>(i)];
-      iters += r.kb1 - r.kb0;
-      ++segs;
+      const double mac = c[2] * static_cast<double>(r.kb1 - r.kb0);
+      t += (r.role == kRoleWhole ? std::max(mac, c[5]) : mac) + c[4];
       if (r.role == kRoleOwner) peers_max = std::max<int64_t>(peers_max, r.peer_last - r.peer_first + 2);
     }
-    worst = std::max(worst, c[2] * static_cast<double>(iters) + c[4] * static_cast<double>(segs));
+    worst = std::max(worst, t);
   }
   const double split = gp.split ? 1.0 : 0.0;
   return c[0] + c[1] * split + c[3] * static_cast<double>(peers_max - 1) * split + worst;
@@ -503,7 +523,7 @@ int describe_grouped_dp(int count, const int64_t* m, const int64_t* n, const int
   if (out == nullptr || count < 1 || m == nullptr || n == nullptr || k == nullptr || num_sms < 1 ||
       num_sms > kMaxGrid)
     return SK_ERR_INVALID;
-  if (tile_n != 0 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  if (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
   int64_t max_n = 0;
   for (int i = 0; i < count; ++i) {
     if (m[i] < 1 || n[i] < 1 || k[i] < 1 || m[i] > INT32_MAX || n[i] > INT32_MAX || k[i] > INT32_MAX)
@@ -545,7 +565,7 @@ int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_
   if (out == nullptr || count < 1 || m == nullptr || n == nullptr || k == nullptr || num_sms < 1 ||
       num_sms > kMaxGrid || grid < 0 || grid > num_sms)
     return SK_ERR_INVALID;
-  if (tile_n != 0 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  if (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
   if (mode != SK_MODE_AUTO && mode != SK_MODE_DP && mode != SK_MODE_SK && mode != SK_MODE_HYBRID)
     return SK_ERR_UNSUPPORTED;
   int64_t max_n = 0;
@@ -580,7 +600,7 @@ int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_
       total_iters += p.tiles * p.ipt;
     }
     if (t > INT32_MAX || total_iters > INT32_MAX) return SK_ERR_INVALID;
-    double c[5];
+    double c[kModelTerms];
     model_coefficients(bn, 1, c);
     const int64_t p = num_sms;
     // candidate (mode, sk_tiles, grid)

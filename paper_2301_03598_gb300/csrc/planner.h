@@ -10,8 +10,16 @@ namespace sk {
 
 constexpr int kTileM = 128;
 // BLK_K, the depth of one MAC-loop iteration: two 64-wide k-blocks for
-// BLK_N = 128 (one pipeline stage each, see the kernel's Cfg), one for 256.
-constexpr int tile_k_for(int tile_n) { return tile_n == 128 ? 128 : 64; }
+// BLK_N = 64 and 128 (one pipeline stage holds both, see the kernel's Cfg),
+// one for 256.
+constexpr int tile_k_for(int tile_n) { return tile_n <= 128 ? 128 : 64; }
+// Pipeline stages the kernel's 192 KiB shared-memory ring holds for a tile
+// configuration (the kernel's Cfg<BN, CM>::kStages): a stage is one MAC-loop
+// iteration of A (128 rows) and this CTA's BN / CM rows of B, 128 bytes each
+// per 64-deep k-block.
+constexpr int max_stages(int tile_n, int cluster_m) {
+  return (192 * 1024) / (tile_k_for(tile_n) / 64 * (kTileM + tile_n / cluster_m) * 128);
+}
 // Workspace layout: kFlagBytes of flags at offset 0 (kFlagsPerCta uint32 per
 // CTA, one per 32-row x 128-byte unit of its partial tile, at most kMaxGrid
 // CTAs), then one BLK_M x BLK_N FP32 partial slot per CTA.
@@ -22,7 +30,13 @@ constexpr int64_t kFlagBytes = static_cast<int64_t>(kMaxGrid) * kFlagsPerCta * 4
 int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
              int cluster_m, int num_sms, sk_schedule_info* out);
 int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]);
-void model_coefficients(int tile_n, int cluster_m, double out[5]);
+// Terms of the planner's time model per tile configuration: Appendix A.1's
+// a, b, c, d, then e (per tile segment) and f (shortest whole-tile period).
+constexpr int kModelTerms = 6;
+// AUTO keeps a split schedule only if its modelled time, raised by this
+// fraction, still beats every data-parallel candidate.
+constexpr double kSplitMargin = 0.10;
+void model_coefficients(int tile_n, int cluster_m, double out[kModelTerms]);
 int64_t workspace_bytes_for(int grid, int tile_n);
 
 // A grouped launch's schedule over the problems' concatenated iteration space

@@ -344,7 +344,7 @@ int launch_slot(sk_server_s* sv, Slot& s) {
     const int64_t tk = f8 ? r.k / 2 : r.k;
     st = cached_map(sv, &pr.tmA, 0, r.A, tt, r.m, tk, sk::kBlkM);
     if (st == SK_OK) st = cached_map(sv, &pr.tmB, 0, r.B, tt, r.n, tk, gp.tile_n);
-    const bool use3d = gp.tile_n == 128 && tk / sk::kBlkK >= 2;
+    const bool use3d = gp.tile_n <= 128 && tk / sk::kBlkK >= 2;
     if (st == SK_OK && use3d) st = cached_map(sv, &pr.tmA3, 1, r.A, tt, r.m, tk, sk::kBlkM);
     if (st == SK_OK && use3d) st = cached_map(sv, &pr.tmB3, 1, r.B, tt, r.n, tk, gp.tile_n);
     if (st != SK_OK) return st;
@@ -394,6 +394,7 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   s.h_status[0] = 0;
   e = f8                ? sk::launch_grouped_f8(sv->c_type, any, a, split, s.stream)
       : gp.tile_n == 256 ? sk::launch_grouped_bn256(sv->c_type, any, a, split, s.stream)
+      : gp.tile_n == 64  ? sk::launch_grouped_bn64(sv->c_type, any, a, split, s.stream)
                          : sk::launch_grouped_bn128(sv->c_type, any, a, split, s.stream);
   if (e == cudaSuccess && split) e = cudaEventRecord(sv->split_done, s.stream);
   if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
@@ -526,8 +527,9 @@ int sk_server_create(sk_server_t* out, sk_dtype ab_type, sk_dtype c_type, int ma
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return SK_ERR_CUDA;
   if (major != 10 || minor != 3) return SK_ERR_DEVICE;
-  size_t s1 = 0, s2 = 0, s3 = 0;
+  size_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   cudaError_t e = sk::prepare_bn128(&s1);
+  if (e == cudaSuccess) e = sk::prepare_bn64(&s0);
   if (e == cudaSuccess) e = sk::prepare_bn256(&s2);
   if (e == cudaSuccess) e = sk::prepare_f8(&s3);
   if (e != cudaSuccess) return cuda_status(e);

@@ -147,6 +147,13 @@ struct SkArgs {
   int32_t debug_skip_signal;  // CTA index that withholds its Signal (tests), -1 off
   uint64_t timeout_ns;
   int32_t pdl;  // launched with programmatic stream serialization (host side only)
+  // 1: the operands (A, B, scales) are not written by the kernels before this
+  // launch in its stream, so the producer and MMA warps start before those
+  // kernels complete; only the epilogue warps (C, workspace) wait for them
+  int32_t early;
+  // pipeline stages the ring cycles through: 0 = all the kernel's ring holds,
+  // else 2 .. that count
+  int32_t stages;
   // grouped launches: the walk table and, per CTA x, the problems holding
   // its first Stream-K iteration (gstart[2x]) and first data-parallel tile
   // (gstart[2x + 1]); tiles / sk_tiles / sk_q / sk_r / grid describe the

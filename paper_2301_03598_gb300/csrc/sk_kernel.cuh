@@ -48,8 +48,8 @@ constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 // Shared-memory stage ring per CTA: 192 KiB of operand stages.  A k-block is
 // one 128-byte row per operand row: 64 16-bit elements, or 128 E4M3 elements
 // (F8).  A stage holds KD consecutive k-blocks (one MAC-loop iteration):
-// KD = 2 for BLK_N = 128, whose 2-D stages are too small for the SM's TMA
-// path (a stage costs about as much as its bytes), KD = 1 for 256.
+// KD = 2 for BLK_N = 64 and 128, whose 2-D stages are too small for the SM's
+// TMA path (a stage costs about as much as its bytes), KD = 1 for 256.
 //
 // F8 (E4M3 operands with one FP32 scale per 128 x 128 block of A and of B):
 // the host describes the operands to TMA as 16-bit rows of k/2 elements (the
@@ -62,13 +62,14 @@ constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 // k-blocks) is zero-filled by TMA and carries scale 0.
 template <int BN, int CM, bool F8 = false>
 struct Cfg {
-  static constexpr int KD = BN == 128 ? 2 : 1;
+  static constexpr int KD = BN <= 128 ? 2 : 1;
   static constexpr int kSubA = kBlkM * 128;          // one k-block of this CTA's 128 A rows
   static constexpr int kSubB = (BN / CM) * 128;      // one k-block of its BN/CM B rows
   static constexpr int kABytes = KD * kSubA;
   static constexpr int kBBytes = KD * kSubB;
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kStages = (192 * 1024) / kStageBytes;  // 3, 4 (BN 128); 4, 6 (BN 256); F8: 6
+  // 4, 4 (BN 64); 3, 4 (BN 128); 4, 6 (BN 256); F8: 3
+  static constexpr int kStages = (192 * 1024) / kStageBytes;
   static constexpr int kAccBufs = F8 ? 3 : 2;
   // F8: three product buffers and the segment sum; else two accumulators
   static constexpr int kTmemCols = F8 ? 4 * BN : 2 * BN;
@@ -501,7 +502,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   static_assert(!GROUPED || CM == 1, "grouped launches use single CTAs");
   using C_ = Cfg<BN, CM, F8>;
   constexpr int NB = C_::kAccBufs;
-  constexpr int S = C_::kStages;
+  // Stages in use: the ring holds C_::kStages (the barrier layout is sized
+  // for them); a plan may cycle through fewer (SkArgs::stages, autotuned).
+  const int S = a.stages >= 2 && a.stages < C_::kStages ? a.stages : C_::kStages;
   constexpr int KD = C_::KD;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -514,10 +517,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto stage_a = [&](int s) { return base + static_cast<uint32_t>(s * C_::kStageBytes); };
   auto stage_b = [&](int s) { return base + static_cast<uint32_t>(s * C_::kStageBytes + C_::kABytes); };
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
-  auto accf_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
-  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * S + NB + b); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * S + 2 * NB);
+  auto empty_bar = [&](int s) { return bar0 + 8u * (C_::kStages + s); };
+  auto accf_bar = [&](int b) { return bar0 + 8u * (2 * C_::kStages + b); };
+  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * C_::kStages + NB + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * C_::kStages + 2 * NB);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -577,10 +580,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   if constexpr (kPair) cluster_sync();  // both CTAs' barriers exist before either signals them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  // Everything above overlaps the previous kernel under programmatic
-  // dependent launch; nothing is loaded into shared memory or written to
-  // global memory before this point.
-  grid_dependency_wait();
+  // Everything above overlaps the previous kernel in the stream under
+  // programmatic dependent launch; nothing is loaded into shared memory or
+  // written to global memory before this point.  By default every thread now
+  // waits for that kernel to complete.  With a.early the caller has declared
+  // the operands independent of the preceding kernels: the producer and MMA
+  // warps go ahead, so the MAC loop overlaps the previous kernel's tail, and
+  // the next kernel may launch at once; only the epilogue warps, which read
+  // and write C and the fixup workspace, wait.
+  if (!a.early || warp >= kEpiWarp0) grid_dependency_wait();
+  if (a.early && warp == 1 && lane == 0) grid_launch_dependents();
 
   if (warp == 0) {
     if (lane == 0) {

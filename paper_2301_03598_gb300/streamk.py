@@ -23,7 +23,9 @@ MODES = {"auto": 0, "dp": 1, "sk": 2, "hybrid": 3, "hybrid1": 4}
 MODE_NAMES = {v: k for k, v in MODES.items()}
 ATTRS = {
     "tile_n": 1, "grid": 2, "raster_group": 3, "timeout_ns": 4, "lda": 5, "ldb": 6, "ldc": 7,
-    "debug_skip_signal": 8, "pdl": 9, "cluster_m": 10, "store": 11, "mode": 20, "tile_m": 21, "tile_k": 22, "tiles_m": 23,
+    "debug_skip_signal": 8, "pdl": 9, "cluster_m": 10, "store": 11, "independent_inputs": 12,
+    "stages": 13,
+    "mode": 20, "tile_m": 21, "tile_k": 22, "tiles_m": 23,
     "tiles_n": 24, "tiles": 25, "iters_per_tile": 26, "sk_tiles": 27, "dp_tiles": 28,
     "workspace_bytes": 29, "num_sms": 30, "trace_ints": 31, "trace_cap": 32, "ctas": 33,
     "segments": 34,
@@ -369,7 +371,8 @@ class GroupedPlan:
 
     def info(self):
         names = ("mode", "tile_m", "tile_n", "tile_k", "grid", "ctas", "tiles", "sk_tiles",
-                 "dp_tiles", "workspace_bytes", "num_sms", "trace_cap", "trace_ints", "segments")
+                 "dp_tiles", "workspace_bytes", "num_sms", "trace_cap", "trace_ints", "segments",
+                 "stages")
         return {name: self.get(name) for name in names}
 
     def destroy(self):

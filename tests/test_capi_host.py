@@ -82,16 +82,32 @@ def test_describe_config_shapes():
 def test_auto_configuration_is_a_candidate(m, n, k):
     """With tile width and cluster size left open the planner returns one of
     the fixed-configuration plans: BLK_N 256 only for n > 128, CTA pairs only
-    for m > 128."""
+    for m > 128 and BLK_N >= 128."""
     d = sk.sk_plan_describe(m, n, k, num_sms=152)
-    assert d["tile_n"] in ((128, 256) if n > 128 else (128,))
-    assert d["cluster_m"] in ((1, 2) if m > 128 else (1,))
+    assert d["tile_n"] in ((64, 128, 256) if n > 128 else (64, 128))
+    assert d["cluster_m"] in ((1, 2) if m > 128 and d["tile_n"] > 64 else (1,))
     fixed = sk.sk_plan_describe(m, n, k, tile_n=d["tile_n"], cluster_m=d["cluster_m"], num_sms=152)
     assert fixed == d
     # a fixed tile width leaves only the cluster size open, and vice versa
-    for tn in ((128, 256) if n > 128 else (128,)):
+    for tn in ((64, 128, 256) if n > 128 else (64, 128)):
         assert sk.sk_plan_describe(m, n, k, tile_n=tn, num_sms=152)["tile_n"] == tn
     assert sk.sk_plan_describe(m, n, k, cluster_m=1, num_sms=152)["cluster_m"] == 1
+    assert sk.sk_plan_describe(m, n, k, cluster_m=2, num_sms=152)["tile_n"] in (128, 256)
+
+
+def test_narrow_tiles_run_on_single_ctas():
+    """BLK_N = 64 (128 x 64 tiles, two 64-deep k-blocks per iteration) is planned
+    on single CTAs; asking for it with CTA pairs is unsupported."""
+    d = sk.sk_plan_describe(384, 384, 4096, "sk", tile_n=64, num_sms=152)
+    assert (d["tile_m"], d["tile_n"], d["tile_k"], d["cluster_m"]) == (128, 64, 128, 1)
+    assert (d["tiles_m"], d["tiles_n"], d["iters_per_tile"]) == (3, 6, 32)
+    assert d["workspace_bytes"] == 4096 * 32 + d["ctas"] * 128 * 64 * 4 or d["workspace_bytes"] == 0
+    with pytest.raises(sk.StreamKError) as e:
+        sk.sk_plan_describe(384, 384, 4096, "sk", tile_n=64, cluster_m=2, num_sms=152)
+    assert e.value.status == sk.SK_ERR_UNSUPPORTED
+    prob = S.Problem(384, 384, 4096, 128, 64, 128)
+    sched = S.persistent_schedule(prob, d["grid"], d["sk_tiles"], d["raster_group"])
+    assert max(len(c) for c in sched.ctas) <= d["max_segments"]
 
 
 @pytest.mark.parametrize("m,n,k,mode", [(8192, 8192, 1024, "hybrid"), (4096, 2048, 512, "sk"),

@@ -153,7 +153,7 @@ def test_grouped_autotune_keeps_a_correct_configuration():
         Cs = [torch.zeros(p.m, p.n, dtype=torch.bfloat16, device="cuda") for p in probs]
         us = sk.sk_grouped_autotune(plan, As, Bs, Cs, reps=2)
         info = plan.info()
-        assert us > 0 and info["tile_n"] in (128, 256)
+        assert us > 0 and info["tile_n"] in (64, 128, 256)
         for C in Cs:
             C.zero_()
         sk.sk_grouped_gemm(plan, As, Bs, Cs)

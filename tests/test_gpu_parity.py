@@ -30,6 +30,9 @@ pytestmark = pytest.mark.gpu
     ("sk", {"grid": 148}),
     ("hybrid", {}),
     ("hybrid1", {}),
+    ("sk", {"tile_n": 64, "grid": 18}),    # 128 x 64 tiles: g = t, data-parallel
+    ("sk", {"tile_n": 64, "grid": 100}),
+    ("dp", {"tile_n": 64}),
 ])
 def test_config_384_fp16_fp32(mode, attrs):
     prob = Problem(384, 384, 4096, "f16", "f32", "uniform", seed=1)
@@ -41,6 +44,8 @@ def test_config_384_fp16_fp32(mode, attrs):
     (129, 255, 80, 128), (200, 136, 1000, 128), (16, 16, 16, 128), (1, 8, 8, 128),
     (130, 300, 72, 256), (257, 513, 64, 256), (127, 1, 8, 128), (128, 128, 64, 128),
     (300, 40, 2000, 128), (64, 520, 136, 256),
+    (129, 255, 80, 64), (200, 136, 1000, 64), (1, 8, 8, 64), (300, 40, 2000, 64),
+    (65, 72, 264, 64), (384, 200, 520, 64),
 ])
 @pytest.mark.parametrize("mode", ["dp", "sk", "hybrid"])
 def test_ragged_shapes(m, n, k, tile_n, mode):
@@ -52,14 +57,14 @@ def test_ragged_shapes(m, n, k, tile_n, mode):
 
 @pytest.mark.parametrize("a_type,c_type", [("bf16", "bf16"), ("bf16", "f16"), ("f16", "f16"),
                                            ("f16", "bf16"), ("bf16", "f32"), ("f16", "f32")])
-@pytest.mark.parametrize("tile_n", [128, 256])
+@pytest.mark.parametrize("tile_n", [64, 128, 256])
 def test_dtypes_alpha_beta(a_type, c_type, tile_n):
     prob = Problem(272, 528, 1088, a_type, c_type, "normal", seed=3, beta=0.5)
     (C,), info, _ = prob.run(1.5, 0.5, "sk", plan_attrs={"tile_n": tile_n, "grid": 60})
     prob.check(C, 1.5, 0.5, f"{a_type}->{c_type} bn={tile_n}")
 
 
-@pytest.mark.parametrize("tile_n", [128, 256])
+@pytest.mark.parametrize("tile_n", [64, 128, 256])
 def test_two_tile_hybrid_with_dp_waves(tile_n):
     # t = 2p + 8 tiles (rounded to whole tile rows): w = 2 full waves plus a
     # partial one; the two-tile hybrid puts (t mod p) + p tiles in the
@@ -113,9 +118,10 @@ def test_column_major_c():
     prob.check(C, 0.75, -1.0, "column-major C")
 
 
-def test_run_to_run_bitwise_determinism():
+@pytest.mark.parametrize("tile_n", [64, 128])
+def test_run_to_run_bitwise_determinism(tile_n):
     prob = Problem(384, 384, 4096, "bf16", "f32", "normal", seed=7)
-    outs, info, _ = prob.run(1.0, 0.0, "sk", plan_attrs={"grid": 148}, reps=3)
+    outs, info, _ = prob.run(1.0, 0.0, "sk", plan_attrs={"grid": 148, "tile_n": tile_n}, reps=3)
     assert info["workspace_bytes"] > 0
     for C in outs[1:]:
         assert torch.equal(C, outs[0])
@@ -126,9 +132,13 @@ def test_sk_with_g_equal_t_is_bitwise_dp():
     # Section 4: with g equal to the number of tiles Stream-K behaves exactly
     # like the data-parallel decomposition -- the same MMA sequence per tile.
     prob = Problem(384, 640, 1024, "bf16", "f32", "normal", seed=8)
-    (C_dp,), i1, _ = prob.run(1.0, 0.0, "dp", plan_attrs={"tile_n": 128})
-    (C_sk,), i2, _ = prob.run(1.0, 0.0, "sk", plan_attrs={"tile_n": 128, "grid": 15})
+    (C_dp,), i1, _ = prob.run(1.0, 0.0, "dp", plan_attrs={"tile_n": 128, "cluster_m": 1})
+    (C_sk,), i2, _ = prob.run(1.0, 0.0, "sk", plan_attrs={"tile_n": 128, "cluster_m": 1, "grid": 15})
     assert i1["tiles"] == 15 and i2["grid"] == 15 and i2["workspace_bytes"] == 0
+    assert torch.equal(C_dp, C_sk)
+    (C_dp,), i1, _ = prob.run(1.0, 0.0, "dp", plan_attrs={"tile_n": 64})
+    (C_sk,), i2, _ = prob.run(1.0, 0.0, "sk", plan_attrs={"tile_n": 64, "grid": 30})
+    assert i1["tiles"] == 30 and i2["grid"] == 30 and i2["workspace_bytes"] == 0
     assert torch.equal(C_dp, C_sk)
 
 
@@ -282,11 +292,34 @@ def test_autotune_keeps_a_correct_configuration(m, n, k):
         C = torch.zeros(m, n, dtype=torch.bfloat16, device="cuda")
         us = sk.sk_plan_autotune(plan, A, B, C, reps=3)
         info = plan.info()
-        assert us > 0 and info["tile_n"] in (128, 256) and info["cluster_m"] in (1, 2)
+        assert us > 0 and info["tile_n"] in (64, 128, 256) and info["cluster_m"] in (1, 2)
         assert info["mode"] in (sk.MODES["dp"], sk.MODES["hybrid"], sk.MODES["sk"])
         C.zero_()
         sk.sk_gemm(plan, A, B, C, 1.0, 0.0)
         assert sk.sk_last_error(plan)[0] == sk.SK_OK
         prob.check(C.cpu(), 1.0, 0.0, f"autotuned {m}x{n}x{k} {info['tile_n']}/{info['cluster_m']}")
+    finally:
+        plan.destroy()
+
+
+@pytest.mark.parametrize("tile_n,cluster_m", [(64, 1), (128, 1), (256, 1), (128, 2), (256, 2)])
+@pytest.mark.parametrize("stages", [2, 3])
+def test_pipeline_stage_counts(tile_n, cluster_m, stages):
+    """A ring cycled through fewer stages than it holds (SK_ATTR_STAGES, the
+    autotuner's pipeline-depth choice) computes the same GEMM."""
+    m, n, k = 1000, 1000, 1000
+    prob = Problem(m, n, k, "bf16", "bf16", "normal", seed=90 + stages)
+    attrs = {"tile_n": tile_n, "cluster_m": cluster_m, "stages": stages}
+    (C,), info, _ = prob.run(1.0, 0.0, "sk", plan_attrs=attrs)
+    prob.check(C, 1.0, 0.0, f"stages={stages} bn={tile_n} cm={cluster_m}")
+    plan = sk.sk_plan(m, n, k, "bf16", "bf16", "bf16", mode="sk")
+    try:
+        plan.set("tile_n", tile_n)
+        plan.set("cluster_m", cluster_m)
+        full = plan.get("stages")
+        plan.set("stages", stages)
+        assert plan.get("stages") == stages and full >= 3
+        with pytest.raises(sk.StreamKError):
+            plan.set("stages", full + 1)
     finally:
         plan.destroy()

@@ -33,6 +33,11 @@ def model_trace(info, m, n, k):
     ("2p+8", 1024, 256, "hybrid", {"tile_n": 128, "raster_group": 5}),
     ("2p+8", 2048, 192, "hybrid", {"tile_n": 256}),
     ("2p+8", 1024, 320, "hybrid1", {"tile_n": 128}),
+    # 128 x 64 tiles
+    (384, 384, 4096, "sk", {"tile_n": 64, "grid": 100}),
+    ("2p+8", 512, 256, "hybrid", {"tile_n": 64, "raster_group": 3}),
+    (1000, 1000, 1000, "auto", {"tile_n": 64}),
+    (640, 200, 3000, "sk", {"tile_n": 64}),
     # CTA pairs (clusters of 2 along M sharing B by multicast)
     (4096, 4096, 512, "hybrid", {"tile_n": 256, "cluster_m": 2}),
     (1000, 3000, 640, "sk", {"tile_n": 256, "cluster_m": 2}),
