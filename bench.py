@@ -60,6 +60,11 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-f8", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=0.5,
+                    help="seconds of Poisson arrivals per serving rate (the serving "
+                         "configuration states 60 s; the default keeps the run short)")
+    ap.add_argument("--serving-rates", default="2000,5000,20000,40000,50000",
+                    help="comma-separated request rates of the serving workload")
     ap.add_argument("--dump-dir", default=None,
                     help="folder for per-shape detail and the clock log (default: "
                          "$SK_BENCH_DUMP_DIR, else a temporary folder)")
@@ -668,7 +673,9 @@ def ours_arm(args):
         line["grouped_e4m3"] = run_grouped_f8(max(3, min(args.steps, 10)), args.warmup)
         line["e4m3_shapes"] = run_f8_shapes(peaks)
     if not args.no_serving:
-        line["serving"] = run_serving()
+        line["serving"] = run_serving(
+            rates=tuple(int(r) for r in args.serving_rates.split(",") if r),
+            seconds=args.serving_seconds)
     print(json.dumps(line), flush=True)
 
 

@@ -439,11 +439,13 @@ int sk_grouped_autotune_scaled(sk_grouped_t plan, const void* const* A, const vo
  * are at least as many free slots as queued requests, each runs alone.  A
  * lone request is one single-GEMM launch from a plan cached per shape and
  * input type (at most 256 plans), on one stream shared by all lone requests,
- * in arrival order.  A batch is one grouped Stream-K launch on its slot's own
- * stream: up to 4 requests planned by the grouped model (SK_MODE_AUTO,
- * schedules cached by batch composition), larger batches as data-parallel
- * waves; the device derives each CTA's segments from a per-problem walk
- * table, so planning a batch costs O(batch + SMs) on the host.  Launches of
+ * in arrival order.  A request with at least one wave of 128 x 128 tiles (the
+ * SM count) always runs alone that way: it fills the GPU by itself, and its
+ * own plan keeps its configuration (CTA pairs, 256-wide tiles).  Requests
+ * below a wave are packed: a batch is one grouped launch on its slot's own
+ * stream, data-parallel waves over all its problems' tiles; the device derives
+ * each CTA's tiles from a per-problem walk table, so planning a batch costs
+ * O(batch + SMs) on the host.  Launches of
  * different slots overlap on the device, except that a launch whose schedule
  * splits tiles runs alone (it waits for all work in flight and later
  * launches wait for it).  A failing launch reports through a mapped pinned

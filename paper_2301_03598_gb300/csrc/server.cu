@@ -44,6 +44,7 @@ struct Request {
   const float* scale_b;
   float alpha, beta;
   int64_t bytes;
+  int64_t tiles;  // 128 x 128 output tiles: at least the SM count fills the GPU alone
   bool f8;
   Clock::time_point submitted;
 };
@@ -99,9 +100,6 @@ struct sk_server_s {
   int64_t submitted = 0, completed = 0, batches = 0, max_batch_seen = 0, problems_launched = 0;
   bool stop = false;
   std::atomic<int64_t> queued{0};  // submissions not yet admitted (read without the lock)
-  // Schedules of batch compositions seen before, keyed by the batch's
-  // (m, n, k) sequence; used by the worker only.
-  std::unordered_map<std::string, std::shared_ptr<const sk::GroupPlan>> plan_cache;
   // Tensor maps encoded before, keyed by (kind, pointer, dtype, rows, cols,
   // box rows); used by the worker only.
   struct MapKey {
@@ -159,10 +157,8 @@ struct sk_server_s {
 
 namespace {
 
-constexpr size_t kPlanCacheEntries = 4096;
 constexpr size_t kMapCacheEntries = 16384;
 constexpr size_t kSinglePlanCap = 256;  // cached single-GEMM plans (each owns a workspace)
-constexpr int kModelledBatch = 4;  // batches up to this size get the full model
 constexpr int kIdleSpinUs = 200;  // idle worker: spin before sleeping
 
 void free_slot(Slot& s) {
@@ -301,37 +297,20 @@ int launch_slot(sk_server_s* sv, Slot& s) {
     n[i] = s.reqs[i].n;
     k[i] = f8 ? s.reqs[i].k / 2 : s.reqs[i].k;
   }
-  // Small batches choose among every schedule (cached by composition); larger
-  // ones take data-parallel waves, planned in O(count + grid) with no records.
-  std::shared_ptr<const sk::GroupPlan> plan;
-  const int tile_n = f8 ? 128 : 0;
-  if (count <= kModelledBatch) {
-    std::string key(3 * sizeof(int64_t) * static_cast<size_t>(count) + 1, '\0');
-    key[0] = f8 ? 1 : 0;
-    for (int i = 0; i < count; ++i) {
-      const int64_t v[3] = {m[i], n[i], k[i]};
-      std::memcpy(&key[1 + 3 * sizeof(int64_t) * static_cast<size_t>(i)], v, sizeof(v));
-    }
-    auto hit = sv->plan_cache.find(key);
-    if (hit != sv->plan_cache.end()) {
-      plan = hit->second;
-    } else {
-      auto fresh = std::make_shared<sk::GroupPlan>();
-      const int st = sk::describe_grouped(count, m.data(), n.data(), k.data(), SK_MODE_AUTO,
-                                          tile_n, 0, sv->num_sms, fresh.get());
-      if (st != SK_OK) return st;
-      fresh->segs.clear();  // the device walks the table; records are not kept
-      fresh->start.clear();
-      if (sv->plan_cache.size() >= kPlanCacheEntries) sv->plan_cache.clear();
-      sv->plan_cache.emplace(std::move(key), fresh);
-      plan = std::move(fresh);
-    }
-  } else {
-    auto fresh = std::make_shared<sk::GroupPlan>();
+  // A batch packs requests below a wave each (larger ones run alone) and is
+  // launched as data-parallel waves over the problems' tiles, planned in
+  // O(count + grid) with no segment records: the worker's planning time is
+  // on every request's path, and a data-parallel launch never has to run
+  // alone (split launches wait for all other work in flight).  128-wide tiles
+  // while the batch has fewer than two waves of them, for parallelism.
+  int64_t tiles128 = 0;
+  for (int i = 0; i < count; ++i) tiles128 += s.reqs[i].tiles;
+  const int tile_n = f8 || tiles128 < 2 * static_cast<int64_t>(sv->num_sms) ? 128 : 0;
+  auto plan = std::make_shared<sk::GroupPlan>();
+  {
     const int st = sk::describe_grouped_dp(count, m.data(), n.data(), k.data(), tile_n,
-                                           sv->num_sms, fresh.get());
+                                           sv->num_sms, plan.get());
     if (st != SK_OK) return st;
-    plan = std::move(fresh);
   }
   const sk::GroupPlan& gp = *plan;
   int st = SK_OK;
@@ -460,8 +439,14 @@ void worker_loop(sk_server_s* sv) {
       for (const Slot& o : sv->slots) free_slots += o.busy ? 0 : 1;
       const int queued = static_cast<int>(q.size());
       const int cap = std::min(sv->max_batch, (queued + free_slots - 1) / free_slots);
+      // A request with at least a wave of tiles fills the GPU on its own:
+      // sharing a launch gains it nothing and would cost it its own plan's
+      // configuration (CTA pairs, 256-wide tiles), so it runs alone; only
+      // requests below a wave are packed together.
+      const int64_t wave = sv->num_sms;
       while (!q.empty() && static_cast<int>(s.reqs.size()) < cap) {
         const Request& r = q.front();
+        if (!s.reqs.empty() && r.tiles >= wave) break;
         const bool nothing_else = s.reqs.empty() && sv->inflight_bytes == 0;
         if (!nothing_else && sv->inflight_bytes + s.bytes + r.bytes > sv->budget) break;
         s.bytes += r.bytes;
@@ -469,6 +454,7 @@ void worker_loop(sk_server_s* sv) {
         sv->entries[r.id].state = 1;
         q.pop_front();
         sv->queued.fetch_sub(1, std::memory_order_relaxed);
+        if (r.tiles >= wave) break;
       }
       if (!s.reqs.empty()) {
         sv->inflight_bytes += s.bytes;
@@ -594,6 +580,7 @@ int submit(sk_server_t sv, int64_t m, int64_t n, int64_t k, const void* A, const
   r.beta = beta;
   const int64_t in_bytes = f8 ? 1 : 2;
   r.bytes = in_bytes * (m * k + n * k) + m * n * static_cast<int64_t>(dtype_size(sv->c_type));
+  r.tiles = ((m + 127) / 128) * ((n + 127) / 128);
   r.submitted = Clock::now();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
