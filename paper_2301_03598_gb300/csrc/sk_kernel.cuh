@@ -12,8 +12,8 @@
 //               128-byte-swizzled shared-memory tiles.
 //   warp 1      TMEM allocator and MMA issuer: one thread issues four
 //               tcgen05.mma per 128-byte k-block into one of two TMEM
-//               accumulators (E4M3: one product per k-block into one of three
-//               rotating buffers).
+//               accumulators (E4M3: one product per k-block, a stage's two
+//               k-blocks into one of two buffer pairs).
 //   warps 2..9  epilogue: (E4M3: first sums the k-block products times their
 //               block scales in FP32) per tile segment, either spill the FP32
 //               partial sums to this CTA's workspace slot and Signal (segment
@@ -54,12 +54,14 @@ constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 // F8 (E4M3 operands with one FP32 scale per 128 x 128 block of A and of B):
 // the host describes the operands to TMA as 16-bit rows of k/2 elements (the
 // same bytes), so loads and stages are the 16-bit path's.  Every k-block is
-// one scale block: the MMA warp writes each k-block's product into one of
-// kAccBufs rotating TMEM buffers and the epilogue warps add it, times the
-// block's two scales, into a running FP32 sum held in registers; the tile
-// segment's sum goes to TMEM columns [kAccBufs * BN, (kAccBufs + 1) * BN) for
-// the common epilogue.  A stage's second k-block beyond k (an odd count of
-// k-blocks) is zero-filled by TMA and carries scale 0.
+// one scale block: the MMA warp writes the products of a stage's KD = 2
+// k-blocks into the two TMEM buffers of one of kAccBufs = 2 buffer pairs and
+// publishes them with one commit; the epilogue warps add each product, times
+// its block's two scales, into a running FP32 sum held in registers, and
+// release the pair.  The tile segment's sum goes to the first buffer of the
+// segment's last pair, which is released only after the common epilogue has
+// read it.  A stage's second k-block beyond k (an odd count of k-blocks) is
+// zero-filled by TMA and carries scale 0.
 template <int BN, int CM, bool F8 = false>
 struct Cfg {
   static constexpr int KD = BN <= 128 ? 2 : 1;
@@ -70,10 +72,10 @@ struct Cfg {
   static constexpr int kStageBytes = kABytes + kBBytes;
   // 4, 4 (BN 64); 3, 4 (BN 128); 4, 6 (BN 256); F8: 3
   static constexpr int kStages = (192 * 1024) / kStageBytes;
-  static constexpr int kAccBufs = F8 ? 3 : 2;
-  // F8: three product buffers and the segment sum; else two accumulators
-  static constexpr int kTmemCols = F8 ? 4 * BN : 2 * BN;
-  static constexpr int kSumCol = kAccBufs * BN;  // F8: the segment sum's first column
+  // two accumulators (F8: two pairs of KD product buffers, one pair per stage)
+  static constexpr int kAccBufs = 2;
+  static constexpr int kAccCols = F8 ? KD * BN : BN;  // TMEM columns of one of them
+  static constexpr int kTmemCols = kAccBufs * kAccCols;
   // Output staging for TMA stores: per epilogue warp one buffer of 32 rows x
   // 128 B, 128-byte swizzled (1 KiB aligned).
   static constexpr int kStagingOffset = kStages * kStageBytes;
@@ -748,46 +750,41 @@ __global__ void __launch_bounds__(kThreads, 1)
       // (probed while the previous k-block's last MMA was issued).
       bool ready = false;
       if constexpr (F8) {
-        // One product per k-block (one scale block) into the rotating
-        // buffers; the epilogue warps scale and sum them.
-        // ready_acc: the current product buffer is known to be free (probed
-        // with the previous k-block's last MMA, like `ready` for the stage)
+        // One product per k-block (one scale block); a stage's KD k-blocks
+        // go to the KD buffers of one pair, published with one commit; the
+        // epilogue warps scale and sum them.
+        // ready_acc: the current pair is known to be free (probed with the
+        // previous stage's last MMA, like `ready` for the stage)
         bool ready_acc = false;
         while (ok && cur.next(a, sg)) {
-          for (int kb = sg.kb0; kb < sg.kb1 && ok; ++kb) {
+          for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
             if (!ready && !wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull)) {
               ok = false;
               break;
             }
+            if (!ready_acc && !wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
             int next = stage + 1;
             uint32_t next_phase = phase;
             if (next == S) {
               next = 0;
               next_phase ^= 1u;
             }
-            // the stage's KD k-blocks, each into its own product buffer
+            const int nacc = acc ^ 1;
+            const uint32_t nacc_phase = acc == 1 ? acc_phase ^ 1u : acc_phase;
 #pragma unroll
             for (int j = 0; j < KD; ++j) {
-              if (!ready_acc && !wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              int nacc = acc + 1;
-              uint32_t nacc_phase = acc_phase;
-              if (nacc == NB) {
-                nacc = 0;
-                nacc_phase ^= 1u;
-              }
-              const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+              const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * C_::kAccCols + j * BN);
               const uint64_t adesc = smem_desc_sw128(stage_a(stage) + j * C_::kSubA);
               const uint64_t bdesc = smem_desc_sw128(stage_b(stage) + j * C_::kSubB);
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
                 // 32 E4M3 elements (32 B) along K per MMA
-                if (kk == 3) {
-                  // with the k-block's last MMA: probe the next product buffer
-                  // and (after the stage's last k-block) the next stage
+                if (j == KD - 1 && kk == 3) {
+                  // the stage's last MMA: probe the next stage and the next pair
                   uint32_t r;
                   if constexpr (kPair)
                     r = mma_f8_pair_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
@@ -795,7 +792,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   else
                     r = mma_f8_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
                                       full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
-                  if (j == KD - 1) ready = (r & 1u) != 0;
+                  ready = (r & 1u) != 0;
                   ready_acc = (r & 2u) != 0;
                 } else if constexpr (kPair) {
                   mma_f8_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
@@ -803,22 +800,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                   mma_f8(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
                 }
               }
-              // publishes the product (in both CTAs of a pair)
-              if constexpr (kPair)
-                mma_commit_pair_multicast(accf_bar(acc), kPairMask);
-              else
-                mma_commit(accf_bar(acc));
-              acc = nacc;
-              acc_phase = nacc_phase;
             }
-            if (!ok) break;
-            // frees the stage once its MMAs finish
-            if constexpr (kPair)
+            // publishes the pair's products, then frees the stage (in both
+            // CTAs of a pair) once these MMAs finish
+            if constexpr (kPair) {
+              mma_commit_pair_multicast(accf_bar(acc), kPairMask);
               mma_commit_pair_multicast(empty_bar(stage), kPairMask);
-            else
+            } else {
+              mma_commit(accf_bar(acc));
               mma_commit(empty_bar(stage));
+            }
             stage = next;
             phase = next_phase;
+            acc = nacc;
+            acc_phase = nacc_phase;
           }
         }
       }
@@ -969,47 +964,55 @@ __global__ void __launch_bounds__(kThreads, 1)
         };
         float s_cur = window(kq0);
         float s_nxt = kq0 + 32 < kq1 ? window(kq0 + 32) : 0.0f;
-        for (int kq = kq0; kq < kq1; ++kq) {
-          const int i = kq - kq0;
-          if (i > 0 && (i & 31) == 0) {
-            s_cur = s_nxt;
-            if (kq + 32 < kq1) s_nxt = window(kq + 32);
-          }
-          const float sc = __shfl_sync(0xffffffffu, s_cur, i & 31);
+        for (int it = kb0; it < kb1; ++it) {
           if (!wait_bar(accf_bar(acc), acc_phase, abort_flag, a, kAtEpiAccFull)) {
             fail = true;
             break;
           }
           tc_fence_after();
-          const uint32_t pbase = tmem_base + lane_base + static_cast<uint32_t>(acc * BN);
-          // 32 columns at a time, so that the product needs 32 registers
-          // next to the sum's 64
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const int mi = kCpu == 2 ? 0 : c;
-            const int j0 = kCpu == 2 ? 32 * c : 0;
-            const uint32_t col = static_cast<uint32_t>((col_half + 2 * mi) * 32 * kCpu + j0);
-            uint32_t r[32];
-            tmem_ld_x32(pbase + col, r);
-            tmem_wait_ld();
-            if (c == 1) {
-              // the product buffer is read: the MMA warp may overwrite it
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) release_acc(acc);
+#pragma unroll 1
+          for (int j = 0; j < KD; ++j) {
+            const int kq = it * KD + j;
+            const int i = kq - kq0;
+            if (i > 0 && (i & 31) == 0) {
+              s_cur = s_nxt;
+              if (kq + 32 < kq1) s_nxt = window(kq + 32);
             }
-            // sum += sc * product, two columns per packed FMA
-            const uint32_t scb = __float_as_uint(sc);
+            const float sc = __shfl_sync(0xffffffffu, s_cur, i & 31);
+            const uint32_t pbase =
+                tmem_base + lane_base + static_cast<uint32_t>(acc * C_::kAccCols + j * BN);
+            // 32 columns at a time, so that the product needs 32 registers
+            // next to the sum's 64
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) fma2(scb, r[j], r[j + 1], sum[mi][j0 + j], sum[mi][j0 + j + 1]);
+            for (int c = 0; c < 2; ++c) {
+              const int mi = kCpu == 2 ? 0 : c;
+              const int j0 = kCpu == 2 ? 32 * c : 0;
+              const uint32_t col = static_cast<uint32_t>((col_half + 2 * mi) * 32 * kCpu + j0);
+              uint32_t r[32];
+              tmem_ld_x32(pbase + col, r);
+              tmem_wait_ld();
+              if (j == KD - 1 && c == 1 && it + 1 < kb1) {
+                // the pair is read: the MMA warp may overwrite it (the
+                // segment's last pair is kept for its sum, below)
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) release_acc(acc);
+              }
+              // sum += sc * product, two columns per packed FMA
+              const uint32_t scb = __float_as_uint(sc);
+#pragma unroll
+              for (int jj = 0; jj < 32; jj += 2)
+                fma2(scb, r[jj], r[jj + 1], sum[mi][j0 + jj], sum[mi][j0 + jj + 1]);
+            }
           }
-          if (++acc == NB) {
-            acc = 0;
-            acc_phase ^= 1u;
+          if (it + 1 < kb1) {
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
           }
         }
         if (!fail) {
-          const uint32_t sbase = tmem_base + lane_base + static_cast<uint32_t>(C_::kSumCol);
+          // the sum goes to the first buffer of the segment's last pair (acc)
+          const uint32_t sbase = tmem_base + lane_base + static_cast<uint32_t>(acc * C_::kAccCols);
 #pragma unroll
           for (int mi = 0; mi < kMine; ++mi) {
             const uint32_t col = static_cast<uint32_t>((col_half + 2 * mi) * 32 * kCpu);
@@ -1029,8 +1032,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t t_acc = tracer ? globaltimer_ns() : 0;
       uint64_t t_fix = t_acc;
 
-      const uint32_t tbase =
-          tmem_base + lane_base + static_cast<uint32_t>(F8 ? C_::kSumCol : acc * BN);
+      // the accumulator (F8: the sum, in the first buffer of the segment's last pair)
+      const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(acc * C_::kAccCols);
       const int grow = tm * kBlkM + row;
       const int col0 = tn * BN;
       // Column units of 128 output bytes (32 FP32 or 64 16-bit columns); the
@@ -1039,7 +1042,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nchunks = (min(BN, out.n - col0) + 31) / 32;
       const int nunits = (nchunks + kCpu - 1) / kCpu;
       const int my_last_unit = (nunits - 1 - col_half) >= 0 ? nunits - 1 - ((nunits - 1 - col_half) & 1) : -1;
-      if (!F8 && my_last_unit < 0) {
+      if (my_last_unit < 0) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) release_acc(acc);
@@ -1055,8 +1058,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           else
             tmem_ld_x32(tbase + static_cast<uint32_t>(u * 32), r);
           tmem_wait_ld();
-          if (!F8 && u == my_last_unit) {
-            // all of this warp's TMEM reads are done: hand the buffer back to the MMA warp
+          if (u == my_last_unit) {
+            // all of this warp's TMEM reads are done: hand the buffer (F8:
+            // the segment's last pair) back to the MMA warp
             tc_fence_before();
             __syncwarp();
             if (lane == 0) release_acc(acc);
@@ -1237,10 +1241,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         ++nrec;
         tb[0] = nrec;
       }
-      if constexpr (!F8) {
-        acc ^= 1;
-        if (acc == 0) acc_phase ^= 1u;
-      }
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1u;
     }
     // The staging buffers are read before the CTA's shared memory goes away;
     // the global writes themselves complete with the grid.
