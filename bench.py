@@ -656,6 +656,20 @@ def ours_arm(args):
                                  "geomean": geomean(sp)}
         line["vs_dp_geomean"] = results[headline]["geomean_tflops"] / \
             results["dp"]["geomean_tflops"]
+        # where both schedules are the same plan the ratio is run-to-run noise
+        # of one plan; the shapes whose plans differ show the planner's choice
+        key = lambda p: (p.get("tile_n"), p.get("cluster_m"), p.get("grid"), p.get("sk_tiles"))
+        differ = np.array([key(a) != key(b) for a, b in zip(results[headline]["_plans"],
+                                                          results["dp"]["_plans"])])
+        if differ.any():
+            spd = sp[differ]
+            line["speedup_vs_dp"]["plans_differ"] = {
+                "shapes": int(differ.sum()), "geomean": geomean(spd), "min": float(spd.min()),
+                "below_0.95": int((spd < 0.95).sum())}
+        same = sp[~differ]
+        if same.size:
+            line["speedup_vs_dp"]["same_plan_spread"] = {
+                "shapes": int(same.size), "min": float(same.min()), "max": float(same.max())}
     if "auto+indep" in results and headline == "auto":
         sp = results["auto+indep"]["_per_shape"] / results["auto"]["_per_shape"]
         line["independent_inputs"] = {
