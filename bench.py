@@ -88,9 +88,9 @@ def load_peaks():
 # summed over the captured launches, divided by their 2mnk), and the sha256 of
 # csrc/sk_kernel.cuh followed by csrc/planner.cpp at that capture.  The
 # summary with its command is profiles/sk_gemm_sweep_launches.md.
-PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.231834e-03,
+PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.177066e-03,
                     "kernel_source_sha256":
-                        "7e1661f37abdaac5c6f310434d5437d8a22f56a2e89241507734b3f2643169af"}
+                        "7f9e887de3973ac1b7cc19e783370c3b123469bf96310fbfbdbea51faf3b4aad"}
 
 
 def profiled_bytes_per_flop():
