@@ -905,6 +905,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float* scale_b = a.scale_b;
     int32_t ld_scale = a.ld_scale;
     constexpr int kCpu = (sizeof(TC) == 4) ? 1 : 2;  // 32-column chunks per output unit
+    // BLK_N = 64 with a 16-bit output has one unit (two 32-column chunks) per
+    // lane quarter: the quarter's two warps take one chunk each for the TMEM
+    // read, the spill and the fixup, and meet in the first warp's staging
+    // buffer for the store (named barrier 2 + quarter, 64 threads).
+    constexpr bool kSplit = !F8 && BN == 64 && kCpu == 2;
     float* const my_slot = a.partials + static_cast<size_t>(cta) * (kBlkM * BN);
     const uint32_t staging = base + static_cast<uint32_t>(C_::kStagingOffset +
                                                          (warp - kEpiWarp0) * C_::kStagingBytesPerWarp);
@@ -1042,6 +1047,132 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nchunks = (min(BN, out.n - col0) + 31) / 32;
       const int nunits = (nchunks + kCpu - 1) / kCpu;
       const int my_last_unit = (nunits - 1 - col_half) >= 0 ? nunits - 1 - ((nunits - 1 - col_half) & 1) : -1;
+      if constexpr (kSplit) {
+        const int c = col_half;  // this warp's 32-column chunk of the unit
+        const bool mine = c < nchunks;
+        float v[32];
+        {
+          uint32_t r[32];
+          if (mine) {
+            tmem_ld_x32(tbase + static_cast<uint32_t>(c * 32), r);
+            tmem_wait_ld();
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) release_acc(acc);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+        }
+        if (role == kRolePartial) {
+          if (mine) {
+            float4* dst = reinterpret_cast<float4*>(my_slot) + (c * 4 + quarter) * 256 + lane;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              __stcg(dst + j * 32, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+            // Signal(flags[cta][quarter][c]); the warp barrier orders every
+            // lane's stores before lane 0's release, which is cumulative
+            __syncwarp();
+            if (lane == 0 && cta != a.debug_skip_signal)
+              st_release_gpu(&a.flags[cta * kFlagsPerCtaDev + quarter * 8 + c], a.epoch);
+          }
+        } else {
+          if (role == kRoleOwner && mine) {
+            for (int y = peer_first + lane * CM; y <= peer_last && !fail; y += 32 * CM)
+              fail = !wait_flag(&a.flags[y * kFlagsPerCtaDev + quarter * 8 + c], abort_flag, a);
+            __syncwarp();
+            fail = __any_sync(0xffffffffu, fail);
+            if (tracer) t_fix = globaltimer_ns();
+            if (!fail) {
+              // acc + P[x+1] + P[x+2] + ... in increasing CTA order
+              for (int y = peer_first; y <= peer_last; y += 2 * CM) {
+                const float4* s0 = reinterpret_cast<const float4*>(
+                                       a.partials + static_cast<size_t>(y) * (kBlkM * BN)) +
+                                   (c * 4 + quarter) * 256 + lane;
+                const bool two = y + CM <= peer_last;
+                const float4* s1 = two ? s0 + CM * (kBlkM * BN) / 4 : s0;
+                float4 p0[8], p1[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) p0[j] = __ldcg(s0 + j * 32);
+                if (two) {
+#pragma unroll
+                  for (int j = 0; j < 8; ++j) p1[j] = __ldcg(s1 + j * 32);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  v[4 * j] += p0[j].x;
+                  v[4 * j + 1] += p0[j].y;
+                  v[4 * j + 2] += p0[j].z;
+                  v[4 * j + 3] += p0[j].w;
+                }
+                if (two) {
+#pragma unroll
+                  for (int j = 0; j < 8; ++j) {
+                    v[4 * j] += p1[j].x;
+                    v[4 * j + 1] += p1[j].y;
+                    v[4 * j + 2] += p1[j].z;
+                    v[4 * j + 3] += p1[j].w;
+                  }
+                }
+              }
+            }
+          }
+          // Every warp takes the same branch below (owners agree on failure
+          // first), so the two warps of a quarter always meet at both barriers.
+          if (role == kRoleOwner && epi_any(fail)) break;
+          if (!out.c_tma) {
+            if (mine) store_row32<TC>(out, grow, col0 + c * 32, v);
+          } else {
+            const float alpha = out.alpha, beta = out.beta;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] *= alpha;
+            if (beta != 0.0f && mine) add_beta_c<TC>(out, grow, col0 + c * 32, v);
+            // the quarter's staging buffer: that of its first warp
+            const uint32_t stage0 =
+                base + static_cast<uint32_t>(C_::kStagingOffset +
+                                             (warp - kEpiWarp0 - 4 * col_half) * C_::kStagingBytesPerWarp);
+            const uint32_t srow = stage0 + static_cast<uint32_t>(lane * 128);
+            const uint32_t bar_id = 2u + static_cast<uint32_t>(quarter);
+            // the previous store from the buffer has finished reading it
+            if (col_half == 0 && lane == 0) bulk_wait_group_read<0>();
+            named_bar_sync(bar_id, 64);
+            if (mine) {
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) {
+                const int j = c * 4 + jj;  // 16-byte granule of the 128-byte row
+                st_shared_v4(srow + static_cast<uint32_t>(((j ^ (lane & 7)) * 16)),
+                             pack2(v[8 * jj], v[8 * jj + 1], static_cast<TC*>(nullptr)),
+                             pack2(v[8 * jj + 2], v[8 * jj + 3], static_cast<TC*>(nullptr)),
+                             pack2(v[8 * jj + 4], v[8 * jj + 5], static_cast<TC*>(nullptr)),
+                             pack2(v[8 * jj + 6], v[8 * jj + 7], static_cast<TC*>(nullptr)));
+              }
+            }
+            fence_proxy_async_smem();
+            named_bar_sync(bar_id, 64);
+            if (col_half == 0) {
+              if (out.c_tma == 1) {
+                if (lane == 0) {
+                  tma_store_2d(out.tmC, stage0, col0, tm * kBlkM + quarter * 32);
+                  bulk_commit_group();
+                }
+              } else {
+                // the same 32 rows x 128 B through coalesced global stores
+                const int chunk = lane & 7;
+                const int gcol = col0 + chunk * (16 / static_cast<int>(sizeof(TC)));
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  const int r = i * 4 + (lane >> 3);
+                  const int grow_r = tm * kBlkM + quarter * 32 + r;
+                  uint32_t w0, w1, w2, w3;
+                  ld_shared_v4(stage0 + static_cast<uint32_t>(r * 128 + ((chunk ^ (r & 7)) * 16)), w0,
+                               w1, w2, w3);
+                  if (grow_r < out.m) store_chunk16<TC>(out, grow_r, gcol, w0, w1, w2, w3);
+                }
+                __syncwarp();
+              }
+            }
+          }
+        }
+      } else {
       if (my_last_unit < 0) {
         tc_fence_before();
         __syncwarp();
@@ -1210,13 +1341,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       // Only owners wait inside the segment; their failure decision must be
       // the same in every epilogue warp.
       if (role == kRoleOwner && epi_any(fail)) break;
+      }
       if (role == kRoleOwner && lane == 0) {
-        // Every unit flag has exactly one consumer, this warp: clear the ones
-        // it consumed so the next launch (even a graph replay carrying the
-        // same epoch) starts clean.
-        for (int u = col_half; u < nunits; u += 2)
-          for (int y = peer_first; y <= peer_last; y += CM)
-            a.flags[y * kFlagsPerCtaDev + quarter * 8 + u] = 0u;
+        // Every flag has exactly one consumer, this warp: clear the ones it
+        // consumed so the next launch (even a graph replay carrying the same
+        // epoch) starts clean.  (kSplit: one flag per chunk, this warp's.)
+        if constexpr (kSplit) {
+          if (col_half < nchunks)
+            for (int y = peer_first; y <= peer_last; y += CM)
+              a.flags[y * kFlagsPerCtaDev + quarter * 8 + col_half] = 0u;
+        } else {
+          for (int u = col_half; u < nunits; u += 2)
+            for (int y = peer_first; y <= peer_last; y += CM)
+              a.flags[y * kFlagsPerCtaDev + quarter * 8 + u] = 0u;
+        }
       }
       if (tracer) {
         const uint64_t t_done = globaltimer_ns();
