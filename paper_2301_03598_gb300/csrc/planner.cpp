@@ -49,11 +49,11 @@ int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]) {
 // data-parallel, two-tile hybrid and basic Stream-K forced (15 plans per
 // shape).
 void model_coefficients(int tile_n, int cluster_m, double out[kModelTerms]) {
-  static const double k64x1[kModelTerms] = {3.414, 2.878, 0.4127, 0.468, 0.181, 0.997};
-  static const double k128x1[kModelTerms] = {3.617, 3.848, 0.5570, 0.554, 0.164, 1.388};
-  static const double k256x1[kModelTerms] = {4.294, 8.719, 0.3935, 0.455, 0.145, 1.101};
-  static const double k128x2[kModelTerms] = {4.197, 4.614, 0.4505, 0.441, 0.330, 1.687};
-  static const double k256x2[kModelTerms] = {4.642, 10.448, 0.3041, 0.350, 0.440, 2.371};
+  static const double k64x1[kModelTerms] = {3.452, 2.219, 0.4159, 0.419, 0.173, 0.996};
+  static const double k128x1[kModelTerms] = {3.742, 3.728, 0.5640, 0.569, 0.141, 1.370};
+  static const double k256x1[kModelTerms] = {4.398, 8.278, 0.3974, 0.711, 0.137, 1.120};
+  static const double k128x2[kModelTerms] = {4.271, 4.468, 0.4521, 0.494, 0.314, 1.681};
+  static const double k256x2[kModelTerms] = {4.756, 9.852, 0.3034, 0.461, 0.435, 2.363};
   const double* c = cluster_m == 2 ? (tile_n == 256 ? k256x2 : k128x2)
                                    : (tile_n == 256 ? k256x1 : tile_n == 64 ? k64x1 : k128x1);
   for (int i = 0; i < kModelTerms; ++i) out[i] = c[i];

@@ -1216,12 +1216,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                v[cc][4 * j + 3]));
           }
           // Signal(flags[cta][quarter][u]): this warp's part of the partial is
-          // written; the release is cumulative over the warp's stores.
+          // written.  The warp barrier orders every lane's stores before lane
+          // 0's release, which is cumulative over them.
           __syncwarp();
-          if (lane == 0 && cta != a.debug_skip_signal) {
-            __threadfence();
+          if (lane == 0 && cta != a.debug_skip_signal)
             st_release_gpu(&a.flags[cta * kFlagsPerCtaDev + quarter * 8 + u], a.epoch);
-          }
           continue;
         }
         if (role == kRoleOwner) {
