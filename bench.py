@@ -719,17 +719,19 @@ def grouped_schedules(gplan, launch, steps, warmup, stream, flops):
         ms = ev[0].elapsed_time(ev[1]) / steps
         info = gplan.info()
         out[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
-                     "plan": {k: info[k] for k in ("tile_n", "grid", "tiles", "sk_tiles",
-                                                   "workspace_bytes")}}
+                     "plan": {k: info[k] for k in ("tile_n", "cluster_m", "grid", "tiles",
+                                                   "sk_tiles", "workspace_bytes")}}
     gplan.set("mode", saved)
     return out
 
 
 def run_grouped(steps, warmup):
     """The grouped workload (256 problems, see inputs.grouped_shapes) as one
-    Stream-K launch across all problems, against the same 256 GEMMs as
-    separate launches of the single-GEMM path replayed from one CUDA graph.
-    Inputs are device-resident; each problem has its own A, B and C."""
+    autotuned Stream-K launch across all problems (tile width, cluster size,
+    schedule and pipeline depth measured; the model's own pick is reported
+    beside it), against the same 256 GEMMs as separate launches of the
+    single-GEMM path replayed from one CUDA graph.  Inputs are
+    device-resident; each problem has its own A, B and C."""
     import torch
     from paper_2301_03598_gb300 import inputs
     from paper_2301_03598_gb300 import streamk as sk
@@ -743,6 +745,8 @@ def run_grouped(steps, warmup):
     flops = float(sum(2.0 * m * n * k for m, n, k in shapes))
     stream = torch.cuda.Stream()
     gplan = sk.sk_grouped_plan(shapes, "bf16", "bf16", "auto")
+    model_plan = gplan.info()
+    tuned_us = sk.sk_grouped_autotune(gplan, As, Bs, Cs, reps=3, stream=stream)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     with torch.cuda.stream(stream):
         for _ in range(max(1, warmup)):
@@ -792,7 +796,11 @@ def run_grouped(steps, warmup):
                     "FP8-e4m3 inputs of the grouped configuration), FP32 accumulate, BF16 out",
         "problems": len(shapes), "gflop": flops / 1e9,
         "grouped": {"ms": g_ms, "tflops": flops / (g_ms * 1e-3) / 1e12, "launches_per_step": 1,
-                    "plan": {k: ginfo[k] for k in ("mode", "tile_n", "grid", "tiles", "sk_tiles")}},
+                    "autotune_best_us": tuned_us,
+                    "plan": {k: ginfo[k] for k in ("mode", "tile_n", "cluster_m", "grid", "tiles",
+                                                   "sk_tiles", "stages")},
+                    "model_plan": {k: model_plan[k] for k in ("mode", "tile_n", "cluster_m",
+                                                              "grid", "sk_tiles")}},
         "schedules": scheds,
         "separate": {"ms": s_ms, "tflops": flops / (s_ms * 1e-3) / 1e12,
                      "launches_per_step": len(shapes),

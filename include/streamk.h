@@ -339,14 +339,19 @@ const char* sk_status_string(int status);
  * Problem i is C_i = alpha_i * A_i * B_i + beta_i * C_i with A_i row-major
  * m_i x k_i, B_i column-major k_i x n_i (an n_i x k_i row-major array), C_i
  * row-major m_i x n_i, all dense, one input type and one output type for the
- * group, FP32 accumulation.  All problems use one tile width (BLK_N);
- * schedules use single CTAs.
+ * group, FP32 accumulation.  All problems use one tile configuration: one
+ * tile width (BLK_N) and single CTAs or, for 16-bit groups with BLK_N 128
+ * or 256, CTA pairs computing 256-row tiles (SK_ATTR_CLUSTER_M).  With
+ * pairs the schedule's unit is the pair: SK_ATTR_GRID and the records of
+ * sk_grouped_schedule count units (CTA 2x + r, r = 0, 1, runs unit x's
+ * segments on 128-row block 2 tm + r of each tile).
  *
  * sk_grouped_plan: count >= 1 problems, m/n/k host arrays of count entries
  *   (each >= 1, k a multiple of 8 so that dense 16-bit rows are 16-byte
  *   multiples as TMA requires; 16 for E4M3); mode SK_MODE_AUTO (the model picks
  *   data-parallel, the two-tile hybrid or basic Stream-K, and the tile width),
- *   SK_MODE_DP, SK_MODE_SK or SK_MODE_HYBRID.  The plan owns its device walk
+ *   SK_MODE_DP, SK_MODE_SK or SK_MODE_HYBRID; the model also picks the
+ *   cluster size (E4M3 groups: single CTAs).  The plan owns its device walk
  *   table (64 bytes per problem and 8 per CTA, from which each CTA derives its
  *   segments), problem table, workspace and status words.
  *   Returns SK_ERR_INVALID / SK_ERR_UNSUPPORTED for bad arguments,
@@ -362,11 +367,12 @@ const char* sk_status_string(int status);
  *   sk_gemm_traced does (field 9 of each record holds the problem index);
  *   trace_ints >= SK_ATTR_TRACE_INTS.
  * sk_grouped_last_error: as sk_last_error.
- * sk_grouped_set: SK_ATTR_TILE_N, SK_ATTR_GRID, SK_ATTR_MODE (replan),
- *   SK_ATTR_TIMEOUT_NS, SK_ATTR_PDL, SK_ATTR_STORE, SK_ATTR_STAGES.
+ * sk_grouped_set: SK_ATTR_TILE_N, SK_ATTR_GRID, SK_ATTR_MODE,
+ *   SK_ATTR_CLUSTER_M (replan), SK_ATTR_TIMEOUT_NS, SK_ATTR_PDL, SK_ATTR_STORE,
+ *   SK_ATTR_STAGES.
  * sk_grouped_get: SK_ATTR_MODE, TILE_M, TILE_N, TILE_K, GRID, CTAS, TILES,
  *   SK_TILES, DP_TILES, WORKSPACE_BYTES, NUM_SMS, TRACE_CAP, TRACE_INTS,
- *   TIMEOUT_NS, PDL, STORE, SEGMENTS, STAGES.
+ *   TIMEOUT_NS, PDL, STORE, SEGMENTS, STAGES, CLUSTER_M.
  * sk_grouped_schedule: the host copy of the schedule, 10 int32 per segment
  *   (cta, problem, tile, tm, tn, kb0, kb1, role, peer_first, peer_last), CTA
  *   by CTA in processing order; *count receives the number of segments; with
@@ -394,17 +400,17 @@ int sk_grouped_get(sk_grouped_t plan, int attr, int64_t* value);
 int sk_grouped_schedule(sk_grouped_t plan, int32_t* records, int64_t capacity, int64_t* count);
 int sk_grouped_destroy(sk_grouped_t plan);
 /* Host-only planning of a grouped launch for num_sms SMs (no device needed):
- * summary receives 8 int64 (mode, tile_n, tile_k, grid, tiles, sk_tiles,
- * workspace_bytes, max_segments) when non-NULL; records and *nrec as in
- * sk_grouped_schedule.  tile_n 0 / grid 0 = automatic. */
+ * summary receives 9 int64 (mode, tile_n, tile_k, grid, tiles, sk_tiles,
+ * workspace_bytes, max_segments, cluster_m) when non-NULL; records and *nrec
+ * as in sk_grouped_schedule.  tile_n 0 / grid 0 / cluster_m 0 = automatic. */
 int sk_grouped_plan_describe(int count, const int64_t* m, const int64_t* n, const int64_t* k,
-                             int mode, int tile_n, int grid, int num_sms, int64_t* summary,
-                             int32_t* records, int64_t capacity, int64_t* nrec);
+                             int mode, int tile_n, int grid, int num_sms, int cluster_m,
+                             int64_t* summary, int32_t* records, int64_t capacity, int64_t* nrec);
 
 /* ---------------------------------------------------------------- autotuning
  * Measured choice among the configurations the planner would otherwise pick
  * by its model: every tile width (64, 128, 256 when n > 128) x cluster size
- * (1, 2 when m > 128 and the tile is at least 128 wide; grouped plans: 1) x
+ * (1, 2 when m > 128 and the tile is at least 128 wide; E4M3: 1) x
  * schedule (data-parallel, two-tile hybrid, basic Stream-K with the model's
  * grid size) x pipeline depth (the full ring, 3 and 2 stages) is planned,
  * launched once untimed and `reps` times timed with CUDA events on `stream`,

@@ -452,3 +452,27 @@ def grouped_trace(probs: List[Problem], ctas: List[List[GroupSegment]],
             out.append((x, s.problem, s.tile_idx, tm, tn, s.local_iter, s.local_iter_end, s.role,
                         pf, pl))
     return out
+
+
+def grouped_cluster_trace(trace: List[Tuple[int, ...]], cluster_m: int) -> List[Tuple[int, ...]]:
+    """The trace of a grouped schedule whose unit of work is a cluster of
+    cluster_m CTAs, from its per-unit records (as grouped_trace returns them,
+    with each problem's tiles cluster_m * 128 rows high): unit x's segments are
+    executed by CTAs x*cluster_m + r, each on its own 128-row block (tile row
+    tm*cluster_m + r), and the peers of CTA x*cluster_m + r are the CTAs with
+    the same r.  Records (cta, problem, tile, tm, tn, kb0, kb1, role,
+    peer_first, peer_last), CTA by CTA."""
+    if cluster_m == 1:
+        return list(trace)
+    by_unit = {}
+    for rec in trace:
+        by_unit.setdefault(rec[0], []).append(rec)
+    out = []
+    for x in sorted(by_unit):
+        for r in range(cluster_m):
+            for (_, prob, tile, tm, tn, k0, k1, role, pf, pl) in by_unit[x]:
+                out.append((x * cluster_m + r, prob, tile, tm * cluster_m + r, tn, k0, k1, role,
+                            pf * cluster_m + r if pf >= 0 else -1,
+                            pl * cluster_m + r if pl >= 0 else -1))
+    return out
+

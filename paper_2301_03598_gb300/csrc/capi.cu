@@ -796,6 +796,7 @@ struct sk_grouped_s {
   bool pdl = true;
   int store_req = 0;
   int stages_req = 0;  // SK_ATTR_STAGES (0: all the ring holds)
+  int cluster_req = 0;  // SK_ATTR_CLUSTER_M (0: planned)
   cudaStream_t last_stream = nullptr;
   bool launched = false;
   InFlight inflight;  // the last launch, for SK_ERR_BUSY
@@ -821,7 +822,7 @@ int grouped_replan(sk_grouped_s* g) {
   if (f8)
     for (int64_t& v : kk) v /= 2;
   int st = sk::describe_grouped(g->count, g->m.data(), g->n.data(), kk.data(), g->mode_req,
-                                g->tile_n_req, g->grid_req, g->num_sms, &gp);
+                                g->tile_n_req, g->grid_req, g->num_sms, &gp, g->cluster_req);
   if (st != SK_OK) return st;
   if (f8) gp.tile_k *= 2;  // in E4M3 elements
   if (g->launched) {
@@ -874,7 +875,7 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
   if (const int bs = busy_check(g->inflight, stream); bs != SK_OK) return bs;
   const sk::GroupPlan& gp = g->plan;
   if (trace != nullptr) {
-    const int64_t need = static_cast<int64_t>(gp.grid) *
+    const int64_t need = static_cast<int64_t>(gp.grid) * gp.cluster_m *
                          (sk::kTraceHeaderInts + static_cast<int64_t>(gp.max_segments) * sk::kTraceRecordInts);
     if (trace_ints < need) return SK_ERR_INVALID;
   }
@@ -913,10 +914,12 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
     const int tt = f8 ? SK_BF16 : g->ab_type;
     const int64_t tk = f8 ? k / 2 : k;
     int st = encode_operand(&pr.tmA, A[i], tt, m, tk, tk, sk::kBlkM);
-    if (st == SK_OK) st = encode_operand(&pr.tmB, B[i], tt, n, tk, tk, gp.tile_n);
+    // a CTA of a pair loads half of the B tile
+    if (st == SK_OK) st = encode_operand(&pr.tmB, B[i], tt, n, tk, tk, gp.tile_n / gp.cluster_m);
     const bool use3d = gp.tile_n <= 128 && tk / sk::kBlkK >= 2;
     if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmA3, A[i], tt, m, tk, tk, sk::kBlkM);
-    if (st == SK_OK && use3d) st = encode_operand_3d(&pr.tmB3, B[i], tt, n, tk, tk, gp.tile_n);
+    if (st == SK_OK && use3d)
+      st = encode_operand_3d(&pr.tmB3, B[i], tt, n, tk, tk, gp.tile_n / gp.cluster_m);
     if (st != SK_OK) {
       g->table_valid = false;
       return st;
@@ -957,9 +960,12 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
   }
   sk::SkArgs a{};
   sk::set_group_walk_args(a, gp);
-  a.idesc = make_idesc(g->ab_type, gp.tile_n, 1);
+  a.idesc = make_idesc(g->ab_type, gp.tile_n, gp.cluster_m);
   a.c_tma = 0;
   const bool split = gp.workspace_bytes > 0;
+  // co-residency of a split schedule: as for single GEMMs, single CTAs ask
+  // for it, CTA pairs rely on the stream order
+  const bool cooperative = split && gp.cluster_m == 1;
   a.flags = split ? reinterpret_cast<uint32_t*>(g->ws) : nullptr;
   a.partials = split ? reinterpret_cast<float*>(g->ws + sk::kFlagBytes) : nullptr;
   a.epoch = next_epoch();
@@ -974,10 +980,12 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
   a.gprobs = g->d_probs;
   a.stages = g->stages_req;
   const CUtensorMap& any = g->h_probs[0].tmA;
-  cudaError_t e = f8                ? sk::launch_grouped_f8(g->c_type, any, a, split, stream)
-                  : gp.tile_n == 256 ? sk::launch_grouped_bn256(g->c_type, any, a, split, stream)
-                  : gp.tile_n == 64  ? sk::launch_grouped_bn64(g->c_type, any, a, split, stream)
-                                     : sk::launch_grouped_bn128(g->c_type, any, a, split, stream);
+  const int cm = gp.cluster_m;
+  cudaError_t e =
+      f8                 ? sk::launch_grouped_f8(g->c_type, any, a, cooperative, stream)
+      : gp.tile_n == 256 ? sk::launch_grouped_bn256(g->c_type, cm, any, a, cooperative, stream)
+      : gp.tile_n == 64  ? sk::launch_grouped_bn64(g->c_type, cm, any, a, cooperative, stream)
+                         : sk::launch_grouped_bn128(g->c_type, cm, any, a, cooperative, stream);
   if (e != cudaSuccess) return cuda_status(e);
   g->last_stream = stream;
   g->launched = true;
@@ -1026,7 +1034,10 @@ int sk_grouped_plan(sk_grouped_t* out, int count, const int64_t* m, const int64_
   g->enc_beta.assign(count, 0.0f);
   g->enc_sa.assign(count, nullptr);
   g->enc_sb.assign(count, nullptr);
-  if (ab_type == SK_E4M3) g->tile_n_req = 128;  // 128 x 128 x 128 tiles
+  if (ab_type == SK_E4M3) {
+    g->tile_n_req = 128;  // 128 x 128 x 128 tiles
+    g->cluster_req = 1;   // on single CTAs (grouped E4M3 launches have no CTA pairs)
+  }
   size_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   cudaError_t e = sk::prepare_bn128(&s1);
   if (e == cudaSuccess) e = sk::prepare_bn64(&s0);
@@ -1141,9 +1152,22 @@ int sk_grouped_set(sk_grouped_t g, int attr, int64_t v) {
       g->table_valid = false;
       return SK_OK;
     case SK_ATTR_STAGES:
-      if (v != 0 && (v < 2 || v > sk::max_stages(g->plan.tile_n, 1))) return SK_ERR_INVALID;
+      if (v != 0 && (v < 2 || v > sk::max_stages(g->plan.tile_n, g->plan.cluster_m)))
+        return SK_ERR_INVALID;
       g->stages_req = static_cast<int>(v);
       return SK_OK;
+    case SK_ATTR_CLUSTER_M: {
+      if (v != 0 && v != 1 && v != 2) return SK_ERR_UNSUPPORTED;
+      if (g->ab_type == SK_E4M3) return v == 0 || v == 1 ? SK_OK : SK_ERR_UNSUPPORTED;
+      const int old = g->cluster_req;
+      g->cluster_req = static_cast<int>(v);
+      const int st = grouped_replan(g);
+      if (st != SK_OK) {
+        g->cluster_req = old;
+        grouped_replan(g);
+      }
+      return st;
+    }
     default:
       return SK_ERR_INVALID;
   }
@@ -1155,10 +1179,11 @@ int sk_grouped_get(sk_grouped_t g, int attr, int64_t* v) {
   switch (attr) {
     case SK_ATTR_MODE: *v = gp.mode; return SK_OK;
     case SK_ATTR_TILE_N: *v = gp.tile_n; return SK_OK;
-    case SK_ATTR_TILE_M: *v = sk::kBlkM; return SK_OK;
+    case SK_ATTR_TILE_M: *v = sk::kBlkM * gp.cluster_m; return SK_OK;
     case SK_ATTR_TILE_K: *v = gp.tile_k; return SK_OK;
     case SK_ATTR_GRID: *v = gp.grid; return SK_OK;
-    case SK_ATTR_CTAS: *v = gp.grid; return SK_OK;
+    case SK_ATTR_CTAS: *v = static_cast<int64_t>(gp.grid) * gp.cluster_m; return SK_OK;
+    case SK_ATTR_CLUSTER_M: *v = gp.cluster_m; return SK_OK;
     case SK_ATTR_TILES: *v = gp.tiles; return SK_OK;
     case SK_ATTR_SK_TILES: *v = gp.sk_tiles; return SK_OK;
     case SK_ATTR_DP_TILES: *v = gp.tiles - gp.sk_tiles; return SK_OK;
@@ -1166,7 +1191,7 @@ int sk_grouped_get(sk_grouped_t g, int attr, int64_t* v) {
     case SK_ATTR_NUM_SMS: *v = g->num_sms; return SK_OK;
     case SK_ATTR_TRACE_CAP: *v = gp.max_segments; return SK_OK;
     case SK_ATTR_TRACE_INTS:
-      *v = static_cast<int64_t>(gp.grid) *
+      *v = static_cast<int64_t>(gp.grid) * gp.cluster_m *
            (sk::kTraceHeaderInts + static_cast<int64_t>(gp.max_segments) * sk::kTraceRecordInts);
       return SK_OK;
     case SK_ATTR_TIMEOUT_NS: *v = static_cast<int64_t>(g->timeout_ns); return SK_OK;
@@ -1174,7 +1199,7 @@ int sk_grouped_get(sk_grouped_t g, int attr, int64_t* v) {
     case SK_ATTR_STORE: *v = g->store_req; return SK_OK;
     case SK_ATTR_SEGMENTS: *v = static_cast<int64_t>(gp.segs.size()); return SK_OK;
     case SK_ATTR_STAGES: {
-      const int mx = sk::max_stages(gp.tile_n, 1);
+      const int mx = sk::max_stages(gp.tile_n, gp.cluster_m);
       *v = g->stages_req >= 2 && g->stages_req < mx ? g->stages_req : mx;
       return SK_OK;
     }
@@ -1285,31 +1310,39 @@ int grouped_autotune(sk_grouped_t g, const void* const* A, const void* const* B,
                      void* stream_v, double* best_us) {
   if (g == nullptr || reps < 1) return SK_ERR_INVALID;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
-  const int saved[4] = {g->tile_n_req, g->mode_req, g->grid_req, g->stages_req};
+  const int saved[5] = {g->tile_n_req, g->mode_req, g->grid_req, g->stages_req, g->cluster_req};
   const int tns[3] = {64, 128, 256}, modes[3] = {SK_MODE_DP, SK_MODE_HYBRID, SK_MODE_SK};
+  const int cms[2] = {1, 2};
   const int stage_opts[3] = {0, 3, 2};
+  int64_t max_m = 0;
+  for (int64_t v : g->m) max_m = std::max(max_m, v);
   double best = -1.0;
-  int bt = saved[0], bm = saved[1], bs = saved[3];
+  int bt = saved[0], bm = saved[1], bs = saved[3], bc = saved[4];
   for (int tn : tns) {
     if (tn != 128 && g->ab_type == SK_E4M3) continue;
-    for (int md : modes) {
-      for (int so : stage_opts) {
-        if (so >= sk::max_stages(tn, 1)) continue;
-        g->tile_n_req = tn;
-        g->mode_req = md;
-        g->grid_req = 0;
-        g->stages_req = so;
-        if (grouped_replan(g) != SK_OK) continue;
-        const double us = time_launches(
-            [&] { return grouped_impl(g, A, B, SA, SB, C, nullptr, nullptr, nullptr, 0, stream); },
-            reps, stream);
-        int dev_status = 0;
-        if (us < 0.0 || sk_grouped_last_error(g, &dev_status) != SK_OK) continue;
-        if (best < 0.0 || us < best) {
-          best = us;
-          bt = tn;
-          bm = md;
-          bs = so;
+    for (int cm : cms) {
+      if (cm == 2 && (tn == 64 || g->ab_type == SK_E4M3 || max_m <= sk::kTileM)) continue;
+      for (int md : modes) {
+        for (int so : stage_opts) {
+          if (so >= sk::max_stages(tn, cm)) continue;
+          g->tile_n_req = tn;
+          g->cluster_req = cm;
+          g->mode_req = md;
+          g->grid_req = 0;
+          g->stages_req = so;
+          if (grouped_replan(g) != SK_OK) continue;
+          const double us = time_launches(
+              [&] { return grouped_impl(g, A, B, SA, SB, C, nullptr, nullptr, nullptr, 0, stream); },
+              reps, stream);
+          int dev_status = 0;
+          if (us < 0.0 || sk_grouped_last_error(g, &dev_status) != SK_OK) continue;
+          if (best < 0.0 || us < best) {
+            best = us;
+            bt = tn;
+            bc = cm;
+            bm = md;
+            bs = so;
+          }
         }
       }
     }
@@ -1318,6 +1351,7 @@ int grouped_autotune(sk_grouped_t g, const void* const* A, const void* const* B,
   g->mode_req = best < 0.0 ? saved[1] : bm;
   g->grid_req = best < 0.0 ? saved[2] : 0;
   g->stages_req = best < 0.0 ? saved[3] : bs;
+  g->cluster_req = best < 0.0 ? saved[4] : bc;
   const int st = grouped_replan(g);
   if (st != SK_OK) return st;
   if (best_us) *best_us = best;

@@ -92,18 +92,25 @@ cudaError_t SK_CAT(launch_bn, SK_BN)(int c_dtype, int cluster_m, const CUtensorM
   return launch_any<kPairs>(c_dtype, cluster_m, ta, tb, tc, ta3, tb3, args, cooperative, stream);
 }
 
-// Grouped launches: single CTAs, the walk table and problem table in args
-// (the tensor-map parameters are not read).
-template <typename TC>
+// Grouped launches: the walk table and problem table in args (the
+// tensor-map parameters are not read); single CTAs or CTA pairs.
+template <int CM, typename TC>
 static cudaError_t launch_grouped_one(const CUtensorMap& tm, const SkArgs& args, bool cooperative,
                                       cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>(args.grid));
+  cfg.gridDim = dim3(static_cast<unsigned>(args.grid * CM));
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = Cfg<SK_BN, 1>::kSmemBytes;
+  cfg.dynamicSmemBytes = Cfg<SK_BN, CM>::kSmemBytes;
   cfg.stream = stream;
-  cudaLaunchAttribute attr[2];
+  cudaLaunchAttribute attr[3];
   unsigned na = 0;
+  if (CM > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = CM;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
   if (cooperative) {
     attr[na].id = cudaLaunchAttributeCooperative;
     attr[na].val.cooperative = 1;
@@ -116,21 +123,40 @@ static cudaError_t launch_grouped_one(const CUtensorMap& tm, const SkArgs& args,
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<SK_BN, 1, TC, true, false>, tm, tm, tm, tm, tm, args);
+  return cudaLaunchKernelEx(&cfg, sk_gemm_kernel<SK_BN, CM, TC, true, false>, tm, tm, tm, tm, tm, args);
 }
 
-cudaError_t SK_CAT(launch_grouped_bn, SK_BN)(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
-                                bool cooperative, cudaStream_t stream) {
+template <int CM>
+static cudaError_t launch_grouped_cm(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
+                                     bool cooperative, cudaStream_t stream) {
   switch (c_dtype) {
     case SK_F32:
-      return launch_grouped_one<float>(tm, args, cooperative, stream);
+      return launch_grouped_one<CM, float>(tm, args, cooperative, stream);
     case SK_BF16:
-      return launch_grouped_one<__nv_bfloat16>(tm, args, cooperative, stream);
+      return launch_grouped_one<CM, __nv_bfloat16>(tm, args, cooperative, stream);
     case SK_F16:
-      return launch_grouped_one<__half>(tm, args, cooperative, stream);
+      return launch_grouped_one<CM, __half>(tm, args, cooperative, stream);
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+template <bool kWithPairs>
+static cudaError_t launch_grouped_any(int c_dtype, int cluster_m, const CUtensorMap& tm,
+                                      const SkArgs& args, bool cooperative, cudaStream_t stream) {
+  if (cluster_m == 2) {
+    if constexpr (kWithPairs)
+      return launch_grouped_cm<2>(c_dtype, tm, args, cooperative, stream);
+    else
+      return cudaErrorInvalidValue;
+  }
+  return launch_grouped_cm<1>(c_dtype, tm, args, cooperative, stream);
+}
+
+cudaError_t SK_CAT(launch_grouped_bn, SK_BN)(int c_dtype, int cluster_m, const CUtensorMap& tm,
+                                             const SkArgs& args, bool cooperative,
+                                             cudaStream_t stream) {
+  return launch_grouped_any<kPairs>(c_dtype, cluster_m, tm, args, cooperative, stream);
 }
 
 template <int CM, typename TC>
@@ -138,8 +164,8 @@ static cudaError_t set_smem() {
   cudaError_t e = cudaFuncSetAttribute(sk_gemm_kernel<SK_BN, CM, TC, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg<SK_BN, CM>::kSmemBytes);
-  if (e != cudaSuccess || CM != 1) return e;
-  return cudaFuncSetAttribute(sk_gemm_kernel<SK_BN, 1, TC, true, false>,
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sk_gemm_kernel<SK_BN, CM, TC, true, false>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<SK_BN, CM>::kSmemBytes);
 }
 

@@ -23,14 +23,15 @@ cudaError_t launch_bn128(int c_dtype, int cluster_m, const CUtensorMap& ta, cons
 cudaError_t launch_bn256(int c_dtype, int cluster_m, const CUtensorMap& ta, const CUtensorMap& tb,
                          const CUtensorMap& tc, const CUtensorMap& ta3, const CUtensorMap& tb3,
                          const SkArgs& args, bool cooperative, cudaStream_t stream);
-// A grouped launch (args.grid single CTAs walking args.gwalk); tm is any valid
-// tensor map (the kernel's tensor-map parameters are unused there).
-cudaError_t launch_grouped_bn64(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
+// A grouped launch (args.grid units of cluster_m CTAs walking args.gwalk; CTA
+// pairs for BLK_N 128 and 256 only); tm is any valid tensor map (the kernel's
+// tensor-map parameters are unused there).
+cudaError_t launch_grouped_bn64(int c_dtype, int cluster_m, const CUtensorMap& tm, const SkArgs& args,
                                 bool cooperative, cudaStream_t stream);
-cudaError_t launch_grouped_bn128(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
-                                 bool cooperative, cudaStream_t stream);
-cudaError_t launch_grouped_bn256(int c_dtype, const CUtensorMap& tm, const SkArgs& args,
-                                 bool cooperative, cudaStream_t stream);
+cudaError_t launch_grouped_bn128(int c_dtype, int cluster_m, const CUtensorMap& tm,
+                                 const SkArgs& args, bool cooperative, cudaStream_t stream);
+cudaError_t launch_grouped_bn256(int c_dtype, int cluster_m, const CUtensorMap& tm,
+                                 const SkArgs& args, bool cooperative, cudaStream_t stream);
 // E4M3 operands with per-128 x 128-block scales (args.scale_a / scale_b):
 // BLK_N = 128, single CTAs or CTA pairs (cluster_m 2, 256 x 128 tiles).  The
 // operand maps view the rows as 16-bit elements (k/2 per row), 2-D and 3-D as

@@ -468,8 +468,10 @@ constexpr double kHbmBytesPerUs = 6.5e6;
 // HBM.
 double group_dram_bytes(const std::vector<GroupShape>& ps, const std::vector<int64_t>& m,
                         const std::vector<int64_t>& n, const std::vector<int64_t>& k,
-                        const GroupPlan& gp, int tile_n) {
-  const double stage = static_cast<double>(kTileM + tile_n) * tile_k_for(tile_n) * 2.0;
+                        const GroupPlan& gp, int tile_n, int cluster_m) {
+  // operand bytes of one unit's MAC-loop iteration
+  const double stage =
+      static_cast<double>(kTileM * cluster_m + tile_n) * tile_k_for(tile_n) * 2.0;
   double bytes = 0.0;
   int64_t tile0 = 0;
   for (size_t i = 0; i < ps.size(); ++i) {
@@ -561,11 +563,13 @@ int describe_grouped_dp(int count, const int64_t* m, const int64_t* n, const int
 }
 
 int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_t* k, int mode,
-                     int tile_n, int grid, int num_sms, GroupPlan* out) {
+                     int tile_n, int grid, int num_sms, GroupPlan* out, int cluster_m) {
   if (out == nullptr || count < 1 || m == nullptr || n == nullptr || k == nullptr || num_sms < 1 ||
       num_sms > kMaxGrid || grid < 0 || grid > num_sms)
     return SK_ERR_INVALID;
   if (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
+  if (cluster_m != 0 && cluster_m != 1 && cluster_m != 2) return SK_ERR_UNSUPPORTED;
+  if (tile_n == 64 && cluster_m == 2) return SK_ERR_UNSUPPORTED;
   if (mode != SK_MODE_AUTO && mode != SK_MODE_DP && mode != SK_MODE_SK && mode != SK_MODE_HYBRID)
     return SK_ERR_UNSUPPORTED;
   int64_t max_n = 0;
@@ -574,35 +578,49 @@ int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_
       return SK_ERR_INVALID;
     max_n = std::max(max_n, n[i]);
   }
-  int tns[2], ntn = 0;
+  int64_t max_m = 0;
+  for (int i = 0; i < count; ++i) max_m = std::max(max_m, m[i]);
+  int tns[2], ntn = 0, cms[2], ncm = 0;
   if (tile_n) {
     tns[ntn++] = tile_n;
   } else {
     tns[ntn++] = 128;
     if (max_n > 128) tns[ntn++] = 256;
   }
+  if (cluster_m) {
+    cms[ncm++] = cluster_m;
+  } else {
+    cms[ncm++] = 1;
+    if (max_m > kTileM && num_sms >= 2) cms[ncm++] = 2;  // a pair needs two 128-row blocks
+  }
   int status = SK_ERR_INVALID;
   double best_us = 0.0;
   for (int i = 0; i < ntn; ++i) {
+  for (int ci = 0; ci < ncm; ++ci) {
     const int bn = tns[i];
+    const int cm = cms[ci];
+    if (bn == 64 && cm == 2) continue;  // BLK_N = 64 runs on single CTAs
     const int bk = tile_k_for(bn);
+    // The schedule's unit is a cluster of cm CTAs computing a (128 * cm) x bn
+    // tile; p counts units.
     std::vector<GroupShape> ps(static_cast<size_t>(count));
     int64_t t = 0, total_iters = 0;
     for (int j = 0; j < count; ++j) {
       GroupShape& p = ps[static_cast<size_t>(j)];
-      p.tiles_m = cdiv(m[j], kTileM);
+      p.tiles_m = cdiv(m[j], int64_t(kTileM) * cm);
       p.tiles_n = cdiv(n[j], bn);
       p.tiles = p.tiles_m * p.tiles_n;
       p.ipt = cdiv(k[j], bk);
-      p.group_m = std::min<int64_t>(p.tiles_m, 16);
+      p.group_m = std::min<int64_t>(p.tiles_m, 16 / cm);
       p.kfull64 = bk == 128 && k[j] / 64 >= 2 ? k[j] / 64 : 0;
       t += p.tiles;
       total_iters += p.tiles * p.ipt;
     }
     if (t > INT32_MAX || total_iters > INT32_MAX) return SK_ERR_INVALID;
     double c[kModelTerms];
-    model_coefficients(bn, 1, c);
-    const int64_t p = num_sms;
+    model_coefficients(bn, cm, c);
+    const int64_t p = num_sms / cm;
+    if (grid > p) continue;
     // candidate (mode, sk_tiles, grid)
     struct Cand { int mode; int64_t sk_tiles, g; };
     std::vector<Cand> cands;
@@ -621,19 +639,22 @@ int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_
       if (!build_group(ps, std::max<int64_t>(cd.g, 1), cd.sk_tiles, &gp)) return SK_ERR_INVALID;
       build_walk(ps, std::max<int64_t>(cd.g, 1), cd.sk_tiles, &gp);
       gp.grid = static_cast<int32_t>(std::max<int64_t>(cd.g, 1));
-      const double us = std::max(predict_group(gp, c),
-                                 c[0] + group_dram_bytes(ps, mv, nv, kv, gp, bn) / kHbmBytesPerUs);
+      const double us =
+          std::max(predict_group(gp, c),
+                   c[0] + group_dram_bytes(ps, mv, nv, kv, gp, bn, cm) / kHbmBytesPerUs);
       if (status != SK_OK || us < best_us) {
         gp.mode = cd.mode;
         gp.tile_n = bn;
         gp.tile_k = bk;
+        gp.cluster_m = cm;
         gp.grid = static_cast<int32_t>(std::max<int64_t>(cd.g, 1));
-        gp.workspace_bytes = gp.split ? workspace_bytes_for(gp.grid, bn) : 0;
+        gp.workspace_bytes = gp.split ? workspace_bytes_for(gp.grid * cm, bn) : 0;
         *out = std::move(gp);
         best_us = us;
         status = SK_OK;
       }
     }
+  }
   }
   return status;
 }
@@ -644,15 +665,15 @@ int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_
 // the segment records of sk_grouped_plan's schedule for num_sms SMs.
 extern "C" int sk_grouped_plan_describe(int count, const int64_t* m, const int64_t* n,
                                         const int64_t* k, int mode, int tile_n, int grid,
-                                        int num_sms, int64_t* summary, int32_t* records,
-                                        int64_t capacity, int64_t* nrec) {
+                                        int num_sms, int cluster_m, int64_t* summary,
+                                        int32_t* records, int64_t capacity, int64_t* nrec) {
   sk::GroupPlan gp;
-  const int st = sk::describe_grouped(count, m, n, k, mode, tile_n, grid, num_sms, &gp);
+  const int st = sk::describe_grouped(count, m, n, k, mode, tile_n, grid, num_sms, &gp, cluster_m);
   if (st != SK_OK) return st;
   if (summary != nullptr) {
-    const int64_t sm[8] = {gp.mode, gp.tile_n, gp.tile_k, gp.grid, gp.tiles, gp.sk_tiles,
-                           gp.workspace_bytes, gp.max_segments};
-    for (int i = 0; i < 8; ++i) summary[i] = sm[i];
+    const int64_t sm[9] = {gp.mode, gp.tile_n, gp.tile_k, gp.grid, gp.tiles, gp.sk_tiles,
+                           gp.workspace_bytes, gp.max_segments, gp.cluster_m};
+    for (int i = 0; i < 9; ++i) summary[i] = sm[i];
   }
   if (nrec != nullptr) *nrec = static_cast<int64_t>(gp.segs.size());
   if (records == nullptr) return SK_OK;

@@ -44,7 +44,8 @@ int64_t workspace_bytes_for(int grid, int tile_n);
 // (CTA x owns segs[start[x] .. start[x+1])) for the model and the schedule
 // query, and the walk table the device derives the same segments from.
 struct GroupPlan {
-  int mode = 0, tile_n = 0, tile_k = 0, grid = 0, max_segments = 1;
+  // grid counts units of cluster_m CTAs; records and the walk are per unit
+  int mode = 0, tile_n = 0, tile_k = 0, grid = 0, max_segments = 1, cluster_m = 1;
   int64_t tiles = 0, sk_tiles = 0, sk_iters = 0, workspace_bytes = 0;
   bool split = false;
   std::vector<GroupSeg> segs;
@@ -53,8 +54,10 @@ struct GroupPlan {
   std::vector<GroupWalk> walk;
   std::vector<int32_t> gstart;
 };
+// cluster_m 0 tries single CTAs and CTA pairs (units of two CTAs computing
+// 256-row tiles); grid counts units.
 int describe_grouped(int count, const int64_t* m, const int64_t* n, const int64_t* k, int mode,
-                     int tile_n, int grid, int num_sms, GroupPlan* out);
+                     int tile_n, int grid, int num_sms, GroupPlan* out, int cluster_m = 1);
 // The launch-wide walk fields of SkArgs for a grouped schedule: grid, tile
 // count, Stream-K region and its within-one split, and their divisors.
 void set_group_walk_args(SkArgs& a, const GroupPlan& gp);

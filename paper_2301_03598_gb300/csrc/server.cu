@@ -372,9 +372,9 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   if (e != cudaSuccess) return cuda_status(e);
   s.h_status[0] = 0;
   e = f8                ? sk::launch_grouped_f8(sv->c_type, any, a, split, s.stream)
-      : gp.tile_n == 256 ? sk::launch_grouped_bn256(sv->c_type, any, a, split, s.stream)
-      : gp.tile_n == 64  ? sk::launch_grouped_bn64(sv->c_type, any, a, split, s.stream)
-                         : sk::launch_grouped_bn128(sv->c_type, any, a, split, s.stream);
+      : gp.tile_n == 256 ? sk::launch_grouped_bn256(sv->c_type, 1, any, a, split, s.stream)
+      : gp.tile_n == 64  ? sk::launch_grouped_bn64(sv->c_type, 1, any, a, split, s.stream)
+                         : sk::launch_grouped_bn128(sv->c_type, 1, any, a, split, s.stream);
   if (e == cudaSuccess && split) e = cudaEventRecord(sv->split_done, s.stream);
   if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
   if (e != cudaSuccess) return cuda_status(e);

@@ -489,6 +489,44 @@ __device__ __forceinline__ void add_beta_c(const OutView& o, int grow, int gcol,
   }
 }
 
+// v += P[first] + P[first + CM] + ... + P[last], added one peer at a time in
+// that order (Algorithm 5's fixup), for one lane's 32 columns of one (32-column
+// chunk, lane quarter) block of the peers' partial slots, blk = chunk * 4 +
+// quarter.  Two peers' 4 KiB blocks per warp are in flight.
+template <int CM, int BN>
+__device__ __forceinline__ void add_peers(const float* partials, int first, int last, int blk,
+                                          int lane, float (&v)[32]) {
+  for (int y = first; y <= last; y += 2 * CM) {
+    const float4* s0 = reinterpret_cast<const float4*>(partials + static_cast<size_t>(y) * (kBlkM * BN)) +
+                       blk * 256 + lane;
+    const bool two = y + CM <= last;
+    const float4* s1 = two ? s0 + CM * (kBlkM * BN) / 4 : s0;
+    float4 p0[8], p1[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) p0[j] = __ldcg(s0 + j * 32);
+    if (two) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) p1[j] = __ldcg(s1 + j * 32);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      v[4 * j] += p0[j].x;
+      v[4 * j + 1] += p0[j].y;
+      v[4 * j + 2] += p0[j].z;
+      v[4 * j + 3] += p0[j].w;
+    }
+    if (two) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        v[4 * j] += p1[j].x;
+        v[4 * j + 1] += p1[j].y;
+        v[4 * j + 2] += p1[j].z;
+        v[4 * j + 3] += p1[j].w;
+      }
+    }
+  }
+}
+
 // CM = CTAs per cluster along M (1 or 2).  With CM = 2 the two CTAs of a
 // cluster form a tcgen05 CTA pair computing one 256 x BN tile: the schedule's
 // unit is that tile.  Each CTA loads its own 128 rows of A and BN/2 rows of B
@@ -501,7 +539,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmA3,
                    const __grid_constant__ CUtensorMap tmB3, const __grid_constant__ SkArgs a) {
   static_assert(CM == 1 || CM == 2, "cluster size along M");
-  static_assert(!GROUPED || CM == 1, "grouped launches use single CTAs");
   using C_ = Cfg<BN, CM, F8>;
   constexpr int NB = C_::kAccBufs;
   constexpr int S = C_::kStages;
@@ -1082,39 +1119,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             fail = __any_sync(0xffffffffu, fail);
             if (tracer) t_fix = globaltimer_ns();
-            if (!fail) {
-              // acc + P[x+1] + P[x+2] + ... in increasing CTA order
-              for (int y = peer_first; y <= peer_last; y += 2 * CM) {
-                const float4* s0 = reinterpret_cast<const float4*>(
-                                       a.partials + static_cast<size_t>(y) * (kBlkM * BN)) +
-                                   (c * 4 + quarter) * 256 + lane;
-                const bool two = y + CM <= peer_last;
-                const float4* s1 = two ? s0 + CM * (kBlkM * BN) / 4 : s0;
-                float4 p0[8], p1[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) p0[j] = __ldcg(s0 + j * 32);
-                if (two) {
-#pragma unroll
-                  for (int j = 0; j < 8; ++j) p1[j] = __ldcg(s1 + j * 32);
-                }
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                  v[4 * j] += p0[j].x;
-                  v[4 * j + 1] += p0[j].y;
-                  v[4 * j + 2] += p0[j].z;
-                  v[4 * j + 3] += p0[j].w;
-                }
-                if (two) {
-#pragma unroll
-                  for (int j = 0; j < 8; ++j) {
-                    v[4 * j] += p1[j].x;
-                    v[4 * j + 1] += p1[j].y;
-                    v[4 * j + 2] += p1[j].z;
-                    v[4 * j + 3] += p1[j].w;
-                  }
-                }
-              }
-            }
+            // acc + P[x+1] + P[x+2] + ... in increasing CTA order
+            if (!fail) add_peers<CM, BN>(a.partials, peer_first, peer_last, c * 4 + quarter, lane, v);
           }
           // Every warp takes the same branch below (owners agree on failure
           // first), so the two warps of a quarter always meet at both barriers.
@@ -1239,42 +1245,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           if (tracer && u == col_half) t_fix = globaltimer_ns();
-          // acc + P[x+1] + P[x+2] + ... in increasing CTA order; two peers'
-          // loads are in flight at a time.
+          // acc + P[x+1] + P[x+2] + ... in increasing CTA order
 #pragma unroll
           for (int cc = 0; cc < kCpu; ++cc) {
             if (cc >= cvalid) break;
-            const int c = u * kCpu + cc;
-            for (int y = peer_first; y <= peer_last; y += 2 * CM) {
-              const float4* s0 = reinterpret_cast<const float4*>(
-                                     a.partials + static_cast<size_t>(y) * (kBlkM * BN)) +
-                                 (c * 4 + quarter) * 256 + lane;
-              const bool two = y + CM <= peer_last;
-              const float4* s1 = two ? s0 + CM * (kBlkM * BN) / 4 : s0;
-              float4 p0[8], p1[8];
-#pragma unroll
-              for (int j = 0; j < 8; ++j) p0[j] = __ldcg(s0 + j * 32);
-              if (two) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) p1[j] = __ldcg(s1 + j * 32);
-              }
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                v[cc][4 * j] += p0[j].x;
-                v[cc][4 * j + 1] += p0[j].y;
-                v[cc][4 * j + 2] += p0[j].z;
-                v[cc][4 * j + 3] += p0[j].w;
-              }
-              if (two) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                  v[cc][4 * j] += p1[j].x;
-                  v[cc][4 * j + 1] += p1[j].y;
-                  v[cc][4 * j + 2] += p1[j].z;
-                  v[cc][4 * j + 3] += p1[j].w;
-                }
-              }
-            }
+            add_peers<CM, BN>(a.partials, peer_first, peer_last, (u * kCpu + cc) * 4 + quarter, lane,
+                              v[cc]);
           }
         }
         if (!out.c_tma) {

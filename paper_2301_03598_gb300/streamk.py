@@ -113,7 +113,7 @@ def lib() -> ctypes.CDLL:
     L.sk_grouped_autotune.argtypes = [vp, vpp, vpp, vpp, i32, vp, dblp]
     L.sk_plan_autotune_scaled.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, dblp]
     L.sk_grouped_autotune_scaled.argtypes = [vp, vpp, vpp, vpp, vpp, vpp, i32, vp, dblp]
-    L.sk_grouped_plan_describe.argtypes = [i32, i64p, i64p, i64p, i32, i32, i32, i32, i64p,
+    L.sk_grouped_plan_describe.argtypes = [i32, i64p, i64p, i64p, i32, i32, i32, i32, i32, i64p,
                                            ctypes.POINTER(ctypes.c_int32), i64, i64p]
     L.sk_status_string.argtypes = [i32]
     L.sk_status_string.restype = ctypes.c_char_p
@@ -372,7 +372,7 @@ class GroupedPlan:
     def info(self):
         names = ("mode", "tile_m", "tile_n", "tile_k", "grid", "ctas", "tiles", "sk_tiles",
                  "dp_tiles", "workspace_bytes", "num_sms", "trace_cap", "trace_ints", "segments",
-                 "stages")
+                 "stages", "cluster_m")
         return {name: self.get(name) for name in names}
 
     def destroy(self):
@@ -461,22 +461,25 @@ def sk_grouped_destroy(plan: GroupedPlan) -> None:
 
 
 def sk_grouped_plan_describe(shapes, mode="auto", tile_n: int = 0, grid: int = 0,
-                             num_sms: int = 148):
-    """Host-only grouped planning: (summary dict, records) without a device."""
+                             num_sms: int = 148, cluster_m: int = 1):
+    """Host-only grouped planning: (summary dict, records) without a device.
+    cluster_m 0 lets the model choose single CTAs or CTA pairs (records and
+    grid then count units)."""
     cnt = len(shapes)
     arr = lambda j: (ctypes.c_int64 * cnt)(*[int(s[j]) for s in shapes])
     m, n, k = arr(0), arr(1), arr(2)
-    summary = (ctypes.c_int64 * 8)()
+    summary = (ctypes.c_int64 * 9)()
     nrec = ctypes.c_int64(0)
     _check(lib().sk_grouped_plan_describe(cnt, m, n, k, _code(MODES, mode, "mode"), tile_n, grid,
-                                          num_sms, summary, None, 0, ctypes.byref(nrec)),
-           "sk_grouped_plan_describe")
+                                          num_sms, cluster_m, summary, None, 0,
+                                          ctypes.byref(nrec)), "sk_grouped_plan_describe")
     buf = (ctypes.c_int32 * (10 * max(1, nrec.value)))()
     _check(lib().sk_grouped_plan_describe(cnt, m, n, k, _code(MODES, mode, "mode"), tile_n, grid,
-                                          num_sms, summary, buf, 10 * max(1, nrec.value),
-                                          ctypes.byref(nrec)), "sk_grouped_plan_describe")
+                                          num_sms, cluster_m, summary, buf,
+                                          10 * max(1, nrec.value), ctypes.byref(nrec)),
+           "sk_grouped_plan_describe")
     keys = ("mode", "tile_n", "tile_k", "grid", "tiles", "sk_tiles", "workspace_bytes",
-            "max_segments")
+            "max_segments", "cluster_m")
     info = dict(zip(keys, list(summary)))
     info["mode_name"] = MODE_NAMES.get(info["mode"], "?")
     vals = list(buf)

@@ -60,11 +60,13 @@ def _decode_grouped(vals, ctas, cap):
 
 
 @pytest.mark.parametrize("mode", ["auto", "dp", "sk", "hybrid"])
-@pytest.mark.parametrize("tile_n", [128, 256])
-def test_grouped_matches_oracle(mode, tile_n):
-    probs, outs, alphas, info, _ = _run(GROUP, mode, "bf16", 0.0, {"tile_n": tile_n}, seed=5)
+@pytest.mark.parametrize("tile_n,cluster_m", [(128, 1), (256, 1), (128, 2), (256, 2)])
+def test_grouped_matches_oracle(mode, tile_n, cluster_m):
+    probs, outs, alphas, info, _ = _run(GROUP, mode, "bf16", 0.0,
+                                        {"tile_n": tile_n, "cluster_m": cluster_m}, seed=5)
+    assert info["cluster_m"] == cluster_m and info["ctas"] == cluster_m * info["grid"]
     for p, C, al in zip(probs, outs[0], alphas):
-        p.check(C, al, 0.0, f"grouped {mode} bn={tile_n} {p.m}x{p.n}x{p.k}")
+        p.check(C, al, 0.0, f"grouped {mode} bn={tile_n} cm={cluster_m} {p.m}x{p.n}x{p.k}")
 
 
 @pytest.mark.parametrize("c_type", ["f32", "f16"])
@@ -75,13 +77,17 @@ def test_grouped_beta_and_output_types(c_type):
 
 
 @pytest.mark.parametrize("mode,attrs", [("sk", {"grid": 23}), ("hybrid", {"tile_n": 128}),
-                                        ("auto", {}), ("dp", {"tile_n": 256})])
+                                        ("auto", {}), ("dp", {"tile_n": 256}),
+                                        ("sk", {"tile_n": 256, "cluster_m": 2, "grid": 23}),
+                                        ("hybrid", {"tile_n": 128, "cluster_m": 2}),
+                                        ("dp", {"tile_n": 256, "cluster_m": 2})])
 def test_grouped_device_schedule_matches_oracle(mode, attrs):
     probs, outs, alphas, info, recs = _run(GROUP, mode, "bf16", 0.0, attrs, trace=True, seed=2)
-    oprobs = [S.Problem(m, n, k, 128, info["tile_n"], info["tile_k"]) for (m, n, k) in GROUP]
+    cm = info["cluster_m"]
+    oprobs = [S.Problem(m, n, k, 128 * cm, info["tile_n"], info["tile_k"]) for (m, n, k) in GROUP]
     ctas = S.grouped_schedule(oprobs, info["grid"], info["sk_tiles"])
-    want = S.grouped_trace(oprobs, ctas, [min(p.tiles_m, 16) for p in oprobs])
-    assert recs == want
+    units = S.grouped_trace(oprobs, ctas, [min(p.tiles_m, 16 // cm) for p in oprobs])
+    assert recs == S.grouped_cluster_trace(units, cm)
     for p, C, al in zip(probs, outs[0], alphas):
         p.check(C, al, 0.0, f"traced grouped {mode}")
 
@@ -118,9 +124,11 @@ def test_grouped_relaunch_with_new_buffers_and_graph_replay():
         plan.destroy()
 
 
-def test_grouped_single_problem_equals_gemm_bitwise():
+@pytest.mark.parametrize("cluster_m,grid", [(1, 36), (2, 18)])
+def test_grouped_single_problem_equals_gemm_bitwise(cluster_m, grid):
     """A group of one problem runs the same schedule as the single-GEMM path
-    with the same tile width and grid, so the results are bitwise equal."""
+    with the same tile configuration and grid, so the results are bitwise
+    equal (single CTAs and CTA pairs)."""
     m, n, k = 384, 384, 4096
     p = Problem(m, n, k, "bf16", "f32", "normal", seed=77)
     A, B = p.A.cuda(), p.B.cuda()
@@ -128,10 +136,11 @@ def test_grouped_single_problem_equals_gemm_bitwise():
     gplan = sk.sk_grouped_plan([(m, n, k)], "bf16", "f32", "sk")
     try:
         plan.set("tile_n", 128)
-        plan.set("cluster_m", 1)
-        plan.set("grid", 36)
+        plan.set("cluster_m", cluster_m)
+        plan.set("grid", grid)
         gplan.set("tile_n", 128)
-        gplan.set("grid", 36)
+        gplan.set("cluster_m", cluster_m)
+        gplan.set("grid", grid)
         C1 = torch.zeros(m, n, dtype=torch.float32, device="cuda")
         C2 = torch.zeros(m, n, dtype=torch.float32, device="cuda")
         sk.sk_gemm(plan, A, B, C1)

@@ -115,3 +115,48 @@ def test_host_planner_rejects_bad_groups():
         sk.sk_grouped_plan_describe([(8, 8, 8)], tile_n=96)
     with pytest.raises(sk.StreamKError):
         sk.sk_grouped_plan_describe([(8, 8, 8)], mode="hybrid1")
+
+
+def test_grouped_cluster_trace_hand_worked():
+    """Two problems in 256 x 128 pair tiles, BLK_K = 64: problem 0 is 256 x 256
+    x 320 (two tiles of 5 iterations), problem 1 is 512 x 128 x 192 (two tiles
+    of 3 iterations); 16 iterations in all, Algorithm 5 within one over g = 3
+    units: q = 5, r = 1, so unit 0 takes [0, 6), unit 1 [6, 11), unit 2
+    [11, 16).  Tiles in the concatenated space: p0 t0 [0, 5), p0 t1 [5, 10),
+    p1 t0 [10, 13), p1 t1 [13, 16).  Raster: p0 (tiles_m 1) t0 -> (0, 0),
+    t1 -> (0, 1); p1 (tiles_m 2) t0 -> (0, 0), t1 -> (1, 0).
+      unit 0: p0 t0 [0, 5) whole; p0 t1 [0, 1) owner, peers 1..1
+      unit 1: p0 t1 [1, 5) partial; p1 t0 [0, 1) owner, peers 2..2
+      unit 2: p1 t0 [1, 3) partial; p1 t1 [0, 3) whole
+    CTA 2x + r runs unit x on 128-row block 2 tm + r; its peers are 2y + r."""
+    W, P, O = S.ROLE_WHOLE, S.ROLE_PARTIAL, S.ROLE_OWNER
+    probs = [S.Problem(256, 256, 320, 256, 128, 64), S.Problem(512, 128, 192, 256, 128, 64)]
+    ctas = S.grouped_schedule(probs, 3, probs[0].tiles + probs[1].tiles)
+    units = S.grouped_trace(probs, ctas, [1, 2])
+    want = [
+        (0, 0, 0, 0, 0, 0, 5, W, -1, -1), (0, 0, 1, 0, 1, 0, 1, O, 2, 2),
+        (1, 0, 0, 1, 0, 0, 5, W, -1, -1), (1, 0, 1, 1, 1, 0, 1, O, 3, 3),
+        (2, 0, 1, 0, 1, 1, 5, P, -1, -1), (2, 1, 0, 0, 0, 0, 1, O, 4, 4),
+        (3, 0, 1, 1, 1, 1, 5, P, -1, -1), (3, 1, 0, 1, 0, 0, 1, O, 5, 5),
+        (4, 1, 0, 0, 0, 1, 3, P, -1, -1), (4, 1, 1, 2, 0, 0, 3, W, -1, -1),
+        (5, 1, 0, 1, 0, 1, 3, P, -1, -1), (5, 1, 1, 3, 0, 0, 3, W, -1, -1),
+    ]
+    assert S.grouped_cluster_trace(units, 2) == want
+    assert S.grouped_cluster_trace(units, 1) == units
+
+
+@pytest.mark.parametrize("mode", ["dp", "sk", "hybrid", "auto"])
+def test_host_planner_pairs_match_oracle(mode):
+    """Grouped plans on CTA pairs: per-unit records equal the oracle's grouped
+    schedule over 256-row tiles on num_sms / 2 units."""
+    for shapes in _groups():
+        info, recs = sk.sk_grouped_plan_describe(shapes, mode, tile_n=256, num_sms=152, cluster_m=2)
+        assert info["cluster_m"] == 2 and info["grid"] <= 76
+        probs = [S.Problem(m, n, k, 256, 256, 64) for (m, n, k) in shapes]
+        assert info["tiles"] == sum(p.tiles for p in probs)
+        ctas = S.grouped_schedule(probs, info["grid"], info["sk_tiles"])
+        assert recs == S.grouped_trace(probs, ctas, [min(p.tiles_m, 8) for p in probs])
+        split = any(r[7] != S.ROLE_WHOLE for r in recs)
+        assert (info["workspace_bytes"] > 0) == split
+        if split:
+            assert info["workspace_bytes"] >= 2 * info["grid"] * 128 * 256 * 4
