@@ -88,9 +88,9 @@ def load_peaks():
 # summed over the captured launches, divided by their 2mnk), and the sha256 of
 # csrc/sk_kernel.cuh followed by csrc/planner.cpp at that capture.  The
 # summary with its command is profiles/sk_gemm_sweep_launches.md.
-PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.175318e-03,
+PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.175560e-03,
                     "kernel_source_sha256":
-                        "714ac8af3cdb4a7ef4069a3bfbb0b0d27c78c581d171c2d0506660cb99488e00"}
+                        "7853cde4847199546570b0d75da1d98cf1b8bf1a0d0579a15e5c86b9cdbd957b"}
 
 
 def profiled_bytes_per_flop():
