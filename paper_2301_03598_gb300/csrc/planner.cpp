@@ -73,7 +73,15 @@ static double predict_us(const sk_schedule_info& s, const double c[kModelTerms])
   const int64_t peers = s.sk_tiles ? cdiv(ipt, std::max<int64_t>(q, 1)) : 1;
   const int64_t sk_segs = s.sk_tiles ? cdiv(q + 1, ipt) + 1 : 0;
   const double tile_period = std::max(c[2] * static_cast<double>(ipt), c[5]);
-  return c[0] + c[1] * split + c[2] * static_cast<double>(sk_share) +
+  // The tile period holds inside the Stream-K share too: the whole tiles a
+  // share can hold (sk_share / ipt of them, e.g. every iteration when
+  // ipt = 1) each take max(c * ipt, f), like data-parallel tiles; the split
+  // segments at its ends take c per iteration, their epilogues being the
+  // spill and the fixup of the b and d terms.
+  const int64_t share_whole = sk_share / ipt;
+  const double sk_time = c[2] * static_cast<double>(sk_share - share_whole * ipt) +
+                         static_cast<double>(share_whole) * tile_period;
+  return c[0] + c[1] * split + sk_time +
          static_cast<double>(dp_per_unit) * tile_period +
          c[3] * static_cast<double>(peers - 1) * split +
          c[4] * static_cast<double>(sk_segs + dp_per_unit);
