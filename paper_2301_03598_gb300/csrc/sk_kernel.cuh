@@ -542,9 +542,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   using C_ = Cfg<BN, CM, F8>;
   constexpr int NB = C_::kAccBufs;
   constexpr int S = C_::kStages;
-  // Pipeline depth: the producer keeps at most `depth` stages loaded ahead of
-  // the MMAs (SkArgs::stages, autotuned; the full ring by default).
-  const int depth = a.stages >= 2 && a.stages < S ? a.stages : S;
+  // The ring's stages the MAC loop cycles through (SkArgs::stages, the
+  // autotuners' pipeline-depth choice; the full ring by default).
+  const int nst = a.stages >= 2 && a.stages < S ? a.stages : S;
   constexpr int KD = C_::KD;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -670,18 +670,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          if (depth < S && issued >= depth) {
-            // a shallower pipeline: iteration issued - depth must have been consumed
-            const int64_t j = issued - depth;
-            if (!wait_bar(empty_bar(static_cast<int>(j % S)), static_cast<uint32_t>((j / S) & 1),
-                          abort_flag, a, kAtProducerEmpty)) {
-              ok = false;
-              break;
-            }
-          }
           int next = stage + 1;
           uint32_t next_phase = phase;
-          if (next == S) {
+          if (next == nst) {
             next = 0;
             next_phase ^= 1u;
           }
@@ -741,9 +732,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (ok) {
         // Tail: wait until the MMA warp has released every stage, so no
         // tcgen05.commit arrival is still in flight when the CTA exits.
-        for (int i = 0; i < S; ++i) {
+        for (int i = 0; i < nst; ++i) {
           if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) break;
-          if (++stage == S) {
+          if (++stage == nst) {
             stage = 0;
             phase ^= 1u;
           }
@@ -756,10 +747,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         constexpr uint64_t kUnwindNs = 1000000;
         const uint64_t t0 = globaltimer_ns();
         if (issuer) {
-          const int64_t first = issued > S ? issued - S : 0;
+          const int64_t first = issued > nst ? issued - nst : 0;
           for (int64_t j = first; j < issued; ++j) {
-            const int s = static_cast<int>(j % S);
-            const uint32_t par = static_cast<uint32_t>((j / S) & 1);
+            const int s = static_cast<int>(j % nst);
+            const uint32_t par = static_cast<uint32_t>((j / nst) & 1);
             while (!mbar_try_wait(full_bar(s), par) && globaltimer_ns() - t0 < kUnwindNs) {
             }
           }
@@ -806,7 +797,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             int next = stage + 1;
             uint32_t next_phase = phase;
-            if (next == S) {
+            if (next == nst) {
               next = 0;
               next_phase ^= 1u;
             }
@@ -867,7 +858,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           int next = stage + 1;
           uint32_t next_phase = phase;
-          if (next == S) {
+          if (next == nst) {
             next = 0;
             next_phase ^= 1u;
           }

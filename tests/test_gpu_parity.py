@@ -323,3 +323,28 @@ def test_pipeline_stage_counts(tile_n, cluster_m, stages):
             plan.set("stages", full + 1)
     finally:
         plan.destroy()
+
+
+@pytest.mark.parametrize("tile_n,cluster_m", [(64, 1), (128, 1), (256, 1), (128, 2), (256, 2)])
+@pytest.mark.parametrize("c_type,beta", [("bf16", 0.0), ("f32", 0.5)])
+def test_fewer_ring_stages_bitwise_many_tiles(tile_n, cluster_m, c_type, beta):
+    """A ring cycled through one stage fewer than it holds, on a data-parallel
+    plan with several tiles per unit, a ragged edge and (BLK_N = 64, 16-bit C)
+    the split epilogue: the result matches the oracle and, the schedule being
+    the same, equals the full ring's bit for bit."""
+    m, n, k = 4000, 2600, 256
+    prob = Problem(m, n, k, "bf16", c_type, "normal", seed=131 + tile_n + cluster_m, beta=beta)
+    base = {"tile_n": tile_n, "cluster_m": cluster_m}
+    plan = sk.sk_plan(m, n, k, "bf16", "bf16", c_type, mode="dp")
+    try:
+        plan.set("tile_n", tile_n)
+        plan.set("cluster_m", cluster_m)
+        full = plan.get("stages")
+        assert plan.info()["tiles"] > plan.info()["grid"]
+    finally:
+        plan.destroy()
+    (C_full,), _, _ = prob.run(1.5, beta, "dp", plan_attrs=base)
+    (C_alt,), info, _ = prob.run(1.5, beta, "dp", plan_attrs=dict(base, stages=full - 1))
+    assert info["mode"] == sk.MODES["dp"]
+    prob.check(C_alt, 1.5, beta, f"ring of full-1 stages bn={tile_n} cm={cluster_m} {c_type}")
+    assert torch.equal(C_alt, C_full), "fewer ring stages changed the result"
