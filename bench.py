@@ -88,9 +88,9 @@ def load_peaks():
 # summed over the captured launches, divided by their 2mnk), and the sha256 of
 # csrc/sk_kernel.cuh followed by csrc/planner.cpp at that capture.  The
 # summary with its command is profiles/sk_gemm_sweep_launches.md.
-PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.175560e-03,
+PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.175476e-03,
                     "kernel_source_sha256":
-                        "7853cde4847199546570b0d75da1d98cf1b8bf1a0d0579a15e5c86b9cdbd957b"}
+                        "cd8381875215d0d15677e8d992eea02a0fea12b03fba750b8ad5e4cf098df410"}
 
 
 def profiled_bytes_per_flop():
