@@ -284,6 +284,27 @@ int sk_grid_model(int64_t m, int64_t n, int64_t k, int bm, int bn, int bk, int p
                   const double coef[4], int* g_out);
 
 /*
+ * The planner's time model, host only (the model SK_MODE_AUTO ranks its
+ * candidates by; Appendix A.1 extended by two terms), for recalibration.
+ * coef = {a, b, c, d, e, f} in microseconds: Appendix A.1's fixed cost a,
+ * split cost b, per-iteration cost c and per-peer fixup cost d, then e per
+ * tile segment and f, the shortest period of consecutive whole tiles.
+ *
+ * sk_model_coefficients: the built-in terms of one tile configuration
+ * (tile_n 64, 128 or 256; cluster_m 1 or 2, 64 with 1 only), else
+ * SK_ERR_UNSUPPORTED.
+ *
+ * sk_model_time: the modelled time of the schedule `s` (as sk_plan_describe
+ * returns it) under the terms `coef`: a + b*[split] + c * (iterations of the
+ * busiest unit's Stream-K share outside whole tiles) + max(c*ipt, f) * (its
+ * whole tiles, data-parallel ones included) + d * (peers - 1)*[split] +
+ * e * (its tile segments).  SK_ERR_INVALID for null pointers or a schedule
+ * with no units.
+ */
+int sk_model_coefficients(int tile_n, int cluster_m, double coef[6]);
+int sk_model_time(const sk_schedule_info* s, const double coef[6], double* us);
+
+/*
  * Allocation-free GEMM: C = alpha * A * B + beta * C like sk_gemm, for callers
  * that cannot allocate device memory -- for example plugins and custom
  * operators that only receive buffers from a host framework which owns the

@@ -306,6 +306,24 @@ extern "C" int sk_grid_model(int64_t m, int64_t n, int64_t k, int bm, int bn, in
   return SK_OK;
 }
 
+extern "C" int sk_model_coefficients(int tile_n, int cluster_m, double coef[6]) {
+  if (coef == nullptr) return SK_ERR_INVALID;
+  if ((tile_n != 64 && tile_n != 128 && tile_n != 256) || (cluster_m != 1 && cluster_m != 2) ||
+      (tile_n == 64 && cluster_m == 2))
+    return SK_ERR_UNSUPPORTED;
+  static_assert(sk::kModelTerms == 6, "sk_model_coefficients returns six terms");
+  sk::model_coefficients(tile_n, cluster_m, coef);
+  return SK_OK;
+}
+
+extern "C" int sk_model_time(const sk_schedule_info* s, const double coef[6], double* us) {
+  if (s == nullptr || coef == nullptr || us == nullptr || s->grid < 1 || s->iters_per_tile < 0 ||
+      s->tiles < 0 || s->sk_tiles < 0 || s->dp_tiles < 0)
+    return SK_ERR_INVALID;
+  *us = sk::predict_us(*s, coef);
+  return SK_OK;
+}
+
 // ------------------------------------------------------------------ grouped
 namespace sk {
 

@@ -83,6 +83,9 @@ def lib() -> ctypes.CDLL:
     L.sk_plan_attach_workspace.argtypes = [vp, vp, ctypes.c_size_t]
     L.sk_plan_describe.argtypes = [i64, i64, i64, i32, i32, i32, i32, i32, i32,
                                    ctypes.POINTER(sk_schedule_info)]
+    L.sk_model_coefficients.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
+    L.sk_model_time.argtypes = [ctypes.POINTER(sk_schedule_info), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double)]
     L.sk_grid_model.argtypes = [i64, i64, i64, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(i32)]
     L.sk_gemm_noalloc.argtypes = [i64, i64, i64, i32, i32, vp, i64, vp, i64, vp, i64, f32, f32,
@@ -119,7 +122,8 @@ def lib() -> ctypes.CDLL:
     L.sk_status_string.restype = ctypes.c_char_p
     for name in ("sk_plan", "sk_gemm", "sk_gemm_traced", "sk_last_error", "sk_plan_destroy",
                  "sk_plan_set", "sk_plan_get", "sk_plan_attach_workspace", "sk_plan_describe",
-                 "sk_grid_model", "sk_gemm_noalloc", "sk_grouped_plan", "sk_grouped_gemm",
+                 "sk_grid_model", "sk_model_coefficients", "sk_model_time", "sk_gemm_noalloc",
+                 "sk_grouped_plan", "sk_grouped_gemm",
                  "sk_grouped_gemm_traced", "sk_grouped_last_error", "sk_grouped_set",
                  "sk_grouped_get", "sk_grouped_schedule", "sk_grouped_destroy",
                  "sk_grouped_plan_describe", "sk_plan_autotune", "sk_grouped_autotune",
@@ -320,6 +324,28 @@ def sk_grid_model(m: int, n: int, k: int, bm: int, bn: int, bk: int, p: int, coe
     g = ctypes.c_int(0)
     _check(lib().sk_grid_model(m, n, k, bm, bn, bk, p, c, ctypes.byref(g)), "sk_grid_model")
     return g.value
+
+
+def sk_model_coefficients(tile_n: int, cluster_m: int):
+    """The planner's six model terms (us) of one tile configuration."""
+    c = (ctypes.c_double * 6)()
+    _check(lib().sk_model_coefficients(tile_n, cluster_m, c), "sk_model_coefficients")
+    return list(c)
+
+
+def sk_model_time(m: int, n: int, k: int, mode="auto", tile_n: int = 0, grid: int = 0,
+                  num_sms: int = 148, cluster_m: int = 0, coef=None):
+    """Modelled time (us) of the schedule sk_plan_describe gives for these
+    arguments, under `coef` (default: its configuration's built-in terms)."""
+    info = sk_schedule_info()
+    _check(lib().sk_plan_describe(m, n, k, _code(MODES, mode, "mode"), tile_n, grid, 0,
+                                  cluster_m, num_sms, ctypes.byref(info)), "sk_plan_describe")
+    if coef is None:
+        coef = sk_model_coefficients(info.tile_n, info.cluster_m)
+    c = (ctypes.c_double * 6)(*coef)
+    us = ctypes.c_double(0.0)
+    _check(lib().sk_model_time(ctypes.byref(info), c, ctypes.byref(us)), "sk_model_time")
+    return us.value
 
 
 def decode_trace(trace_host, grid: int, cap: int, with_times: bool = False):

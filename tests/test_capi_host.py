@@ -156,3 +156,60 @@ def test_plan_without_device_reports_cuda_error():
     with pytest.raises(sk.StreamKError) as e:
         sk.sk_plan(128, 128, 128)
     assert e.value.status in (sk.SK_ERR_CUDA, sk.SK_ERR_DEVICE)
+
+
+def test_model_coefficients_per_configuration():
+    for tn, cm in [(64, 1), (128, 1), (256, 1), (128, 2), (256, 2)]:
+        c = sk.sk_model_coefficients(tn, cm)
+        assert len(c) == 6 and all(v > 0 for v in c), (tn, cm, c)
+    with pytest.raises(sk.StreamKError) as e:
+        sk.sk_model_coefficients(64, 2)
+    assert e.value.status == sk.SK_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("coef", [(1.0, 2.0, 3.0, 4.0, 5.0, 6.0), (4.0, 3.0, 0.25, 0.5, 0.1, 1.5)])
+def test_model_time_closed_forms(coef):
+    a, b, c, d, e, f = coef
+    # data-parallel, one full wave: a + max(c * ipt, f) + e
+    assert sk.sk_model_time(1024, 1024, 1024, "dp", tile_n=128, cluster_m=1, num_sms=152,
+                            coef=coef) == pytest.approx(a + max(c * 8, f) + e)
+    # two waves of 64 tiles on 32 units (ipt = 8): a + 2 * max(c * 8, f) + 2 e
+    assert sk.sk_model_time(1024, 1024, 1024, "dp", tile_n=128, cluster_m=1, num_sms=32,
+                            coef=coef) == pytest.approx(a + 2 * max(c * 8, f) + 2 * e)
+    # basic Stream-K of one 128 x 128 tile with ipt = 32 over g = 4: shares of 8
+    # iterations, 4 contributors, split: a + b + 8 c + 3 d + e * segs, where a
+    # share of q = 8 < ipt touches at most ceil((q + 1) / ipt) + 1 = 2 segments
+    assert sk.sk_model_time(128, 128, 4096, "sk", tile_n=128, cluster_m=1, grid=4, num_sms=152,
+                            coef=coef) == pytest.approx(a + b + 8 * c + 3 * d + 2 * e)
+    # k = 128 (ipt = 1): every iteration of a share is a whole tile and takes
+    # the tile period, so the hybrid over all 225 tiles on 152 units prices
+    # like two data-parallel waves
+    hyb = sk.sk_model_time(544, 5712, 128, "hybrid", tile_n=128, cluster_m=1, num_sms=152,
+                           coef=coef)
+    info = sk.sk_plan_describe(544, 5712, 128, "hybrid", tile_n=128, cluster_m=1, num_sms=152)
+    assert info["iters_per_tile"] == 1 and info["sk_tiles"] == info["tiles"] == 225
+    assert hyb == pytest.approx(a + 2 * max(c, f) + e * (-(-2 // 1) + 1))
+
+
+@pytest.mark.parametrize("m,n,k", [(384, 384, 4096), (544, 5712, 128), (1000, 776, 1104),
+                                   (592, 192, 7312), (4016, 304, 6736), (8192, 8192, 8192),
+                                   (256, 256, 65536), (3000, 200, 128)])
+def test_auto_is_the_argmin_of_the_exported_model(m, n, k):
+    """AUTO's pick has the smallest modelled time (splits raised by the 10%
+    margin) among the fixed candidates it ranks."""
+    p = 152
+    margin = lambda info, us: us * (1.1 if info["workspace_bytes"] > 0 else 1.0)  # noqa: E731
+    auto = sk.sk_plan_describe(m, n, k, "auto", num_sms=p)
+    best = margin(auto, sk.sk_model_time(m, n, k, "auto", num_sms=p))
+    for tn in (64, 128, 256):
+        for cm in (1, 2):
+            if tn == 64 and cm == 2:
+                continue
+            if cm == 2 and m <= 128:
+                continue
+            if tn == 256 and n <= 128:
+                continue
+            for mode in ("dp", "hybrid"):
+                info = sk.sk_plan_describe(m, n, k, mode, tile_n=tn, cluster_m=cm, num_sms=p)
+                us = sk.sk_model_time(m, n, k, mode, tile_n=tn, cluster_m=cm, num_sms=p)
+                assert best <= margin(info, us) + 1e-9, (mode, tn, cm)
