@@ -74,7 +74,7 @@ def measure(args):
             for p in plans:
                 sk.sk_plan_attach_workspace(p, ws, ws.numel())
             _, _, per, _ = run_variant(plans, sweep, args.steps, args.warmup, lambda: None)
-            med = np.median(per, axis=0)
+            med = np.median(per, axis=0) * 1e3  # per-GEMM ms -> us
             infos = [p.info() for p in plans]
             out["plans"][f"{mode}/{tn}x{cm}"] = {
                 "us": [float(v) for v in med],
