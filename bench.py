@@ -104,6 +104,30 @@ def profiled_bytes_per_flop():
     return PROFILED_TRAFFIC["dram_bytes_per_flop"]
 
 
+# Dense BF16 tcgen05 rate of one SM per clock: 8192 flops (the nominal 2.25
+# PFLOP/s of a 148-SM part at 1.86 GHz).
+FLOP_PER_CLK_PER_SM = 8192
+
+
+def theoretical_peak(clocks):
+    """Clock-derived dense BF16 tensor peak of this GPU: SMs x flops per SM
+    per clock x the median SM clock under load (the maximum clock when no
+    sample was taken)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    if clocks and clocks.get("sm_mhz"):
+        mhz, which = float(clocks["sm_mhz"]), "median SM clock under load"
+    else:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz = float(json.load(f)["sm_max_mhz"])
+        except Exception:
+            mhz = 2070.0
+        which = "maximum SM clock"
+    return {"tflops": sms * FLOP_PER_CLK_PER_SM * mhz * 1e6 / 1e12, "sms": sms,
+            "flop_per_clk_per_sm": FLOP_PER_CLK_PER_SM, "sm_mhz": mhz, "clock": which}
+
+
 def dump_dir():
     """Where per-shape detail and the clock log go: --dump-dir, else the
     SK_BENCH_DUMP_DIR environment variable, else a fresh temporary folder."""
@@ -497,6 +521,7 @@ def ours_arm(args):
                    "us": {v: (r["_med"] * 1e3).tolist() for v, r in results.items()}}, f)
     kernel_ms = float(np.sum(H["_med"]))
     bpf = profiled_bytes_per_flop()
+    theo = theoretical_peak(H["_clocks"])
     achieved = float(flops.sum() / (kernel_ms * 1e-3) / 1e12)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -516,6 +541,8 @@ def ours_arm(args):
             "event_node_us": ev_us,
         },
         "pct_of_peak": value / world / peak,
+        "theoretical_peak": theo,
+        "pct_of_theoretical_peak": value / world / theo["tflops"],
         "variants": {v: {kk: vv for kk, vv in r.items() if not kk.startswith("_")}
                      for v, r in results.items()},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
