@@ -48,13 +48,13 @@ int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]) {
 // measurement (python -m paper_2301_03598_gb300.calibrate) to the times of the
 // 2,000-shape log-uniform sweep planned with each configuration and each of
 // data-parallel, two-tile hybrid and basic Stream-K forced (15 plans per
-// shape), measured on a GB300 with this kernel.
+// shape), measured on a GB300.
 void model_coefficients(int tile_n, int cluster_m, double out[kModelTerms]) {
-  static const double k64x1[kModelTerms] = {3.408, 2.346, 0.4216, 0.410, 0.153, 0.943};
-  static const double k128x1[kModelTerms] = {3.650, 3.706, 0.5697, 0.561, 0.112, 1.307};
-  static const double k256x1[kModelTerms] = {4.297, 8.636, 0.3990, 0.683, 0.175, 0.880};
-  static const double k128x2[kModelTerms] = {4.323, 4.533, 0.4661, 0.506, 0.185, 1.599};
-  static const double k256x2[kModelTerms] = {5.103, 10.109, 0.3179, 0.520, 0.179, 2.075};
+  static const double k64x1[kModelTerms] = {3.452, 2.219, 0.4159, 0.419, 0.173, 0.996};
+  static const double k128x1[kModelTerms] = {3.742, 3.728, 0.5640, 0.569, 0.141, 1.370};
+  static const double k256x1[kModelTerms] = {4.398, 8.278, 0.3974, 0.711, 0.137, 1.120};
+  static const double k128x2[kModelTerms] = {4.271, 4.468, 0.4521, 0.494, 0.314, 1.681};
+  static const double k256x2[kModelTerms] = {4.756, 9.852, 0.3034, 0.461, 0.435, 2.363};
   const double* c = cluster_m == 2 ? (tile_n == 256 ? k256x2 : k128x2)
                                    : (tile_n == 256 ? k256x1 : tile_n == 64 ? k64x1 : k128x1);
   for (int i = 0; i < kModelTerms; ++i) out[i] = c[i];
