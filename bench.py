@@ -86,9 +86,9 @@ def load_peaks():
 # summed over the captured launches, divided by their 2mnk), and the sha256 of
 # csrc/sk_kernel.cuh followed by csrc/planner.cpp at that capture.  The
 # summary with its command is profiles/sk_gemm_sweep_launches.md.
-PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.175476e-03,
+PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.175066e-03,
                     "kernel_source_sha256":
-                        "cd8381875215d0d15677e8d992eea02a0fea12b03fba750b8ad5e4cf098df410"}
+                        "cdf696ecff49ebfd5c4ea62c6da00f6c9ac8282540344c3e9777a76245d1415d"}
 
 
 def profiled_bytes_per_flop():
