@@ -826,8 +826,9 @@ F8_SHAPES = [(8192, 8192, 8192), (4096, 4096, 4096), (2048, 2048, 8192), (384, 3
 
 def run_f8_shapes(peaks, reps=20):
     """Single E4M3 GEMMs (AUTO plans, BF16 out), each timed over `reps`
-    back-to-back launches after warm-up; TFLOP/s against the FP8 peak taken
-    as twice the measured BF16 burst peak (the nominal dense ratio)."""
+    back-to-back launches replayed from one CUDA graph after warm-up; TFLOP/s
+    against the FP8 peak taken as twice the measured BF16 burst peak (the
+    nominal dense ratio)."""
     import torch
     from paper_2301_03598_gb300 import inputs
     from paper_2301_03598_gb300 import streamk as sk
@@ -841,14 +842,19 @@ def run_f8_shapes(peaks, reps=20):
         C = torch.empty(m, n, dtype=torch.bfloat16, device=dev)
         plan = sk.sk_plan(m, n, k, "e4m3", "e4m3", "bf16")
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        graph = torch.cuda.CUDAGraph()
         with torch.cuda.stream(stream):
             for _ in range(3):
                 sk.sk_gemm_scaled(plan, qa, qb, sa, sb, C, stream=stream)
+            with torch.cuda.graph(graph, stream=stream):
+                for _ in range(reps):
+                    sk.sk_gemm_scaled(plan, qa, qb, sa, sb, C, stream=stream)
+            graph.replay()
             ev[0].record(stream)
-            for _ in range(reps):
-                sk.sk_gemm_scaled(plan, qa, qb, sa, sb, C, stream=stream)
+            graph.replay()
             ev[1].record(stream)
         torch.cuda.synchronize()
+        del graph
         st, dstat = sk.sk_last_error(plan)
         if st != sk.SK_OK:
             raise RuntimeError(f"e4m3 {m}x{n}x{k} status {st}/{dstat}")
@@ -873,7 +879,8 @@ CONFIG_SHAPES = [("single GEMM, FP16 in U[-1,1], FP32 out, beta = 0", "f16", "f3
 def run_config_shapes(peaks, reps=20):
     """The single-GEMM and extreme-shape workloads under each schedule (DP
     tiling, basic Stream-K at the modelled grid, the two-tile hybrid, AUTO),
-    each timed over `reps` back-to-back launches after warm-up on the same
+    each timed over `reps` back-to-back launches replayed from one CUDA graph
+    (so no host launch cost sits between them), after warm-up, on the same
     operands (only 8192^3's exceed the L2).  TFLOP/s against the measured BF16
     burst peak and against the shape's attainable roofline
     min(peak, AI x HBM bandwidth), AI = flops / (A + B read, C read if beta != 0,
@@ -904,18 +911,23 @@ def run_config_shapes(peaks, reps=20):
             for mode in ("dp", "sk", "hybrid", "auto"):
                 plan = sk.sk_plan(m, n, k, ab, ab, c_type, mode=mode)
                 ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                graph = torch.cuda.CUDAGraph()
                 with torch.cuda.stream(stream):
                     for _ in range(3):
                         sk.sk_gemm(plan, A, B, C, 1.0, beta, stream=stream)
+                    with torch.cuda.graph(graph, stream=stream):
+                        for _ in range(reps):
+                            sk.sk_gemm(plan, A, B, C, 1.0, beta, stream=stream)
+                    graph.replay()
                     ev[0].record(stream)
-                    for _ in range(reps):
-                        sk.sk_gemm(plan, A, B, C, 1.0, beta, stream=stream)
+                    graph.replay()
                     ev[1].record(stream)
                 torch.cuda.synchronize()
                 st, dstat = sk.sk_last_error(plan)
                 if st != sk.SK_OK:
                     raise RuntimeError(f"{m}x{n}x{k} {mode} status {st}/{dstat}")
                 us = ev[0].elapsed_time(ev[1]) * 1e3 / reps
+                del graph
                 tf = flops / (us * 1e-6) / 1e12
                 info = plan.info()
                 row["modes"][mode] = {"us": us, "tflops": tf, "frac_of_peak": tf / peak,
