@@ -824,44 +824,81 @@ F8_SHAPES = [(8192, 8192, 8192), (4096, 4096, 4096), (2048, 2048, 8192), (384, 3
              (256, 256, 65536)]
 
 
-def run_f8_shapes(peaks, reps=20):
-    """Single E4M3 GEMMs (AUTO plans, BF16 out), each timed over `reps`
-    back-to-back launches replayed from one CUDA graph after warm-up; TFLOP/s
-    against the FP8 peak taken as twice the measured BF16 burst peak (the
-    nominal dense ratio)."""
+SHAPE_ROUNDS = 7
+
+
+def _shape_reps(m, n, k):
+    """Back-to-back launches in one timed replay of a single shape: about a
+    millisecond of work for the largest shapes, at least ~150 us for the
+    smallest, so the timing events' own cost stays near 1%."""
+    fl = 2.0 * m * n * k
+    return 32 if fl < 1e10 else 8 if fl < 1e11 else 2
+
+
+def _graph_times_us(launches, reps, stream, rounds=SHAPE_ROUNDS):
+    """Per-launch device time (us) of each callable in `launches`: each is
+    captured `reps` times back to back into its own CUDA graph, all graphs are
+    replayed once to warm up, then `rounds` times in turn (one replay of each
+    per round, between two events on the launching stream), so a drift of the
+    clock or power state over the measurement reaches every arm alike.
+    Returns the median over rounds per callable."""
+    import torch
+    graphs = []
+    with torch.cuda.stream(stream):
+        for fn in launches:
+            for _ in range(3):
+                fn()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for _ in range(reps):
+                    fn()
+            graphs.append(g)
+        for g in graphs:
+            g.replay()
+        evs = []
+        for _ in range(rounds):
+            row = []
+            for g in graphs:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.replay()
+                e1.record(stream)
+                row.append((e0, e1))
+            evs.append(row)
+    torch.cuda.synchronize()
+    out = [float(np.median([evs[r][i][0].elapsed_time(evs[r][i][1]) for r in range(rounds)]))
+           * 1e3 / reps for i in range(len(graphs))]
+    del graphs
+    return out
+
+
+def run_f8_shapes(peaks):
+    """Single E4M3 GEMMs (AUTO plans, BF16 out), each timed as the median over
+    rounds of one CUDA-graph replay of back-to-back launches after warm-up
+    (_graph_times_us); TFLOP/s against the FP8 peak taken as twice the measured
+    BF16 burst peak (the nominal dense ratio)."""
     import torch
     from paper_2301_03598_gb300 import inputs
     from paper_2301_03598_gb300 import streamk as sk
     dev = torch.device("cuda", torch.cuda.current_device())
     out = {"peak_tflops": 2.0 * peaks["bf16_tflops"],
-           "peak_kind": "2 x bf16 burst (" + peaks["source"] + ")", "shapes": []}
+           "peak_kind": "2 x bf16 burst (" + peaks["source"] + ")",
+           "timing": f"median of {SHAPE_ROUNDS} graph replays of back-to-back launches", "shapes": []}
     stream = torch.cuda.Stream()
     for (m, n, k) in F8_SHAPES:
         qa, sa = inputs.device_e4m3_matrix(m, k, 77, dev)
         qb, sb = inputs.device_e4m3_matrix(n, k, 78, dev)
         C = torch.empty(m, n, dtype=torch.bfloat16, device=dev)
         plan = sk.sk_plan(m, n, k, "e4m3", "e4m3", "bf16")
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                sk.sk_gemm_scaled(plan, qa, qb, sa, sb, C, stream=stream)
-            with torch.cuda.graph(graph, stream=stream):
-                for _ in range(reps):
-                    sk.sk_gemm_scaled(plan, qa, qb, sa, sb, C, stream=stream)
-            graph.replay()
-            ev[0].record(stream)
-            graph.replay()
-            ev[1].record(stream)
-        torch.cuda.synchronize()
-        del graph
+        reps = _shape_reps(m, n, k)
+        (us,) = _graph_times_us(
+            [lambda: sk.sk_gemm_scaled(plan, qa, qb, sa, sb, C, stream=stream)], reps, stream)
         st, dstat = sk.sk_last_error(plan)
         if st != sk.SK_OK:
             raise RuntimeError(f"e4m3 {m}x{n}x{k} status {st}/{dstat}")
-        us = ev[0].elapsed_time(ev[1]) * 1e3 / reps
         tf = 2.0 * m * n * k / (us * 1e-6) / 1e12
         info = plan.info()
-        out["shapes"].append({"m": m, "n": n, "k": k, "us": us, "tflops": tf,
+        out["shapes"].append({"m": m, "n": n, "k": k, "us": us, "tflops": tf, "reps": reps,
                               "frac_of_peak": tf / out["peak_tflops"],
                               "plan": {x: info[x] for x in ("mode", "grid", "tiles", "sk_tiles")}})
         plan.destroy()
@@ -876,13 +913,14 @@ CONFIG_SHAPES = [("single GEMM, FP16 in U[-1,1], FP32 out, beta = 0", "f16", "f3
                                 (1536, 1536, 1536)])]
 
 
-def run_config_shapes(peaks, reps=20):
+def run_config_shapes(peaks):
     """The single-GEMM and extreme-shape workloads under each schedule (DP
-    tiling, basic Stream-K at the modelled grid, the two-tile hybrid, AUTO),
-    each timed over `reps` back-to-back launches replayed from one CUDA graph
-    (so no host launch cost sits between them), after warm-up, on the same
-    operands (only 8192^3's exceed the L2).  TFLOP/s against the measured BF16
-    burst peak and against the shape's attainable roofline
+    tiling, basic Stream-K at the modelled grid, the two-tile hybrid, AUTO).
+    The four plans of a shape are timed together by _graph_times_us: one CUDA
+    graph of back-to-back launches each (no host launch cost between them),
+    replayed in turn over several rounds after warm-up, median per plan, on the
+    same operands (only 8192^3's exceed the L2).  TFLOP/s against the measured
+    BF16 burst peak and against the shape's attainable roofline
     min(peak, AI x HBM bandwidth), AI = flops / (A + B read, C read if beta != 0,
     C written)."""
     import torch
@@ -892,8 +930,11 @@ def run_config_shapes(peaks, reps=20):
     peak, bw = peaks["bf16_tflops"], peaks["hbm_gbs"]
     out = {"peak_tflops": peak, "peak_kind": "bf16 burst (" + peaks["source"] + ")",
            "hbm_gbs": bw, "l2": "operands reused across the timed launches; only 8192^3 "
-                               "exceeds the L2", "configs": []}
+                               "exceeds the L2",
+           "timing": f"median of {SHAPE_ROUNDS} rounds, each one graph replay of back-to-back "
+                     "launches per schedule in turn", "configs": []}
     stream = torch.cuda.Stream()
+    modes = ("dp", "sk", "hybrid", "auto")
     for what, ab, c_type, beta, shapes in CONFIG_SHAPES:
         dist = "uniform" if ab == "f16" else "normal"
         rows = []
@@ -906,28 +947,17 @@ def run_config_shapes(peaks, reps=20):
             cb = C.element_size() * m * n
             nbytes = A.element_size() * (m * k + n * k) + cb * (2 if beta else 1)
             attainable = min(peak, flops / nbytes * bw / 1e3)
+            reps = _shape_reps(m, n, k)
             row = {"m": m, "n": n, "k": k, "gflop": flops / 1e9, "mbytes": nbytes / 1e6,
-                   "attainable_tflops": attainable, "modes": {}}
-            for mode in ("dp", "sk", "hybrid", "auto"):
-                plan = sk.sk_plan(m, n, k, ab, ab, c_type, mode=mode)
-                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-                graph = torch.cuda.CUDAGraph()
-                with torch.cuda.stream(stream):
-                    for _ in range(3):
-                        sk.sk_gemm(plan, A, B, C, 1.0, beta, stream=stream)
-                    with torch.cuda.graph(graph, stream=stream):
-                        for _ in range(reps):
-                            sk.sk_gemm(plan, A, B, C, 1.0, beta, stream=stream)
-                    graph.replay()
-                    ev[0].record(stream)
-                    graph.replay()
-                    ev[1].record(stream)
-                torch.cuda.synchronize()
+                   "attainable_tflops": attainable, "reps": reps, "modes": {}}
+            plans = [sk.sk_plan(m, n, k, ab, ab, c_type, mode=mode) for mode in modes]
+            times = _graph_times_us(
+                [lambda p=p: sk.sk_gemm(p, A, B, C, 1.0, beta, stream=stream) for p in plans],
+                reps, stream)
+            for mode, plan, us in zip(modes, plans, times):
                 st, dstat = sk.sk_last_error(plan)
                 if st != sk.SK_OK:
                     raise RuntimeError(f"{m}x{n}x{k} {mode} status {st}/{dstat}")
-                us = ev[0].elapsed_time(ev[1]) * 1e3 / reps
-                del graph
                 tf = flops / (us * 1e-6) / 1e12
                 info = plan.info()
                 row["modes"][mode] = {"us": us, "tflops": tf, "frac_of_peak": tf / peak,
