@@ -164,9 +164,10 @@ typedef struct {
  *   m, n, k   >= 0 (m*n == 0: sk_gemm is a no-op; k == 0: C = beta*C).
  *   a_type == b_type in {SK_F16, SK_BF16, SK_E4M3}; c_type in {SK_F32, SK_BF16,
  *   SK_F16}; compute_type must be SK_F32 (FP32 accumulation, Section 6).
- *   E4M3 plans run BLK_N = 128, BLK_K = 128 tiles (SK_ATTR_TILE_N 128 only) on
- *   single CTAs by default (SK_ATTR_CLUSTER_M 2 selects CTA pairs) and are
- *   launched with sk_gemm_scaled.
+ *   E4M3 plans run BLK_N = 128, BLK_K = 128 tiles on single CTAs by default
+ *   (SK_ATTR_CLUSTER_M 2 selects CTA pairs of 256 x 128 tiles; SK_ATTR_TILE_N
+ *   256 selects 128 x 256 tiles on single CTAs, SK_ERR_UNSUPPORTED with pairs)
+ *   and are launched with sk_gemm_scaled.
  *   a_layout SK_ROW_MAJOR, b_layout SK_COL_MAJOR, c_layout either.
  *   mode: an sk_mode.
  * Allocates the plan's device workspace (fixup partials and flags, Algorithm 5
@@ -445,8 +446,10 @@ int sk_plan_autotune(sk_plan_t plan, const void* A, const void* B, void* C, int 
                      double* best_us);
 int sk_grouped_autotune(sk_grouped_t plan, const void* const* A, const void* const* B,
                         void* const* C, int reps, void* stream, double* best_us);
-/* The same for E4M3 plans (one tile shape, so only the schedule is chosen),
- * with the block scales of sk_gemm_scaled / sk_grouped_gemm_scaled. */
+/* The same for E4M3 plans (tile widths 128, on single CTAs or pairs, and 256
+ * on single CTAs; E4M3 groups: 128 on single CTAs, so only the schedule and
+ * depth are chosen), with the block scales of sk_gemm_scaled /
+ * sk_grouped_gemm_scaled. */
 int sk_plan_autotune_scaled(sk_plan_t plan, const void* A, const void* B, const float* scale_a,
                             const float* scale_b, void* C, int reps, void* stream, double* best_us);
 int sk_grouped_autotune_scaled(sk_grouped_t plan, const void* const* A, const void* const* B,

@@ -34,7 +34,8 @@ def _nvcc() -> str:
 # Sources compiled more than once, each time with its own defines (the kernel
 # instantiations of one tile width per object).
 PER_VARIANT = {"kernels_bn.cu": [("bn64", ["-DSK_BN=64"]), ("bn128", ["-DSK_BN=128"]),
-                                 ("bn256", ["-DSK_BN=256"])]}
+                                 ("bn256", ["-DSK_BN=256"])],
+               "kernels_f8.cu": [("bn128", ["-DSK_F8_BN=128"]), ("bn256", ["-DSK_F8_BN=256"])]}
 
 
 def sources():

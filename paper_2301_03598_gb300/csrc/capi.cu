@@ -277,7 +277,7 @@ int gemm_impl(sk_plan_t p, const void* A, const void* B, const float* scale_a,
   const CUtensorMap& tb3 = use3d ? p->tm_b3 : p->tm_b;
   cudaError_t e;
   if (f8)
-    e = sk::launch_f8(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3, a, cooperative,
+    e = sk::launch_f8(p->c_type, s.tile_n, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3, a, cooperative,
                       stream);
   else if (s.tile_n == 64)
     e = sk::launch_bn64(p->c_type, s.cluster_m, p->tm_a, p->tm_b, p->tm_c, ta3, tb3, a, cooperative,
@@ -446,7 +446,11 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
   switch (attr) {
     case SK_ATTR_TILE_N: {
       if (v != 0 && v != 64 && v != 128 && v != 256) return SK_ERR_UNSUPPORTED;
-      if (p->a_type == SK_E4M3) return v == 0 || v == 128 ? SK_OK : SK_ERR_UNSUPPORTED;
+      if (p->a_type == SK_E4M3) {
+        // E4M3: 128 (the default; single CTAs or pairs) or 256 (single CTAs)
+        if (v == 0) v = 128;
+        if (v != 128 && !(v == 256 && p->cluster_req != 2)) return SK_ERR_UNSUPPORTED;
+      }
       const int old = p->tile_n_req;
       p->tile_n_req = static_cast<int>(v);
       int st = replan(p);
@@ -514,6 +518,7 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
       return SK_OK;
     case SK_ATTR_CLUSTER_M: {
       if (v != 0 && v != 1 && v != 2) return SK_ERR_UNSUPPORTED;
+      if (p->a_type == SK_E4M3 && v == 2 && p->tile_n_req == 256) return SK_ERR_UNSUPPORTED;
       const int old = p->cluster_req;
       p->cluster_req = static_cast<int>(v);
       int st = replan(p);
@@ -982,7 +987,7 @@ int grouped_impl(sk_grouped_s* g, const void* const* A, const void* const* B,
   const CUtensorMap& any = g->h_probs[0].tmA;
   const int cm = gp.cluster_m;
   cudaError_t e =
-      f8                 ? sk::launch_grouped_f8(g->c_type, any, a, cooperative, stream)
+      f8                 ? sk::launch_grouped_f8(g->c_type, gp.tile_n, any, a, cooperative, stream)
       : gp.tile_n == 256 ? sk::launch_grouped_bn256(g->c_type, cm, any, a, cooperative, stream)
       : gp.tile_n == 64  ? sk::launch_grouped_bn64(g->c_type, cm, any, a, cooperative, stream)
                          : sk::launch_grouped_bn128(g->c_type, cm, any, a, cooperative, stream);
@@ -1256,16 +1261,16 @@ int plan_autotune(sk_plan_t p, const void* A, const void* B, const float* scale_
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
   const int saved[5] = {p->tile_n_req, p->cluster_req, p->mode_req, p->grid_req, p->stages_req};
   const int64_t km = p->swap ? p->n : p->m, kn = p->swap ? p->m : p->n;
-  const bool f8 = p->a_type == SK_E4M3;  // BLK_N = 128 only
+  const bool f8 = p->a_type == SK_E4M3;  // BLK_N = 128 (single CTAs or pairs) or 256 (single)
   const int tns[3] = {64, 128, 256}, cms[2] = {1, 2};
   const int modes[3] = {SK_MODE_DP, SK_MODE_HYBRID, SK_MODE_SK};
   double best = -1.0;
   int bt = saved[0], bc = saved[1], bm = saved[2], bs = saved[4];
   for (int tn : tns) {
-    if (tn == 256 && (kn <= 128 || f8)) continue;
+    if (tn == 256 && kn <= 128) continue;
     if (tn == 64 && f8) continue;
     for (int cm : cms) {
-      if (cm == 2 && (km <= sk::kTileM || tn == 64)) continue;
+      if (cm == 2 && (km <= sk::kTileM || tn == 64 || (f8 && tn == 256))) continue;
       // pipeline depth: the full ring, and two or three stages
       const int mx = sk::max_stages(tn, cm);
       const int stage_opts[3] = {0, 3, 2};

@@ -23,7 +23,7 @@ static cudaError_t launch_one(const CUtensorMap& ta, const CUtensorMap& tb,
                               const SkArgs& args, bool cooperative, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(args.grid * CM));
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(Cfg<SK_BN, CM>::kThreads);
   cfg.dynamicSmemBytes = Cfg<SK_BN, CM>::kSmemBytes;
   cfg.stream = stream;
   cudaLaunchAttribute attr[3];
@@ -99,7 +99,7 @@ static cudaError_t launch_grouped_one(const CUtensorMap& tm, const SkArgs& args,
                                       cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(args.grid * CM));
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(Cfg<SK_BN, CM>::kThreads);
   cfg.dynamicSmemBytes = Cfg<SK_BN, CM>::kSmemBytes;
   cfg.stream = stream;
   cudaLaunchAttribute attr[3];

@@ -371,7 +371,7 @@ int launch_slot(sk_server_s* sv, Slot& s) {
   e = order_launch(sv, s, s.stream, split);
   if (e != cudaSuccess) return cuda_status(e);
   s.h_status[0] = 0;
-  e = f8                ? sk::launch_grouped_f8(sv->c_type, any, a, split, s.stream)
+  e = f8                ? sk::launch_grouped_f8(sv->c_type, gp.tile_n, any, a, split, s.stream)
       : gp.tile_n == 256 ? sk::launch_grouped_bn256(sv->c_type, 1, any, a, split, s.stream)
       : gp.tile_n == 64  ? sk::launch_grouped_bn64(sv->c_type, 1, any, a, split, s.stream)
                          : sk::launch_grouped_bn128(sv->c_type, 1, any, a, split, s.stream);

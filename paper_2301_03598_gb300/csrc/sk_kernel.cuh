@@ -40,8 +40,6 @@
 namespace sk {
 
 constexpr int kEpiWarps = 8;  // two warps per TMEM lane quarter, splitting the columns
-constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kEpiWarp0 = 2;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 
@@ -54,14 +52,15 @@ constexpr uint32_t kEpiBarrier = 1;  // named barrier id of the epilogue warps
 // F8 (E4M3 operands with one FP32 scale per 128 x 128 block of A and of B):
 // the host describes the operands to TMA as 16-bit rows of k/2 elements (the
 // same bytes), so loads and stages are the 16-bit path's.  Every k-block is
-// one scale block: the MMA warp writes the products of a stage's KD = 2
-// k-blocks into the two TMEM buffers of one of kAccBufs = 2 buffer pairs and
-// publishes them with one commit; the epilogue warps add each product, times
-// its block's two scales, into a running FP32 sum held in registers, and
-// release the pair.  The tile segment's sum goes to the first buffer of the
-// segment's last pair, which is released only after the common epilogue has
-// read it.  A stage's second k-block beyond k (an odd count of k-blocks) is
-// zero-filled by TMA and carries scale 0.
+// one scale block: the MMA warp writes the products of a stage's KD k-blocks
+// into the KD TMEM buffers of one of kAccBufs = 2 buffer groups (pairs for
+// BLK_N = 128, single 256-column buffers for BLK_N = 256) and publishes them
+// with one commit; the epilogue warps add each product, times its block's two
+// scales, into a running FP32 sum held in registers (BLK_N / 2 per thread),
+// and release the group.  The tile segment's sum goes to the first buffer of
+// the segment's last group, which is released only after the common epilogue
+// has read it.  A stage's second k-block beyond k (an odd count of k-blocks
+// with KD = 2) is zero-filled by TMA and carries scale 0.
 template <int BN, int CM, bool F8 = false>
 struct Cfg {
   static constexpr int KD = BN <= 128 ? 2 : 1;
@@ -86,8 +85,24 @@ struct Cfg {
   static constexpr int kSmemBytes = kBarOffset + 256 + 1024;  // + barriers, + 1 KiB alignment
   static_assert(kNumBars * 8 + 8 <= 256, "barrier area");
   static_assert(kSmemBytes <= 232448, "shared memory per CTA");
-  static_assert(!F8 || BN == 128, "F8 tiles are 128 (or 256 for a pair) x 128");
+  static_assert(!F8 || BN == 128 || (BN == 256 && CM == 1),
+                "F8 tiles are 128 x 128 (256 x 128 on a pair) or 128 x 256");
   static_assert(kTmemCols <= 512, "TMEM columns");
+  // Warps: 0 producer, 1 MMA issuer, then the epilogue warps from kEpiWarp0.
+  // 10 warps put three on two of the SM's four sub-partitions, which caps a
+  // thread at 168 registers (a sub-partition's file holds 512 per lane).  The
+  // E4M3 128 x 256 tile's running sum alone is 128 registers per epilogue
+  // thread, so that kernel runs 12 warps -- warpgroup 0 (producer, MMA issuer
+  // and two idle warps) and two epilogue warpgroups -- launched at 168 and
+  // rebalanced with setmaxnreg: warpgroup 0 gives up registers down to
+  // kRegsLow, the epilogue raises to kRegsHigh, kRegsLow + 2 kRegsHigh = 3 x 168.
+  static constexpr bool kRebalance = F8 && BN == 256;
+  static constexpr int kEpiWarp0 = kRebalance ? 4 : 2;
+  static constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
+  static constexpr int kRegsLaunch = 168;
+  static constexpr int kRegsLow = 56;
+  static constexpr int kRegsHigh = 224;
+  static_assert(kRegsLow + 2 * kRegsHigh <= 3 * kRegsLaunch, "register rebalance exceeds the launch");
 };
 
 // Where a bounded wait gave up (err[2]).
@@ -534,7 +549,7 @@ __device__ __forceinline__ void add_peers(const float* partials, int first, int 
 // TMEM receives its own 128 rows of the accumulator, which its epilogue
 // spills, fixes up and stores exactly as a single CTA does.
 template <int BN, int CM, typename TC, bool GROUPED, bool F8>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(Cfg<BN, CM, F8>::kThreads, 1)
     sk_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmA3,
                    const __grid_constant__ CUtensorMap tmB3, const __grid_constant__ SkArgs a) {
@@ -620,6 +635,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if constexpr (kPair) cluster_sync();  // both CTAs' barriers exist before either signals them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+
   // Everything above overlaps the previous kernel in the stream under
   // programmatic dependent launch; nothing is loaded into shared memory or
   // written to global memory before this point.  By default every thread
@@ -631,6 +647,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   // workspace, wait.  (The wait sits inside each role's branch: one shared
   // conditional wait here made the grouped E4M3 kernel 11% slower.)
 
+  if (warp < C_::kEpiWarp0) {
+  // Register rebalance (warpgroup-uniform; the host checked that the launch's
+  // registers cover it): warpgroup 0 releases, the epilogue warpgroups take.
+  if constexpr (C_::kRebalance) setmaxnreg_dec<C_::kRegsLow>();
   if (warp == 0) {
     if (!a.early) grid_dependency_wait();
     if (lane == 0) {
@@ -914,11 +934,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < a.timeout_ns) {
       }
     }
+  }
   } else {
+    if constexpr (C_::kRebalance) setmaxnreg_inc<C_::kRegsHigh>();
     grid_dependency_wait();
     // -------------------------------------------------------------- epilogue
     const int quarter = warp & 3;                     // TMEM lanes this warp may access
-    const int col_half = (warp - kEpiWarp0) >> 2;     // which interleaved column units
+    const int col_half = (warp - C_::kEpiWarp0) >> 2;     // which interleaved column units
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
     SegCursor<GROUPED> cur;
@@ -940,8 +962,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr bool kSplit = !F8 && BN == 64 && kCpu == 2;
     float* const my_slot = a.partials + static_cast<size_t>(cta) * (kBlkM * BN);
     const uint32_t staging = base + static_cast<uint32_t>(C_::kStagingOffset +
-                                                         (warp - kEpiWarp0) * C_::kStagingBytesPerWarp);
-    const bool tracer = a.trace != nullptr && warp == kEpiWarp0 && lane == 0;
+                                                         (warp - C_::kEpiWarp0) * C_::kStagingBytesPerWarp);
+    const bool tracer = a.trace != nullptr && warp == C_::kEpiWarp0 && lane == 0;
     int32_t* const tb =
         a.trace + static_cast<size_t>(cta) * (kTraceHeaderInts + a.trace_cap * kTraceRecordInts);
     if (tracer) {
@@ -982,21 +1004,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < kMine; ++i)
 #pragma unroll
           for (int j = 0; j < 32 * kCpu; ++j) sum[i][j] = 0u;
+        // A tile is kHalves blocks of 128 B rows wide, each with its own row
+        // of B scales (BLK_N = 256: two; the second exists only inside n).
+        constexpr int kHalves = BN / 128;
         const float* sa = scale_a + static_cast<size_t>(tm) * ld_scale;
-        const float* sb = scale_b + static_cast<size_t>(tn) * ld_scale;
+        const float* sb = scale_b + static_cast<size_t>(tn * kHalves) * ld_scale;
+        const int nblk_b = (out.n + 127) / 128;
         // The segment's k-blocks: KD per MAC-loop iteration.  Those inside k
         // (ld_scale of them per row of scales) carry scales; a stage's second
         // k-block beyond k is all zeros and gets scale 0.
         const int kq0 = kb0 * KD, kq1 = kb1 * KD;
         const int kreal = min(kq1, ld_scale);
-        // lane l holds the scale product of k-block first + l; the next 32
-        // are loaded one window ahead
-        auto window = [&](int first) {
+        // lane l holds the scale product of k-block first + l (per half);
+        // the next 32 are loaded one window ahead
+        auto window = [&](int first, int h) {
           const int kq = first + lane;
-          return kq < kreal ? __ldg(sa + kq) * __ldg(sb + kq) : 0.0f;
+          return kq < kreal && (kHalves == 1 || tn * kHalves + h < nblk_b)
+                     ? __ldg(sa + kq) * __ldg(sb + static_cast<size_t>(h) * ld_scale + kq)
+                     : 0.0f;
         };
-        float s_cur = window(kq0);
-        float s_nxt = kq0 + 32 < kq1 ? window(kq0 + 32) : 0.0f;
+        float s_cur[kHalves], s_nxt[kHalves];
+#pragma unroll
+        for (int h = 0; h < kHalves; ++h) {
+          s_cur[h] = window(kq0, h);
+          s_nxt[h] = kq0 + 32 < kq1 ? window(kq0 + 32, h) : 0.0f;
+        }
         for (int it = kb0; it < kb1; ++it) {
           if (!wait_bar(accf_bar(acc), acc_phase, abort_flag, a, kAtEpiAccFull)) {
             fail = true;
@@ -1008,33 +1040,47 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int kq = it * KD + j;
             const int i = kq - kq0;
             if (i > 0 && (i & 31) == 0) {
-              s_cur = s_nxt;
-              if (kq + 32 < kq1) s_nxt = window(kq + 32);
+#pragma unroll
+              for (int h = 0; h < kHalves; ++h) {
+                s_cur[h] = s_nxt[h];
+                if (kq + 32 < kq1) s_nxt[h] = window(kq + 32, h);
+              }
             }
-            const float sc = __shfl_sync(0xffffffffu, s_cur, i & 31);
+            float sc[kHalves];
+#pragma unroll
+            for (int h = 0; h < kHalves; ++h) sc[h] = __shfl_sync(0xffffffffu, s_cur[h], i & 31);
             const uint32_t pbase =
                 tmem_base + lane_base + static_cast<uint32_t>(acc * C_::kAccCols + j * BN);
-            // 32 columns at a time, so that the product needs 32 registers
-            // next to the sum's 64
+            // kW columns at a time, so that the product needs kW registers
+            // next to the sum's BN / 2 (16 for BLK_N = 256, whose sum fills
+            // most of a thread's registers)
+            constexpr int kW = BN == 256 ? 16 : 32;
+            constexpr int kSub = 32 / kW;
+            constexpr int kChunks = kMine * kCpu * kSub;
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              const int mi = kCpu == 2 ? 0 : c;
-              const int j0 = kCpu == 2 ? 32 * c : 0;
+            for (int c = 0; c < kChunks; ++c) {
+              const int mi = c / (kCpu * kSub);
+              const int j0 = kW * (c % (kCpu * kSub));
               const uint32_t col = static_cast<uint32_t>((col_half + 2 * mi) * 32 * kCpu + j0);
-              uint32_t r[32];
-              tmem_ld_x32(pbase + col, r);
+              uint32_t r[kW];
+              if constexpr (kW == 16)
+                tmem_ld_x16(pbase + col, r);
+              else
+                tmem_ld_x32(pbase + col, r);
               tmem_wait_ld();
-              if (j == KD - 1 && c == 1 && it + 1 < kb1) {
+              if (j == KD - 1 && c == kChunks - 1 && it + 1 < kb1) {
                 // the pair is read: the MMA warp may overwrite it (the
                 // segment's last pair is kept for its sum, below)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) release_acc(acc);
               }
-              // sum += sc * product, two columns per packed FMA
-              const uint32_t scb = __float_as_uint(sc);
+              // sum += sc * product, two columns per packed FMA; the unit's
+              // columns (col_half + 2 mi) * 32 * kCpu onward lie in half
+              // mi * kCpu / 2 of the tile for either col_half
+              const uint32_t scb = __float_as_uint(sc[kHalves == 1 ? 0 : (mi * kCpu) / 2]);
 #pragma unroll
-              for (int jj = 0; jj < 32; jj += 2)
+              for (int jj = 0; jj < kW; jj += 2)
                 fma2(scb, r[jj], r[jj + 1], sum[mi][j0 + jj], sum[mi][j0 + jj + 1]);
             }
           }
@@ -1126,7 +1172,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // the quarter's staging buffer: that of its first warp
             const uint32_t stage0 =
                 base + static_cast<uint32_t>(C_::kStagingOffset +
-                                             (warp - kEpiWarp0 - 4 * col_half) * C_::kStagingBytesPerWarp);
+                                             (warp - C_::kEpiWarp0 - 4 * col_half) * C_::kStagingBytesPerWarp);
             const uint32_t srow = stage0 + static_cast<uint32_t>(lane * 128);
             const uint32_t bar_id = 2u + static_cast<uint32_t>(quarter);
             // the previous store from the buffer has finished reading it

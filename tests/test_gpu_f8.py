@@ -93,6 +93,59 @@ def test_f8_cta_pairs(shape, mode, grid):
     p.check(outs[0], 1.0, 0.0, f"e4m3 pair {shape} {mode} g={grid}")
 
 
+@pytest.mark.parametrize("mode,grid", [("dp", 0), ("sk", 0), ("sk", 37), ("hybrid", 0)])
+@pytest.mark.parametrize("shape", [(1000, 520, 2048), (384, 384, 4096), (129, 1000, 144),
+                                   (300, 260, 1008), (16, 128, 16), (1, 1, 16)])
+def test_f8_wide_tiles(shape, mode, grid):
+    # 128 x 256 tiles on single CTAs (one k-block of 128 per MAC-loop
+    # iteration, two 256-column product buffers): ragged rows, columns and k
+    p = F8Problem(*shape, seed=14, scale_spread=True)
+    attrs = {"tile_n": 256}
+    if grid:
+        attrs["grid"] = grid
+    outs, info = p.run(1.0, 0.0, mode, attrs)
+    assert info["tile_n"] == 256 and info["tile_k"] == 128 and info["cluster_m"] == 1
+    p.check(outs[0], 1.0, 0.0, f"e4m3 wide {shape} {mode} g={grid}")
+
+
+@pytest.mark.parametrize("c_type,layout", [("f32", "row"), ("f16", "row"), ("bf16", "col"),
+                                           ("f32", "col")])
+def test_f8_wide_tiles_output_types_and_beta(c_type, layout):
+    p = F8Problem(520, 600, 1024, c_type=c_type, seed=15, beta=0.5)
+    outs, info = p.run(1.5, 0.5, "sk", {"tile_n": 256, "grid": 41}, c_layout=layout)
+    assert info["tile_n"] == 256
+    p.check(outs[0], 1.5, 0.5, f"e4m3 wide beta {c_type} {layout}")
+
+
+def test_f8_wide_tiles_bitwise_reproducible():
+    p = F8Problem(640, 768, 8192, seed=16)
+    outs, _ = p.run(1.0, 0.0, "sk", {"tile_n": 256, "grid": 100}, reps=3)
+    assert all(torch.equal(outs[0], o) for o in outs[1:])
+    p.check(outs[0], 1.0, 0.0, "e4m3 wide reproducible")
+
+
+def test_f8_autotune_single_plan():
+    # the autotuner ranks 128-wide tiles (single CTAs and pairs) and 256-wide
+    # tiles (single CTAs); whatever it keeps must still match the oracle
+    p = F8Problem(1000, 1100, 2048, seed=17, scale_spread=True)
+    plan = sk.sk_plan(p.m, p.n, p.k, "e4m3", "e4m3", "bf16")
+    try:
+        A, B, sA, sB = p.qA.cuda(), p.qB.cuda(), p.sA.cuda(), p.sB.cuda()
+        C = torch.empty(p.m, p.n, dtype=torch.bfloat16, device="cuda")
+        us = sk.sk_plan_autotune_scaled(plan, A, B, sA, sB, C, reps=2)
+        assert us > 0.0
+        info = plan.info()
+        assert info["tile_n"] in (128, 256)
+        assert info["tile_n"] == 128 or info["cluster_m"] == 1
+        C.fill_(float("nan"))
+        sk.sk_gemm_scaled(plan, A, B, sA, sB, C)
+        assert sk.sk_last_error(plan)[0] == sk.SK_OK
+        out = C.cpu()
+    finally:
+        plan.destroy()
+    p.check(out, 1.0, 0.0, f"e4m3 autotuned ({info['tile_n']}, {info['cluster_m']})")
+
+
 @pytest.mark.parametrize("grid", [7, 40, 143])
 def test_f8_split_tiles_with_spread_scales(grid):
     # 9 tiles of 16 iterations (two k-blocks of 128 each) over g CTAs: every
@@ -133,8 +186,20 @@ def test_f8_entry_point_contract():
             sk.sk_gemm(plan, A, A, C)                    # scales are required
         assert e.value.status == sk.SK_ERR_INVALID
         with pytest.raises(sk.StreamKError) as e:
+            plan.set("tile_n", 64)
+        assert e.value.status == sk.SK_ERR_UNSUPPORTED
+        # 256-wide E4M3 tiles run on single CTAs only
+        plan.set("tile_n", 256)
+        with pytest.raises(sk.StreamKError) as e:
+            plan.set("cluster_m", 2)
+        assert e.value.status == sk.SK_ERR_UNSUPPORTED
+        plan.set("tile_n", 128)
+        plan.set("cluster_m", 2)
+        with pytest.raises(sk.StreamKError) as e:
             plan.set("tile_n", 256)
         assert e.value.status == sk.SK_ERR_UNSUPPORTED
+        plan.set("cluster_m", 1)
+        assert plan.info()["tile_n"] == 128 and plan.info()["cluster_m"] == 1
         sk.sk_gemm_scaled(plan, A, A, s, s, C)
         assert sk.sk_last_error(plan)[0] == sk.SK_OK
         assert float(C.float().abs().max()) == 0.0
@@ -151,7 +216,8 @@ def test_f8_entry_point_contract():
         plan16.destroy()
 
 
-@pytest.mark.parametrize("mode,attrs", [("auto", {}), ("sk", {"grid": 151})])
+@pytest.mark.parametrize("mode,attrs", [("auto", {}), ("sk", {"grid": 151}),
+                                        ("dp", {"tile_n": 256}), ("sk", {"tile_n": 256})])
 def test_f8_large_sampled_entries(mode, attrs):
     # 4096 x 4096 x 8192 on device-drawn operands: 4,096 sampled outputs plus
     # entries along tile edges (Stream-K seams, ragged-free but split tiles)
