@@ -104,9 +104,13 @@ int replan(sk_plan_s* p) {
   sk_schedule_info s;
   // An E4M3 row of k elements is, byte for byte, a 16-bit row of k/2: the
   // schedule and the TMA boxes are the 16-bit path's for k/2.
+  // E4M3's automatic width ranks 128 and 256 on single CTAs (256-wide E4M3
+  // tiles have no CTA-pair kernel, so pairs take 128).
   const bool f8 = p->a_type == SK_E4M3;
-  int st = sk::describe(m, n, f8 ? p->k / 2 : p->k, p->mode_req, p->tile_n_req, p->grid_req, p->group_req,
-                        p->cluster_req, p->num_sms, &s);
+  const int tile_n = f8 && p->tile_n_req == 0 && p->cluster_req == 2 ? 128 : p->tile_n_req;
+  int st = sk::describe(m, n, f8 ? p->k / 2 : p->k, p->mode_req, tile_n, p->grid_req, p->group_req,
+                        f8 && p->cluster_req == 0 ? 1 : p->cluster_req, p->num_sms, &s,
+                        f8 ? 128 : 64);
   if (st != SK_OK) return st;
   if (s.workspace_bytes > 0 && static_cast<size_t>(s.workspace_bytes) > p->ws_bytes) {
     if (!p->ws_owned) return SK_ERR_INVALID;  // attached buffer too small for the new schedule
@@ -360,10 +364,10 @@ int sk_plan(sk_plan_t* out, int64_t m, int64_t n, int64_t k, sk_dtype a_type, sk
   p->device = dev;
   p->num_sms = sms;
   if (a_type == SK_E4M3) {
-    // 128 x 128 x 128 tiles on single CTAs: a pair's per-k-block buffer
-    // hand-off crosses SMs and was measured 2.4x slower (SK_ATTR_CLUSTER_M 2
-    // still selects it)
-    p->tile_n_req = 128;
+    // Single CTAs: a pair's per-k-block buffer hand-off crosses SMs and was
+    // measured 2.4x slower (SK_ATTR_CLUSTER_M 2 still selects it); the model
+    // picks 128- or 256-wide tiles (tile_n_req 0).
+    p->tile_n_req = 0;
     p->cluster_req = 1;
   }
   size_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
@@ -446,11 +450,10 @@ int sk_plan_set(sk_plan_t p, int attr, int64_t v) {
   switch (attr) {
     case SK_ATTR_TILE_N: {
       if (v != 0 && v != 64 && v != 128 && v != 256) return SK_ERR_UNSUPPORTED;
-      if (p->a_type == SK_E4M3) {
-        // E4M3: 128 (the default; single CTAs or pairs) or 256 (single CTAs)
-        if (v == 0) v = 128;
-        if (v != 128 && !(v == 256 && p->cluster_req != 2)) return SK_ERR_UNSUPPORTED;
-      }
+      // E4M3: 0 (the model's choice of 128 and 256), 128 (single CTAs or
+      // pairs) or 256 (single CTAs)
+      if (p->a_type == SK_E4M3 && v != 0 && v != 128 && !(v == 256 && p->cluster_req != 2))
+        return SK_ERR_UNSUPPORTED;
       const int old = p->tile_n_req;
       p->tile_n_req = static_cast<int>(v);
       int st = replan(p);

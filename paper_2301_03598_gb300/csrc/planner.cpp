@@ -102,7 +102,7 @@ static int describe_fixed(int64_t m, int64_t n, int64_t k, int mode, int tile_n,
 // than the model's error (kSplitMargin, relative): the model's rms error on
 // the sweep is 5-8%, and a mistaken split costs more than a mistaken wave.
 int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
-             int cluster_m, int num_sms, sk_schedule_info* out) {
+             int cluster_m, int num_sms, sk_schedule_info* out, int min_tile_n) {
   if (out == nullptr || num_sms < 1) return SK_ERR_INVALID;
   if (cluster_m != 0 && cluster_m != 1 && cluster_m != 2) return SK_ERR_UNSUPPORTED;
   if (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256) return SK_ERR_UNSUPPORTED;
@@ -112,7 +112,7 @@ int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, in
   if (tile_n) {
     tns[ntn++] = tile_n;
   } else {
-    if (cluster_m != 2) tns[ntn++] = 64;  // narrow tiles: more tiles for few-tile shapes
+    if (cluster_m != 2 && min_tile_n <= 64) tns[ntn++] = 64;  // narrow tiles: more tiles for few-tile shapes
     tns[ntn++] = 128;
     if (n > 128) tns[ntn++] = 256;  // a 256-wide tile over <= 128 columns only wastes work
   }

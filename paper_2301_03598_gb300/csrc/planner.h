@@ -27,8 +27,10 @@ constexpr int kMaxGrid = 1024;
 constexpr int kFlagsPerCta = 32;
 constexpr int64_t kFlagBytes = static_cast<int64_t>(kMaxGrid) * kFlagsPerCta * 4;
 
+// tile_n 0 ranks the widths 64, 128 and 256 that are at least min_tile_n
+// (E4M3 plans: 128 and 256).
 int describe(int64_t m, int64_t n, int64_t k, int mode, int tile_n, int grid, int raster_group,
-             int cluster_m, int num_sms, sk_schedule_info* out);
+             int cluster_m, int num_sms, sk_schedule_info* out, int min_tile_n = 64);
 int grid_model(int64_t tiles, int64_t ipt, int p, const double coef[4]);
 // Terms of the planner's time model per tile configuration: Appendix A.1's
 // a, b, c, d, then e (per tile segment) and f (shortest whole-tile period).

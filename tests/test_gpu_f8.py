@@ -75,9 +75,35 @@ SHAPES = [(384, 384, 4096), (300, 260, 1008), (129, 1000, 144), (16, 128, 16), (
 @pytest.mark.parametrize("shape", SHAPES)
 def test_f8_matches_oracle(shape, mode):
     p = F8Problem(*shape, seed=3)
-    outs, info = p.run(1.0, 0.0, mode, {"cluster_m": 1})
+    outs, info = p.run(1.0, 0.0, mode, {"cluster_m": 1, "tile_n": 128})
     assert info["tile_n"] == 128 and info["tile_k"] == 256 and info["cluster_m"] == 1
     p.check(outs[0], 1.0, 0.0, f"e4m3 {shape} {mode}")
+
+
+def _modelled_width(m, n, k, num_sms):
+    """The width (128 or 256) whose AUTO schedule has the smaller modelled
+    time, the rule an AUTO E4M3 plan follows: E4M3 rows are planned as 16-bit
+    rows of k/2, a split schedule carries the planner's 10% margin, and a tie
+    keeps 128."""
+    best = {}
+    for tn in (128, 256):
+        if tn == 256 and n <= 128:
+            continue
+        info = sk.sk_plan_describe(m, n, k // 2, "auto", tile_n=tn, cluster_m=1, num_sms=num_sms)
+        us = sk.sk_model_time(m, n, k // 2, "auto", tile_n=tn, num_sms=num_sms, cluster_m=1)
+        best[tn] = us * (1.10 if info["workspace_bytes"] > 0 else 1.0)
+    return min(best, key=lambda t: (best[t], t))
+
+
+@pytest.mark.parametrize("shape", [(384, 384, 4096), (1000, 1100, 2048), (2048, 2048, 1024),
+                                   (129, 1000, 144)])
+def test_f8_auto_width_follows_the_model(shape):
+    p = F8Problem(*shape, seed=18)
+    outs, info = p.run(1.0, 0.0, "auto")
+    assert info["cluster_m"] == 1
+    assert info["tile_n"] == _modelled_width(*shape, info["num_sms"])
+    assert info["tile_k"] == (256 if info["tile_n"] == 128 else 128)
+    p.check(outs[0], 1.0, 0.0, f"e4m3 auto width {shape} ({info['tile_n']})")
 
 
 @pytest.mark.parametrize("mode,grid", [("dp", 0), ("sk", 0), ("sk", 37), ("hybrid", 0)])
@@ -216,8 +242,8 @@ def test_f8_entry_point_contract():
         plan16.destroy()
 
 
-@pytest.mark.parametrize("mode,attrs", [("auto", {}), ("sk", {"grid": 151}),
-                                        ("dp", {"tile_n": 256}), ("sk", {"tile_n": 256})])
+@pytest.mark.parametrize("mode,attrs", [("auto", {}), ("sk", {"tile_n": 128, "grid": 151}),
+                                        ("dp", {"tile_n": 128}), ("sk", {"tile_n": 256})])
 def test_f8_large_sampled_entries(mode, attrs):
     # 4096 x 4096 x 8192 on device-drawn operands: 4,096 sampled outputs plus
     # entries along tile edges (Stream-K seams, ragged-free but split tiles)
@@ -234,6 +260,8 @@ def test_f8_large_sampled_entries(mode, attrs):
         info = plan.info()
     finally:
         plan.destroy()
+    if mode == "auto":
+        assert info["tile_n"] == 256  # a wave or more of 128 x 256 tiles
     g = np.random.Generator(np.random.PCG64(5))
     rows, cols = list(g.integers(0, m, 4096)), list(g.integers(0, n, 4096))
     for e in (0, 127, 128, 2047, 2048, m - 1):
