@@ -405,7 +405,8 @@ int sk_grouped_plan(sk_grouped_t* out, int count, const int64_t* m, const int64_
 int sk_grouped_gemm(sk_grouped_t plan, const void* const* A, const void* const* B,
                     void* const* C, const float* alpha, const float* beta, void* stream);
 /* sk_grouped_gemm for an SK_E4M3 group (ab_type SK_E4M3: 128 x 128 x 128
- * tiles, k_i a multiple of 16): SA / SB are host arrays of count device
+ * tiles by default, 128 x 256 x 128 after SK_ATTR_TILE_N 256, single CTAs;
+ * k_i a multiple of 16): SA / SB are host arrays of count device
  * pointers to each problem's block scales, laid out as for sk_gemm_scaled
  * ([ceil(m_i/128)][ceil(k_i/128)] and [ceil(n_i/128)][ceil(k_i/128)] FP32,
  * row-major).  sk_grouped_gemm on an E4M3 group, or this call on a 16-bit
@@ -447,9 +448,8 @@ int sk_plan_autotune(sk_plan_t plan, const void* A, const void* B, void* C, int 
 int sk_grouped_autotune(sk_grouped_t plan, const void* const* A, const void* const* B,
                         void* const* C, int reps, void* stream, double* best_us);
 /* The same for E4M3 plans (tile widths 128, on single CTAs or pairs, and 256
- * on single CTAs; E4M3 groups: 128 on single CTAs, so only the schedule and
- * depth are chosen), with the block scales of sk_gemm_scaled /
- * sk_grouped_gemm_scaled. */
+ * on single CTAs; E4M3 groups: 128 and 256 on single CTAs), with the block
+ * scales of sk_gemm_scaled / sk_grouped_gemm_scaled. */
 int sk_plan_autotune_scaled(sk_plan_t plan, const void* A, const void* B, const float* scale_a,
                             const float* scale_b, void* C, int reps, void* stream, double* best_us);
 int sk_grouped_autotune_scaled(sk_grouped_t plan, const void* const* A, const void* const* B,

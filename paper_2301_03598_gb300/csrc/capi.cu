@@ -1043,7 +1043,7 @@ int sk_grouped_plan(sk_grouped_t* out, int count, const int64_t* m, const int64_
   g->enc_sa.assign(count, nullptr);
   g->enc_sb.assign(count, nullptr);
   if (ab_type == SK_E4M3) {
-    g->tile_n_req = 128;  // 128 x 128 x 128 tiles
+    g->tile_n_req = 128;  // 128 x 128 x 128 tiles by default (SK_ATTR_TILE_N 256: 128 x 256)
     g->cluster_req = 1;   // on single CTAs (grouped E4M3 launches have no CTA pairs)
   }
   size_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
@@ -1131,8 +1131,11 @@ int sk_grouped_set(sk_grouped_t g, int attr, int64_t v) {
     case SK_ATTR_TILE_N:
     case SK_ATTR_GRID:
     case SK_ATTR_MODE: {
-      if (attr == SK_ATTR_TILE_N && g->ab_type == SK_E4M3)
-        return v == 0 || v == 128 ? SK_OK : SK_ERR_UNSUPPORTED;
+      // E4M3 groups: 128 (the default) or 256, single CTAs either way
+      if (attr == SK_ATTR_TILE_N && g->ab_type == SK_E4M3) {
+        if (v == 0) v = 128;
+        if (v != 128 && v != 256) return SK_ERR_UNSUPPORTED;
+      }
       const int t = g->tile_n_req, gr = g->grid_req, md = g->mode_req;
       if (attr == SK_ATTR_TILE_N) g->tile_n_req = static_cast<int>(v);
       if (attr == SK_ATTR_GRID) g->grid_req = static_cast<int>(v);
@@ -1327,7 +1330,7 @@ int grouped_autotune(sk_grouped_t g, const void* const* A, const void* const* B,
   double best = -1.0;
   int bt = saved[0], bm = saved[1], bs = saved[3], bc = saved[4];
   for (int tn : tns) {
-    if (tn != 128 && g->ab_type == SK_E4M3) continue;
+    if (tn == 64 && g->ab_type == SK_E4M3) continue;
     for (int cm : cms) {
       if (cm == 2 && (tn == 64 || g->ab_type == SK_E4M3 || max_m <= sk::kTileM)) continue;
       for (int md : modes) {

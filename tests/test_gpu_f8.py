@@ -306,10 +306,12 @@ def _grouped(shapes, mode, c_type="bf16", beta=0.0, attrs=None, seed=0, autotune
 
 
 @pytest.mark.parametrize("mode,attrs", [("auto", {}), ("dp", {}), ("sk", {"grid": 29}),
-                                        ("hybrid", {})])
+                                        ("hybrid", {}), ("dp", {"tile_n": 256}),
+                                        ("sk", {"tile_n": 256, "grid": 31}),
+                                        ("hybrid", {"tile_n": 256})])
 def test_f8_grouped_matches_oracle(mode, attrs):
     probs, outs, alphas, info = _grouped(GROUP, mode, attrs=attrs, seed=4)
-    assert info["tile_n"] == 128
+    assert info["tile_n"] == attrs.get("tile_n", 128)
     for p, C, al in zip(probs, outs, alphas):
         p.check(C, al, 0.0, f"e4m3 grouped {mode} {p.m}x{p.n}x{p.k}")
 
