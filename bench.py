@@ -86,9 +86,9 @@ def load_peaks():
 # summed over the captured launches, divided by their 2mnk), and the sha256 of
 # csrc/sk_kernel.cuh followed by csrc/planner.cpp at that capture.  The
 # summary with its command is profiles/sk_gemm_sweep_launches.md.
-PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.175066e-03,
+PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.174380e-03,
                     "kernel_source_sha256":
-                        "cdf696ecff49ebfd5c4ea62c6da00f6c9ac8282540344c3e9777a76245d1415d"}
+                        "4602c8944a490170fecb0f75ea527a8b498a1713adcdc81ccfbd61714be66702"}
 
 
 def profiled_bytes_per_flop():
