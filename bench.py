@@ -86,9 +86,9 @@ def load_peaks():
 # summed over the captured launches, divided by their 2mnk), and the sha256 of
 # csrc/sk_kernel.cuh followed by csrc/planner.cpp at that capture.  The
 # summary with its command is profiles/sk_gemm_sweep_launches.md.
-PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.174380e-03,
+PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.175011e-03,
                     "kernel_source_sha256":
-                        "4602c8944a490170fecb0f75ea527a8b498a1713adcdc81ccfbd61714be66702"}
+                        "232b635e65be4231518c1b4c8cc03b320531a754a9a1f2a8d753bde76ab884d5"}
 
 
 def profiled_bytes_per_flop():

@@ -1051,22 +1051,16 @@ __global__ void __launch_bounds__(Cfg<BN, CM, F8>::kThreads, 1)
             for (int h = 0; h < kHalves; ++h) sc[h] = __shfl_sync(0xffffffffu, s_cur[h], i & 31);
             const uint32_t pbase =
                 tmem_base + lane_base + static_cast<uint32_t>(acc * C_::kAccCols + j * BN);
-            // kW columns at a time, so that the product needs kW registers
-            // next to the sum's BN / 2 (16 for BLK_N = 256, whose sum fills
-            // most of a thread's registers)
-            constexpr int kW = BN == 256 ? 16 : 32;
-            constexpr int kSub = 32 / kW;
-            constexpr int kChunks = kMine * kCpu * kSub;
+            // 32 columns at a time, so that the product needs 32 registers
+            // next to the sum's BN / 2
+            constexpr int kChunks = kMine * kCpu;
 #pragma unroll
             for (int c = 0; c < kChunks; ++c) {
-              const int mi = c / (kCpu * kSub);
-              const int j0 = kW * (c % (kCpu * kSub));
+              const int mi = c / kCpu;
+              const int j0 = 32 * (c % kCpu);
               const uint32_t col = static_cast<uint32_t>((col_half + 2 * mi) * 32 * kCpu + j0);
-              uint32_t r[kW];
-              if constexpr (kW == 16)
-                tmem_ld_x16(pbase + col, r);
-              else
-                tmem_ld_x32(pbase + col, r);
+              uint32_t r[32];
+              tmem_ld_x32(pbase + col, r);
               tmem_wait_ld();
               if (j == KD - 1 && c == kChunks - 1 && it + 1 < kb1) {
                 // the pair is read: the MMA warp may overwrite it (the
@@ -1080,7 +1074,7 @@ __global__ void __launch_bounds__(Cfg<BN, CM, F8>::kThreads, 1)
               // mi * kCpu / 2 of the tile for either col_half
               const uint32_t scb = __float_as_uint(sc[kHalves == 1 ? 0 : (mi * kCpu) / 2]);
 #pragma unroll
-              for (int jj = 0; jj < kW; jj += 2)
+              for (int jj = 0; jj < 32; jj += 2)
                 fma2(scb, r[jj], r[jj + 1], sum[mi][j0 + jj], sum[mi][j0 + jj + 1]);
             }
           }
