@@ -172,6 +172,57 @@ def test_f8_autotune_single_plan():
     p.check(out, 1.0, 0.0, f"e4m3 autotuned ({info['tile_n']}, {info['cluster_m']})")
 
 
+@pytest.mark.parametrize("tile_n,mode,grid", [(128, "sk", 90), (256, "sk", 61), (256, "hybrid", 0)])
+def test_f8_independent_inputs_back_to_back(tile_n, mode, grid):
+    # SK_ATTR_INDEPENDENT_INPUTS: the MAC loop may overlap the previous launch,
+    # while C and the shared fixup workspace keep stream order
+    p = F8Problem(700, 900, 3072, seed=19, scale_spread=True)
+    plan = sk.sk_plan(p.m, p.n, p.k, "e4m3", "e4m3", "f32", mode=mode)
+    try:
+        plan.set("tile_n", tile_n)
+        if grid:
+            plan.set("grid", grid)
+        plan.set("independent_inputs", 1)
+        A, B, sA, sB = p.qA.cuda(), p.qB.cuda(), p.sA.cuda(), p.sB.cuda()
+        outs = [torch.zeros(p.m, p.n, dtype=torch.float32, device="cuda") for _ in range(8)]
+        for C in outs:
+            sk.sk_gemm_scaled(plan, A, B, sA, sB, C)
+        assert sk.sk_last_error(plan)[0] == sk.SK_OK
+        assert plan.info()["tile_n"] == tile_n
+        for C in outs[1:]:
+            assert torch.equal(C, outs[0])
+        first = outs[0].cpu()
+    finally:
+        plan.destroy()
+    p.check(first, 1.0, 0.0, f"e4m3 independent {tile_n} {mode}")
+
+
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_f8_independent_inputs_chain_into_one_c(tile_n):
+    # C_{j+1} = A_j B_j + C_j: each launch reads the C its predecessor wrote
+    m, n, k = 520, 640, 1024
+    probs = [F8Problem(m, n, k, "f32", seed=40 + j) for j in range(4)]
+    plan = sk.sk_plan(m, n, k, "e4m3", "e4m3", "f32", mode="sk")
+    try:
+        plan.set("tile_n", tile_n)
+        plan.set("grid", 77)
+        plan.set("independent_inputs", 1)
+        C = torch.zeros(m, n, dtype=torch.float32, device="cuda")
+        ops = [(q.qA.cuda(), q.qB.cuda(), q.sA.cuda(), q.sB.cuda()) for q in probs]
+        for A, B, sA, sB in ops:
+            sk.sk_gemm_scaled(plan, A, B, sA, sB, C, 1.0, 1.0)
+        assert sk.sk_last_error(plan)[0] == sk.SK_OK
+        got = inputs.widen(C.cpu())
+    finally:
+        plan.destroy()
+    parts = [q.oracle(1.0, 0.0) for q in probs]
+    want = sum(c for c, _ in parts)
+    absab = sum(ab for _, ab in parts)
+    # four FP32 block-scaled sums within k * 2^-22 |A||B| each, plus the chain's FP32 adds
+    tol = 4 * k * 2.0 ** -22 * absab + 2.0 ** -20 * np.abs(want) + 1e-30
+    assert np.all(np.abs(got - want) <= tol)
+
+
 @pytest.mark.parametrize("grid", [7, 40, 143])
 def test_f8_split_tiles_with_spread_scales(grid):
     # 9 tiles of 16 iterations (two k-blocks of 128 each) over g CTAs: every
