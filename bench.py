@@ -86,9 +86,9 @@ def load_peaks():
 # summed over the captured launches, divided by their 2mnk), and the sha256 of
 # csrc/sk_kernel.cuh followed by csrc/planner.cpp at that capture.  The
 # summary with its command is profiles/sk_gemm_sweep_launches.md.
-PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.175011e-03,
+PROFILED_TRAFFIC = {"dram_bytes_per_flop": 2.169549e-03,
                     "kernel_source_sha256":
-                        "232b635e65be4231518c1b4c8cc03b320531a754a9a1f2a8d753bde76ab884d5"}
+                        "a9e83151ebf17b8fb1d37945f5ea29acdc7f7e7993a6ec75536351aadda4757e"}
 
 
 def profiled_bytes_per_flop():

@@ -648,169 +648,230 @@ __global__ void __launch_bounds__(Cfg<BN, CM, F8>::kThreads, 1)
   // conditional wait here made the grouped E4M3 kernel 11% slower.)
 
   if (warp < C_::kEpiWarp0) {
-  // Register rebalance (warpgroup-uniform; the host checked that the launch's
-  // registers cover it): warpgroup 0 releases, the epilogue warpgroups take.
-  if constexpr (C_::kRebalance) setmaxnreg_dec<C_::kRegsLow>();
-  if (warp == 0) {
-    if (!a.early) grid_dependency_wait();
-    if (lane == 0) {
-      // ------------------------------------------------------------ producer
-      SegCursor<GROUPED> cur;
-      cur.init(a, x);
-      Seg sg;
-      int last_problem = -1;  // grouped: the problem whose tensor maps were last acquired
-      int stage = 0;
-      uint32_t phase = 0;
-      int64_t issued = 0;
-      bool ok = true;
-      // ready: the current stage's empty barrier is known to have completed
-      // (probed while the previous stage's B load was issued).
-      bool ready = false;
-      while (ok && cur.next(a, sg)) {
-        const int kb0 = sg.kb0, kb1 = sg.kb1;
-        const int tm = sg.tm * CM + rank;  // this CTA's 128-row block
-        const int tn = sg.tn;
-        const CUtensorMap *pA = &tmA, *pB = &tmB, *pA3 = &tmA3, *pB3 = &tmB3;
-        if constexpr (GROUPED) {
-          const GroupProblem* gp = a.gprobs + sg.problem;
-          pA = &gp->tmA;
-          pB = &gp->tmB;
-          pA3 = &gp->tmA3;
-          pB3 = &gp->tmB3;
-          if (sg.problem != last_problem) {
-            tensormap_acquire(pA);
-            tensormap_acquire(pB);
-            tensormap_acquire(pA3);
-            tensormap_acquire(pB3);
-            last_problem = sg.problem;
-          }
-        }
-        for (int kb = kb0; kb < kb1; ++kb) {
-          if (!ready && !wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) {
-            ok = false;
-            break;
-          }
-          int next = stage + 1;
-          uint32_t next_phase = phase;
-          if (next == nst) {
-            next = 0;
-            next_phase ^= 1u;
-          }
-          // k-blocks k0 .. k0+KD-1 of this CTA's A rows and its BN/CM rows of
-          // B.  A KD = 2 stage of two full k-blocks is one 3-D box per
-          // operand; a stage reaching into the k tail loads its k-blocks as
-          // 2-D boxes, whose out-of-range columns TMA fills with zeros.
-          const int k0 = kb * KD;
-          const bool box3 = KD == 2 && k0 + 2 <= sg.kfull64;
-          const int brow = tn * BN + rank * (BN / CM);
-          if constexpr (kPair) {
-            // completing on the issuer's full barrier, which expects both
-            // CTAs' bytes
-            const uint32_t fb = full0 + 8u * stage;
-            if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C_::kStageBytes);
-            if (box3) {
-              tma_load_3d_pair(stage_a(stage), pA3, fb, 0, tm * kBlkM, k0);
-              ready = tma_load_3d_pair_probe(stage_b(stage), pB3, fb, 0, brow, k0, empty_bar(next),
-                                             next_phase ^ 1u);
-            } else if constexpr (KD == 1) {
-              tma_load_2d_pair(stage_a(stage), pA, fb, k0 * kBlkK, tm * kBlkM);
-              ready = tma_load_2d_pair_probe(stage_b(stage), pB, fb, k0 * kBlkK, brow,
-                                             empty_bar(next), next_phase ^ 1u);
-            } else {
-#pragma unroll
-              for (int j = 0; j < KD; ++j) {
-                tma_load_2d_pair(stage_a(stage) + j * C_::kSubA, pA, fb, (k0 + j) * kBlkK, tm * kBlkM);
-                tma_load_2d_pair(stage_b(stage) + j * C_::kSubB, pB, fb, (k0 + j) * kBlkK, brow);
-              }
-              ready = false;
-            }
-          } else {
-            const uint32_t fb = full_bar(stage);
-            mbar_arrive_expect_tx(fb, C_::kStageBytes);
-            if (box3) {
-              tma_load_3d(stage_a(stage), pA3, fb, 0, tm * kBlkM, k0);
-              ready = tma_load_3d_probe(stage_b(stage), pB3, fb, 0, brow, k0, empty_bar(next),
-                                        next_phase ^ 1u);
-            } else if constexpr (KD == 1) {
-              tma_load_2d(stage_a(stage), pA, fb, k0 * kBlkK, tm * kBlkM);
-              ready = tma_load_2d_probe(stage_b(stage), pB, fb, k0 * kBlkK, brow, empty_bar(next),
-                                        next_phase ^ 1u);
-            } else {
-#pragma unroll
-              for (int j = 0; j < KD; ++j) {
-                tma_load_2d(stage_a(stage) + j * C_::kSubA, pA, fb, (k0 + j) * kBlkK, tm * kBlkM);
-                tma_load_2d(stage_b(stage) + j * C_::kSubB, pB, fb, (k0 + j) * kBlkK, brow);
-              }
-              ready = false;
-            }
-          }
-          ++issued;
-          stage = next;
-          phase = next_phase;
-        }
-      }
-      if (ok) {
-        // Tail: wait until the MMA warp has released every stage, so no
-        // tcgen05.commit arrival is still in flight when the CTA exits.
-        for (int i = 0; i < nst; ++i) {
-          if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) break;
-          if (++stage == nst) {
-            stage = 0;
-            phase ^= 1u;
-          }
-        }
-      } else {
-        // Unwind: let the loads already issued land before shared memory
-        // goes away.  They complete within microseconds; the waits share one
-        // bound.  A pair's odd CTA cannot observe its loads (they complete on
-        // the even CTA's barriers), so it waits out a fixed interval.
-        constexpr uint64_t kUnwindNs = 1000000;
-        const uint64_t t0 = globaltimer_ns();
-        if (issuer) {
-          const int64_t first = issued > nst ? issued - nst : 0;
-          for (int64_t j = first; j < issued; ++j) {
-            const int s = static_cast<int>(j % nst);
-            const uint32_t par = static_cast<uint32_t>((j / nst) & 1);
-            while (!mbar_try_wait(full_bar(s), par) && globaltimer_ns() - t0 < kUnwindNs) {
-            }
-          }
-        } else {
-          while (globaltimer_ns() - t0 < kUnwindNs / 20) {
-          }
-        }
-      }
-    }
-  } else if (warp == 1) {
-    if (!a.early)
-      grid_dependency_wait();
-    else if (lane == 0)
-      grid_launch_dependents();
-    if (lane == 0 && !issuer) grid_launch_dependents();  // a pair's odd CTA issues nothing
-    if (lane == 0 && issuer) {
-      // ------------------------------------------------------------ MMA issuer
-      SegCursor<GROUPED> cur;
-      cur.init(a, x);
-      Seg sg;
-      int stage = 0, acc = 0;
-      uint32_t phase = 0, acc_phase = 0;
-      bool ok = true;
-      // ready: the current stage's full barrier is known to have completed
-      // (probed while the previous k-block's last MMA was issued).
-      bool ready = false;
-      if constexpr (F8) {
-        // One product per k-block (one scale block); a stage's KD k-blocks
-        // go to the KD buffers of one pair, published with one commit; the
-        // epilogue warps scale and sum them.
-        // ready_acc: the current pair is known to be free (probed with the
-        // previous stage's last MMA, like `ready` for the stage)
-        bool ready_acc = false;
+    // Register rebalance (warpgroup-uniform; the host checked that the launch's
+    // registers cover it): warpgroup 0 releases, the epilogue warpgroups take.
+    if constexpr (C_::kRebalance) setmaxnreg_dec<C_::kRegsLow>();
+    if (warp == 0) {
+      if (!a.early) grid_dependency_wait();
+      if (lane == 0) {
+        // ------------------------------------------------------------ producer
+        SegCursor<GROUPED> cur;
+        cur.init(a, x);
+        Seg sg;
+        int last_problem = -1;  // grouped: the problem whose tensor maps were last acquired
+        int stage = 0;
+        uint32_t phase = 0;
+        int64_t issued = 0;
+        bool ok = true;
+        // ready: the current stage's empty barrier is known to have completed
+        // (probed while the previous stage's B load was issued).
+        bool ready = false;
         while (ok && cur.next(a, sg)) {
-          for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
-            if (!ready && !wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull)) {
+          const int kb0 = sg.kb0, kb1 = sg.kb1;
+          const int tm = sg.tm * CM + rank;  // this CTA's 128-row block
+          const int tn = sg.tn;
+          const CUtensorMap *pA = &tmA, *pB = &tmB, *pA3 = &tmA3, *pB3 = &tmB3;
+          if constexpr (GROUPED) {
+            const GroupProblem* gp = a.gprobs + sg.problem;
+            pA = &gp->tmA;
+            pB = &gp->tmB;
+            pA3 = &gp->tmA3;
+            pB3 = &gp->tmB3;
+            if (sg.problem != last_problem) {
+              tensormap_acquire(pA);
+              tensormap_acquire(pB);
+              tensormap_acquire(pA3);
+              tensormap_acquire(pB3);
+              last_problem = sg.problem;
+            }
+          }
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!ready && !wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) {
               ok = false;
               break;
             }
-            if (!ready_acc && !wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) {
+            int next = stage + 1;
+            uint32_t next_phase = phase;
+            if (next == nst) {
+              next = 0;
+              next_phase ^= 1u;
+            }
+            // k-blocks k0 .. k0+KD-1 of this CTA's A rows and its BN/CM rows of
+            // B.  A KD = 2 stage of two full k-blocks is one 3-D box per
+            // operand; a stage reaching into the k tail loads its k-blocks as
+            // 2-D boxes, whose out-of-range columns TMA fills with zeros.
+            const int k0 = kb * KD;
+            const bool box3 = KD == 2 && k0 + 2 <= sg.kfull64;
+            const int brow = tn * BN + rank * (BN / CM);
+            if constexpr (kPair) {
+              // completing on the issuer's full barrier, which expects both
+              // CTAs' bytes
+              const uint32_t fb = full0 + 8u * stage;
+              if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C_::kStageBytes);
+              if (box3) {
+                tma_load_3d_pair(stage_a(stage), pA3, fb, 0, tm * kBlkM, k0);
+                ready = tma_load_3d_pair_probe(stage_b(stage), pB3, fb, 0, brow, k0, empty_bar(next),
+                                               next_phase ^ 1u);
+              } else if constexpr (KD == 1) {
+                tma_load_2d_pair(stage_a(stage), pA, fb, k0 * kBlkK, tm * kBlkM);
+                ready = tma_load_2d_pair_probe(stage_b(stage), pB, fb, k0 * kBlkK, brow,
+                                               empty_bar(next), next_phase ^ 1u);
+              } else {
+#pragma unroll
+                for (int j = 0; j < KD; ++j) {
+                  tma_load_2d_pair(stage_a(stage) + j * C_::kSubA, pA, fb, (k0 + j) * kBlkK, tm * kBlkM);
+                  tma_load_2d_pair(stage_b(stage) + j * C_::kSubB, pB, fb, (k0 + j) * kBlkK, brow);
+                }
+                ready = false;
+              }
+            } else {
+              const uint32_t fb = full_bar(stage);
+              mbar_arrive_expect_tx(fb, C_::kStageBytes);
+              if (box3) {
+                tma_load_3d(stage_a(stage), pA3, fb, 0, tm * kBlkM, k0);
+                ready = tma_load_3d_probe(stage_b(stage), pB3, fb, 0, brow, k0, empty_bar(next),
+                                          next_phase ^ 1u);
+              } else if constexpr (KD == 1) {
+                tma_load_2d(stage_a(stage), pA, fb, k0 * kBlkK, tm * kBlkM);
+                ready = tma_load_2d_probe(stage_b(stage), pB, fb, k0 * kBlkK, brow, empty_bar(next),
+                                          next_phase ^ 1u);
+              } else {
+#pragma unroll
+                for (int j = 0; j < KD; ++j) {
+                  tma_load_2d(stage_a(stage) + j * C_::kSubA, pA, fb, (k0 + j) * kBlkK, tm * kBlkM);
+                  tma_load_2d(stage_b(stage) + j * C_::kSubB, pB, fb, (k0 + j) * kBlkK, brow);
+                }
+                ready = false;
+              }
+            }
+            ++issued;
+            stage = next;
+            phase = next_phase;
+          }
+        }
+        if (ok) {
+          // Tail: wait until the MMA warp has released every stage, so no
+          // tcgen05.commit arrival is still in flight when the CTA exits.
+          for (int i = 0; i < nst; ++i) {
+            if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, a, kAtProducerEmpty)) break;
+            if (++stage == nst) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        } else {
+          // Unwind: let the loads already issued land before shared memory
+          // goes away.  They complete within microseconds; the waits share one
+          // bound.  A pair's odd CTA cannot observe its loads (they complete on
+          // the even CTA's barriers), so it waits out a fixed interval.
+          constexpr uint64_t kUnwindNs = 1000000;
+          const uint64_t t0 = globaltimer_ns();
+          if (issuer) {
+            const int64_t first = issued > nst ? issued - nst : 0;
+            for (int64_t j = first; j < issued; ++j) {
+              const int s = static_cast<int>(j % nst);
+              const uint32_t par = static_cast<uint32_t>((j / nst) & 1);
+              while (!mbar_try_wait(full_bar(s), par) && globaltimer_ns() - t0 < kUnwindNs) {
+              }
+            }
+          } else {
+            while (globaltimer_ns() - t0 < kUnwindNs / 20) {
+            }
+          }
+        }
+      }
+    } else if (warp == 1) {
+      if (!a.early)
+        grid_dependency_wait();
+      else if (lane == 0)
+        grid_launch_dependents();
+      if (lane == 0 && !issuer) grid_launch_dependents();  // a pair's odd CTA issues nothing
+      if (lane == 0 && issuer) {
+        // ------------------------------------------------------------ MMA issuer
+        SegCursor<GROUPED> cur;
+        cur.init(a, x);
+        Seg sg;
+        int stage = 0, acc = 0;
+        uint32_t phase = 0, acc_phase = 0;
+        bool ok = true;
+        // ready: the current stage's full barrier is known to have completed
+        // (probed while the previous k-block's last MMA was issued).
+        bool ready = false;
+        if constexpr (F8) {
+          // One product per k-block (one scale block); a stage's KD k-blocks
+          // go to the KD buffers of one pair, published with one commit; the
+          // epilogue warps scale and sum them.
+          // ready_acc: the current pair is known to be free (probed with the
+          // previous stage's last MMA, like `ready` for the stage)
+          bool ready_acc = false;
+          while (ok && cur.next(a, sg)) {
+            for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
+              if (!ready && !wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull)) {
+                ok = false;
+                break;
+              }
+              if (!ready_acc && !wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              int next = stage + 1;
+              uint32_t next_phase = phase;
+              if (next == nst) {
+                next = 0;
+                next_phase ^= 1u;
+              }
+              const int nacc = acc ^ 1;
+              const uint32_t nacc_phase = acc == 1 ? acc_phase ^ 1u : acc_phase;
+#pragma unroll
+              for (int j = 0; j < KD; ++j) {
+                const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * C_::kAccCols + j * BN);
+                const uint64_t adesc = smem_desc_sw128(stage_a(stage) + j * C_::kSubA);
+                const uint64_t bdesc = smem_desc_sw128(stage_b(stage) + j * C_::kSubB);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                  // 32 E4M3 elements (32 B) along K per MMA
+                  if (j == KD - 1 && kk == 3) {
+                    // the stage's last MMA: probe the next stage and the next pair
+                    uint32_t r;
+                    if constexpr (kPair)
+                      r = mma_f8_pair_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
+                                             full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
+                    else
+                      r = mma_f8_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
+                                        full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
+                    ready = (r & 1u) != 0;
+                    ready_acc = (r & 2u) != 0;
+                  } else if constexpr (kPair) {
+                    mma_f8_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
+                  } else {
+                    mma_f8(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
+                  }
+                }
+              }
+              // publishes the pair's products, then frees the stage (in both
+              // CTAs of a pair) once these MMAs finish
+              if constexpr (kPair) {
+                mma_commit_pair_multicast(accf_bar(acc), kPairMask);
+                mma_commit_pair_multicast(empty_bar(stage), kPairMask);
+              } else {
+                mma_commit(accf_bar(acc));
+                mma_commit(empty_bar(stage));
+              }
+              stage = next;
+              phase = next_phase;
+              acc = nacc;
+              acc_phase = nacc_phase;
+            }
+          }
+        }
+        while (!F8 && ok && cur.next(a, sg)) {
+          const int kb0 = sg.kb0, kb1 = sg.kb1;
+          if (!wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) break;
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!ready && !wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull)) {
               ok = false;
               break;
             }
@@ -821,126 +882,65 @@ __global__ void __launch_bounds__(Cfg<BN, CM, F8>::kThreads, 1)
               next = 0;
               next_phase ^= 1u;
             }
-            const int nacc = acc ^ 1;
-            const uint32_t nacc_phase = acc == 1 ? acc_phase ^ 1u : acc_phase;
 #pragma unroll
             for (int j = 0; j < KD; ++j) {
-              const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * C_::kAccCols + j * BN);
               const uint64_t adesc = smem_desc_sw128(stage_a(stage) + j * C_::kSubA);
               const uint64_t bdesc = smem_desc_sw128(stage_b(stage) + j * C_::kSubB);
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                // 32 E4M3 elements (32 B) along K per MMA
-                if (j == KD - 1 && kk == 3) {
-                  // the stage's last MMA: probe the next stage and the next pair
-                  uint32_t r;
+              for (int kk = 0; kk < kBlkK / 16; ++kk) {
+                // advance 16 elements (32 B) along K inside the swizzle atom
+                const uint32_t acc_flag = (kb > kb0 || j > 0 || kk > 0) ? 1u : 0u;
+                if (j == KD - 1 && kk == kBlkK / 16 - 1) {
+                  // the stage's last MMA, fused with a probe of the next stage
                   if constexpr (kPair)
-                    r = mma_f8_pair_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
-                                           full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
+                    ready = mma_f16_pair_probe(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
+                                               acc_flag, full_bar(next), next_phase);
                   else
-                    r = mma_f8_probe2(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, 1u,
-                                      full_bar(next), next_phase, acce_bar(nacc), nacc_phase ^ 1u);
-                  ready = (r & 1u) != 0;
-                  ready_acc = (r & 2u) != 0;
+                    ready = mma_f16_probe(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, acc_flag,
+                                          full_bar(next), next_phase);
                 } else if constexpr (kPair) {
-                  mma_f8_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
+                  mma_f16_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, acc_flag);
                 } else {
-                  mma_f8(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, kk > 0 ? 1u : 0u);
+                  mma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, acc_flag);
                 }
               }
             }
-            // publishes the pair's products, then frees the stage (in both
-            // CTAs of a pair) once these MMAs finish
-            if constexpr (kPair) {
-              mma_commit_pair_multicast(accf_bar(acc), kPairMask);
+            // frees the stage (in both CTAs of a pair) once these MMAs finish
+            if constexpr (kPair)
               mma_commit_pair_multicast(empty_bar(stage), kPairMask);
-            } else {
-              mma_commit(accf_bar(acc));
+            else
               mma_commit(empty_bar(stage));
-            }
             stage = next;
             phase = next_phase;
-            acc = nacc;
-            acc_phase = nacc_phase;
           }
-        }
-      }
-      while (!F8 && ok && cur.next(a, sg)) {
-        const int kb0 = sg.kb0, kb1 = sg.kb1;
-        if (!wait_bar(acce_bar(acc), acc_phase ^ 1u, abort_flag, a, kAtMmaAccEmpty)) break;
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
-        for (int kb = kb0; kb < kb1; ++kb) {
-          if (!ready && !wait_bar(full_bar(stage), phase, abort_flag, a, kAtMmaFull)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          int next = stage + 1;
-          uint32_t next_phase = phase;
-          if (next == nst) {
-            next = 0;
-            next_phase ^= 1u;
-          }
-#pragma unroll
-          for (int j = 0; j < KD; ++j) {
-            const uint64_t adesc = smem_desc_sw128(stage_a(stage) + j * C_::kSubA);
-            const uint64_t bdesc = smem_desc_sw128(stage_b(stage) + j * C_::kSubB);
-#pragma unroll
-            for (int kk = 0; kk < kBlkK / 16; ++kk) {
-              // advance 16 elements (32 B) along K inside the swizzle atom
-              const uint32_t acc_flag = (kb > kb0 || j > 0 || kk > 0) ? 1u : 0u;
-              if (j == KD - 1 && kk == kBlkK / 16 - 1) {
-                // the stage's last MMA, fused with a probe of the next stage
-                if constexpr (kPair)
-                  ready = mma_f16_pair_probe(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc,
-                                             acc_flag, full_bar(next), next_phase);
-                else
-                  ready = mma_f16_probe(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, acc_flag,
-                                        full_bar(next), next_phase);
-              } else if constexpr (kPair) {
-                mma_f16_pair(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, acc_flag);
-              } else {
-                mma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, a.idesc, acc_flag);
-              }
-            }
-          }
-          // frees the stage (in both CTAs of a pair) once these MMAs finish
+          if (!ok) break;
+          // accumulator complete (in both CTAs' TMEM for a pair)
           if constexpr (kPair)
-            mma_commit_pair_multicast(empty_bar(stage), kPairMask);
+            mma_commit_pair_multicast(accf_bar(acc), kPairMask);
           else
-            mma_commit(empty_bar(stage));
-          stage = next;
-          phase = next_phase;
+            mma_commit(accf_bar(acc));
+          acc ^= 1;
+          if (acc == 0) acc_phase ^= 1u;
         }
-        if (!ok) break;
-        // accumulator complete (in both CTAs' TMEM for a pair)
+        // All MMAs are issued: the next kernel in the stream may start launching
+        // (it runs its prologue and then waits for this grid to complete).
+        grid_launch_dependents();
+        // Drain: every MMA issued above completes before TMEM is released.
         if constexpr (kPair)
-          mma_commit_pair_multicast(accf_bar(acc), kPairMask);
+          mma_commit_pair_multicast(drain_bar, 0x1);
         else
-          mma_commit(accf_bar(acc));
-        acc ^= 1;
-        if (acc == 0) acc_phase ^= 1u;
-      }
-      // All MMAs are issued: the next kernel in the stream may start launching
-      // (it runs its prologue and then waits for this grid to complete).
-      grid_launch_dependents();
-      // Drain: every MMA issued above completes before TMEM is released.
-      if constexpr (kPair)
-        mma_commit_pair_multicast(drain_bar, 0x1);
-      else
-        mma_commit(drain_bar);
-      const uint64_t t0 = globaltimer_ns();
-      while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < a.timeout_ns) {
+          mma_commit(drain_bar);
+        const uint64_t t0 = globaltimer_ns();
+        while (!mbar_try_wait(drain_bar, 0) && globaltimer_ns() - t0 < a.timeout_ns) {
+        }
       }
     }
-  }
   } else {
     if constexpr (C_::kRebalance) setmaxnreg_inc<C_::kRegsHigh>();
     grid_dependency_wait();
     // -------------------------------------------------------------- epilogue
     const int quarter = warp & 3;                     // TMEM lanes this warp may access
-    const int col_half = (warp - C_::kEpiWarp0) >> 2;     // which interleaved column units
+    const int col_half = (warp - C_::kEpiWarp0) >> 2;  // which interleaved column units
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
     SegCursor<GROUPED> cur;
