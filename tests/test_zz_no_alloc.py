@@ -7,8 +7,9 @@ It must give the same results as the plan-based sk_gemm, within the tolerance
 the parity tests use (k * 2^-22 * |alpha| |A||B| + 2^-22 |beta C| + one output
 ulp), on two calls in a row -- the second call finds the first call's leftovers
 in the shared scratch -- and the two calls must agree bit for bit (the fixup
-adds partials in a fixed order, so stale flags or partials would show).  This
-file is collected last on purpose.
+adds partials in a fixed order, so stale flags or partials would show).  The
+same holds for the call captured in a CUDA graph after a first eager call.
+This file is collected last on purpose.
 """
 import pytest
 import torch
@@ -75,6 +76,41 @@ def test_noalloc_k0_scales_c_twice():
         torch.cuda.synchronize()
         assert int(status.item()) == 0
         assert torch.equal(C.cpu(), C_ref.cpu()), f"call {call}"
+
+
+@pytest.mark.parametrize("m,n,k,mode", [(384, 384, 4096, "sk"), (1000, 776, 1104, "hybrid")])
+def test_noalloc_captured_in_a_graph_matches_eager(m, n, k, mode):
+    """The documented use under stream capture: one eager call first (it sets
+    the device up), then the call captured into a CUDA graph; two replays
+    must reproduce the eager result bit for bit (split schedules: the
+    captured memsets clear the scratch's flags before every replay)."""
+    prob = Problem(m, n, k, "bf16", "f32", "normal", seed=33, beta=0.5)
+    A, B = prob.A.cuda(), prob.B.cuda()
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    C_eager = prob.Cin.clone().cuda()
+    sk.sk_gemm_noalloc(m, n, k, "bf16", "f32", A, k, B, k, C_eager, n, 1.0, 0.5, mode,
+                       device_status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    C = prob.Cin.clone().cuda()
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(graph, stream=stream):
+            sk.sk_gemm_noalloc(m, n, k, "bf16", "f32", A, k, B, k, C, n, 1.0, 0.5, mode,
+                               device_status=status, stream=stream)
+    for replay in range(2):
+        C.copy_(prob.Cin.cuda())
+        status.fill_(-1)
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0, f"replay {replay}"
+        assert torch.equal(C, C_eager), f"replay {replay} differs from the eager call"
+    C64, absAB = prob.oracle(1.0, 0.5)
+    tol = bound(k, 1.0, 0.5, absAB, C64, inputs.widen(prob.Cin), "f32")
+    check_bound(inputs.widen(C_eager.cpu()), C64, tol, f"noalloc eager {mode}")
+    del graph
 
 
 def test_noalloc_rejects_bad_arguments():
