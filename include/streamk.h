@@ -164,10 +164,11 @@ typedef struct {
  *   m, n, k   >= 0 (m*n == 0: sk_gemm is a no-op; k == 0: C = beta*C).
  *   a_type == b_type in {SK_F16, SK_BF16, SK_E4M3}; c_type in {SK_F32, SK_BF16,
  *   SK_F16}; compute_type must be SK_F32 (FP32 accumulation, Section 6).
- *   E4M3 plans run BLK_N = 128, BLK_K = 128 tiles on single CTAs by default
- *   (SK_ATTR_CLUSTER_M 2 selects CTA pairs of 256 x 128 tiles; SK_ATTR_TILE_N
- *   256 selects 128 x 256 tiles on single CTAs, SK_ERR_UNSUPPORTED with pairs)
- *   and are launched with sk_gemm_scaled.
+ *   E4M3 plans run 128 x 128 or 128 x 256 tiles on single CTAs, the width
+ *   chosen by the planner's model unless SK_ATTR_TILE_N fixes it (128 or 256;
+ *   64 is SK_ERR_UNSUPPORTED); SK_ATTR_CLUSTER_M 0 and 1 mean single CTAs, 2
+ *   selects CTA pairs of 256 x 128 tiles (width 128 only: 256 with pairs is
+ *   SK_ERR_UNSUPPORTED).  They are launched with sk_gemm_scaled.
  *   a_layout SK_ROW_MAJOR, b_layout SK_COL_MAJOR, c_layout either.
  *   mode: an sk_mode.
  * Allocates the plan's device workspace (fixup partials and flags, Algorithm 5

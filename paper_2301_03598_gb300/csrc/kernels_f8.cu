@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 #include "../../include/streamk.h"
 #include "launch.h"
 #include "sk_kernel.cuh"
@@ -33,17 +35,20 @@ static cudaError_t registers_cover_rebalance() {
   if constexpr (!C_::kRebalance) {
     return cudaSuccess;
   } else {
-    static int ok = -1;
-    if (ok < 0) {
+    // -1 until read; any thread may read it, all store the same value
+    static std::atomic<int> ok{-1};
+    int v = ok.load(std::memory_order_relaxed);
+    if (v < 0) {
       cudaFuncAttributes fa;
       const cudaError_t e = cudaFuncGetAttributes(&fa, sk_gemm_kernel<SK_F8_BN, CM, TC, GROUPED, true>);
       if (e != cudaSuccess) return e;
-      ok = (C_::kRegsLow + 2 * C_::kRegsHigh <= 3 * fa.numRegs &&
-            fa.maxThreadsPerBlock >= C_::kThreads)
-               ? 1
-               : 0;
+      v = (C_::kRegsLow + 2 * C_::kRegsHigh <= 3 * fa.numRegs &&
+           fa.maxThreadsPerBlock >= C_::kThreads)
+              ? 1
+              : 0;
+      ok.store(v, std::memory_order_relaxed);
     }
-    return ok == 1 ? cudaSuccess : cudaErrorInvalidConfiguration;
+    return v == 1 ? cudaSuccess : cudaErrorInvalidConfiguration;
   }
 }
 
